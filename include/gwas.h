@@ -1,0 +1,155 @@
+/*
+ * gwas.h -- C interface of the GB300 multi-trait GWAS library.
+ *
+ * The library solves the m x t grid of generalized least-squares problems of
+ * Section 2, Eq. (1):
+ *
+ *     b_ij = (X_i^T M_j^-1 X_i)^-1 X_i^T M_j^-1 y_j,
+ *     X_i  = [X_L | x_i]            (X_L: n x (p-1) covariates, x_i: SNP i),
+ *     M_j  = h_j^2 Phi + (1 - h_j^2) I                               (Eq. 2),
+ *
+ * by the eigendecomposition method of Section 3 (Algorithm 5): one FP64
+ * eigendecomposition Phi = Z Lambda Z^T, a rotation of genotypes and traits
+ * by Z^T, and, per (SNP, trait) pair, dense contractions over n followed by
+ * a p x p solve.  The scale sigma_j^2 of Eq. (2) does not change b_ij nor
+ * the standard error and is not an input.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are column-major.  X_R (genotypes) is n x m int8, i.e. SNP-major:
+ *   the n genotypes of SNP i are contiguous.  Y is n x t FP64: the n values of
+ *   trait j are contiguous.
+ * - Every array argument may be a host pointer (pageable or pinned) or a device
+ *   pointer on the context's device; the library tells them apart with
+ *   cudaPointerGetAttributes and copies host data itself.  The caller keeps
+ *   ownership of all its buffers and may release them when the call returns.
+ * - The context owns every device allocation it makes (Z, Lambda, the rotated
+ *   covariates, the resident rotated genotypes and the work buffers) and frees
+ *   them in gwas_destroy.
+ * - Calls on one context are not thread-safe; different contexts are
+ *   independent.  All work runs on the context's stream; calls return after
+ *   their results are complete (host outputs written, device outputs ready).
+ * - Every call returns a status code; on failure gwas_last_error() returns a
+ *   one-line description.  A failed call leaves previously loaded state valid
+ *   unless the message says otherwise.
+ */
+#ifndef GWAS_GB300_H
+#define GWAS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GWAS_API __attribute__((visibility("default")))
+#else
+#define GWAS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GWAS_OK                 0
+#define GWAS_ERR_ARG            1  /* invalid argument (size, range, pointer on another device) */
+#define GWAS_ERR_NOT_SPD        2  /* some M_j is not positive definite, or the eigensolver failed */
+#define GWAS_ERR_OOM            3  /* the request exceeds the HBM budget or a device allocation failed */
+#define GWAS_ERR_CUDA           4  /* a CUDA runtime or library call failed */
+#define GWAS_ERR_TIMEOUT        5  /* a bounded wait inside a kernel ran out; results are invalid */
+#define GWAS_ERR_SINGULAR_PAIRS 6  /* warning: some pairs have a (numerically) singular p x p system;
+                                      their outputs are NaN, every other output is valid */
+#define GWAS_ERR_STATE          7  /* call out of order (e.g. gwas_solve before gwas_load_snps) */
+#define GWAS_ERR_UNSUPPORTED    8  /* a size or mode this build does not implement */
+
+/* precision modes */
+#define GWAS_FP64  0  /* every step in FP64 (the paper's arithmetic, Section 6) */
+#define GWAS_MIXED 1  /* bf16 tensor-core contractions on exact fixed-point slices with
+                         FP32 accumulation; FP64 eigendecomposition and per-trait algebra */
+
+/* output modes */
+#define GWAS_OUT_FULL_B  0  /* double b[t][i1-i0][p]: every coefficient, SNP coefficient last */
+#define GWAS_OUT_LAST_SE 1  /* float beta[t][i1-i0] followed by float se[t][i1-i0]:
+                               the SNP coefficient and its standard error */
+
+typedef struct gwas_ctx gwas_ctx;
+
+typedef struct gwas_opts {
+  int precision;      /* GWAS_FP64 or GWAS_MIXED */
+  int output;         /* GWAS_OUT_FULL_B or GWAS_OUT_LAST_SE */
+  int trait_block;    /* traits per internal block of gwas_solve; 0 = all traits at once */
+  int device;         /* CUDA device ordinal of the context */
+  size_t hbm_budget;  /* bytes the context may allocate on the device; 0 = no limit */
+  void* stream;       /* cudaStream_t the context runs on; NULL = the context creates one */
+} gwas_opts;
+
+/* Fill *opts with the defaults: GWAS_MIXED, GWAS_OUT_LAST_SE, trait_block 0,
+ * device 0, no budget, own stream. */
+GWAS_API void gwas_default_opts(gwas_opts* opts);
+
+/*
+ * gwas_setup -- create a context and perform the preloop work that involves
+ * neither stream (Algorithm 5, the eigendecomposition and X'_L := Z^T X_L).
+ *
+ *   ctx   out: the new context (NULL on failure)
+ *   n     number of individuals, 1 <= n <= 16384
+ *   pm1   number of covariates p-1 (columns of X_L), 0 <= pm1 <= 7
+ *   phi   n x n symmetric kinship matrix Phi, FP64 (only the lower triangle is read)
+ *   XL    n x pm1 covariates X_L, FP64 column-major (may be NULL when pm1 == 0)
+ *   t     number of traits, t >= 1
+ *   h2    t heritabilities h_j^2, each in [0, 1]
+ *   opts  options (NULL = defaults)
+ *
+ * Fails with GWAS_ERR_NOT_SPD when some h_j^2 lambda_k + 1 - h_j^2 <= 1e-12 *
+ * max_k(...) (M_j not SPD; Section 3.1 needs D_j > 0), and with GWAS_ERR_ARG
+ * when X_L does not have full column rank.
+ */
+GWAS_API int gwas_setup(gwas_ctx** ctx, int n, int pm1, const double* phi, const double* XL, int t,
+               const double* h2, const gwas_opts* opts);
+
+/*
+ * gwas_load_snps -- make the genotypes X_R resident on the device and rotate
+ * them by Z^T once (Algorithm 5, X'_R := Z^T X_R; Section 3.2 explains why
+ * this is hoisted out of both loops).  Replaces previously loaded SNPs.
+ *
+ *   m   number of SNPs, m >= 1
+ *   XR  n x m int8 genotypes, column-major (SNP-major), values in {0, 1, 2}
+ *       (other values are accepted and used as given)
+ */
+GWAS_API int gwas_load_snps(gwas_ctx* ctx, int64_t m, const int8_t* XR);
+
+/*
+ * gwas_solve -- solve the grid block SNPs [i0, i1) x all t traits
+ * (Algorithm 5, Y' := Z^T Y and the double loop).
+ *
+ *   Y    n x t phenotypes, FP64 column-major
+ *   i0, i1  SNP range, 0 <= i0 <= i1 <= m
+ *   out  GWAS_OUT_FULL_B: double[t][i1-i0][p];
+ *        GWAS_OUT_LAST_SE: float beta[t][i1-i0], then float se[t][i1-i0].
+ *
+ * The standard error is sqrt(sigma^2 [S^-1]_pp) with sigma^2 = RSS/(n-p),
+ * RSS the squared norm of the whitened residual (the paper defines none).
+ * Returns GWAS_ERR_SINGULAR_PAIRS (a warning) when some pair's Schur
+ * complement is <= 1e-10 times its diagonal entry; those outputs are NaN.
+ */
+GWAS_API int gwas_solve(gwas_ctx* ctx, const double* Y, int64_t i0, int64_t i1, void* out);
+
+/* Replace the t heritabilities given at setup (same t). */
+GWAS_API int gwas_set_h2(gwas_ctx* ctx, int t, const double* h2);
+
+/* Number of pairs flagged singular by the last gwas_solve. */
+GWAS_API int64_t gwas_singular_count(const gwas_ctx* ctx);
+
+/* Number of kernels this context launched since it was created. */
+GWAS_API int64_t gwas_kernel_launches(const gwas_ctx* ctx);
+
+/* One-line description of the last failure on ctx (or of the last failed
+ * gwas_setup when ctx is NULL).  Owned by the library. */
+GWAS_API const char* gwas_last_error(const gwas_ctx* ctx);
+
+/* Free every device and host resource of the context.  NULL is ignored. */
+GWAS_API void gwas_destroy(gwas_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GWAS_GB300_H */

@@ -1,0 +1,184 @@
+"""Python binding of the GB300 multi-trait GWAS library (``include/gwas.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libgwas_gb300.so`` built in-tree by :mod:`.build`.  The first call
+into the library fails loudly when it has not been built; there is no CPU
+fallback.
+
+Array arguments may be numpy arrays (host memory) or torch tensors (host or
+CUDA); their dtype, shape and contiguity are checked here and their addresses
+are passed to the C functions, which tell host from device memory themselves.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgwas_gb300.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "gwas.h")
+
+
+def _status_codes():
+    codes = {}
+    with open(HEADER) as f:
+        for line in f:
+            mt = re.match(r"#define (GWAS_[A-Z0-9_]+)\s+(\d+)", line)
+            if mt:
+                codes[mt.group(1)] = int(mt.group(2))
+    return codes
+
+
+_CODES = _status_codes()
+globals().update(_CODES)
+_NAMES = {v: k for k, v in _CODES.items() if k.startswith("GWAS_ERR") or k == "GWAS_OK"}
+
+
+class GwasError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class gwas_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("output", C.c_int), ("trait_block", C.c_int), ("device", C.c_int),
+                ("hbm_budget", C.c_size_t), ("stream", C.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1210_7683_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, ci = C.c_void_p, C.c_int64, C.c_int
+    lib.gwas_default_opts.argtypes = [C.POINTER(gwas_opts)]
+    lib.gwas_default_opts.restype = None
+    lib.gwas_setup.argtypes = [C.POINTER(vp), ci, ci, vp, vp, ci, vp, C.POINTER(gwas_opts)]
+    lib.gwas_setup.restype = ci
+    lib.gwas_load_snps.argtypes = [vp, i64, vp]
+    lib.gwas_load_snps.restype = ci
+    lib.gwas_solve.argtypes = [vp, vp, i64, i64, vp]
+    lib.gwas_solve.restype = ci
+    lib.gwas_set_h2.argtypes = [vp, ci, vp]
+    lib.gwas_set_h2.restype = ci
+    lib.gwas_singular_count.argtypes = [vp]
+    lib.gwas_singular_count.restype = i64
+    lib.gwas_kernel_launches.argtypes = [vp]
+    lib.gwas_kernel_launches.restype = i64
+    lib.gwas_last_error.argtypes = [vp]
+    lib.gwas_last_error.restype = C.c_char_p
+    lib.gwas_destroy.argtypes = [vp]
+    lib.gwas_destroy.restype = None
+    return lib
+
+
+_lib = None
+
+
+class _LazyLib:
+    """Loads the CUDA library on first use and raises if it has not been built."""
+
+    def __getattr__(self, name):
+        global _lib
+        if _lib is None:
+            _lib = _load()
+        return getattr(_lib, name)
+
+
+lib = _LazyLib()
+
+
+def _addr(x, dtype, shape=None, name="array"):
+    """Address of a C-contiguous numpy array or torch tensor of the given dtype."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.dtype(dtype):
+            raise TypeError(f"{name}: dtype {x.dtype}, expected {np.dtype(dtype)}")
+        if not x.flags.c_contiguous:
+            raise ValueError(f"{name} must be C-contiguous")
+        if shape is not None and tuple(x.shape) != tuple(shape):
+            raise ValueError(f"{name}: shape {x.shape}, expected {tuple(shape)}")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):  # torch tensor
+        import torch
+        tmap = {np.float64: torch.float64, np.float32: torch.float32, np.int8: torch.int8}
+        if x.dtype != tmap[np.dtype(dtype).type]:
+            raise TypeError(f"{name}: dtype {x.dtype}, expected {dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if shape is not None and tuple(x.shape) != tuple(shape):
+            raise ValueError(f"{name}: shape {tuple(x.shape)}, expected {tuple(shape)}")
+        return x.data_ptr()
+    raise TypeError(f"{name}: expected a numpy array or a torch tensor")
+
+
+def _check(rc: int, ctx=None, allow=()):
+    if rc != GWAS_OK and rc not in allow:
+        raise GwasError(rc, lib.gwas_last_error(ctx).decode())
+    return rc
+
+
+def gwas_default_opts(**kw) -> gwas_opts:
+    o = gwas_opts()
+    lib.gwas_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def gwas_setup(n, pm1, phi, XL, t, h2, opts: gwas_opts | None = None):
+    """Create a context (see include/gwas.h).  phi: (n, n); XL: (p-1, n); h2: (t,)."""
+    ctx = C.c_void_p()
+    rc = lib.gwas_setup(C.byref(ctx), n, pm1, _addr(phi, np.float64, (n, n), "phi"),
+                        _addr(XL, np.float64, (pm1, n), "XL") if pm1 > 0 else None, t,
+                        _addr(h2, np.float64, (t,), "h2"), C.byref(opts) if opts is not None else None)
+    _check(rc, None)
+    return ctx
+
+
+def gwas_load_snps(ctx, m, XR, n=None):
+    """XR: (m, n) int8, SNP-major."""
+    shape = None if n is None else (m, n)
+    return _check(lib.gwas_load_snps(ctx, m, _addr(XR, np.int8, shape, "XR")), ctx)
+
+
+def gwas_solve(ctx, Y, i0, i1, out):
+    """Y: (t, n) float64; out: FULL_B (t, i1-i0, p) float64 or LAST_SE (2, t, i1-i0) float32.
+
+    Returns GWAS_OK or GWAS_ERR_SINGULAR_PAIRS (a warning); raises on errors.
+    """
+    yv = _addr(Y, np.float64, None, "Y")
+    dt = np.float64 if getattr(out, "dtype", None) in (np.float64, getattr(_torch(), "float64", None)) else np.float32
+    return _check(lib.gwas_solve(ctx, yv, int(i0), int(i1), _addr(out, dt, None, "out")), ctx,
+                  allow=(GWAS_ERR_SINGULAR_PAIRS,))
+
+
+def gwas_set_h2(ctx, t, h2):
+    return _check(lib.gwas_set_h2(ctx, t, _addr(h2, np.float64, (t,), "h2")), ctx)
+
+
+def gwas_singular_count(ctx) -> int:
+    return lib.gwas_singular_count(ctx)
+
+
+def gwas_kernel_launches(ctx) -> int:
+    return lib.gwas_kernel_launches(ctx)
+
+
+def gwas_last_error(ctx=None) -> str:
+    return lib.gwas_last_error(ctx).decode()
+
+
+def gwas_destroy(ctx) -> None:
+    lib.gwas_destroy(ctx)
+
+
+def _torch():
+    try:
+        import torch
+        return torch
+    except ImportError:  # pragma: no cover
+        return None

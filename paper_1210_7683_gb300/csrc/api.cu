@@ -1,0 +1,438 @@
+// C interface of the GWAS library: contexts, device memory, argument checks and the
+// orchestration of the preloop and loop phases of Algorithm 5 (Section 3).
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "gwas_internal.cuh"
+
+static thread_local std::string g_setup_err;
+
+namespace {
+
+// Restores the caller's current device when a call returns.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+std::string fmt(const char* f, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, f);
+  vsnprintf(buf, sizeof buf, f, ap);
+  va_end(ap);
+  return buf;
+}
+
+}  // namespace
+
+int ctx_fail(gwas_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg; else g_setup_err = msg;
+  return code;
+}
+
+bool ctx_cuda_ok(gwas_ctx* c, cudaError_t e, const char* what, int* rc) {
+  if (e == cudaSuccess) return true;
+  cudaGetLastError();
+  *rc = ctx_fail(c, e == cudaErrorMemoryAllocation ? GWAS_ERR_OOM : GWAS_ERR_CUDA,
+                 fmt("%s: %s", what, cudaGetErrorString(e)));
+  return false;
+}
+
+int ctx_alloc(gwas_ctx* c, size_t bytes, void** out) {
+  *out = nullptr;
+  size_t b = (bytes + 255) & ~size_t(255);
+  if (b == 0) b = 256;
+  if (c->budget && c->allocated + b > c->budget)
+    return ctx_fail(c, GWAS_ERR_OOM, fmt("allocation of %zu bytes exceeds the HBM budget (%zu of %zu in use)", b,
+                                         c->allocated, c->budget));
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, b);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(c, GWAS_ERR_OOM, fmt("cudaMalloc(%zu): %s", b, cudaGetErrorString(e)));
+  }
+  c->bufs.push_back({p, b});
+  c->allocated += b;
+  *out = p;
+  return GWAS_OK;
+}
+
+void ctx_free(gwas_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->bufs.size(); ++i)
+    if (c->bufs[i].ptr == p) {
+      cudaFree(p);
+      c->allocated -= c->bufs[i].bytes;
+      c->bufs.erase(c->bufs.begin() + i);
+      return;
+    }
+}
+
+int ptr_kind(gwas_ctx* c, const void* p, bool* is_device) {
+  cudaPointerAttributes a;
+  *is_device = false;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return GWAS_OK;  // unregistered host memory
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+    if (a.type == cudaMemoryTypeDevice && a.device != c->device)
+      return ctx_fail(c, GWAS_ERR_ARG, fmt("device pointer on device %d, context on device %d", a.device, c->device));
+    *is_device = true;
+  }
+  return GWAS_OK;
+}
+
+int ctx_upload(gwas_ctx* c, const void* src, size_t bytes, void* dst) {
+  bool dev;
+  int rc = ptr_kind(c, src, &dev);
+  if (rc) return rc;
+  if (!ctx_cuda_ok(c, cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+                   "upload", &rc))
+    return rc;
+  return GWAS_OK;
+}
+
+extern "C" void gwas_default_opts(gwas_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->precision = GWAS_MIXED;
+  o->output = GWAS_OUT_LAST_SE;
+}
+
+static void destroy_impl(gwas_ctx* c) {
+  if (!c) return;
+  int dev;
+  bool have = cudaGetDevice(&dev) == cudaSuccess;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  mixed_free(c);
+  for (auto& b : c->bufs) cudaFree(b.ptr);
+  c->bufs.clear();
+  if (c->solver) cusolverDnDestroy((cusolverDnHandle_t)c->solver);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (have) cudaSetDevice(dev);
+  delete c;
+}
+
+extern "C" void gwas_destroy(gwas_ctx* c) { destroy_impl(c); }
+
+extern "C" const char* gwas_last_error(const gwas_ctx* c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
+
+extern "C" int64_t gwas_singular_count(const gwas_ctx* c) { return c ? c->singular : 0; }
+
+extern "C" int64_t gwas_kernel_launches(const gwas_ctx* c) { return c ? c->launches : 0; }
+
+static int check_h2(gwas_ctx* c, const std::vector<double>& h2) {
+  double lmin = c->h_lam.front(), lmax = c->h_lam.back();
+  for (size_t j = 0; j < h2.size(); ++j) {
+    double h = h2[j];
+    if (!(h >= 0.0 && h <= 1.0)) return ctx_fail(c, GWAS_ERR_ARG, fmt("h2[%zu] = %g outside [0, 1]", j, h));
+    double dmin = std::min(h * lmin + 1.0 - h, h * lmax + 1.0 - h);
+    double dmax = std::max(h * lmin + 1.0 - h, h * lmax + 1.0 - h);
+    if (!(dmin > 1e-12 * dmax))
+      return ctx_fail(c, GWAS_ERR_NOT_SPD,
+                      fmt("M_j not positive definite for trait %zu: min_k h2*lambda_k + 1 - h2 = %g", j, dmin));
+  }
+  return GWAS_OK;
+}
+
+extern "C" int gwas_setup(gwas_ctx** out, int n, int pm1, const double* phi, const double* XL, int t,
+                          const double* h2, const gwas_opts* opts) {
+  if (!out) return ctx_fail(nullptr, GWAS_ERR_ARG, "ctx pointer is NULL");
+  *out = nullptr;
+  gwas_opts o;
+  gwas_default_opts(&o);
+  if (opts) o = *opts;
+  if (n < 1 || n > 16384) return ctx_fail(nullptr, GWAS_ERR_ARG, fmt("n = %d outside [1, 16384]", n));
+  if (pm1 < 0 || pm1 > GWAS_MAX_PM1) return ctx_fail(nullptr, GWAS_ERR_UNSUPPORTED, fmt("p-1 = %d outside [0, 7]", pm1));
+  if (n <= pm1 + 1) return ctx_fail(nullptr, GWAS_ERR_ARG, "need n > p");
+  if (t < 1) return ctx_fail(nullptr, GWAS_ERR_ARG, "t must be >= 1");
+  if (!phi || !h2 || (pm1 > 0 && !XL)) return ctx_fail(nullptr, GWAS_ERR_ARG, "NULL input array");
+  if (o.precision != GWAS_FP64 && o.precision != GWAS_MIXED) return ctx_fail(nullptr, GWAS_ERR_ARG, "bad precision mode");
+  if (o.output != GWAS_OUT_FULL_B && o.output != GWAS_OUT_LAST_SE) return ctx_fail(nullptr, GWAS_ERR_ARG, "bad output mode");
+  if (o.precision == GWAS_MIXED && pm1 != 3)
+    return ctx_fail(nullptr, GWAS_ERR_UNSUPPORTED, "the mixed-precision path is built for p-1 = 3 covariates");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return ctx_fail(nullptr, GWAS_ERR_CUDA, "no CUDA device");
+  }
+  if (o.device < 0 || o.device >= ndev) return ctx_fail(nullptr, GWAS_ERR_ARG, "bad device ordinal");
+  DeviceGuard guard(o.device);
+
+  gwas_ctx* c = new gwas_ctx;
+  c->n = n; c->pm1 = pm1; c->p = pm1 + 1; c->t = t; c->device = o.device;
+  c->precision = o.precision; c->output = o.output; c->trait_block = o.trait_block; c->budget = o.hbm_budget;
+  int rc = GWAS_OK;
+  auto fail = [&](int code) { g_setup_err = c->err; destroy_impl(c); return code; };
+  if (o.stream) {
+    c->stream = (cudaStream_t)o.stream;
+  } else {
+    if (!ctx_cuda_ok(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream", &rc)) return fail(rc);
+    c->own_stream = true;
+  }
+  if ((rc = ctx_alloc(c, 32, (void**)&c->d_status))) return fail(rc);
+  cudaMemsetAsync(c->d_status, 0, 32, c->stream);
+
+  // ---- eigendecomposition Phi = Z Lambda Z^T (Algorithm 5, eigendec), FP64
+  if ((rc = ctx_alloc(c, sizeof(double) * n * n, (void**)&c->Z))) return fail(rc);
+  if ((rc = ctx_alloc(c, sizeof(double) * n, (void**)&c->lam))) return fail(rc);
+  if ((rc = ctx_upload(c, phi, sizeof(double) * n * n, c->Z))) return fail(rc);
+  cusolverDnHandle_t h;
+  if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) return fail(ctx_fail(c, GWAS_ERR_CUDA, "cusolverDnCreate failed"));
+  c->solver = h;
+  cusolverDnSetStream(h, c->stream);
+  int lwork = 0;
+  if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, c->Z, n, c->lam, &lwork) !=
+      CUSOLVER_STATUS_SUCCESS)
+    return fail(ctx_fail(c, GWAS_ERR_CUDA, "syevd workspace query failed"));
+  double* work = nullptr;
+  int* info = nullptr;
+  if ((rc = ctx_alloc(c, sizeof(double) * std::max(lwork, 1), (void**)&work))) return fail(rc);
+  if ((rc = ctx_alloc(c, sizeof(int), (void**)&info))) return fail(rc);
+  if (cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, c->Z, n, c->lam, work, lwork, info) !=
+      CUSOLVER_STATUS_SUCCESS)
+    return fail(ctx_fail(c, GWAS_ERR_CUDA, "syevd failed to launch"));
+  int hinfo = 0;
+  c->h_lam.resize(n);
+  if (!ctx_cuda_ok(c, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "info", &rc))
+    return fail(rc);
+  if (!ctx_cuda_ok(c, cudaMemcpyAsync(c->h_lam.data(), c->lam, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream),
+                   "lambda", &rc))
+    return fail(rc);
+  if (!ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "eigendecomposition", &rc)) return fail(rc);
+  ctx_free(c, work);
+  ctx_free(c, info);
+  if (hinfo != 0) return fail(ctx_fail(c, GWAS_ERR_NOT_SPD, fmt("eigensolver did not converge (info %d)", hinfo)));
+  for (double v : c->h_lam)
+    if (!std::isfinite(v)) return fail(ctx_fail(c, GWAS_ERR_ARG, "Phi has non-finite entries"));
+
+  // ---- heritabilities
+  c->h_h2.assign(t, 0.0);
+  {
+    bool dev;
+    if ((rc = ptr_kind(c, h2, &dev))) return fail(rc);
+    if (dev) cudaMemcpy(c->h_h2.data(), h2, sizeof(double) * t, cudaMemcpyDeviceToHost);
+    else std::memcpy(c->h_h2.data(), h2, sizeof(double) * t);
+  }
+  if ((rc = check_h2(c, c->h_h2))) return fail(rc);
+  if ((rc = ctx_alloc(c, sizeof(double) * t, (void**)&c->h2))) return fail(rc);
+  cudaMemcpyAsync(c->h2, c->h_h2.data(), sizeof(double) * t, cudaMemcpyHostToDevice, c->stream);
+
+  // ---- covariates X_L and X'_L := Z^T X_L (Algorithm 5, gemm)
+  if (pm1 > 0) {
+    c->h_XL.resize((size_t)pm1 * n);
+    bool dev;
+    if ((rc = ptr_kind(c, XL, &dev))) return fail(rc);
+    if (dev) cudaMemcpy(c->h_XL.data(), XL, sizeof(double) * pm1 * n, cudaMemcpyDeviceToHost);
+    else std::memcpy(c->h_XL.data(), XL, sizeof(double) * pm1 * n);
+    // X_L^T X_L and its inverse (full column rank is assumed by the paper, Section 2)
+    std::vector<double> G(pm1 * pm1), L(pm1 * pm1, 0.0);
+    for (int a = 0; a < pm1; ++a)
+      for (int b = 0; b < pm1; ++b) {
+        double s = 0;
+        for (int k = 0; k < n; ++k) s += c->h_XL[(size_t)a * n + k] * c->h_XL[(size_t)b * n + k];
+        G[a * pm1 + b] = s;
+      }
+    for (int a = 0; a < pm1; ++a)
+      for (int b = 0; b <= a; ++b) {
+        double s = G[a * pm1 + b];
+        for (int k = 0; k < b; ++k) s -= L[a * pm1 + k] * L[b * pm1 + k];
+        if (a == b) {
+          if (!(s > 1e-12 * G[a * pm1 + a])) return fail(ctx_fail(c, GWAS_ERR_ARG, "X_L does not have full column rank"));
+          L[a * pm1 + a] = std::sqrt(s);
+        } else {
+          L[a * pm1 + b] = s / L[b * pm1 + b];
+        }
+      }
+    c->h_XtXinv.assign(pm1 * pm1, 0.0);
+    for (int col = 0; col < pm1; ++col) {  // solve G x = e_col
+      std::vector<double> z(pm1), x(pm1);
+      for (int r = 0; r < pm1; ++r) {
+        double s = (r == col);
+        for (int k = 0; k < r; ++k) s -= L[r * pm1 + k] * z[k];
+        z[r] = s / L[r * pm1 + r];
+      }
+      for (int r = pm1 - 1; r >= 0; --r) {
+        double s = z[r];
+        for (int k = r + 1; k < pm1; ++k) s -= L[k * pm1 + r] * x[k];
+        x[r] = s / L[r * pm1 + r];
+      }
+      for (int r = 0; r < pm1; ++r) c->h_XtXinv[r * pm1 + col] = x[r];
+    }
+    if ((rc = ctx_alloc(c, sizeof(double) * pm1 * n, (void**)&c->XL))) return fail(rc);
+    if ((rc = ctx_alloc(c, sizeof(double) * pm1 * n, (void**)&c->XLt))) return fail(rc);
+    cudaMemcpyAsync(c->XL, c->h_XL.data(), sizeof(double) * pm1 * n, cudaMemcpyHostToDevice, c->stream);
+    launch_rotate_fp64_f64(c, c->XL, pm1, n, c->XLt);
+  }
+  if (!ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "setup", &rc)) return fail(rc);
+  if (!ctx_cuda_ok(c, cudaGetLastError(), "setup kernels", &rc)) return fail(rc);
+  *out = c;
+  return GWAS_OK;
+}
+
+extern "C" int gwas_set_h2(gwas_ctx* c, int t, const double* h2) {
+  if (!c) return GWAS_ERR_ARG;
+  if (t != c->t || !h2) return ctx_fail(c, GWAS_ERR_ARG, "t differs from setup or h2 is NULL");
+  DeviceGuard guard(c->device);
+  std::vector<double> v(t);
+  bool dev;
+  int rc = ptr_kind(c, h2, &dev);
+  if (rc) return rc;
+  if (dev) cudaMemcpy(v.data(), h2, sizeof(double) * t, cudaMemcpyDeviceToHost);
+  else std::memcpy(v.data(), h2, sizeof(double) * t);
+  if ((rc = check_h2(c, v))) return rc;
+  c->h_h2 = v;
+  cudaMemcpyAsync(c->h2, v.data(), sizeof(double) * t, cudaMemcpyHostToDevice, c->stream);
+  if (!ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "set_h2", &rc)) return rc;
+  return GWAS_OK;
+}
+
+extern "C" int gwas_load_snps(gwas_ctx* c, int64_t m, const int8_t* XR) {
+  if (!c) return GWAS_ERR_ARG;
+  if (m < 1 || !XR) return ctx_fail(c, GWAS_ERR_ARG, "m must be >= 1 and XR non-NULL");
+  DeviceGuard guard(c->device);
+  int rc = GWAS_OK;
+  // drop previous genotypes
+  ctx_free(c, c->Xt);
+  c->Xt = nullptr;
+  mixed_free(c);
+  c->m = 0;
+  bool dev;
+  if ((rc = ptr_kind(c, XR, &dev))) return rc;
+  const size_t bytes = (size_t)m * c->n;
+  int8_t* dX = nullptr;
+  if (dev) {
+    dX = (int8_t*)XR;
+  } else {
+    if ((rc = ctx_alloc(c, bytes, (void**)&dX))) return rc;
+    if (!ctx_cuda_ok(c, cudaMemcpyAsync(dX, XR, bytes, cudaMemcpyHostToDevice, c->stream), "genotype upload", &rc)) {
+      ctx_free(c, dX);
+      return rc;
+    }
+  }
+  if (c->precision == GWAS_FP64) {
+    // X'_R := Z^T X_R (Algorithm 5, gemm), kept resident as [m][n] FP64
+    if ((rc = ctx_alloc(c, sizeof(double) * m * c->n, (void**)&c->Xt)) == GWAS_OK)
+      launch_rotate_fp64_i8(c, dX, m, c->n, c->Xt);
+  } else {
+    rc = mixed_load(c, dX);
+  }
+  if (rc == GWAS_OK) ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "load_snps", &rc);
+  if (rc == GWAS_OK) ctx_cuda_ok(c, cudaGetLastError(), "load_snps kernels", &rc);
+  if (!dev) ctx_free(c, dX);
+  if (rc == GWAS_OK) c->m = m;
+  return rc;
+}
+
+extern "C" int gwas_solve(gwas_ctx* c, const double* Y, int64_t i0, int64_t i1, void* out) {
+  if (!c) return GWAS_ERR_ARG;
+  if (c->m == 0) return ctx_fail(c, GWAS_ERR_STATE, "gwas_solve before gwas_load_snps");
+  if (!Y || !out) return ctx_fail(c, GWAS_ERR_ARG, "NULL Y or out");
+  if (i0 < 0 || i1 < i0 || i1 > c->m) return ctx_fail(c, GWAS_ERR_ARG, "SNP range outside [0, m]");
+  DeviceGuard guard(c->device);
+  int rc = GWAS_OK;
+  c->singular = 0;
+  const int64_t M = i1 - i0;
+  if (M == 0) return GWAS_OK;
+  const int n = c->n, t = c->t, p = c->p;
+  const int tb = (c->trait_block > 0 && c->trait_block < t) ? c->trait_block : t;
+  bool ydev, odev;
+  if ((rc = ptr_kind(c, Y, &ydev))) return rc;
+  if ((rc = ptr_kind(c, out, &odev))) return rc;
+  cudaMemsetAsync(c->d_status, 0, 32, c->stream);
+
+  std::vector<void*> tmp;
+  auto cleanup = [&]() { for (void* q : tmp) ctx_free(c, q); };
+  auto talloc = [&](size_t b, void** q) {
+    int r = ctx_alloc(c, b, q);
+    if (r == GWAS_OK) tmp.push_back(*q);
+    return r;
+  };
+  const double* dY = Y;
+  if (!ydev) {
+    double* y;
+    if ((rc = talloc(sizeof(double) * t * n, (void**)&y))) { cleanup(); return rc; }
+    if ((rc = ctx_upload(c, Y, sizeof(double) * t * n, y))) { cleanup(); return rc; }
+    dY = y;
+  }
+  const size_t pair_bytes = c->output == GWAS_OUT_FULL_B ? sizeof(double) * p : 2 * sizeof(float);
+  void* stage = nullptr;
+  if (!odev && (rc = talloc(pair_bytes * (size_t)tb * M, &stage))) { cleanup(); return rc; }
+
+  double *Yt = nullptr, *R = nullptr, *cst = nullptr;
+  if (c->precision == GWAS_FP64) {
+    if ((rc = talloc(sizeof(double) * tb * n, (void**)&Yt)) || (rc = talloc(sizeof(double) * tb * (p + 1) * n, (void**)&R)) ||
+        (rc = talloc(sizeof(double) * tb * consts_stride(c->pm1), (void**)&cst))) {
+      cleanup();
+      return rc;
+    }
+  }
+  for (int j0 = 0; j0 < t && rc == GWAS_OK; j0 += tb) {
+    const int nb = std::min(tb, t - j0);
+    // block outputs: device pointers of this trait block's results
+    void *ob, *os = nullptr;
+    if (odev) {
+      if (c->output == GWAS_OUT_FULL_B) {
+        ob = (double*)out + (size_t)j0 * M * p;
+      } else {
+        ob = (float*)out + (size_t)j0 * M;
+        os = (float*)out + (size_t)t * M + (size_t)j0 * M;
+      }
+    } else {
+      ob = stage;
+      if (c->output == GWAS_OUT_LAST_SE) os = (float*)stage + (size_t)nb * M;
+    }
+    if (c->precision == GWAS_FP64) {
+      launch_rotate_fp64_f64(c, dY + (size_t)j0 * n, nb, n, Yt);          // Y' := Z^T Y (gemm)
+      launch_prep_fp64(c, Yt, nb, c->h2 + j0, R, cst);                    // per-trait scalar-ops, syrk, gemv
+      if (c->output == GWAS_OUT_FULL_B) launch_fused_fp64(c, i0, i1, j0, nb, M, R, cst, ob);
+      else {
+        void* pair[2] = {ob, os};
+        launch_fused_fp64(c, i0, i1, j0, nb, M, R, cst, pair);
+      }
+    } else {
+      void* o2 = ob;
+      void* pair[2] = {ob, os};
+      if (c->output == GWAS_OUT_LAST_SE) o2 = pair;
+      rc = mixed_solve_block(c, dY + (size_t)j0 * n, j0, nb, i0, i1, M, o2);
+    }
+    if (rc == GWAS_OK && !odev) {
+      if (c->output == GWAS_OUT_FULL_B) {
+        ctx_cuda_ok(c, cudaMemcpyAsync((double*)out + (size_t)j0 * M * p, ob, sizeof(double) * p * nb * M,
+                                       cudaMemcpyDeviceToHost, c->stream), "result download", &rc);
+      } else {
+        ctx_cuda_ok(c, cudaMemcpyAsync((float*)out + (size_t)j0 * M, ob, sizeof(float) * nb * M, cudaMemcpyDeviceToHost,
+                                       c->stream), "result download", &rc);
+        if (rc == GWAS_OK)
+          ctx_cuda_ok(c, cudaMemcpyAsync((float*)out + (size_t)t * M + (size_t)j0 * M, os, sizeof(float) * nb * M,
+                                         cudaMemcpyDeviceToHost, c->stream), "result download", &rc);
+      }
+      if (rc == GWAS_OK) ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "solve block", &rc);
+    }
+  }
+  unsigned long long st[2] = {0, 0};
+  if (rc == GWAS_OK) ctx_cuda_ok(c, cudaGetLastError(), "solve kernels", &rc);
+  if (rc == GWAS_OK) ctx_cuda_ok(c, cudaMemcpyAsync(st, c->d_status, 16, cudaMemcpyDeviceToHost, c->stream), "status", &rc);
+  if (rc == GWAS_OK) ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "solve", &rc);
+  cleanup();
+  if (rc) return rc;
+  if (st[0]) return ctx_fail(c, GWAS_ERR_TIMEOUT, "a bounded wait inside the contraction kernel ran out");
+  c->singular = (int64_t)st[1];
+  if (c->singular) return ctx_fail(c, GWAS_ERR_SINGULAR_PAIRS, fmt("%lld pairs with a singular system", (long long)st[1]));
+  return GWAS_OK;
+}

@@ -1,0 +1,76 @@
+// Internal declarations shared by the translation units of the GWAS library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gwas.h"
+
+#define GWAS_MAX_PM1 7
+
+// Raw device buffer owned by a context; freed in gwas_destroy.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct MixedState;  // mixed-precision resident data (mixed.cu)
+
+struct gwas_ctx {
+  int n = 0, pm1 = 0, p = 0, t = 0, device = 0;
+  int precision = GWAS_MIXED, output = GWAS_OUT_LAST_SE, trait_block = 0;
+  size_t budget = 0, allocated = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* solver = nullptr;  // cusolverDnHandle_t
+  std::string err;
+  std::vector<DevBuf> bufs;
+
+  // preloop state (setup)
+  double* Z = nullptr;     // n x n, column k = eigenvector k
+  double* lam = nullptr;   // n eigenvalues, ascending
+  double* XL = nullptr;    // [pm1][n]: row l = covariate l
+  double* XLt = nullptr;   // [pm1][n]: row l = Z^T x_L,l
+  double* h2 = nullptr;    // [t]
+  std::vector<double> h_lam, h_h2;
+  std::vector<double> h_XL;    // [pm1][n]
+  std::vector<double> h_XtXinv;// (X_L^T X_L)^-1, pm1 x pm1
+
+  // genotypes
+  int64_t m = 0;
+  double* Xt = nullptr;        // FP64 path: [m][n] rotated genotypes
+  MixedState* mixed = nullptr; // mixed path state
+
+  // device status words: [0] timeout flag, [1..2] singular-pair counter (u64)
+  unsigned long long* d_status = nullptr;
+  int64_t singular = 0;
+  int64_t launches = 0;
+};
+
+// ---------------------------------------------------------------- helpers (api.cu)
+int ctx_fail(gwas_ctx* c, int code, const std::string& msg);
+int ctx_alloc(gwas_ctx* c, size_t bytes, void** out);          // budget-checked cudaMalloc
+void ctx_free(gwas_ctx* c, void* p);
+bool ctx_cuda_ok(gwas_ctx* c, cudaError_t e, const char* what, int* rc);
+// Copy `bytes` from a host or device pointer to a new or given device buffer.
+int ctx_upload(gwas_ctx* c, const void* src, size_t bytes, void* dst);
+int ptr_kind(gwas_ctx* c, const void* p, bool* is_device);
+
+// ---------------------------------------------------------------- FP64 path (fp64.cu)
+// C[r][col] = sum_k A[r][k] * Z[k][col] for r < rows, col < n (A row-major with leading dim lda).
+void launch_rotate_fp64_i8(gwas_ctx* c, const int8_t* A, int64_t rows, int64_t lda, double* C);
+void launch_rotate_fp64_f64(gwas_ctx* c, const double* A, int64_t rows, int64_t lda, double* C);
+// Per-trait FP64 prep: R[j] = [e∘y~ | e∘x~_L | e] ([t][p+1][n]); consts[j] = {S_TL, b_T, yy}.
+void launch_prep_fp64(gwas_ctx* c, const double* Yt, int tb, const double* h2, double* R, double* consts);
+// Fused FP64 contraction + per-pair solve for SNPs [i0,i1) x traits [j0, j0+tb).
+void launch_fused_fp64(gwas_ctx* c, int64_t i0, int64_t i1, int j0, int tb, int64_t ldo, const double* R,
+                       const double* consts, void* out);
+int consts_stride(int pm1);
+
+// ---------------------------------------------------------------- mixed path (mixed.cu)
+int mixed_load(gwas_ctx* c, const int8_t* dXR);                // genotypes already on the device
+int mixed_solve_block(gwas_ctx* c, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
+                      void* dout);
+void mixed_free(gwas_ctx* c);

@@ -15,3 +15,30 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def root():
     return ROOT
+
+
+def _has_gpu():
+    import ctypes
+    try:
+        rt = ctypes.CDLL("libcudart.so")
+    except OSError:
+        return False
+    cnt = ctypes.c_int(0)
+    return rt.cudaGetDeviceCount(ctypes.byref(cnt)) == 0 and cnt.value > 0
+
+
+def pytest_collection_modifyitems(config, items):
+    if any("gpu" in it.keywords for it in items) and not _has_gpu():
+        skip = pytest.mark.skip(reason="no CUDA device")
+        for it in items:
+            if "gpu" in it.keywords:
+                it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def gw():
+    """The binding with a freshly built library (fails loudly if the build fails)."""
+    from paper_1210_7683_gb300 import build as gbuild
+    gbuild.build()
+    import paper_1210_7683_gb300 as g
+    return g

@@ -1,0 +1,58 @@
+"""The C-ABI library builds, loads and exports every symbol that include/gwas.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1210_7683_gb300 import build as gbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return gbuild.build()
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "gwas.h")) as f:
+        src = f.read()
+    return re.findall(r"GWAS_API\s+[\w\s\*]+?\b(gwas_\w+)\s*\(", src)
+
+
+def test_header_declares_the_api():
+    names = declared_functions()
+    for need in ("gwas_setup", "gwas_load_snps", "gwas_solve", "gwas_last_error", "gwas_destroy"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_the_header():
+    import paper_1210_7683_gb300 as g
+    for name in declared_functions():
+        assert callable(getattr(g, name)), name
+
+
+def test_status_codes_parsed():
+    import paper_1210_7683_gb300 as g
+    assert g.GWAS_OK == 0 and g.GWAS_ERR_SINGULAR_PAIRS == 6 and g.GWAS_MIXED == 1
+
+
+def test_argument_errors_without_gpu(libpath):
+    # argument checks run before any device work, so they answer on a CPU-only host too
+    lib = ctypes.CDLL(libpath)
+    ctx = ctypes.c_void_p()
+    rc = lib.gwas_setup(ctypes.byref(ctx), 0, 3, None, None, 1, None, None)
+    assert rc == 1  # GWAS_ERR_ARG
+    lib.gwas_last_error.restype = ctypes.c_char_p
+    assert b"n = 0" in lib.gwas_last_error(None)
+    rc = lib.gwas_setup(ctypes.byref(ctx), 100, 9, None, None, 1, None, None)
+    assert rc == 8  # GWAS_ERR_UNSUPPORTED
+    rc = lib.gwas_solve(None, None, 0, 0, None)
+    assert rc == 1
