@@ -78,6 +78,7 @@ typedef struct gwas_opts {
   int output;         /* GWAS_OUT_FULL_B or GWAS_OUT_LAST_SE */
   int trait_block;    /* traits per internal block of gwas_solve; 0 = all traits at once */
   int device;         /* CUDA device ordinal of the context */
+  int profile;        /* nonzero: time every kernel launch with CUDA events (see gwas_kernel_time) */
   size_t hbm_budget;  /* bytes the context may allocate on the device; 0 = no limit */
   void* stream;       /* cudaStream_t the context runs on; NULL = the context creates one */
 } gwas_opts;
@@ -141,6 +142,16 @@ GWAS_API int64_t gwas_singular_count(const gwas_ctx* ctx);
 
 /* Number of kernels this context launched since it was created. */
 GWAS_API int64_t gwas_kernel_launches(const gwas_ctx* ctx);
+
+/* Accumulated device time (ms, from CUDA events recorded on the context's stream
+ * around each launch) and launch count of one kernel family since the last
+ * gwas_reset_timers; zero unless the context was created with opts.profile.
+ * Families: "eigendecomposition", "rotate_fp64", "prep_fp64", "fused_fp64",
+ * "setup_rotation_operands", "slice_rows", "genotypes_bf16", "xgemm_rotate_snps",
+ * "slice_snp_squares", "xgemm_rotate_traits", "prep_traits", "xgemm_back_rotate",
+ * "pack_trait_columns", "fused". */
+GWAS_API int gwas_kernel_time(const gwas_ctx* ctx, const char* kernel, double* ms, int64_t* launches);
+GWAS_API void gwas_reset_timers(gwas_ctx* ctx);
 
 /* One-line description of the last failure on ctx (or of the last failed
  * gwas_setup when ctx is NULL).  Owned by the library. */

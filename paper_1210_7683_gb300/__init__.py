@@ -45,7 +45,7 @@ class GwasError(RuntimeError):
 
 class gwas_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("output", C.c_int), ("trait_block", C.c_int), ("device", C.c_int),
-                ("hbm_budget", C.c_size_t), ("stream", C.c_void_p)]
+                ("profile", C.c_int), ("hbm_budget", C.c_size_t), ("stream", C.c_void_p)]
 
 
 def _load():
@@ -69,6 +69,10 @@ def _load():
     lib.gwas_kernel_launches.restype = i64
     lib.gwas_last_error.argtypes = [vp]
     lib.gwas_last_error.restype = C.c_char_p
+    lib.gwas_kernel_time.argtypes = [vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(i64)]
+    lib.gwas_kernel_time.restype = ci
+    lib.gwas_reset_timers.argtypes = [vp]
+    lib.gwas_reset_timers.restype = None
     lib.gwas_destroy.argtypes = [vp]
     lib.gwas_destroy.restype = None
     return lib
@@ -166,6 +170,17 @@ def gwas_singular_count(ctx) -> int:
 
 def gwas_kernel_launches(ctx) -> int:
     return lib.gwas_kernel_launches(ctx)
+
+
+def gwas_kernel_time(ctx, kernel: str):
+    """(milliseconds, launches) of one kernel family (profiling contexts only)."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib.gwas_kernel_time(ctx, kernel.encode(), C.byref(ms), C.byref(n)), ctx)
+    return ms.value, n.value
+
+
+def gwas_reset_timers(ctx) -> None:
+    lib.gwas_reset_timers(ctx)
 
 
 def gwas_last_error(ctx=None) -> str:

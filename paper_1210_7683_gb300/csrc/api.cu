@@ -106,6 +106,57 @@ int ctx_upload(gwas_ctx* c, const void* src, size_t bytes, void* dst) {
   return GWAS_OK;
 }
 
+static cudaEvent_t pool_event(gwas_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(gwas_ctx* ctx, const char* name) : c(ctx), idx(SIZE_MAX) {
+  if (!c->profile) return;
+  ProfPending p{name, pool_event(c), pool_event(c)};
+  cudaEventRecord(p.start, c->stream);
+  idx = c->pending.size();
+  c->pending.push_back(p);
+}
+
+ProfScope::~ProfScope() {
+  if (idx != SIZE_MAX) cudaEventRecord(c->pending[idx].stop, c->stream);
+}
+
+void prof_flush(gwas_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.start, p.stop) == cudaSuccess) {
+      auto& e = c->prof[p.name];
+      e.first += ms;
+      e.second += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->event_pool.push_back(p.start);
+    c->event_pool.push_back(p.stop);
+  }
+  c->pending.clear();
+}
+
+extern "C" int gwas_kernel_time(const gwas_ctx* c, const char* kernel, double* ms, int64_t* launches) {
+  if (!c || !kernel) return GWAS_ERR_ARG;
+  auto it = c->prof.find(kernel);
+  if (ms) *ms = it == c->prof.end() ? 0.0 : it->second.first;
+  if (launches) *launches = it == c->prof.end() ? 0 : it->second.second;
+  return GWAS_OK;
+}
+
+extern "C" void gwas_reset_timers(gwas_ctx* c) {
+  if (c) c->prof.clear();
+}
+
 extern "C" void gwas_default_opts(gwas_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof *o);
@@ -119,7 +170,12 @@ static void destroy_impl(gwas_ctx* c) {
   bool have = cudaGetDevice(&dev) == cudaSuccess;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  prof_flush(c);
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  c->event_pool.clear();
   mixed_free(c);
+  delete c->mixed;
+  c->mixed = nullptr;
   for (auto& b : c->bufs) cudaFree(b.ptr);
   c->bufs.clear();
   if (c->solver) cusolverDnDestroy((cusolverDnHandle_t)c->solver);
@@ -177,6 +233,7 @@ extern "C" int gwas_setup(gwas_ctx** out, int n, int pm1, const double* phi, con
   gwas_ctx* c = new gwas_ctx;
   c->n = n; c->pm1 = pm1; c->p = pm1 + 1; c->t = t; c->device = o.device;
   c->precision = o.precision; c->output = o.output; c->trait_block = o.trait_block; c->budget = o.hbm_budget;
+  c->profile = o.profile != 0;
   int rc = GWAS_OK;
   auto fail = [&](int code) { g_setup_err = c->err; destroy_impl(c); return code; };
   if (o.stream) {
@@ -204,9 +261,11 @@ extern "C" int gwas_setup(gwas_ctx** out, int n, int pm1, const double* phi, con
   int* info = nullptr;
   if ((rc = ctx_alloc(c, sizeof(double) * std::max(lwork, 1), (void**)&work))) return fail(rc);
   if ((rc = ctx_alloc(c, sizeof(int), (void**)&info))) return fail(rc);
+  ProfScope* eig_scope = new ProfScope(c, "eigendecomposition");
   if (cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, c->Z, n, c->lam, work, lwork, info) !=
       CUSOLVER_STATUS_SUCCESS)
     return fail(ctx_fail(c, GWAS_ERR_CUDA, "syevd failed to launch"));
+  delete eig_scope;
   int hinfo = 0;
   c->h_lam.resize(n);
   if (!ctx_cuda_ok(c, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "info", &rc))
@@ -281,6 +340,7 @@ extern "C" int gwas_setup(gwas_ctx** out, int n, int pm1, const double* phi, con
   }
   if (!ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "setup", &rc)) return fail(rc);
   if (!ctx_cuda_ok(c, cudaGetLastError(), "setup kernels", &rc)) return fail(rc);
+  prof_flush(c);
   *out = c;
   return GWAS_OK;
 }
@@ -330,11 +390,12 @@ extern "C" int gwas_load_snps(gwas_ctx* c, int64_t m, const int8_t* XR) {
     if ((rc = ctx_alloc(c, sizeof(double) * m * c->n, (void**)&c->Xt)) == GWAS_OK)
       launch_rotate_fp64_i8(c, dX, m, c->n, c->Xt);
   } else {
-    rc = mixed_load(c, dX);
+    rc = mixed_load(c, dX, m);
   }
   if (rc == GWAS_OK) ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "load_snps", &rc);
   if (rc == GWAS_OK) ctx_cuda_ok(c, cudaGetLastError(), "load_snps kernels", &rc);
   if (!dev) ctx_free(c, dX);
+  if (rc == GWAS_OK) prof_flush(c);
   if (rc == GWAS_OK) c->m = m;
   return rc;
 }
@@ -429,6 +490,7 @@ extern "C" int gwas_solve(gwas_ctx* c, const double* Y, int64_t i0, int64_t i1, 
   if (rc == GWAS_OK) ctx_cuda_ok(c, cudaGetLastError(), "solve kernels", &rc);
   if (rc == GWAS_OK) ctx_cuda_ok(c, cudaMemcpyAsync(st, c->d_status, 16, cudaMemcpyDeviceToHost, c->stream), "status", &rc);
   if (rc == GWAS_OK) ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "solve", &rc);
+  if (rc == GWAS_OK) prof_flush(c);
   cleanup();
   if (rc) return rc;
   if (st[0]) return ctx_fail(c, GWAS_ERR_TIMEOUT, "a bounded wait inside the contraction kernel ran out");

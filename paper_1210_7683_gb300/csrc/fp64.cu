@@ -63,6 +63,7 @@ template <typename TA>
 void rotate(gwas_ctx* c, const TA* A, int64_t rows, int64_t lda, double* C) {
   if (rows <= 0) return;
   dim3 grid((unsigned)((rows + RT - 1) / RT), (c->n + RT - 1) / RT);
+  ProfScope ps(c, "rotate_fp64");
   rotate_fp64_kernel<TA><<<grid, 256, 0, c->stream>>>(A, rows, lda, c->Z, c->n, C);
   c->launches++;
 }
@@ -269,6 +270,7 @@ void launch_rotate_fp64_f64(gwas_ctx* c, const double* A, int64_t rows, int64_t 
 }
 
 void launch_prep_fp64(gwas_ctx* c, const double* Yt, int tb, const double* h2, double* R, double* consts) {
+  ProfScope ps(c, "prep_fp64");
   prep_fp64_kernel<<<tb, 256, 0, c->stream>>>(Yt, h2, c->lam, c->XLt, c->n, c->pm1, R, consts, consts_stride(c->pm1));
   c->launches++;
 }
@@ -287,6 +289,7 @@ void launch_fused_fp64(gwas_ctx* c, int64_t i0, int64_t i1, int j0, int tb, int6
   dim3 grid((unsigned)((i1 - i0 + FT_S - 1) / FT_S), (tb + FT_T - 1) / FT_T);
   unsigned long long* sing = c->d_status + 1;
   const int cst = consts_stride(c->pm1);
+  ProfScope ps(c, "fused_fp64");
 #define GWAS_FUSED_CASE(K)                                                                                      \
   case K:                                                                                                       \
     fused_fp64_kernel<K><<<grid, 256, 0, c->stream>>>(c->Xt, c->n, i0, i1, tb, R, consts, cst, full, ldo, ob, os, \

@@ -1,0 +1,39 @@
+// Fused contraction + Schur solve kernel (fused.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cstdint>
+
+struct gwas_ctx;
+
+// Per-trait FP32 constants of the epilogue (stride FUSED_CST):
+//   [0] scale of w, [1..3] scales of v'_1..3, [4] scale of e, [5] r^T M^-1 r,
+//   [6..8] g = S_TL^-1 b_T, [9..17] L^-T (row-major), used for the full coefficient vector.
+#define FUSED_CST 20
+
+struct FusedArgs {
+  int64_t row0;       // first SNP (row of G and of the x'_c^2 planes) of the range
+  int64_t i0;         // SNP index that maps to output column 0
+  int64_t nsnp;       // SNPs in the range
+  int n_stiles;       // ceil(nsnp / 128)
+  int n_ttiles;       // ceil(ntrait / 32)
+  int group;          // SNP tiles per traversal group (L2 reuse of the genotype tiles)
+  int ntrait;         // traits in this block
+  int Kpad;           // padded n (multiple of 64)
+  int64_t mpad;       // rows per plane of G and of the x'_c^2 planes
+  float dof;          // n - p
+  const float* sA;    // [m] scale of the x'_c^2 slices of each SNP (0 marks a singular SNP)
+  const float* acoef; // [m][3] centring coefficients a_i (full output only)
+  const float* cst;   // [ntrait][FUSED_CST]
+  int full_b;         // 1: double b[ntrait][ldo][4]; 0: float beta/se [ntrait][ldo]
+  int64_t ldo;        // output stride between traits (SNPs)
+  float* out_beta;
+  float* out_se;
+  double* out_b64;
+  unsigned long long* status;    // [0] <- 1 when a bounded wait expires
+  unsigned long long* singular;  // singular-pair counter
+  int max_ctas;       // 0 = one CTA per SM
+};
+
+int launch_fused(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
+                 const __nv_bfloat16* B1, const __nv_bfloat16* B2);

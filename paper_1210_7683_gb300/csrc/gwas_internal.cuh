@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -17,6 +18,12 @@ struct DevBuf {
 };
 
 struct MixedState;  // mixed-precision resident data (mixed.cu)
+
+// A kernel launch bracketed by two events on the context's stream (profiling mode).
+struct ProfPending {
+  const char* name;
+  cudaEvent_t start, stop;
+};
 
 struct gwas_ctx {
   int n = 0, pm1 = 0, p = 0, t = 0, device = 0;
@@ -47,7 +54,23 @@ struct gwas_ctx {
   unsigned long long* d_status = nullptr;
   int64_t singular = 0;
   int64_t launches = 0;
+
+  // profiling: per-kernel device time from CUDA events on `stream`
+  bool profile = false;
+  std::vector<ProfPending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::map<std::string, std::pair<double, int64_t>> prof;  // name -> (ms, launches)
 };
+
+// Brackets the kernel launches of its scope with events when profiling is on.
+struct ProfScope {
+  gwas_ctx* c;
+  size_t idx;
+  ProfScope(gwas_ctx* ctx, const char* name);
+  ~ProfScope();
+};
+// Resolves the pending events (call after the stream has been synchronised).
+void prof_flush(gwas_ctx* c);
 
 // ---------------------------------------------------------------- helpers (api.cu)
 int ctx_fail(gwas_ctx* c, int code, const std::string& msg);
@@ -70,7 +93,7 @@ void launch_fused_fp64(gwas_ctx* c, int64_t i0, int64_t i1, int j0, int tb, int6
 int consts_stride(int pm1);
 
 // ---------------------------------------------------------------- mixed path (mixed.cu)
-int mixed_load(gwas_ctx* c, const int8_t* dXR);                // genotypes already on the device
+int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m);  // genotypes already on the device
 int mixed_solve_block(gwas_ctx* c, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
                       void* dout);
 void mixed_free(gwas_ctx* c);

@@ -1,8 +1,589 @@
-// Mixed-precision path (tensor cores).  Placeholder until the tcgen05 kernels land.
-#include "gwas_internal.cuh"
+// Mixed-precision path of Algorithm 5: exact fixed-point slices of the operands on
+// the bf16 tensor cores (FP32 accumulation), FP64 for the eigendecomposition and
+// the per-trait algebra (S_TL, its Cholesky factor, g, the residual r_j).
+//
+// Resident data (per loaded genotype set):
+//   G   [mpad][Kpad] bf16  exact genotypes x_i
+//   A2  [3][mpad][Kpad] bf16  slices of x'_c^2, x'_c = Z^T P_c x_i (P_c: projector onto
+//                             the complement of span(X_L), applied through the B operand)
+//   sA  [m] float            per-SNP scale of the slices (0 for SNPs in span(X_L))
+//   acoef [m][p-1] float     a_i with P_c x_i = x_i - X_L a_i (full coefficient output)
+// Per gwas_solve trait block: Y' = Z^T Y and the back-rotated per-trait columns
+//   w_j = M_j^-1 r_j and v'_j = P_c M_j^-1 X_L L_j^-T, both by exact sliced GEMMs.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
 
-int mixed_load(gwas_ctx* c, const int8_t*) { return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "mixed path not built"); }
-int mixed_solve_block(gwas_ctx* c, const double*, int, int, int64_t, int64_t, int64_t, void*) {
-  return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "mixed path not built");
+#include "fused.cuh"
+#include "gwas_internal.cuh"
+#include "xgemm.cuh"
+
+struct MixedState {
+  int Kpad = 0, bits = 0, ldx = 0;
+  __nv_bfloat16 *Brot = nullptr, *Bzt = nullptr, *Bz = nullptr;  // B planes of the three rotations
+  double *sBrot = nullptr, *sBzt = nullptr, *sBz = nullptr;       // their row scales
+  double* XtXinv = nullptr;                                       // (X_L^T X_L)^-1 on the device
+  int64_t m = 0, mpad = 0;
+  __nv_bfloat16 *G = nullptr, *A2 = nullptr;
+  float *sA = nullptr, *acoef = nullptr;
+};
+
+namespace {
+
+constexpr int PM1 = 3;
+constexpr int TT = 32;
+constexpr int B1_ROWS = 10 * TT, B2_ROWS = 4 * TT;
+
+inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// Rows of the FP64 B operand of the genotype rotation: row k < n is P_c z_k (so that
+// (P_c Z)^T x = Z^T P_c x); row n + a holds the map x -> a_i[a] = ((X_L^T X_L)^-1 X_L^T x)[a].
+__global__ void rot_b_kernel(const double* __restrict__ Zc, const double* __restrict__ XL,
+                             const double* __restrict__ XtXinv, int n, double* __restrict__ out) {
+  const int k = blockIdx.x;
+  __shared__ double red[PM1][8];
+  __shared__ double coef[PM1];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (k < n) {
+    const double* z = Zc + (size_t)k * n;
+    double u[PM1] = {0, 0, 0};
+    for (int l = threadIdx.x; l < n; l += blockDim.x)
+      for (int a = 0; a < PM1; ++a) u[a] += XL[(size_t)a * n + l] * z[l];
+    for (int a = 0; a < PM1; ++a) {
+      double v = u[a];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[a][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < PM1) {
+      double s[PM1];
+      for (int a = 0; a < PM1; ++a) {
+        s[a] = 0;
+        for (int w = 0; w < (int)blockDim.x / 32; ++w) s[a] += red[a][w];
+      }
+      double cf = 0;
+      for (int b = 0; b < PM1; ++b) cf += XtXinv[threadIdx.x * PM1 + b] * s[b];
+      coef[threadIdx.x] = cf;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+      double v = z[l];
+      for (int a = 0; a < PM1; ++a) v -= XL[(size_t)a * n + l] * coef[a];
+      out[(size_t)k * n + l] = v;
+    }
+  } else {
+    const int a = k - n;
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+      double v = 0;
+      for (int b = 0; b < PM1; ++b) v += XtXinv[a * PM1 + b] * XL[(size_t)b * n + l];
+      out[(size_t)k * n + l] = v;
+    }
+  }
 }
-void mixed_free(gwas_ctx*) {}
+
+__global__ void transpose_kernel(const double* __restrict__ in, int n, double* __restrict__ out) {
+  __shared__ double t[32][33];
+  const int x = blockIdx.x * 32 + threadIdx.x, y0 = blockIdx.y * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y)
+    if (x < n && y0 + dy < n) t[dy][threadIdx.x] = in[(size_t)(y0 + dy) * n + x];
+  __syncthreads();
+  const int ox = y0 + threadIdx.x, oy0 = blockIdx.x * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y)
+    if (ox < n && oy0 + dy < n) out[(size_t)(oy0 + dy) * n + ox] = t[threadIdx.x][dy];
+}
+
+// int8 genotypes [m][n] -> bf16 [mpad][Kpad] (zero padded)
+__global__ void geno_bf16_kernel(const int8_t* __restrict__ X, int64_t m, int n, int64_t mpad, int Kpad,
+                                 __nv_bfloat16* __restrict__ G) {
+  const int64_t total = mpad * (int64_t)Kpad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / Kpad;
+    const int k = (int)(e % Kpad);
+    const float v = (i < m && k < n) ? (float)X[i * n + k] : 0.f;
+    G[e] = __float2bfloat16(v);
+  }
+}
+
+// One warp per SNP: slices of x'_c^2 (three 8-bit fixed-point slices, scale = max/256,
+// doubled while the level-0 partial sums could reach 2^24) and the centring coefficients.
+__global__ void a2_slice_kernel(const float* __restrict__ Xc, int ldx, const int8_t* __restrict__ X, int64_t row0,
+                                int64_t rows, int n, int64_t mpad, int Kpad, __nv_bfloat16* __restrict__ A2,
+                                float* __restrict__ sA, float* __restrict__ acoef) {
+  const int warps = blockDim.x / 32;
+  const int64_t r = blockIdx.x * (int64_t)warps + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (r >= rows) return;
+  const int64_t i = row0 + r;
+  const float* x = Xc + r * ldx;
+  float mx = 0.f, nc = 0.f, nx = 0.f;
+  for (int k = lane; k < n; k += 32) {
+    const float v = x[k];
+    mx = fmaxf(mx, v * v);
+    nc = fmaf(v, v, nc);
+    const float g = (float)X[i * n + k];
+    nx = fmaf(g, g, nx);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    nc += __shfl_xor_sync(0xffffffffu, nc, o);
+    nx += __shfl_xor_sync(0xffffffffu, nx, o);
+  }
+  // a SNP (numerically) inside span(X_L) has no Schur complement: flag it with scale 0
+  const bool singular = !(nc > 1e-9f * fmaxf(nx, 1.f)) || !(mx > 0.f);
+  float s = singular ? 1.f : mx / 256.f;
+  // keep sum_k q0_k * 256 <= 2^24 so that level-0 products are exact
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    float sum = 0.f;
+    const float inv = 1.f / s;
+    for (int k = lane; k < n; k += 32) sum += rintf(x[k] * x[k] * inv);
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (sum <= 65536.f) break;
+    s *= 2.f;
+  }
+  const float inv = 1.f / s;
+  for (int k = lane; k < Kpad; k += 32) {
+    float q0 = 0.f, q1 = 0.f, q2 = 0.f;
+    if (k < n && !singular) {
+      const float t = x[k] * x[k] * inv;
+      q0 = rintf(t);
+      const float r1 = (t - q0) * 256.f;
+      q1 = rintf(r1);
+      q2 = rintf((r1 - q1) * 256.f);
+    }
+    A2[(0 * mpad + i) * Kpad + k] = __float2bfloat16(q0);
+    A2[(1 * mpad + i) * Kpad + k] = __float2bfloat16(q1);
+    A2[(2 * mpad + i) * Kpad + k] = __float2bfloat16(q2 * (1.f / 256.f));
+  }
+  if (lane == 0) sA[i] = singular ? 0.f : s;
+  if (lane < PM1) acoef[i * PM1 + lane] = x[n + lane];
+}
+
+// Per-trait FP64 algebra (Algorithm 5, per-trait lines) with e_j = diag(D_j^-1):
+//   S_TL = X'_L^T diag(e) X'_L, b_T = X'_L^T (e . y'), L L^T = S_TL, g = S_TL^-1 b_T,
+//   r' = y' - X'_L g,  rr = r'^T diag(e) r',
+//   rows of Wt: [e . r' | (e . X'_L) L^-T]  (rotated basis; back-rotated by Z later),
+//   slices of e in the C2 operand layout [E2s | E1 | E2 | E3s].
+__global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restrict__ Yt, int ldy,
+                                                         const double* __restrict__ h2, const double* __restrict__ lam,
+                                                         const double* __restrict__ XLt, int n, int Kpad,
+                                                         double* __restrict__ Wt, __nv_bfloat16* __restrict__ B2,
+                                                         float* __restrict__ cst) {
+  const int j = blockIdx.x;
+  const double h = h2[j];
+  const double* y = Yt + (size_t)j * ldy;
+  __shared__ double red[8][PM1 * PM1 + PM1 + 1];
+  __shared__ double sh_g[PM1], sh_Lit[PM1 * PM1], sh_se;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  double part[PM1 * PM1 + PM1 + 1];
+  for (int q = 0; q < PM1 * PM1 + PM1 + 1; ++q) part[q] = 0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double e = 1.0 / (h * lam[k] + (1.0 - h));
+    double xl[PM1];
+    for (int a = 0; a < PM1; ++a) xl[a] = XLt[(size_t)a * n + k];
+    for (int a = 0; a < PM1; ++a) {
+      for (int b = 0; b < PM1; ++b) part[a * PM1 + b] += e * xl[a] * xl[b];
+      part[PM1 * PM1 + a] += e * xl[a] * y[k];
+    }
+    part[PM1 * PM1 + PM1] = fmax(part[PM1 * PM1 + PM1], e);
+  }
+  for (int q = 0; q < PM1 * PM1 + PM1 + 1; ++q) {
+    double v = part[q];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = (q == PM1 * PM1 + PM1) ? fmax(v, w) : v + w;
+    }
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S[PM1][PM1], bT[PM1], emax = 0;
+    for (int a = 0; a < PM1; ++a) {
+      for (int b = 0; b < PM1; ++b) {
+        double v = 0;
+        for (int w = 0; w < nw; ++w) v += red[w][a * PM1 + b];
+        S[a][b] = v;
+      }
+      double v = 0;
+      for (int w = 0; w < nw; ++w) v += red[w][PM1 * PM1 + a];
+      bT[a] = v;
+    }
+    for (int w = 0; w < nw; ++w) emax = fmax(emax, red[w][PM1 * PM1 + PM1]);
+    double L[PM1][PM1] = {};
+    for (int a = 0; a < PM1; ++a)
+      for (int b = 0; b <= a; ++b) {
+        double v = S[a][b];
+        for (int k = 0; k < b; ++k) v -= L[a][k] * L[b][k];
+        L[a][b] = (a == b) ? sqrt(fmax(v, 1e-300)) : v / L[b][b];
+      }
+    // Linv = L^-1 (lower)
+    double Li[PM1][PM1] = {};
+    for (int c = 0; c < PM1; ++c)
+      for (int a = 0; a < PM1; ++a) {
+        double v = (a == c) ? 1.0 : 0.0;
+        for (int k = 0; k < a; ++k) v -= L[a][k] * Li[k][c];
+        Li[a][c] = v / L[a][a];
+      }
+    // g = L^-T L^-1 b_T
+    double zt[PM1];
+    for (int a = 0; a < PM1; ++a) {
+      double v = 0;
+      for (int k = 0; k <= a; ++k) v += Li[a][k] * bT[k];
+      zt[a] = v;
+    }
+    for (int a = 0; a < PM1; ++a) {
+      double v = 0;
+      for (int k = a; k < PM1; ++k) v += Li[k][a] * zt[k];
+      sh_g[a] = v;
+    }
+    for (int a = 0; a < PM1; ++a)
+      for (int c = 0; c < PM1; ++c) sh_Lit[a * PM1 + c] = Li[c][a];  // (L^-T)[a][c]
+    sh_se = emax / 256.0;
+  }
+  __syncthreads();
+  const double se = sh_se, inv_se = 1.0 / se;
+  double rr = 0;
+  const int p = PM1 + 1;
+  const int tile = j / TT, jj = j % TT;
+  __nv_bfloat16* b2 = B2 + (size_t)tile * B2_ROWS * Kpad;
+  for (int k = threadIdx.x; k < Kpad; k += blockDim.x) {
+    double w = 0, v[PM1] = {0, 0, 0};
+    float q0 = 0, q1 = 0, q2 = 0;
+    if (k < n) {
+      const double e = 1.0 / (h * lam[k] + (1.0 - h));
+      double xl[PM1];
+      for (int a = 0; a < PM1; ++a) xl[a] = XLt[(size_t)a * n + k];
+      double r = y[k];
+      for (int a = 0; a < PM1; ++a) r -= xl[a] * sh_g[a];
+      w = e * r;
+      rr += e * r * r;
+      for (int c = 0; c < PM1; ++c) {
+        double t = 0;
+        for (int a = 0; a < PM1; ++a) t += xl[a] * sh_Lit[a * PM1 + c];
+        v[c] = e * t;
+      }
+      const double t = e * inv_se;
+      const double d0 = rint(t);
+      const double r1 = (t - d0) * 256.0;
+      const double d1 = rint(r1);
+      q0 = (float)d0;
+      q1 = (float)d1;
+      q2 = (float)rint((r1 - d1) * 256.0);
+    }
+    Wt[((size_t)j * p + 0) * Kpad + k] = w;
+    for (int c = 0; c < PM1; ++c) Wt[((size_t)j * p + 1 + c) * Kpad + k] = v[c];
+    b2[(size_t)(0 * TT + jj) * Kpad + k] = __float2bfloat16(q1 * (1.f / 256.f));
+    b2[(size_t)(1 * TT + jj) * Kpad + k] = __float2bfloat16(q0);
+    b2[(size_t)(2 * TT + jj) * Kpad + k] = __float2bfloat16(q1);
+    b2[(size_t)(3 * TT + jj) * Kpad + k] = __float2bfloat16(q2 * (1.f / 256.f));
+  }
+  for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+  __syncthreads();
+  if (lane == 0) red[warp][0] = rr;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0;
+    for (int w = 0; w < nw; ++w) v += red[w][0];
+    float* cj = cst + (size_t)j * FUSED_CST;
+    cj[4] = (float)se;
+    cj[5] = (float)v;
+    for (int a = 0; a < PM1; ++a) cj[6 + a] = (float)sh_g[a];
+    for (int q = 0; q < PM1 * PM1; ++q) cj[9 + q] = (float)sh_Lit[q];
+  }
+}
+
+// Per trait: project the back-rotated columns [w | v_1..3] with P_c and write their
+// fixed-point slices in the C1 operand layout (w: 4 slices, v: 2 slices).
+__global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__ W, const double* __restrict__ XL,
+                                                      const double* __restrict__ XtXinv, int n, int Kpad,
+                                                      __nv_bfloat16* __restrict__ B1, float* __restrict__ cst) {
+  const int j = blockIdx.x;
+  const int p = PM1 + 1;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  __shared__ double red[8][PM1 + 1];
+  __shared__ double coef[PM1], smax;
+  const int tile = j / TT, jj = j % TT;
+  __nv_bfloat16* b1 = B1 + (size_t)tile * B1_ROWS * Kpad;
+  for (int c = 0; c < p; ++c) {
+    const double* col = W + ((size_t)j * p + c) * Kpad;
+    double u[PM1] = {0, 0, 0};
+    for (int l = threadIdx.x; l < n; l += blockDim.x)
+      for (int a = 0; a < PM1; ++a) u[a] += XL[(size_t)a * n + l] * col[l];
+    for (int a = 0; a < PM1; ++a) {
+      double v = u[a];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][a] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < PM1) {
+      double s[PM1];
+      for (int a = 0; a < PM1; ++a) {
+        s[a] = 0;
+        for (int w = 0; w < nw; ++w) s[a] += red[w][a];
+      }
+      double cf = 0;
+      for (int b = 0; b < PM1; ++b) cf += XtXinv[threadIdx.x * PM1 + b] * s[b];
+      coef[threadIdx.x] = cf;
+    }
+    __syncthreads();
+    double mx = 0;
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+      double v = col[l];
+      for (int a = 0; a < PM1; ++a) v -= XL[(size_t)a * n + l] * coef[a];
+      mx = fmax(mx, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp][PM1] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = 0;
+      for (int w = 0; w < nw; ++w) v = fmax(v, red[w][PM1]);
+      smax = v > 0 ? v / 256.0 : 1.0;
+      cst[(size_t)j * FUSED_CST + (c == 0 ? 0 : c)] = (float)smax;
+    }
+    __syncthreads();
+    const double inv = 1.0 / smax;
+    const int nsl = c == 0 ? 4 : 2;
+    for (int l = threadIdx.x; l < Kpad; l += blockDim.x) {
+      double t = 0;
+      if (l < n) {
+        t = col[l];
+        for (int a = 0; a < PM1; ++a) t -= XL[(size_t)a * n + l] * coef[a];
+        t *= inv;
+      }
+      for (int s = 0; s < nsl; ++s) {
+        const double q = rint(t);
+        int row;
+        if (s < 2) row = s * 128 + c * TT + jj;
+        else row = (s == 2 ? 256 : 288) + jj;
+        b1[(size_t)row * Kpad + l] = __float2bfloat16((float)q);
+        t = (t - q) * 256.0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+void mixed_free(gwas_ctx* c) {
+  MixedState* s = c->mixed;
+  if (!s) return;
+  ctx_free(c, s->G);
+  ctx_free(c, s->A2);
+  ctx_free(c, s->sA);
+  ctx_free(c, s->acoef);
+  s->G = s->A2 = nullptr;
+  s->sA = s->acoef = nullptr;
+  s->m = s->mpad = 0;
+}
+
+static void mixed_destroy_setup(gwas_ctx* c) {
+  MixedState* s = c->mixed;
+  if (!s) return;
+  ctx_free(c, s->Brot); ctx_free(c, s->Bzt); ctx_free(c, s->Bz);
+  ctx_free(c, s->sBrot); ctx_free(c, s->sBzt); ctx_free(c, s->sBz);
+  ctx_free(c, s->XtXinv);
+}
+
+// One-time preparation of the B operands of the three rotations.
+static int mixed_setup(gwas_ctx* c) {
+  if (c->mixed && c->mixed->Brot) return GWAS_OK;
+  if (c->pm1 != PM1) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "mixed path needs p-1 = 3");
+  if (!c->mixed) c->mixed = new MixedState;
+  MixedState* s = c->mixed;
+  const int n = c->n;
+  s->Kpad = (int)rup(n, 64);
+  s->bits = xgemm_bits(s->Kpad);
+  s->ldx = (int)rup(n + PM1, 64);
+  int rc;
+  double *rot = nullptr, *zr = nullptr;
+  const size_t plane_rows_rot = (size_t)s->ldx, plane_rows_z = (size_t)s->Kpad;
+  if ((rc = ctx_alloc(c, sizeof(double) * PM1 * PM1, (void**)&s->XtXinv)) ||
+      (rc = ctx_alloc(c, sizeof(double) * (size_t)(n + PM1) * n, (void**)&rot)) ||
+      (rc = ctx_alloc(c, sizeof(double) * (size_t)n * n, (void**)&zr)) ||
+      (rc = ctx_alloc(c, 2ull * 4 * plane_rows_rot * s->Kpad, (void**)&s->Brot)) ||
+      (rc = ctx_alloc(c, 2ull * 4 * plane_rows_z * s->Kpad, (void**)&s->Bzt)) ||
+      (rc = ctx_alloc(c, 2ull * 4 * plane_rows_z * s->Kpad, (void**)&s->Bz)) ||
+      (rc = ctx_alloc(c, sizeof(double) * plane_rows_rot, (void**)&s->sBrot)) ||
+      (rc = ctx_alloc(c, sizeof(double) * plane_rows_z, (void**)&s->sBzt)) ||
+      (rc = ctx_alloc(c, sizeof(double) * plane_rows_z, (void**)&s->sBz))) {
+    ctx_free(c, rot);
+    ctx_free(c, zr);
+    mixed_destroy_setup(c);
+    return rc;
+  }
+  cudaMemcpyAsync(s->XtXinv, c->h_XtXinv.data(), sizeof(double) * PM1 * PM1, cudaMemcpyHostToDevice, c->stream);
+  { ProfScope ps(c, "setup_rotation_operands");
+  rot_b_kernel<<<n + PM1, 256, 0, c->stream>>>(c->Z, c->XL, s->XtXinv, n, rot);
+  c->launches++;
+  dim3 tb(32, 8), tg((n + 31) / 32, (n + 31) / 32);
+  transpose_kernel<<<tg, tb, 0, c->stream>>>(c->Z, n, zr);
+  c->launches++; }
+  launch_slice_rows(c, rot, n, n + PM1, n, s->ldx, s->Kpad, 4, s->bits, s->Brot, s->sBrot);
+  launch_slice_rows(c, c->Z, n, n, n, s->Kpad, s->Kpad, 4, s->bits, s->Bzt, s->sBzt);
+  launch_slice_rows(c, zr, n, n, n, s->Kpad, s->Kpad, 4, s->bits, s->Bz, s->sBz);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  ctx_free(c, rot);
+  ctx_free(c, zr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(c, GWAS_ERR_CUDA, std::string("mixed setup: ") + cudaGetErrorString(e));
+  }
+  return GWAS_OK;
+}
+
+int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m) {
+  int rc = mixed_setup(c);
+  if (rc) return rc;
+  MixedState* s = c->mixed;
+  const int n = c->n;
+  s->mpad = rup(m, 128);
+  if ((rc = ctx_alloc(c, 2ull * s->mpad * s->Kpad, (void**)&s->G)) ||
+      (rc = ctx_alloc(c, 2ull * 3 * s->mpad * s->Kpad, (void**)&s->A2)) ||
+      (rc = ctx_alloc(c, sizeof(float) * m, (void**)&s->sA)) ||
+      (rc = ctx_alloc(c, sizeof(float) * m * PM1, (void**)&s->acoef))) {
+    mixed_free(c);
+    return rc;
+  }
+  { ProfScope ps(c, "genotypes_bf16");
+  geno_bf16_kernel<<<4 * 152, 256, 0, c->stream>>>(dXR, m, n, s->mpad, s->Kpad, s->G);
+  c->launches++; }
+  // rotate in chunks of SNPs to bound the FP32 scratch
+  const int64_t chunk = std::min<int64_t>(s->mpad, 1 << 18);
+  float* Xc = nullptr;
+  if ((rc = ctx_alloc(c, sizeof(float) * chunk * s->ldx, (void**)&Xc))) {
+    mixed_free(c);
+    return rc;
+  }
+  for (int64_t r0 = 0; r0 < m && rc == GWAS_OK; r0 += chunk) {
+    const int64_t rows = std::min<int64_t>(chunk, m - r0);
+    XgemmArgs g{};
+    g.rows = (int)rows;
+    g.cols = n + PM1;
+    g.rowsA_pad = (int)rup(rows, 128);
+    g.rowsB_pad = s->ldx;
+    g.Kpad = s->Kpad;
+    g.level_scale = std::ldexp(1.0, -s->bits);
+    g.scaleA = nullptr;
+    g.scaleB = s->sBrot;
+    g.out32 = Xc;
+    g.ldo = s->ldx;
+    g.status = c->d_status;
+    g.name = "xgemm_rotate_snps";
+    // x'_c = (P_c Z)^T x  (Algorithm 5, X'_R := Z^T X_R, on the centred SNPs)
+    rc = launch_xgemm(c, 1, 4, 3, g, s->G + r0 * s->Kpad, s->Brot);
+    if (rc == GWAS_OK) {
+      const int warps = 8;
+      ProfScope ps(c, "slice_snp_squares");
+      a2_slice_kernel<<<(unsigned)((rows + warps - 1) / warps), warps * 32, 0, c->stream>>>(
+          Xc, s->ldx, dXR, r0, rows, n, s->mpad, s->Kpad, s->A2, s->sA, s->acoef);
+      c->launches++;
+    }
+  }
+  cudaStreamSynchronize(c->stream);
+  ctx_free(c, Xc);
+  if (rc) {
+    mixed_free(c);
+    return rc;
+  }
+  s->m = m;
+  return GWAS_OK;
+}
+
+int mixed_solve_block(gwas_ctx* c, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo, void* out) {
+  MixedState* s = c->mixed;
+  if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
+  const int n = c->n, p = PM1 + 1, Kpad = s->Kpad;
+  const int nt_tiles = (tb + TT - 1) / TT;
+  const int tb_pad = nt_tiles * TT;
+  const int rowsY = (int)rup(tb, 128), rowsW = (int)rup((int64_t)tb * p, 128);
+  int rc = GWAS_OK;
+  std::vector<void*> tmp;
+  auto alloc = [&](size_t b, void** q) {
+    int r = ctx_alloc(c, b, q);
+    if (r == GWAS_OK) tmp.push_back(*q);
+    return r;
+  };
+  __nv_bfloat16 *Ysl = nullptr, *Wsl = nullptr, *B1 = nullptr, *B2 = nullptr;
+  double *sY = nullptr, *Yt = nullptr, *Wt = nullptr, *sW = nullptr;
+  float* cst = nullptr;
+  if ((rc = alloc(2ull * 4 * rowsY * Kpad, (void**)&Ysl)) || (rc = alloc(sizeof(double) * rowsY, (void**)&sY)) ||
+      (rc = alloc(sizeof(double) * (size_t)tb * Kpad, (void**)&Yt)) ||
+      (rc = alloc(sizeof(double) * (size_t)tb * p * Kpad, (void**)&Wt)) ||
+      (rc = alloc(2ull * 4 * rowsW * Kpad, (void**)&Wsl)) || (rc = alloc(sizeof(double) * rowsW, (void**)&sW)) ||
+      (rc = alloc(2ull * (size_t)nt_tiles * B1_ROWS * Kpad, (void**)&B1)) ||
+      (rc = alloc(2ull * (size_t)nt_tiles * B2_ROWS * Kpad, (void**)&B2)) ||
+      (rc = alloc(sizeof(float) * (size_t)tb_pad * FUSED_CST, (void**)&cst))) {
+    for (void* q : tmp) ctx_free(c, q);
+    return rc;
+  }
+  cudaMemsetAsync(B1, 0, 2ull * nt_tiles * B1_ROWS * Kpad, c->stream);
+  cudaMemsetAsync(B2, 0, 2ull * nt_tiles * B2_ROWS * Kpad, c->stream);
+  // Y' := Z^T Y (Algorithm 5, gemm) as an exact sliced GEMM
+  launch_slice_rows(c, dY, n, tb, n, rowsY, Kpad, 4, s->bits, Ysl, sY);
+  XgemmArgs g{};
+  g.rows = tb;
+  g.cols = n;
+  g.rowsA_pad = rowsY;
+  g.rowsB_pad = Kpad;
+  g.Kpad = Kpad;
+  g.level_scale = std::ldexp(1.0, -s->bits);
+  g.scaleA = sY;
+  g.scaleB = s->sBzt;
+  g.out64 = Yt;
+  g.ldo = Kpad;
+  g.status = c->d_status;
+  g.name = "xgemm_rotate_traits";
+  if ((rc = launch_xgemm(c, 4, 4, 3, g, Ysl, s->Bzt)) == GWAS_OK) {
+    // per-trait algebra and the C2 operand
+    ProfScope ps(c, "prep_traits");
+    prep_mixed_kernel<<<tb, 256, 0, c->stream>>>(Yt, Kpad, c->h2 + j0, c->lam, c->XLt, n, Kpad, Wt, B2, cst);
+    c->launches++;
+    // back-rotation [w | v] = Z [e.r' | (e.X'_L) L^-T]
+    launch_slice_rows(c, Wt, Kpad, tb * p, n, rowsW, Kpad, 4, s->bits, Wsl, sW);
+    XgemmArgs b = g;
+    b.rows = tb * p;
+    b.cols = n;
+    b.rowsA_pad = rowsW;
+    b.scaleA = sW;
+    b.scaleB = s->sBz;
+    b.out64 = Wt;
+    b.name = "xgemm_back_rotate";
+    rc = launch_xgemm(c, 4, 4, 3, b, Wsl, s->Bz);
+  }
+  if (rc == GWAS_OK) {
+    { ProfScope ps(c, "pack_trait_columns");
+    pack_c1_kernel<<<tb, 256, 0, c->stream>>>(Wt, c->XL, s->XtXinv, n, Kpad, B1, cst);
+    c->launches++; }
+    FusedArgs a{};
+    a.row0 = i0;
+    a.i0 = i0;
+    a.nsnp = i1 - i0;
+    a.n_stiles = (int)((a.nsnp + 127) / 128);
+    a.n_ttiles = nt_tiles;
+    a.group = 64;
+    a.ntrait = tb;
+    a.Kpad = Kpad;
+    a.mpad = s->mpad;
+    a.dof = (float)(n - p);
+    a.sA = s->sA;
+    a.acoef = s->acoef;
+    a.cst = cst;
+    a.full_b = c->output == GWAS_OUT_FULL_B;
+    a.ldo = ldo;
+    if (a.full_b) {
+      a.out_b64 = (double*)out;
+    } else {
+      void** pr = (void**)out;
+      a.out_beta = (float*)pr[0];
+      a.out_se = (float*)pr[1];
+    }
+    a.status = c->d_status;
+    a.singular = c->d_status + 1;
+    rc = launch_fused(c, a, s->G, s->A2, B1, B2);
+  }
+  cudaStreamSynchronize(c->stream);
+  for (void* q : tmp) ctx_free(c, q);
+  return rc;
+}

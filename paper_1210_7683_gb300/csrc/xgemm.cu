@@ -1,0 +1,229 @@
+// Exact sliced GEMM on the tensor cores (the error-free splitting of Ozaki, Ogita,
+// Oishi and Rump, "Error-free transformations of matrix multiplication by using
+// fast routines of matrix multiplication", 2012, in fixed-point form).
+//
+// Each operand row is written as  x = s * sum_a q_a 2^(-bits*a)  with integer
+// slices |q_a| <= 2^bits (exact in bf16) and a per-row scale s.  The product
+// C = A B^T is assembled from the slice products A_a B_b^T with a + b <= L; all
+// products of one level a + b share a TMEM accumulator.  Level 0 is a single
+// product whose partial sums stay below 2^24 (2*bits + log2(K) <= 24), so it is
+// exact in FP32 whatever the accumulation order; the higher levels are 2^-bits
+// smaller and their FP32 rounding is negligible.  The epilogue combines the
+// levels and the scales in FP64.
+//
+// Used for the rotations by Z of Algorithm 5 (X'_R := Z^T X_R with exact int8
+// genotypes as A, and Y' := Z^T Y) and for the back-rotation Z W' of the
+// per-trait operands.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "gwas_internal.cuh"
+#include "tc.cuh"
+#include "xgemm.cuh"
+
+namespace {
+
+constexpr int BM = 128, BN = 64, BK = 64;
+
+template <int SA, int SB, int L>
+struct XCfg {
+  static constexpr int A_BYTES = BM * BK * 2;            // one slice plane tile
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE = SA * A_BYTES + SB * B_BYTES;
+  static constexpr int STAGES = (200 * 1024) / STAGE >= 4 ? 4 : (200 * 1024) / STAGE;
+  static constexpr int TMEM_COLS = (L + 1) * BN <= 128 ? 128 : ((L + 1) * BN <= 256 ? 256 : 512);
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+};
+
+template <int SA, int SB, int L>
+__global__ void __launch_bounds__(192, 1) xgemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                       const __grid_constant__ CUtensorMap mapB, XgemmArgs g) {
+  using Cfg = XCfg<SA, SB, L>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + Cfg::STAGES * Cfg::STAGE);
+  uint64_t* empty = full + Cfg::STAGES;
+  uint64_t* done = empty + Cfg::STAGES;
+  uint32_t* tslot = (uint32_t*)(done + 1);
+  volatile int* abort = (volatile int*)(tslot + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;
+  const int nk = g.Kpad / BK;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Cfg::STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(done, 1);
+    *abort = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) tc::tmem_alloc(tslot, Cfg::TMEM_COLS);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_map(&mapA);
+    tc::prefetch_map(&mapB);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % Cfg::STAGES;
+      if (kb >= Cfg::STAGES && !tc::mbar_wait(&empty[s], ((kb / Cfg::STAGES) - 1) & 1, g.status, abort)) break;
+      uint8_t* st = smem + s * Cfg::STAGE;
+      tc::mbar_expect_tx(&full[s], Cfg::STAGE);
+#pragma unroll
+      for (int a = 0; a < SA; ++a) tc::tma_load_2d(st + a * Cfg::A_BYTES, &mapA, &full[s], kb * BK, a * g.rowsA_pad + r0);
+#pragma unroll
+      for (int b = 0; b < SB; ++b)
+        tc::tma_load_2d(st + SA * Cfg::A_BYTES + b * Cfg::B_BYTES, &mapB, &full[s], kb * BK, b * g.rowsB_pad + c0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = tc::idesc_bf16(BM, BN);
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int s = kb % Cfg::STAGES;
+      if (!tc::mbar_wait(&full[s], (kb / Cfg::STAGES) & 1, g.status, abort)) { ok = false; break; }
+      tc::fence_after();
+      uint8_t* st = smem + s * Cfg::STAGE;
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k) {
+        bool first[L + 1];
+#pragma unroll
+        for (int l = 0; l <= L; ++l) first[l] = (kb == 0 && k == 0);
+#pragma unroll
+        for (int a = 0; a < SA; ++a)
+#pragma unroll
+          for (int b = 0; b < SB; ++b) {
+            if (a + b > L) continue;
+            const uint64_t ad = tc::sdesc_add(tc::sdesc_sw128(st + a * Cfg::A_BYTES), k * 32);
+            const uint64_t bd = tc::sdesc_add(tc::sdesc_sw128(st + SA * Cfg::A_BYTES + b * Cfg::B_BYTES), k * 32);
+            tc::mma_bf16(tbase + (a + b) * BN, ad, bd, idesc, first[a + b] ? 0u : 1u);
+            first[a + b] = false;
+          }
+      }
+      tc::mma_commit(&empty[s]);
+    }
+    tc::mma_commit(done);
+  } else if (warp >= 2) {
+    const int q = warp % 4;
+    const bool ok = tc::mbar_wait(done, 0, g.status, abort);
+    tc::fence_after();
+    const int r = r0 + q * 32 + lane;
+    const double sa = (ok && r < g.rows) ? (g.scaleA ? g.scaleA[r] : 1.0) : 0.0;
+    for (int cc = 0; cc < BN; cc += 8) {
+      uint32_t v[L + 1][8];
+#pragma unroll
+      for (int l = 0; l <= L; ++l) tc::tmem_ld8(tbase + ((uint32_t)(q * 32) << 16) + l * BN + cc, v[l]);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int l = 0; l <= L; ++l) tc::reg_fence(v[l]);
+      if (!ok || r >= g.rows) continue;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = c0 + cc + j;
+        if (c >= g.cols) break;
+        double acc = (double)__uint_as_float(v[L][j]);
+#pragma unroll
+        for (int l = L - 1; l >= 0; --l) acc = fma(acc, g.level_scale, (double)__uint_as_float(v[l][j]));
+        const double val = acc * sa * g.scaleB[c];
+        if (g.out64) g.out64[(size_t)r * g.ldo + c] = val;
+        else g.out32[(size_t)r * g.ldo + c] = (float)val;
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tbase, Cfg::TMEM_COLS);
+}
+
+// ------------------------------------------------------------------ row slicing
+// Slices of each row of a FP64 matrix (row r at src + r*lds, K valid entries) into
+// S bf16 planes [S][rows_pad][Kpad]: x = scale * sum_a q_a 2^(-bits a), scale =
+// max|x| / 2^bits, q_0 in [-2^bits, 2^bits], later |q_a| <= 2^(bits-1).
+__global__ void slice_rows_kernel(const double* __restrict__ src, int64_t lds, int rows, int K, int rows_pad, int Kpad,
+                                  int S, int bits, __nv_bfloat16* __restrict__ planes, double* __restrict__ scale) {
+  const int warps = blockDim.x / 32;
+  const int r = blockIdx.x * warps + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (r >= rows_pad) return;
+  const double two = ldexp(1.0, bits);
+  double mx = 0;
+  if (r < rows)
+    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(src[(size_t)r * lds + k]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const double s = mx > 0 ? mx / two : 1.0;
+  const double inv = 1.0 / s;
+  if (lane == 0 && r < rows) scale[r] = s;
+  for (int k = lane; k < Kpad; k += 32) {
+    double x = (r < rows && k < K) ? src[(size_t)r * lds + k] * inv : 0.0;
+    for (int a = 0; a < S; ++a) {
+      const double q = rint(x);
+      planes[((size_t)a * rows_pad + r) * Kpad + k] = __double2bfloat16(q);
+      x = (x - q) * two;
+    }
+  }
+}
+
+}  // namespace
+
+bool make_bf16_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+  typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn enc = nullptr;
+  if (!enc) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    enc = (EncodeFn)fn;
+  }
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * 2};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void launch_slice_rows(gwas_ctx* c, const double* src, int64_t lds, int rows, int K, int rows_pad, int Kpad, int S,
+                       int bits, __nv_bfloat16* planes, double* scale) {
+  const int warps = 8;
+  ProfScope ps(c, "slice_rows");
+  slice_rows_kernel<<<(rows_pad + warps - 1) / warps, warps * 32, 0, c->stream>>>(src, lds, rows, K, rows_pad, Kpad, S,
+                                                                                  bits, planes, scale);
+  c->launches++;
+}
+
+template <int SA, int SB, int L>
+static int run_xgemm(gwas_ctx* c, const XgemmArgs& g, const __nv_bfloat16* A, const __nv_bfloat16* B) {
+  using Cfg = XCfg<SA, SB, L>;
+  CUtensorMap ma, mb;
+  if (!make_bf16_map(&ma, A, (uint64_t)SA * g.rowsA_pad, g.Kpad, BM) ||
+      !make_bf16_map(&mb, B, (uint64_t)SB * g.rowsB_pad, g.Kpad, BN))
+    return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(xgemm_kernel<SA, SB, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    attr = true;
+  }
+  dim3 grid(g.rowsA_pad / BM, g.rowsB_pad / BN);
+  ProfScope ps(c, g.name ? g.name : "xgemm");
+  xgemm_kernel<SA, SB, L><<<grid, 192, Cfg::SMEM, c->stream>>>(ma, mb, g);
+  c->launches++;
+  return GWAS_OK;
+}
+
+int launch_xgemm(gwas_ctx* c, int SA, int SB, int L, const XgemmArgs& g, const __nv_bfloat16* A,
+                 const __nv_bfloat16* B) {
+  if (g.rowsA_pad % BM || g.rowsB_pad % BN || g.Kpad % BK)
+    return ctx_fail(c, GWAS_ERR_ARG, "xgemm: padded sizes are not tile multiples");
+  if (SA == 4 && SB == 4 && L == 3) return run_xgemm<4, 4, 3>(c, g, A, B);
+  if (SA == 1 && SB == 4 && L == 3) return run_xgemm<1, 4, 3>(c, g, A, B);
+  return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "xgemm: slice configuration not instantiated");
+}

@@ -1,0 +1,35 @@
+// Exact sliced GEMM (see xgemm.cu): C[r][c] = sA[r] sB[c] sum_l 2^(-bits l) sum_{a+b=l} A_a[r] . B_b[c].
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cstdint>
+
+struct gwas_ctx;
+
+struct XgemmArgs {
+  int rows, cols;            // valid output rows (A rows) and columns (B rows)
+  int rowsA_pad, rowsB_pad;  // plane row counts (multiples of 128 and 64)
+  int Kpad;                  // K extent of the planes (multiple of 64), zero beyond the valid K
+  double level_scale;        // 2^-bits
+  const double* scaleA;      // per-row scale of A (NULL = 1)
+  const double* scaleB;      // per-row scale of B
+  double* out64;             // FP64 output (or NULL)
+  float* out32;              // FP32 output when out64 is NULL
+  int64_t ldo;               // output row stride (elements)
+  unsigned long long* status;  // status[0] <- 1 when a bounded wait expires
+  const char* name;          // timer name in profiling mode
+};
+
+// Bits per slice for which the level-0 product of two slices is exact in FP32
+// over a K extent of Kpad: 2 * bits + log2(Kpad) <= 24.
+inline int xgemm_bits(int Kpad) {
+  int lg = 0;
+  while ((1 << lg) < Kpad) ++lg;
+  int b = (24 - lg) / 2;
+  return b > 8 ? 8 : b;
+}
+
+void launch_slice_rows(gwas_ctx* c, const double* src, int64_t lds, int rows, int K, int rows_pad, int Kpad, int S,
+                       int bits, __nv_bfloat16* planes, double* scale);
+int launch_xgemm(gwas_ctx* c, int SA, int SB, int L, const XgemmArgs& g, const __nv_bfloat16* A,
+                 const __nv_bfloat16* B);

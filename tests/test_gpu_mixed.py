@@ -1,0 +1,113 @@
+"""Parity of the mixed-precision tensor-core path with the FP64 oracle.
+
+Bar: relative error <= 1e-6 on the SNP coefficient, measured against
+max(|b*|, SE*) (the coefficients of pure-noise traits scatter around zero), and
+<= 1e-6 relative on its standard error.
+"""
+import numpy as np
+import pytest
+
+from oracle import EigOracle
+from synth import make_problem, genotypes, phenotypes, heritabilities, kinship, covariates
+from tests._metrics import full_b_err, last_coef_err, se_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+def solve(g, P, output, i0=0, i1=None, trait_block=0, precision=None):
+    precision = g.GWAS_MIXED if precision is None else precision
+    i1 = P.m if i1 is None else i1
+    o = g.gwas_default_opts(precision=precision, output=output, trait_block=trait_block)
+    ctx = g.gwas_setup(P.n, P.pm1, P.phi, P.XL, P.t, P.h2, o)
+    try:
+        g.gwas_load_snps(ctx, P.m, P.XR, P.n)
+        M = i1 - i0
+        out = np.full((P.t, M, P.p), np.nan) if output == g.GWAS_OUT_FULL_B else \
+            np.full((2, P.t, M), np.nan, dtype=np.float32)
+        rc = g.gwas_solve(ctx, P.Y, i0, i1, out)
+        return out, rc, g.gwas_singular_count(ctx)
+    finally:
+        g.gwas_destroy(ctx)
+
+
+def check_last(out, b, se, tol=TOL):
+    beta = out[0].T.astype(np.float64)
+    s = out[1].T.astype(np.float64)
+    e1, e2 = last_coef_err(beta, s, b, se), se_err(s, se)
+    assert e1 <= tol and e2 <= tol, (e1, e2)
+    return e1, e2
+
+
+@pytest.mark.parametrize("n,m,t", [(256, 1000, 10), (300, 777, 45), (1000, 300, 70), (130, 129, 33)])
+def test_last_se_parity(gw, n, m, t):
+    P = make_problem(n, m, t, seed=n * 7 + m)
+    out, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE)
+    assert rc == gw.GWAS_OK
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    check_last(out, b, se)
+
+
+def test_full_b_parity(gw):
+    P = make_problem(256, 400, 40, seed=21)
+    out, rc, _ = solve(gw, P, gw.GWAS_OUT_FULL_B)
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    err = full_b_err(out.transpose(1, 0, 2), b, se)
+    assert err <= TOL, err
+
+
+def test_range_and_blocks_are_bitwise_stable(gw):
+    P = make_problem(200, 700, 70, seed=5)
+    full, _, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE)
+    part, _, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE, 133, 601, trait_block=33)
+    np.testing.assert_array_equal(part, full[:, :, 133:601])
+
+
+def test_singular_snp(gw):
+    P = make_problem(128, 60, 6, seed=4)
+    P.XR[17] = 2
+    out, rc, cnt = solve(gw, P, gw.GWAS_OUT_LAST_SE)
+    assert rc == gw.GWAS_ERR_SINGULAR_PAIRS and cnt == P.t
+    assert np.isnan(out[:, :, 17]).all()
+    keep = np.r_[0:17, 18:P.m]
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR[keep], P.Y, P.h2)
+    check_last(out[:, :, keep], b, se)
+
+
+def test_mixed_matches_fp64_gpu(gw):
+    P = make_problem(512, 2000, 64, seed=8)
+    mixed, _, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE)
+    fp64, _, _ = solve(gw, P, gw.GWAS_OUT_FULL_B, precision=gw.GWAS_FP64)
+    b = fp64.transpose(1, 0, 2)
+    _, se_ref = EigOracle(P.phi, P.XL).solve(P.XR[:1], P.Y, P.h2)
+    # SE of the FP64 path from its own LAST_SE run
+    fse, _, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE, precision=gw.GWAS_FP64)
+    check_last(mixed, b, fse[1].T.astype(np.float64))
+
+
+def test_sampled_pairs_at_full_mixed_workload(gw):
+    """n=1000, p=4, m=1,000,000, t=10,000 on the device; the oracle checks sampled pairs."""
+    torch = pytest.importorskip("torch")
+    n, m, t = 1000, 1_000_000, 10_000
+    dev = torch.device("cuda:0")
+    phi, XL, h2 = kinship(n), covariates(n), heritabilities(t)
+    XR = genotypes(n, m)
+    Y = phenotypes(n, t)
+    o = gw.gwas_default_opts(precision=gw.GWAS_MIXED, output=gw.GWAS_OUT_LAST_SE)
+    ctx = gw.gwas_setup(n, 3, phi, XL, t, h2, o)
+    try:
+        gw.gwas_load_snps(ctx, m, torch.from_numpy(XR).to(dev), n)
+        out = torch.empty((2, t, m), dtype=torch.float32, device=dev)
+        assert gw.gwas_solve(ctx, torch.from_numpy(Y).to(dev), 0, m, out) == gw.GWAS_OK
+        rng = np.random.default_rng(1)
+        idx = np.unique(np.concatenate([np.arange(64), m - 64 + np.arange(64), rng.choice(m, 256, replace=False)]))
+        tj = np.unique(np.concatenate([np.arange(16), t - 16 + np.arange(16), rng.choice(t, 64, replace=False)]))
+        it, jt = torch.from_numpy(idx).to(dev), torch.from_numpy(tj).to(dev)
+        got = out[:, jt][:, :, it].cpu().numpy()
+        finite = bool(torch.isfinite(out).all().item())
+    finally:
+        gw.gwas_destroy(ctx)
+    assert finite
+    b, se = EigOracle(phi, XL).solve(XR[idx], Y[tj], h2[tj])
+    check_last(got, b, se)
