@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GWAS grid of GLS solves on GB300.
+
+Workload (one step = the whole path of Algorithm 5 on one synthetic batch):
+n = 1000 individuals, p = 4 (intercept + 2 covariates + SNP), m = 1,000,000 SNPs,
+t = 10,000 traits, mixed precision, SNP coefficient and its standard error
+returned in FP32.  A step runs gwas_setup (eigendecomposition of Phi, rotation
+of X_L), gwas_load_snps (rotation of the int8 genotypes) and gwas_solve
+(rotation of Y, per-trait algebra, fused contraction + Schur solve) through the
+C interface, inputs resident in HBM.  Metric: GLS pairs/s = m * t / step time.
+
+Also reported: the same metric end to end from pinned host buffers (e2e), the
+plain FP64 GPU path on a SNP sample of the same workload, the roofline of the
+fused contraction kernel, the CPU oracle on a bounded sample (cpu_baseline),
+and the error of sampled pairs against that oracle.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank solves its own SNP set (weak scaling, no
+collective on the data path); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import covariates, genotypes, heritabilities, kinship, phenotypes  # noqa: E402
+
+N_IND, PM1, M_SNP, T_TRAIT = 1000, 3, 1_000_000, 10_000
+METRIC = "GLS pairs/s (n=1000, p=4, m=1e6 SNPs, t=1e4 traits; SNP coefficient + SE)"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--m", type=int, default=M_SNP)
+    ap.add_argument("--t", type=int, default=T_TRAIT)
+    ap.add_argument("--n", type=int, default=N_IND)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(n, m, t, seed_offset=0):
+    from synth import BASE_SEED
+    seed = BASE_SEED + seed_offset
+    return {"phi": kinship(n), "XL": covariates(n, PM1), "h2": heritabilities(t), "XR": genotypes(n, m, seed),
+            "Y": phenotypes(n, t)}
+
+
+def step(g, opts, n, m, t, inp, out):
+    """One pass of the whole path; returns the context's per-kernel timings and launch count."""
+    ctx = g.gwas_setup(n, PM1, inp["phi"], inp["XL"], t, inp["h2"], opts)
+    try:
+        g.gwas_load_snps(ctx, m, inp["XR"], n)
+        rc = g.gwas_solve(ctx, inp["Y"], 0, m, out)
+        names = ["eigendecomposition", "setup_rotation_operands", "slice_rows", "genotypes_bf16", "xgemm_rotate_snps",
+                 "slice_snp_squares", "xgemm_rotate_traits", "prep_traits", "xgemm_back_rotate",
+                 "pack_trait_columns", "fused", "rotate_fp64", "prep_fp64", "fused_fp64"]
+        times = {k: g.gwas_kernel_time(ctx, k) for k in names}
+        return rc, {k: v for k, v in times.items() if v[1]}, g.gwas_kernel_launches(ctx)
+    finally:
+        g.gwas_destroy(ctx)
+
+
+def cpu_baseline(n, inp, m_s=8192, t_s=128):
+    """The oracle as it stands, on a bounded sample of the workload, on the host cores."""
+    from oracle import EigOracle
+    t0 = time.perf_counter()
+    o = EigOracle(inp["phi"], inp["XL"])
+    t_eig = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b, se = o.solve(inp["XR"][:m_s], inp["Y"][:t_s], inp["h2"][:t_s])
+    t_solve = time.perf_counter() - t0
+    total_pairs = inp["XR"].shape[0] * inp["Y"].shape[0]
+    pairs = m_s * t_s
+    # the eigendecomposition is charged in proportion to the share of the full grid
+    secs = t_solve + t_eig * pairs / total_pairs
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max(int(i.get("num_threads", 0)) for i in threadpool_info()) or cores
+    except Exception:
+        pass
+    return {"value": pairs / secs, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+            "sample": f"SNPs [0,{m_s}) x traits [0,{t_s}) of the same workload ({pairs} pairs, FP64 numpy/LAPACK); "
+                      f"eigendecomposition charged pro rata ({t_eig:.2f} s for the full grid)",
+            "seconds": t_solve + t_eig}, (b, se, m_s, t_s)
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle, timed as it stands on the host cores."""
+    if rank != 0:
+        return
+    n, m, t = args.n, args.m, args.t
+    from oracle import EigOracle
+    phi, XL, h2 = kinship(n), covariates(n, PM1), heritabilities(t)
+    m_s, t_s = 2048, 64
+    XR = genotypes(n, m, i0=0, i1=m_s)
+    Y = phenotypes(n, t, j0=0, j1=t_s)
+    secs = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        o = EigOracle(phi, XL)
+        t_eig = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        o.solve(XR, Y, h2[:t_s])
+        dt = time.perf_counter() - t0 + t_eig * (m_s * t_s) / (m * t)
+        if it >= args.warmup:
+            secs.append(dt)
+    ms = 1e3 * sum(secs) / len(secs)
+    value = m_s * t_s / (ms / 1e3)
+    cores = os.cpu_count()
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"GLS grid n={n} p=4 m={m} t={t}; each step a bounded sample "
+                                   f"(SNPs [0,{m_s}) x traits [0,{t_s}))", "n": n, "p": 4, "m": m, "t": t},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"SNPs [0,{m_s}) x traits [0,{t_s}) per step, FP64 numpy/LAPACK"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import paper_1210_7683_gb300 as g
+    from paper_1210_7683_gb300 import build as gbuild
+    gbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n, m, t = args.n, args.m, args.t
+    pairs = m * t
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    inp_h = make_inputs(n, m, t, seed_offset=rank)
+    inp_d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in inp_h.items()}
+    out = torch.empty((2, t, m), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    opts = g.gwas_default_opts(precision=g.GWAS_MIXED, output=g.GWAS_OUT_LAST_SE, device=local, profile=1,
+                               stream=stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step(g, opts, n, m, t, inp_d, out)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    ktimes = {}
+    ev0.record(stream)
+    for _ in range(args.steps):
+        rc, kt, nl = step(g, opts, n, m, t, inp_d, out)
+        launches += nl
+        for k, (ms, cnt) in kt.items():
+            a = ktimes.setdefault(k, [0.0, 0])
+            a[0] += ms
+            a[1] += cnt
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(tt.item())
+    value = world * pairs / (ms_step / 1e3)
+
+    # ---------------------------------------------------------------- roofline of the fused kernel
+    pk, pk_src = peaks()
+    fused_ms = ktimes["fused"][0] / ktimes["fused"][1]
+    useful = 2.0 * (PM1 + 2) * n * pairs                     # 2 (p+1) n flops per pair
+    kpad = (n + 63) // 64 * 64
+    tiles = ((m + 127) // 128) * ((t + 31) // 32)
+    issued = 2.0 * 128 * 512 * kpad * tiles                  # MMA columns per tile per K: 512
+    peak = pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+    achieved = useful / (fused_ms / 1e3) / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "fused_kernel",
+                "peak_source": f"{pk_src} bf16 sustained (kernel runs ~{fused_ms:.0f} ms inside a long step)",
+                "issued_tflops": issued / (fused_ms / 1e3) / 1e12,
+                "issued_frac": issued / (fused_ms / 1e3) / 1e12 / peak,
+                "algorithmic_flops_per_launch": useful, "launch_ms": fused_ms}
+    solve_ms = sum(v[0] for k, v in ktimes.items() if k in (
+        "xgemm_rotate_traits", "prep_traits", "xgemm_back_rotate", "pack_trait_columns", "fused")) / args.steps
+    breakdown = {k: round(v[0] / args.steps, 3) for k, v in ktimes.items()}
+
+    result = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+              "config": {"workload": f"GLS grid n={n} p=4 m={m} t={t}, mixed precision, beta+SE fp32 out",
+                         "n": n, "p": 4, "m": m, "t": t, "parallelism": f"snp-shard x{world}",
+                         "l2": "inputs larger than L2 (1 GB genotypes, 8 GB resident operand slices per step)"},
+              "roofline": roofline, "gpu_launches": launches, "clocks": clk,
+              "kernel_ms_per_step": breakdown,
+              "solve_only": {"value": pairs / (solve_ms / 1e3), "unit": "pairs/s",
+                             "note": "device time of gwas_solve kernels (Y rotation, per-trait prep, fused)"}}
+
+    # ---------------------------------------------------------------- FP64 GPU path on a SNP sample
+    if not args.no_fp64 and rank == 0:
+        m64 = min(m, 10_000)
+        o64 = g.gwas_default_opts(precision=g.GWAS_FP64, output=g.GWAS_OUT_LAST_SE, device=local, profile=1,
+                                  stream=stream.cuda_stream)
+        out64 = torch.empty((2, t, m64), dtype=torch.float32, device=dev)
+        sub = dict(inp_d)
+        sub["XR"] = inp_d["XR"][:m64].contiguous()
+        step(g, o64, n, m64, t, sub, out64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, kt64, _ = step(g, o64, n, m64, t, sub, out64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s64 = sum(v[0] for k, v in kt64.items() if k in ("rotate_fp64", "prep_fp64", "fused_fp64")) / 1e3
+        # the Y rotation and the per-trait prep do not depend on m: charge them pro rata to the SNP sample
+        y_part = sum(v[0] for k, v in kt64.items() if k == "prep_fp64") / 1e3
+        fused64 = kt64["fused_fp64"][0] / 1e3
+        result["fp64_gpu"] = {"value": m64 * t / fused64, "unit": "pairs/s",
+                              "sample": f"SNPs [0,{m64}) x {t} traits, fused FP64 kernel device time",
+                              "step_ms": e0.elapsed_time(e1), "kernel_ms": {k: v[0] for k, v in kt64.items()}}
+        result["mixed_over_fp64"] = (pairs / (fused_ms / 1e3)) / (m64 * t / fused64)
+        del out64, y_part, s64
+
+    # ---------------------------------------------------------------- end to end from pinned host buffers
+    if not args.no_e2e:
+        pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in inp_h.items()}
+        try:
+            hout = torch.empty((2, t, m), dtype=torch.float32).pin_memory()
+            out_note = "full beta+SE grid to pinned host memory"
+        except RuntimeError:
+            hout = None
+        if hout is not None:
+            h2d = sum(v.numel() * v.element_size() for v in pin.values())
+            d2h = hout.numel() * hout.element_size()
+            opts_h = g.gwas_default_opts(precision=g.GWAS_MIXED, output=g.GWAS_OUT_LAST_SE, device=local,
+                                         stream=stream.cuda_stream, trait_block=2500)
+            step(g, opts_h, n, m, t, pin, hout)
+            barrier()
+            e_steps = max(1, min(args.steps, 3))
+            t0 = time.perf_counter()
+            for _ in range(e_steps):
+                step(g, opts_h, n, m, t, pin, hout)
+            barrier()
+            e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
+            result["e2e"] = {"value": world * pairs / (e_ms / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                             "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": e_steps,
+                             "note": out_note + "; inputs from pinned host memory; wall clock around the C calls"}
+            del hout
+
+    # ---------------------------------------------------------------- CPU oracle and sampled error
+    if not args.no_cpu and rank == 0:
+        cb, (b, se, m_s, t_s) = cpu_baseline(n, inp_h)
+        result["cpu_baseline"] = cb
+        got = out[:, :t_s, :m_s].cpu().numpy()
+        beta, s = got[0].T.astype(np.float64), got[1].T.astype(np.float64)
+        bl = b[..., -1]
+        err = np.abs(beta - bl) / np.maximum(np.abs(bl), se)
+        result["err"] = {"max": float(err.max()), "median": float(np.median(err)),
+                         "se_max": float(np.max(np.abs(s - se) / se)),
+                         "definition": "|beta - beta*| / max(|beta*|, SE*) over the cpu_baseline sample",
+                         "pairs": int(err.size)}
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+if __name__ == "__main__":
+    main()
