@@ -153,6 +153,38 @@ GWAS_API int64_t gwas_kernel_launches(const gwas_ctx* ctx);
 GWAS_API int gwas_kernel_time(const gwas_ctx* ctx, const char* kernel, double* ms, int64_t* launches);
 GWAS_API void gwas_reset_timers(gwas_ctx* ctx);
 
+/*
+ * gwas_solve_fp64_noalloc -- the FP64 per-trait preparation and the fused FP64
+ * contraction + solve of gwas_solve, for callers that cannot allocate device
+ * memory.  The paper has no counterpart: it serves host applications whose
+ * memory manager owns the whole device (a framework's caching allocator, an
+ * arena fixed at start-up) and plug-in code that is handed only buffers and a
+ * stream.  It calls no cudaMalloc, cudaFree or allocating library routine; its
+ * scratch is a fixed 8 MiB device array inside the library, which every GPU
+ * that loads the library keeps until the process exits.
+ *
+ * Inputs are the already-rotated quantities of Algorithm 5, all device pointers
+ * on the current device:
+ *   lam  n eigenvalues of Phi          XLt  [pm1][n] rows Z^T x_L,l
+ *   Xt   [m][n] rows Z^T x_i (FP64)    Yt   [t][n] rows Z^T y_j
+ *   h2   t heritabilities
+ * out: GWAS_OUT_FULL_B double[t][m][p]; GWAS_OUT_LAST_SE float beta[t][m], then
+ * float se[t][m].  stream: cudaStream_t (NULL = legacy default stream); the call
+ * returns after the stream has finished.  *singular (may be NULL) receives the
+ * number of singular pairs.
+ *
+ * The scratch must hold t (p+1) n + t (pm1^2 + pm1 + 1) doubles plus 256 bytes:
+ * larger requests return GWAS_ERR_UNSUPPORTED before any device work.  The first
+ * call on a device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture.  Every
+ * call shares the one array and it keeps the last call's contents: calls that
+ * overlap on the GPU race on it.  Returns GWAS_OK, GWAS_ERR_SINGULAR_PAIRS (a
+ * warning), GWAS_ERR_ARG or GWAS_ERR_CUDA; gwas_last_error is not set.
+ */
+GWAS_API int gwas_solve_fp64_noalloc(int n, int pm1, const double* lam, const double* XLt, const double* Xt,
+                                     int64_t m, const double* Yt, const double* h2, int t, int output, void* out,
+                                     void* stream, int64_t* singular);
+
 /* One-line description of the last failure on ctx (or of the last failed
  * gwas_setup when ctx is NULL).  Owned by the library. */
 GWAS_API const char* gwas_last_error(const gwas_ctx* ctx);

@@ -73,6 +73,8 @@ def _load():
     lib.gwas_kernel_time.restype = ci
     lib.gwas_reset_timers.argtypes = [vp]
     lib.gwas_reset_timers.restype = None
+    lib.gwas_solve_fp64_noalloc.argtypes = [ci, ci, vp, vp, vp, i64, vp, vp, ci, ci, vp, vp, C.POINTER(i64)]
+    lib.gwas_solve_fp64_noalloc.restype = ci
     lib.gwas_destroy.argtypes = [vp]
     lib.gwas_destroy.restype = None
     return lib
@@ -181,6 +183,24 @@ def gwas_kernel_time(ctx, kernel: str):
 
 def gwas_reset_timers(ctx) -> None:
     lib.gwas_reset_timers(ctx)
+
+
+def gwas_solve_fp64_noalloc(n, pm1, lam, XLt, Xt, m, Yt, h2, t, output, out, stream=None):
+    """Allocation-free FP64 solve on rotated inputs (see include/gwas.h).
+
+    Returns (status, singular_pairs); raises GwasError on failures other than
+    the singular-pairs warning.
+    """
+    sing = C.c_int64(0)
+    dt = np.float64 if output == GWAS_OUT_FULL_B else np.float32
+    rc = lib.gwas_solve_fp64_noalloc(n, pm1, _addr(lam, np.float64, (n,), "lam"),
+                                     _addr(XLt, np.float64, (pm1, n), "XLt") if pm1 > 0 else None,
+                                     _addr(Xt, np.float64, (m, n), "Xt"), m, _addr(Yt, np.float64, (t, n), "Yt"),
+                                     _addr(h2, np.float64, (t,), "h2"), t, output, _addr(out, dt, None, "out"),
+                                     stream, C.byref(sing))
+    if rc not in (GWAS_OK, GWAS_ERR_SINGULAR_PAIRS):
+        raise GwasError(rc, "gwas_solve_fp64_noalloc failed")
+    return rc, sing.value
 
 
 def gwas_last_error(ctx=None) -> str:
