@@ -131,8 +131,29 @@ GWAS_API int gwas_load_snps(gwas_ctx* ctx, int64_t m, const int8_t* XR);
  * RSS the squared norm of the whitened residual (the paper defines none).
  * Returns GWAS_ERR_SINGULAR_PAIRS (a warning) when some pair's Schur
  * complement is <= 1e-10 times its diagonal entry; those outputs are NaN.
+ * A host `out` receives the results trait block by trait block (opts.trait_block),
+ * each block's copy overlapping the next block's computation when `out` is
+ * page-locked.
  */
 GWAS_API int gwas_solve(gwas_ctx* ctx, const double* Y, int64_t i0, int64_t i1, void* out);
+
+/*
+ * gwas_solve_stream -- gwas_solve for grids whose results do not fit in host
+ * memory at once (the output stream of Section 4, double-buffered).
+ *
+ * The traits are processed in blocks of block_traits.  The results of block b
+ * (traits [j0, j0+nb)) are copied to host_buf[b % 2] on a side stream while block
+ * b+1 is computed; once a copy has landed, fn(user, j0, nb, buf) is called on the
+ * calling thread, and buf is reused (for block b+2) only after fn returns.  Each
+ * buffer must hold one block in the output layout of the context:
+ *   GWAS_OUT_FULL_B  double[nb][i1-i0][p]
+ *   GWAS_OUT_LAST_SE float beta[nb][i1-i0], then float se[nb][i1-i0]
+ * i.e. block_traits * (i1-i0) * (8p or 8) bytes.  Page-locked buffers let the
+ * copies overlap the computation; pageable ones work but serialise the copies.
+ */
+typedef void (*gwas_block_fn)(void* user, int j0, int nb, const void* host_block);
+GWAS_API int gwas_solve_stream(gwas_ctx* ctx, const double* Y, int64_t i0, int64_t i1, int block_traits,
+                               void* host_buf0, void* host_buf1, gwas_block_fn fn, void* user);
 
 /* Replace the t heritabilities given at setup (same t). */
 GWAS_API int gwas_set_h2(gwas_ctx* ctx, int t, const double* h2);

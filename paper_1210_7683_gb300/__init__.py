@@ -48,6 +48,10 @@ class gwas_opts(C.Structure):
                 ("profile", C.c_int), ("hbm_budget", C.c_size_t), ("stream", C.c_void_p)]
 
 
+# void (*)(void* user, int j0, int nb, const void* host_block)
+GWAS_BLOCK_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_int, C.c_void_p)
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with paper_1210_7683_gb300.build.build()")
@@ -75,6 +79,8 @@ def _load():
     lib.gwas_reset_timers.restype = None
     lib.gwas_solve_fp64_noalloc.argtypes = [ci, ci, vp, vp, vp, i64, vp, vp, ci, ci, vp, vp, C.POINTER(i64)]
     lib.gwas_solve_fp64_noalloc.restype = ci
+    lib.gwas_solve_stream.argtypes = [vp, vp, i64, i64, ci, vp, vp, GWAS_BLOCK_FN, vp]
+    lib.gwas_solve_stream.restype = ci
     lib.gwas_destroy.argtypes = [vp]
     lib.gwas_destroy.restype = None
     return lib
@@ -160,6 +166,19 @@ def gwas_solve(ctx, Y, i0, i1, out):
     dt = np.float64 if getattr(out, "dtype", None) in (np.float64, getattr(_torch(), "float64", None)) else np.float32
     return _check(lib.gwas_solve(ctx, yv, int(i0), int(i1), _addr(out, dt, None, "out")), ctx,
                   allow=(GWAS_ERR_SINGULAR_PAIRS,))
+
+
+def gwas_solve_stream(ctx, Y, i0, i1, block_traits, buf0, buf1, fn):
+    """Blocked solve into two host buffers; fn(j0, nb, address) is called per finished block.
+
+    buf0/buf1: host numpy arrays or (pinned) torch tensors large enough for one block
+    (see include/gwas.h).  Returns GWAS_OK or GWAS_ERR_SINGULAR_PAIRS; raises otherwise.
+    """
+    cb = GWAS_BLOCK_FN(lambda user, j0, nb, ptr: fn(j0, nb, ptr))
+    dt = np.float64 if getattr(buf0, "dtype", None) in (np.float64, getattr(_torch(), "float64", None)) else np.float32
+    rc = lib.gwas_solve_stream(ctx, _addr(Y, np.float64, None, "Y"), int(i0), int(i1), int(block_traits),
+                               _addr(buf0, dt, None, "buf0"), _addr(buf1, dt, None, "buf1"), cb, None)
+    return _check(rc, ctx, allow=(GWAS_ERR_SINGULAR_PAIRS,))
 
 
 def gwas_set_h2(ctx, t, h2):

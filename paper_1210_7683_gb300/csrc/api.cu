@@ -173,6 +173,12 @@ static void destroy_impl(gwas_ctx* c) {
   prof_flush(c);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   c->event_pool.clear();
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  for (int k = 0; k < 2; ++k) {
+    if (c->ev_compute[k]) cudaEventDestroy(c->ev_compute[k]);
+    if (c->ev_copy[k]) cudaEventDestroy(c->ev_copy[k]);
+  }
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   mixed_free(c);
   delete c->mixed;
   c->mixed = nullptr;
@@ -400,101 +406,217 @@ extern "C" int gwas_load_snps(gwas_ctx* c, int64_t m, const int8_t* XR) {
   return rc;
 }
 
-extern "C" int gwas_solve(gwas_ctx* c, const double* Y, int64_t i0, int64_t i1, void* out) {
-  if (!c) return GWAS_ERR_ARG;
-  if (c->m == 0) return ctx_fail(c, GWAS_ERR_STATE, "gwas_solve before gwas_load_snps");
-  if (!Y || !out) return ctx_fail(c, GWAS_ERR_ARG, "NULL Y or out");
-  if (i0 < 0 || i1 < i0 || i1 > c->m) return ctx_fail(c, GWAS_ERR_ARG, "SNP range outside [0, m]");
-  DeviceGuard guard(c->device);
-  int rc = GWAS_OK;
-  c->singular = 0;
-  const int64_t M = i1 - i0;
-  if (M == 0) return GWAS_OK;
-  const int n = c->n, t = c->t, p = c->p;
-  const int tb = (c->trait_block > 0 && c->trait_block < t) ? c->trait_block : t;
-  bool ydev, odev;
-  if ((rc = ptr_kind(c, Y, &ydev))) return rc;
-  if ((rc = ptr_kind(c, out, &odev))) return rc;
-  cudaMemsetAsync(c->d_status, 0, 32, c->stream);
+namespace {
 
+// Where the results of a trait block go.
+struct OutSink {
+  int kind = 0;           // 0: device array, 1: host array, 2: caller's host ring + callback
+  void* out = nullptr;    // kinds 0 and 1: the full output array
+  void* ring[2] = {nullptr, nullptr};
+  gwas_block_fn fn = nullptr;
+  void* user = nullptr;
+};
+
+int ensure_copy_stream(gwas_ctx* c) {
+  int rc = GWAS_OK;
+  if (!c->copy_stream &&
+      !ctx_cuda_ok(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "copy stream", &rc))
+    return rc;
+  for (int k = 0; k < 2; ++k) {
+    if (!c->ev_compute[k] &&
+        !ctx_cuda_ok(c, cudaEventCreateWithFlags(&c->ev_compute[k], cudaEventDisableTiming), "event", &rc))
+      return rc;
+    if (!c->ev_copy[k] && !ctx_cuda_ok(c, cudaEventCreateWithFlags(&c->ev_copy[k], cudaEventDisableTiming), "event", &rc))
+      return rc;
+  }
+  return GWAS_OK;
+}
+
+// Runs the loops of Algorithm 5 over SNPs [i0, i1) x all traits in trait blocks of tb.
+// Host-bound results are double-buffered through two device staging buffers: the
+// copy of block b to the host (on a side stream) overlaps the computation of block
+// b+1 (Section 4's double buffering, applied to the output stream).
+int run_blocks(gwas_ctx* c, const double* dY, int64_t i0, int64_t i1, int tb, const OutSink& sink) {
+  const int n = c->n, t = c->t, p = c->p;
+  const int64_t M = i1 - i0;
+  const int nblocks = (t + tb - 1) / tb;
+  const bool lastse = c->output == GWAS_OUT_LAST_SE;
+  const size_t pair_bytes = lastse ? 2 * sizeof(float) : sizeof(double) * p;
+  int rc = GWAS_OK;
   std::vector<void*> tmp;
-  auto cleanup = [&]() { for (void* q : tmp) ctx_free(c, q); };
   auto talloc = [&](size_t b, void** q) {
     int r = ctx_alloc(c, b, q);
     if (r == GWAS_OK) tmp.push_back(*q);
     return r;
   };
-  const double* dY = Y;
-  if (!ydev) {
-    double* y;
-    if ((rc = talloc(sizeof(double) * t * n, (void**)&y))) { cleanup(); return rc; }
-    if ((rc = ctx_upload(c, Y, sizeof(double) * t * n, y))) { cleanup(); return rc; }
-    dY = y;
-  }
-  const size_t pair_bytes = c->output == GWAS_OUT_FULL_B ? sizeof(double) * p : 2 * sizeof(float);
-  void* stage = nullptr;
-  if (!odev && (rc = talloc(pair_bytes * (size_t)tb * M, &stage))) { cleanup(); return rc; }
-
+  MixedWs* ws = nullptr;
   double *Yt = nullptr, *R = nullptr, *cst = nullptr;
+  void* stage[2] = {nullptr, nullptr};
+  auto cleanup = [&]() {
+    if (ws) mixed_ws_free(c, ws);
+    for (void* q : tmp) ctx_free(c, q);
+  };
   if (c->precision == GWAS_FP64) {
     if ((rc = talloc(sizeof(double) * tb * n, (void**)&Yt)) || (rc = talloc(sizeof(double) * tb * (p + 1) * n, (void**)&R)) ||
         (rc = talloc(sizeof(double) * tb * consts_stride(c->pm1), (void**)&cst))) {
       cleanup();
       return rc;
     }
+  } else if ((rc = mixed_ws_alloc(c, tb, &ws))) {
+    cleanup();
+    return rc;
   }
-  for (int j0 = 0; j0 < t && rc == GWAS_OK; j0 += tb) {
-    const int nb = std::min(tb, t - j0);
-    // block outputs: device pointers of this trait block's results
-    void *ob, *os = nullptr;
-    if (odev) {
-      if (c->output == GWAS_OUT_FULL_B) {
-        ob = (double*)out + (size_t)j0 * M * p;
+  if (sink.kind != 0) {
+    if ((rc = ensure_copy_stream(c)) || (rc = talloc(pair_bytes * (size_t)tb * M, &stage[0])) ||
+        (rc = talloc(pair_bytes * (size_t)tb * M, &stage[1]))) {
+      cleanup();
+      return rc;
+    }
+  }
+  // block b's device output pointers (beta or b, and se)
+  auto block_out = [&](int b, int nb, void** ob, void** os) {
+    const int j0 = b * tb;
+    *os = nullptr;
+    if (sink.kind == 0) {
+      if (!lastse) {
+        *ob = (double*)sink.out + (size_t)j0 * M * p;
       } else {
-        ob = (float*)out + (size_t)j0 * M;
-        os = (float*)out + (size_t)t * M + (size_t)j0 * M;
+        *ob = (float*)sink.out + (size_t)j0 * M;
+        *os = (float*)sink.out + (size_t)t * M + (size_t)j0 * M;
       }
     } else {
-      ob = stage;
-      if (c->output == GWAS_OUT_LAST_SE) os = (float*)stage + (size_t)nb * M;
+      *ob = stage[b & 1];
+      if (lastse) *os = (float*)stage[b & 1] + (size_t)nb * M;
     }
+  };
+  auto compute = [&](int b) -> int {
+    const int j0 = b * tb, nb = std::min(tb, t - j0);
+    void *ob, *os;
+    block_out(b, nb, &ob, &os);
     if (c->precision == GWAS_FP64) {
-      launch_rotate_fp64_f64(c, dY + (size_t)j0 * n, nb, n, Yt);          // Y' := Z^T Y (gemm)
-      launch_prep_fp64(c, Yt, nb, c->h2 + j0, R, cst);                    // per-trait scalar-ops, syrk, gemv
-      if (c->output == GWAS_OUT_FULL_B) launch_fused_fp64(c, i0, i1, j0, nb, M, R, cst, ob);
-      else {
+      launch_rotate_fp64_f64(c, dY + (size_t)j0 * n, nb, n, Yt);  // Y' := Z^T Y (gemm)
+      launch_prep_fp64(c, Yt, nb, c->h2 + j0, R, cst);            // per-trait scalar-ops, syrk, gemv
+      if (!lastse) {
+        launch_fused_fp64(c, i0, i1, j0, nb, M, R, cst, ob);
+      } else {
         void* pair[2] = {ob, os};
         launch_fused_fp64(c, i0, i1, j0, nb, M, R, cst, pair);
       }
+      return GWAS_OK;
+    }
+    void* pair[2] = {ob, os};
+    return mixed_solve_block(c, ws, dY + (size_t)j0 * n, j0, nb, i0, i1, M, lastse ? (void*)pair : ob);
+  };
+  auto copy_out = [&](int b) -> int {
+    const int j0 = b * tb, nb = std::min(tb, t - j0);
+    const int k = b & 1;
+    int r = GWAS_OK;
+    if (!ctx_cuda_ok(c, cudaEventRecord(c->ev_compute[k], c->stream), "event", &r)) return r;
+    if (!ctx_cuda_ok(c, cudaStreamWaitEvent(c->copy_stream, c->ev_compute[k], 0), "event wait", &r)) return r;
+    if (sink.kind == 2) {
+      ctx_cuda_ok(c, cudaMemcpyAsync(sink.ring[k], stage[k], pair_bytes * (size_t)nb * M, cudaMemcpyDeviceToHost,
+                                     c->copy_stream), "block download", &r);
+    } else if (!lastse) {
+      ctx_cuda_ok(c, cudaMemcpyAsync((double*)sink.out + (size_t)j0 * M * p, stage[k], sizeof(double) * p * nb * M,
+                                     cudaMemcpyDeviceToHost, c->copy_stream), "block download", &r);
     } else {
-      void* o2 = ob;
-      void* pair[2] = {ob, os};
-      if (c->output == GWAS_OUT_LAST_SE) o2 = pair;
-      rc = mixed_solve_block(c, dY + (size_t)j0 * n, j0, nb, i0, i1, M, o2);
+      ctx_cuda_ok(c, cudaMemcpyAsync((float*)sink.out + (size_t)j0 * M, stage[k], sizeof(float) * nb * M,
+                                     cudaMemcpyDeviceToHost, c->copy_stream), "block download", &r);
+      if (r == GWAS_OK)
+        ctx_cuda_ok(c, cudaMemcpyAsync((float*)sink.out + (size_t)t * M + (size_t)j0 * M, (float*)stage[k] + (size_t)nb * M,
+                                       sizeof(float) * nb * M, cudaMemcpyDeviceToHost, c->copy_stream),
+                    "block download", &r);
     }
-    if (rc == GWAS_OK && !odev) {
-      if (c->output == GWAS_OUT_FULL_B) {
-        ctx_cuda_ok(c, cudaMemcpyAsync((double*)out + (size_t)j0 * M * p, ob, sizeof(double) * p * nb * M,
-                                       cudaMemcpyDeviceToHost, c->stream), "result download", &rc);
-      } else {
-        ctx_cuda_ok(c, cudaMemcpyAsync((float*)out + (size_t)j0 * M, ob, sizeof(float) * nb * M, cudaMemcpyDeviceToHost,
-                                       c->stream), "result download", &rc);
-        if (rc == GWAS_OK)
-          ctx_cuda_ok(c, cudaMemcpyAsync((float*)out + (size_t)t * M + (size_t)j0 * M, os, sizeof(float) * nb * M,
-                                         cudaMemcpyDeviceToHost, c->stream), "result download", &rc);
-      }
-      if (rc == GWAS_OK) ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "solve block", &rc);
+    if (r == GWAS_OK) ctx_cuda_ok(c, cudaEventRecord(c->ev_copy[k], c->copy_stream), "event", &r);
+    if (r == GWAS_OK && sink.kind == 2) {
+      ctx_cuda_ok(c, cudaEventSynchronize(c->ev_copy[k]), "block download", &r);
+      if (r == GWAS_OK) sink.fn(sink.user, j0, nb, sink.ring[k]);
     }
+    return r;
+  };
+  for (int b = 0; b <= nblocks && rc == GWAS_OK; ++b) {
+    if (b < nblocks) {
+      // staging buffer b&1 was last read by the copy of block b-2
+      if (sink.kind != 0 && b >= 2)
+        ctx_cuda_ok(c, cudaStreamWaitEvent(c->stream, c->ev_copy[b & 1], 0), "event wait", &rc);
+      if (rc == GWAS_OK) rc = compute(b);
+    }
+    if (rc == GWAS_OK && sink.kind != 0 && b >= 1) rc = copy_out(b - 1);
   }
+  if (rc == GWAS_OK) ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "solve", &rc);
+  if (rc == GWAS_OK && c->copy_stream) ctx_cuda_ok(c, cudaStreamSynchronize(c->copy_stream), "solve copies", &rc);
+  cleanup();
+  return rc;
+}
+
+int solve_impl(gwas_ctx* c, const double* Y, int64_t i0, int64_t i1, int tb, const OutSink& sink) {
+  int rc = GWAS_OK;
+  c->singular = 0;
+  const int64_t M = i1 - i0;
+  if (M == 0) return GWAS_OK;
+  const int n = c->n, t = c->t;
+  bool ydev;
+  if ((rc = ptr_kind(c, Y, &ydev))) return rc;
+  cudaMemsetAsync(c->d_status, 0, 32, c->stream);
+  double* yd = nullptr;
+  const double* dY = Y;
+  if (!ydev) {
+    if ((rc = ctx_alloc(c, sizeof(double) * t * n, (void**)&yd))) return rc;
+    if ((rc = ctx_upload(c, Y, sizeof(double) * t * n, yd))) {
+      ctx_free(c, yd);
+      return rc;
+    }
+    dY = yd;
+  }
+  rc = run_blocks(c, dY, i0, i1, tb, sink);
   unsigned long long st[2] = {0, 0};
   if (rc == GWAS_OK) ctx_cuda_ok(c, cudaGetLastError(), "solve kernels", &rc);
   if (rc == GWAS_OK) ctx_cuda_ok(c, cudaMemcpyAsync(st, c->d_status, 16, cudaMemcpyDeviceToHost, c->stream), "status", &rc);
   if (rc == GWAS_OK) ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "solve", &rc);
   if (rc == GWAS_OK) prof_flush(c);
-  cleanup();
+  ctx_free(c, yd);
   if (rc) return rc;
-  if (st[0]) return ctx_fail(c, GWAS_ERR_TIMEOUT, "a bounded wait inside the contraction kernel ran out");
+  if (st[0]) return ctx_fail(c, GWAS_ERR_TIMEOUT, "a bounded wait inside a kernel ran out");
   c->singular = (int64_t)st[1];
   if (c->singular) return ctx_fail(c, GWAS_ERR_SINGULAR_PAIRS, fmt("%lld pairs with a singular system", (long long)st[1]));
   return GWAS_OK;
+}
+
+}  // namespace
+
+extern "C" int gwas_solve(gwas_ctx* c, const double* Y, int64_t i0, int64_t i1, void* out) {
+  if (!c) return GWAS_ERR_ARG;
+  if (c->m == 0) return ctx_fail(c, GWAS_ERR_STATE, "gwas_solve before gwas_load_snps");
+  if (!Y || !out) return ctx_fail(c, GWAS_ERR_ARG, "NULL Y or out");
+  if (i0 < 0 || i1 < i0 || i1 > c->m) return ctx_fail(c, GWAS_ERR_ARG, "SNP range outside [0, m]");
+  DeviceGuard guard(c->device);
+  bool odev;
+  int rc = ptr_kind(c, out, &odev);
+  if (rc) return rc;
+  OutSink sink;
+  sink.kind = odev ? 0 : 1;
+  sink.out = out;
+  const int tb = (c->trait_block > 0 && c->trait_block < c->t) ? c->trait_block : c->t;
+  return solve_impl(c, Y, i0, i1, tb, sink);
+}
+
+extern "C" int gwas_solve_stream(gwas_ctx* c, const double* Y, int64_t i0, int64_t i1, int block_traits,
+                                 void* host_buf0, void* host_buf1, gwas_block_fn fn, void* user) {
+  if (!c) return GWAS_ERR_ARG;
+  if (c->m == 0) return ctx_fail(c, GWAS_ERR_STATE, "gwas_solve_stream before gwas_load_snps");
+  if (!Y || !host_buf0 || !host_buf1 || !fn || block_traits < 1)
+    return ctx_fail(c, GWAS_ERR_ARG, "NULL argument or block_traits < 1");
+  if (i0 < 0 || i1 < i0 || i1 > c->m) return ctx_fail(c, GWAS_ERR_ARG, "SNP range outside [0, m]");
+  DeviceGuard guard(c->device);
+  bool d0, d1;
+  int rc;
+  if ((rc = ptr_kind(c, host_buf0, &d0)) || (rc = ptr_kind(c, host_buf1, &d1))) return rc;
+  if (d0 || d1) return ctx_fail(c, GWAS_ERR_ARG, "gwas_solve_stream buffers must be host memory");
+  OutSink sink;
+  sink.kind = 2;
+  sink.ring[0] = host_buf0;
+  sink.ring[1] = host_buf1;
+  sink.fn = fn;
+  sink.user = user;
+  return solve_impl(c, Y, i0, i1, std::min(block_traits, c->t), sink);
 }

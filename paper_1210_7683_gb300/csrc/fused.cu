@@ -17,13 +17,20 @@
 // lower levels go to separate accumulators, and the levels are recombined in the
 // epilogue.
 //
-// Tile: 128 SNPs (TMEM lanes) x 32 traits.  TMEM columns:
+// Work is split into tiles of 128 SNPs x 32 traits.  A thread-block cluster of
+// CS x CT CTAs works on CS SNP tiles x CT trait tiles at once: the CTAs on the same
+// SNP tile share its genotype operands through TMA multicast (each loads 1/CT of
+// the rows for all of them), those on the same trait tile share the trait
+// operands (1/CS each), and every CTA releases a ring slot to all CTAs that write
+// into it.  TMEM columns of each CTA:
 //   [0,128)   C1 level 0  (slice 1 of w, v1, v2, v3; 32 traits each)
 //   [128,256) C1 level 1  (slice 2)
 //   [256,288) w slice 3   [288,320) w slice 4
 //   [320,352) C2 level 0  [352,384) C2 level-1 units (a)  [384,416) (b)
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
+#include <string>
 
 #include "fused.cuh"
 #include "gwas_internal.cuh"
@@ -34,53 +41,75 @@ namespace {
 constexpr int BM = 128, TT = 32, BK = 64;
 constexpr int PM1 = 3;
 constexpr int G_BYTES = BM * BK * 2;                 // 16 KB: one A tile
-constexpr int B1_ROWS = 10 * TT, B2_ROWS = 4 * TT;   // 320 and 128 rows
+constexpr int B1_ROWS = 10 * TT, B2_ROWS = 4 * TT;   // 320 and 128 rows per trait tile
+constexpr int BBOX = 32;                             // rows per TMA box of the trait operands
 constexpr int SLOT = 64 * 1024;                      // a ring slot holds either half-stage
 constexpr int SLOTS = 3;
 constexpr int H1_BYTES = G_BYTES + B1_ROWS * BK * 2; // 57344
 constexpr int H2_BYTES = 3 * G_BYTES + B2_ROWS * BK * 2;  // 65536
-constexpr int SMEM_BYTES = SLOTS * SLOT + 1024 + 512;
+constexpr int CST_BYTES = TT * FUSED_CST * 4;          // per-trait constants of one tile
+constexpr int SMEM_BYTES = SLOTS * SLOT + 2 * CST_BYTES + 1024 + 512;
 constexpr int TMEM_COLS = 512;
 static_assert(H1_BYTES <= SLOT && H2_BYTES <= SLOT, "half-stage does not fit a slot");
 
-__device__ __forceinline__ void tile_coords(int tile, const FusedArgs& a, int& st, int& tt) {
-  const int per_group = a.group * a.n_ttiles;
-  const int g = tile / per_group;
-  const int w = tile % per_group;
+template <int CS, int CT>
+__device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us, int& ut) {
+  const int nss = (a.n_stiles + CS - 1) / CS, nst = (a.n_ttiles + CT - 1) / CT;
+  const int per_group = a.group * nst;
+  const int g = u / per_group;
+  const int w = u % per_group;
   const int g0 = g * a.group;
-  const int gs = min(a.group, a.n_stiles - g0);
-  tt = w / gs;
-  st = g0 + w % gs;
+  const int gs = min(a.group, nss - g0);
+  ut = w / gs;
+  us = g0 + w % gs;
 }
 
-__global__ void __launch_bounds__(192, 1) fused_kernel(const __grid_constant__ CUtensorMap mapG,
-                                                       const __grid_constant__ CUtensorMap mapA2,
-                                                       const __grid_constant__ CUtensorMap mapB1,
-                                                       const __grid_constant__ CUtensorMap mapB2, FusedArgs a) {
+template <int CS, int CT, int EPW>
+__global__ void __launch_bounds__(64 + 32 * EPW, 1)
+    fused_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapA2,
+                 const __grid_constant__ CUtensorMap mapB1, const __grid_constant__ CUtensorMap mapB2, FusedArgs a) {
+  constexpr int NC = CS * CT;
+  constexpr int AROWS = BM / CT;                    // genotype rows this CTA loads per plane
+  constexpr int B1_BOXES = B1_ROWS / BBOX / CS, B2_BOXES = B2_ROWS / BBOX / CS;
+  static_assert(B1_ROWS % (BBOX * CS) == 0 && B2_ROWS % (BBOX * CS) == 0 && BM % (8 * CT) == 0, "cluster shape");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + SLOTS * SLOT);
+  float* cst_smem = (float*)(smem + SLOTS * SLOT);      // [2][TT][FUSED_CST], double-buffered by tile
+  uint64_t* full = (uint64_t*)(smem + SLOTS * SLOT + 2 * CST_BYTES);
   uint64_t* empty = full + SLOTS;
   uint64_t* acc_full = empty + SLOTS;
   uint64_t* acc_empty = acc_full + 1;
   uint32_t* tslot = (uint32_t*)(acc_empty + 1);
   volatile int* abort = (volatile int*)(tslot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int ntiles = a.n_stiles * a.n_ttiles;
+  uint32_t crank = 0, cid = blockIdx.x, ncl = gridDim.x;
+  if (NC > 1) {
+    crank = tc::cluster_ctarank();
+    cid = tc::cluster_id_x();
+    ncl = tc::cluster_count_x();
+  }
+  const int sr = crank % CS, tr = crank / CS;
+  uint16_t maskA = 0, maskB = 0;   // CTAs sharing this CTA's genotype / trait operands
+#pragma unroll
+  for (int k = 0; k < CT; ++k) maskA |= (uint16_t)(1u << (sr + CS * k));
+#pragma unroll
+  for (int k = 0; k < CS; ++k) maskB |= (uint16_t)(1u << (CS * tr + k));
+  const int nsuper = ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
   const int nkb = a.Kpad / BK;
   if (threadIdx.x == 0) {
     for (int s = 0; s < SLOTS; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], 1);
+      tc::mbar_init(&empty[s], CS + CT - 1);
     }
     tc::mbar_init(acc_full, 1);
-    tc::mbar_init(acc_empty, 4);
+    tc::mbar_init(acc_empty, EPW);
     *abort = 0;
     tc::fence_mbar_init();
   }
   if (warp == 1) tc::tmem_alloc(tslot, TMEM_COLS);
   tc::fence_before();
   __syncthreads();
+  if (NC > 1) tc::cluster_sync();
   tc::fence_after();
   const uint32_t tbase = *tslot;
 
@@ -93,10 +122,11 @@ __global__ void __launch_bounds__(192, 1) fused_kernel(const __grid_constant__ C
       tc::prefetch_map(&mapB2);
       uint32_t h = 0;  // half-stage counter
       bool ok = true;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        int st, tt;
-        tile_coords(tile, a, st, tt);
-        const int row = a.row0 + st * BM;
+      for (int u = cid; u < nsuper && ok; u += ncl) {
+        int us, ut;
+        super_coords<CS, CT>(u, a, us, ut);
+        const int row = (int)a.row0 + (us * CS + sr) * BM + tr * AROWS;
+        const int tt = ut * CT + tr;
         for (int kb = 0; kb < nkb && ok; ++kb) {
           for (int half = 0; half < 2; ++half, ++h) {
             const uint32_t s = h % SLOTS;
@@ -105,20 +135,38 @@ __global__ void __launch_bounds__(192, 1) fused_kernel(const __grid_constant__ C
             const int x = kb * BK;
             if (half == 0) {
               tc::mbar_expect_tx(&full[s], H1_BYTES);
-              tc::tma_load_2d(buf, &mapG, &full[s], x, row);
+              if (CT > 1) tc::tma_load_2d_mc(buf + tr * AROWS * 128, &mapG, &full[s], x, row, maskA);
+              else tc::tma_load_2d(buf, &mapG, &full[s], x, row);
 #pragma unroll
-              for (int q = 0; q < B1_ROWS / 64; ++q)
-                tc::tma_load_2d(buf + G_BYTES + q * 64 * BK * 2, &mapB1, &full[s], x, tt * B1_ROWS + q * 64);
+              for (int q = 0; q < B1_BOXES; ++q) {
+                const int r = (sr * B1_BOXES + q) * BBOX;
+                uint8_t* dst = buf + G_BYTES + r * 128;
+                if (CS > 1) tc::tma_load_2d_mc(dst, &mapB1, &full[s], x, tt * B1_ROWS + r, maskB);
+                else tc::tma_load_2d(dst, &mapB1, &full[s], x, tt * B1_ROWS + r);
+              }
             } else {
               tc::mbar_expect_tx(&full[s], H2_BYTES);
 #pragma unroll
-              for (int p = 0; p < 3; ++p) tc::tma_load_2d(buf + p * G_BYTES, &mapA2, &full[s], x, p * a.mpad + row);
+              for (int p = 0; p < 3; ++p) {
+                uint8_t* dst = buf + p * G_BYTES + tr * AROWS * 128;
+                if (CT > 1) tc::tma_load_2d_mc(dst, &mapA2, &full[s], x, (int)(p * a.mpad) + row, maskA);
+                else tc::tma_load_2d(dst, &mapA2, &full[s], x, (int)(p * a.mpad) + row);
+              }
 #pragma unroll
-              for (int q = 0; q < B2_ROWS / 64; ++q)
-                tc::tma_load_2d(buf + 3 * G_BYTES + q * 64 * BK * 2, &mapB2, &full[s], x, tt * B2_ROWS + q * 64);
+              for (int q = 0; q < B2_BOXES; ++q) {
+                const int r = (sr * B2_BOXES + q) * BBOX;
+                uint8_t* dst = buf + 3 * G_BYTES + r * 128;
+                if (CS > 1) tc::tma_load_2d_mc(dst, &mapB2, &full[s], x, tt * B2_ROWS + r, maskB);
+                else tc::tma_load_2d(dst, &mapB2, &full[s], x, tt * B2_ROWS + r);
+              }
             }
           }
         }
+      }
+      // the last release of every slot (ours and the peers') must land before we exit
+      for (uint32_t s = 0; s < SLOTS && h > s; ++s) {
+        const uint32_t uses = (h - s + SLOTS - 1) / SLOTS;
+        tc::mbar_wait(&empty[s], (uses - 1) & 1, a.status, abort);
       }
     }
   } else if (warp == 1) {
@@ -126,9 +174,10 @@ __global__ void __launch_bounds__(192, 1) fused_kernel(const __grid_constant__ C
     if (lane == 0) {
       constexpr uint32_t id256 = tc::idesc_bf16(BM, 8 * TT), id64 = tc::idesc_bf16(BM, 2 * TT);
       constexpr uint32_t id96 = tc::idesc_bf16(BM, 3 * TT), id32 = tc::idesc_bf16(BM, TT);
+      const uint16_t release = maskA | maskB;
       uint32_t h = 0, tcount = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tcount) {
+      for (int u = cid; u < nsuper && ok; u += ncl, ++tcount) {
         if (tcount > 0 && !tc::mbar_wait(acc_empty, (tcount - 1) & 1, a.status, abort)) { ok = false; break; }
         tc::fence_after();
         for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -161,71 +210,86 @@ __global__ void __launch_bounds__(192, 1) fused_kernel(const __grid_constant__ C
                 tc::mma_bf16(tbase + 11 * TT, tc::sdesc_add(d3, k * 32), tc::sdesc_add(de, TT * 128 + k * 32), id32, 1u);
               }
             }
-            tc::mma_commit(&empty[s]);
+            if (NC > 1) tc::mma_commit_mc(&empty[s], release);
+            else tc::mma_commit(&empty[s]);
           }
         }
         if (ok) tc::mma_commit(acc_full);
       }
     }
   } else {
-    // ------------------------------------------------------------ epilogue (warps 2..5)
-    const int q = warp % 4;                    // TMEM lane quarter
+    // ------------------------------------------------------------ epilogue (EPW warps)
+    const int ew = warp - 2;
+    const int q = warp % 4;                            // TMEM lane quarter this warp may access
+    constexpr int JPW = TT / (EPW / 4);                // traits per epilogue warp
+    const int jbeg = (ew / 4) * JPW;
     const uint32_t lane_base = tbase + ((uint32_t)(q * 32) << 16);
+    const float inv_dof = 1.f / a.dof;
     uint32_t tcount = 0;
     unsigned long long nsing = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
-      int st, tt;
-      tile_coords(tile, a, st, tt);
+    for (int u = cid; u < nsuper; u += ncl, ++tcount) {
+      int us, ut;
+      super_coords<CS, CT>(u, a, us, ut);
+      const int st = us * CS + sr, tt = ut * CT + tr;
+      // stage this tile's per-trait constants (double buffer: the barrier of the previous
+      // tile guarantees every epilogue warp has finished reading this buffer)
+      float* cs = cst_smem + (tcount & 1) * TT * FUSED_CST;
+      for (int e = ew * 32 + lane; e < TT * FUSED_CST; e += EPW * 32) {
+        const int jj = tt * TT + e / FUSED_CST;
+        cs[e] = jj < a.ntrait ? a.cst[(size_t)jj * FUSED_CST + e % FUSED_CST] : 0.f;
+      }
+      tc::named_sync(1, EPW * 32);
       const bool ok = tc::mbar_wait(acc_full, tcount & 1, a.status, abort);
       tc::fence_after();
       const int64_t i = (int64_t)st * BM + q * 32 + lane;   // SNP index relative to row0
-      const bool valid_i = ok && i < a.nsnp;
+      const bool valid_i = ok && st < a.n_stiles && i < a.nsnp;
       const float sA = valid_i ? a.sA[a.row0 + i] : 0.f;
       float ac[PM1] = {0.f, 0.f, 0.f};
       if (valid_i && a.full_b) {
 #pragma unroll
         for (int c = 0; c < PM1; ++c) ac[c] = a.acoef[(a.row0 + i) * PM1 + c];
       }
-      for (int j0 = 0; j0 < TT; j0 += 8) {
-        uint32_t hw[8], hz[3][8], lw[8], lz[3][8], w3[8], w4[8], d0[8], da[8], db[8];
-        tc::tmem_ld8(lane_base + 0 * TT + j0, hw);
+      for (int j0 = jbeg; j0 < jbeg + JPW; j0 += 4) {
+        uint32_t hw[4], hz[3][4], lw[4], lz[3][4], w3[4], w4[4], d0[4], da[4], db[4];
+        tc::tmem_ld4(lane_base + 0 * TT + j0, hw);
 #pragma unroll
-        for (int c = 0; c < PM1; ++c) tc::tmem_ld8(lane_base + (1 + c) * TT + j0, hz[c]);
-        tc::tmem_ld8(lane_base + 4 * TT + j0, lw);
+        for (int c = 0; c < PM1; ++c) tc::tmem_ld4(lane_base + (1 + c) * TT + j0, hz[c]);
+        tc::tmem_ld4(lane_base + 4 * TT + j0, lw);
 #pragma unroll
-        for (int c = 0; c < PM1; ++c) tc::tmem_ld8(lane_base + (5 + c) * TT + j0, lz[c]);
-        tc::tmem_ld8(lane_base + 8 * TT + j0, w3);
-        tc::tmem_ld8(lane_base + 9 * TT + j0, w4);
-        tc::tmem_ld8(lane_base + 10 * TT + j0, d0);
-        tc::tmem_ld8(lane_base + 11 * TT + j0, da);
-        tc::tmem_ld8(lane_base + 12 * TT + j0, db);
+        for (int c = 0; c < PM1; ++c) tc::tmem_ld4(lane_base + (5 + c) * TT + j0, lz[c]);
+        tc::tmem_ld4(lane_base + 8 * TT + j0, w3);
+        tc::tmem_ld4(lane_base + 9 * TT + j0, w4);
+        tc::tmem_ld4(lane_base + 10 * TT + j0, d0);
+        tc::tmem_ld4(lane_base + 11 * TT + j0, da);
+        tc::tmem_ld4(lane_base + 12 * TT + j0, db);
         tc::tmem_ld_wait();
         tc::reg_fence(hw); tc::reg_fence(lw); tc::reg_fence(w3); tc::reg_fence(w4);
         tc::reg_fence(d0); tc::reg_fence(da); tc::reg_fence(db);
 #pragma unroll
         for (int c = 0; c < PM1; ++c) { tc::reg_fence(hz[c]); tc::reg_fence(lz[c]); }
-        if (j0 + 8 == TT) {
-          // every TMEM read of this tile is complete: release the accumulators
+        if (j0 + 4 == jbeg + JPW) {
+          // every TMEM read of this warp for this tile is complete: release the accumulators
           tc::fence_before();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(acc_empty);
         }
         if (!valid_i) continue;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int jj = tt * TT + j0 + u;     // trait index within the block
+        for (int v = 0; v < 4; ++v) {
+          const int jl = j0 + v;
+          const int jj = tt * TT + jl;          // trait index within the block
           if (jj >= a.ntrait) break;
-          const float* cj = a.cst + (size_t)jj * FUSED_CST;
+          const float* cj = cs + jl * FUSED_CST;
           const float F = 1.f / 256.f;
-          const float num = cj[0] * fmaf(F, fmaf(F, fmaf(F, __uint_as_float(w4[u]), __uint_as_float(w3[u])),
-                                                 __uint_as_float(lw[u])), __uint_as_float(hw[u]));
+          const float num = cj[0] * fmaf(F, fmaf(F, fmaf(F, __uint_as_float(w4[v]), __uint_as_float(w3[v])),
+                                                 __uint_as_float(lw[v])), __uint_as_float(hw[v]));
           float z[PM1], zz = 0.f;
 #pragma unroll
           for (int c = 0; c < PM1; ++c) {
-            z[c] = cj[1 + c] * fmaf(F, __uint_as_float(lz[c][u]), __uint_as_float(hz[c][u]));
+            z[c] = cj[1 + c] * fmaf(F, __uint_as_float(lz[c][v]), __uint_as_float(hz[c][v]));
             zz = fmaf(z[c], z[c], zz);
           }
-          const float s = (sA * cj[4]) * fmaf(F, __uint_as_float(da[u]) + __uint_as_float(db[u]), __uint_as_float(d0[u]));
+          const float s = (sA * cj[4]) * fmaf(F, __uint_as_float(da[v]) + __uint_as_float(db[v]), __uint_as_float(d0[v]));
           const float delta = s - zz;
           float beta, se;
           const bool sing = !(delta > 1e-6f * s) || !(sA > 0.f);
@@ -233,9 +297,10 @@ __global__ void __launch_bounds__(192, 1) fused_kernel(const __grid_constant__ C
             beta = se = __int_as_float(0x7fc00000);
             ++nsing;
           } else {
-            beta = num / delta;
+            const float inv = __frcp_rn(delta);
+            beta = num * inv;
             const float rss = fmaxf(fmaf(-num, beta, cj[5]), 0.f);
-            se = sqrtf(rss / (a.dof * delta));
+            se = __fsqrt_rn(rss * inv * inv_dof);
           }
           const int64_t o = (int64_t)jj * a.ldo + (a.row0 + i - a.i0);
           if (a.full_b) {
@@ -263,29 +328,89 @@ __global__ void __launch_bounds__(192, 1) fused_kernel(const __grid_constant__ C
   }
   tc::fence_before();
   __syncthreads();
+  if (NC > 1) tc::cluster_sync();
   if (warp == 1) tc::tmem_dealloc(tbase, TMEM_COLS);
+}
+
+struct Shape {
+  int cs, ct, epw;
+};
+
+Shape shape_from_env() {
+  Shape sh{1, 1, 16};
+  if (const char* e = getenv("GWAS_FUSED_SHAPE")) {
+    int cs = 0, ct = 0, epw = 0;
+    if (sscanf(e, "%dx%dx%d", &cs, &ct, &epw) == 3) sh = {cs, ct, epw};
+  }
+  return sh;
+}
+
+template <int CS, int CT, int EPW>
+int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const CUtensorMap& ma,
+                 const CUtensorMap& m1, const CUtensorMap& m2) {
+  constexpr int NC = CS * CT;
+  auto kern = fused_kernel<CS, CT, EPW>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = NC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(64 + 32 * EPW);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = c->stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+  int nclusters = nsm / NC;
+  cfg.gridDim = dim3(nclusters * NC);
+  int maxc = 0;
+  if (cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg) == cudaSuccess && maxc > 0) nclusters = maxc;
+  cudaGetLastError();
+  const int nsuper = ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
+  nclusters = std::min(nclusters, nsuper);
+  if (a.max_ctas > 0) nclusters = std::max(1, std::min(nclusters, a.max_ctas / NC));
+  cfg.gridDim = dim3(nclusters * NC);
+  ProfScope ps(c, "fused");
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mg, ma, m1, m2, a);
+  c->launches++;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(c, GWAS_ERR_CUDA, std::string("fused kernel launch: ") + cudaGetErrorString(e));
+  }
+  return GWAS_OK;
 }
 
 }  // namespace
 
+int fused_trait_tile_multiple() { return 4; }
+
 int launch_fused(gwas_ctx* c, const FusedArgs& args, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2) {
-  CUtensorMap mg, ma, m1, m2;
   FusedArgs a = args;
-  if (!make_bf16_map(&mg, G, a.mpad, a.Kpad, BM) || !make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM) ||
-      !make_bf16_map(&m1, B1, (uint64_t)a.n_ttiles * B1_ROWS, a.Kpad, 64) ||
-      !make_bf16_map(&m2, B2, (uint64_t)a.n_ttiles * B2_ROWS, a.Kpad, 64))
+  if (a.n_stiles == 0 || a.n_ttiles == 0) return GWAS_OK;
+  const Shape sh = shape_from_env();
+  const int ttiles_pad = (a.n_ttiles + 3) / 4 * 4;   // trait operands are allocated for a multiple of 4 tiles
+  CUtensorMap mg, ma, m1, m2;
+  if (!make_bf16_map(&mg, G, a.mpad, a.Kpad, BM / sh.ct) || !make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM / sh.ct) ||
+      !make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * B1_ROWS, a.Kpad, BBOX) ||
+      !make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * B2_ROWS, a.Kpad, BBOX))
     return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
-  static int nsm = 0;
-  if (!nsm) {
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-    cudaFuncSetAttribute(fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  }
-  const int ntiles = a.n_stiles * a.n_ttiles;
-  if (ntiles == 0) return GWAS_OK;
-  const int grid = std::min(ntiles, a.max_ctas > 0 ? a.max_ctas : nsm);
-  ProfScope ps(c, "fused");
-  fused_kernel<<<grid, 192, SMEM_BYTES, c->stream>>>(mg, ma, m1, m2, a);
-  c->launches++;
-  return GWAS_OK;
+#define GWAS_SHAPE(CS, CT, EPW) \
+  if (sh.cs == CS && sh.ct == CT && sh.epw == EPW) return launch_shape<CS, CT, EPW>(c, a, mg, ma, m1, m2);
+  GWAS_SHAPE(1, 1, 4)
+  GWAS_SHAPE(1, 1, 8)
+  GWAS_SHAPE(1, 1, 16)
+  GWAS_SHAPE(1, 2, 8)
+  GWAS_SHAPE(1, 2, 16)
+  GWAS_SHAPE(2, 1, 16)
+  GWAS_SHAPE(2, 2, 16)
+#undef GWAS_SHAPE
+  return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: cluster shape not instantiated");
 }

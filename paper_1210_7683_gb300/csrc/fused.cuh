@@ -17,7 +17,7 @@ struct FusedArgs {
   int64_t nsnp;       // SNPs in the range
   int n_stiles;       // ceil(nsnp / 128)
   int n_ttiles;       // ceil(ntrait / 32)
-  int group;          // SNP tiles per traversal group (L2 reuse of the genotype tiles)
+  int group;          // cluster-wide SNP super-tiles per traversal group (L2 reuse of genotype tiles)
   int ntrait;         // traits in this block
   int Kpad;           // padded n (multiple of 64)
   int64_t mpad;       // rows per plane of G and of the x'_c^2 planes
@@ -34,6 +34,9 @@ struct FusedArgs {
   unsigned long long* singular;  // singular-pair counter
   int max_ctas;       // 0 = one CTA per SM
 };
+
+// Trait operands (B1, B2) must be allocated (and zeroed) for a multiple of this many trait tiles.
+int fused_trait_tile_multiple();
 
 int launch_fused(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2);

@@ -55,6 +55,10 @@ struct gwas_ctx {
   int64_t singular = 0;
   int64_t launches = 0;
 
+  // output streaming: side stream and events of the double-buffered device-to-host copies
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_compute[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
+
   // profiling: per-kernel device time from CUDA events on `stream`
   bool profile = false;
   std::vector<ProfPending> pending;
@@ -94,6 +98,10 @@ int consts_stride(int pm1);
 
 // ---------------------------------------------------------------- mixed path (mixed.cu)
 int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m);  // genotypes already on the device
-int mixed_solve_block(gwas_ctx* c, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
+struct MixedWs;  // work buffers of one gwas_solve call (mixed.cu)
+int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** ws);
+void mixed_ws_free(gwas_ctx* c, MixedWs* ws);
+// Enqueues (no synchronisation) the solve of traits [j0, j0+tb) x SNPs [i0, i1) into dout.
+int mixed_solve_block(gwas_ctx* c, MixedWs* ws, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
                       void* dout);
 void mixed_free(gwas_ctx* c);

@@ -12,6 +12,7 @@
 //   w_j = M_j^-1 r_j and v'_j = P_c M_j^-1 X_L L_j^-T, both by exact sliced GEMMs.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -491,35 +492,65 @@ int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m) {
   return GWAS_OK;
 }
 
-int mixed_solve_block(gwas_ctx* c, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo, void* out) {
-  MixedState* s = c->mixed;
-  if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
-  const int n = c->n, p = PM1 + 1, Kpad = s->Kpad;
-  const int nt_tiles = (tb + TT - 1) / TT;
-  const int tb_pad = nt_tiles * TT;
-  const int rowsY = (int)rup(tb, 128), rowsW = (int)rup((int64_t)tb * p, 128);
-  int rc = GWAS_OK;
-  std::vector<void*> tmp;
-  auto alloc = [&](size_t b, void** q) {
-    int r = ctx_alloc(c, b, q);
-    if (r == GWAS_OK) tmp.push_back(*q);
-    return r;
-  };
+struct MixedWs {
+  int tb_max = 0;
   __nv_bfloat16 *Ysl = nullptr, *Wsl = nullptr, *B1 = nullptr, *B2 = nullptr;
   double *sY = nullptr, *Yt = nullptr, *Wt = nullptr, *sW = nullptr;
   float* cst = nullptr;
-  if ((rc = alloc(2ull * 4 * rowsY * Kpad, (void**)&Ysl)) || (rc = alloc(sizeof(double) * rowsY, (void**)&sY)) ||
-      (rc = alloc(sizeof(double) * (size_t)tb * Kpad, (void**)&Yt)) ||
-      (rc = alloc(sizeof(double) * (size_t)tb * p * Kpad, (void**)&Wt)) ||
-      (rc = alloc(2ull * 4 * rowsW * Kpad, (void**)&Wsl)) || (rc = alloc(sizeof(double) * rowsW, (void**)&sW)) ||
-      (rc = alloc(2ull * (size_t)nt_tiles * B1_ROWS * Kpad, (void**)&B1)) ||
-      (rc = alloc(2ull * (size_t)nt_tiles * B2_ROWS * Kpad, (void**)&B2)) ||
-      (rc = alloc(sizeof(float) * (size_t)tb_pad * FUSED_CST, (void**)&cst))) {
-    for (void* q : tmp) ctx_free(c, q);
+};
+
+void mixed_ws_free(gwas_ctx* c, MixedWs* w) {
+  if (!w) return;
+  void* ps[] = {w->Ysl, w->Wsl, w->B1, w->B2, w->sY, w->Yt, w->Wt, w->sW, w->cst};
+  for (void* q : ps) ctx_free(c, q);
+  delete w;
+}
+
+// Work buffers of a trait block of up to tb_max traits, allocated once per gwas_solve.
+int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** out) {
+  *out = nullptr;
+  MixedState* s = c->mixed;
+  if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
+  const int p = PM1 + 1, Kpad = s->Kpad;
+  const int nt_tiles = (tb_max + TT - 1) / TT;
+  const int nt_alloc = (nt_tiles + fused_trait_tile_multiple() - 1) / fused_trait_tile_multiple() *
+                       fused_trait_tile_multiple();
+  const int rowsY = (int)rup(tb_max, 128), rowsW = (int)rup((int64_t)tb_max * p, 128);
+  MixedWs* w = new MixedWs;
+  w->tb_max = tb_max;
+  int rc;
+  if ((rc = ctx_alloc(c, 2ull * 4 * rowsY * Kpad, (void**)&w->Ysl)) ||
+      (rc = ctx_alloc(c, sizeof(double) * rowsY, (void**)&w->sY)) ||
+      (rc = ctx_alloc(c, sizeof(double) * (size_t)tb_max * Kpad, (void**)&w->Yt)) ||
+      (rc = ctx_alloc(c, sizeof(double) * (size_t)tb_max * p * Kpad, (void**)&w->Wt)) ||
+      (rc = ctx_alloc(c, 2ull * 4 * rowsW * Kpad, (void**)&w->Wsl)) ||
+      (rc = ctx_alloc(c, sizeof(double) * rowsW, (void**)&w->sW)) ||
+      (rc = ctx_alloc(c, 2ull * (size_t)nt_alloc * B1_ROWS * Kpad, (void**)&w->B1)) ||
+      (rc = ctx_alloc(c, 2ull * (size_t)nt_alloc * B2_ROWS * Kpad, (void**)&w->B2)) ||
+      (rc = ctx_alloc(c, sizeof(float) * (size_t)nt_tiles * TT * FUSED_CST, (void**)&w->cst))) {
+    mixed_ws_free(c, w);
     return rc;
   }
-  cudaMemsetAsync(B1, 0, 2ull * nt_tiles * B1_ROWS * Kpad, c->stream);
-  cudaMemsetAsync(B2, 0, 2ull * nt_tiles * B2_ROWS * Kpad, c->stream);
+  *out = w;
+  return GWAS_OK;
+}
+
+int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
+                      void* out) {
+  MixedState* s = c->mixed;
+  if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
+  if (tb > w->tb_max) return ctx_fail(c, GWAS_ERR_ARG, "trait block larger than its workspace");
+  const int n = c->n, p = PM1 + 1, Kpad = s->Kpad;
+  const int nt_tiles = (tb + TT - 1) / TT;
+  const int nt_alloc = (nt_tiles + fused_trait_tile_multiple() - 1) / fused_trait_tile_multiple() *
+                       fused_trait_tile_multiple();
+  const int rowsY = (int)rup(tb, 128), rowsW = (int)rup((int64_t)tb * p, 128);
+  int rc = GWAS_OK;
+  __nv_bfloat16 *Ysl = w->Ysl, *Wsl = w->Wsl, *B1 = w->B1, *B2 = w->B2;
+  double *sY = w->sY, *Yt = w->Yt, *Wt = w->Wt, *sW = w->sW;
+  float* cst = w->cst;
+  cudaMemsetAsync(B1, 0, 2ull * nt_alloc * B1_ROWS * Kpad, c->stream);
+  cudaMemsetAsync(B2, 0, 2ull * nt_alloc * B2_ROWS * Kpad, c->stream);
   // Y' := Z^T Y (Algorithm 5, gemm) as an exact sliced GEMM
   launch_slice_rows(c, dY, n, tb, n, rowsY, Kpad, 4, s->bits, Ysl, sY);
   XgemmArgs g{};
@@ -562,7 +593,8 @@ int mixed_solve_block(gwas_ctx* c, const double* dY, int j0, int tb, int64_t i0,
     a.nsnp = i1 - i0;
     a.n_stiles = (int)((a.nsnp + 127) / 128);
     a.n_ttiles = nt_tiles;
-    a.group = 64;
+    a.group = 16;
+    if (const char* e = getenv("GWAS_FUSED_GROUP")) a.group = std::max(1, atoi(e));
     a.ntrait = tb;
     a.Kpad = Kpad;
     a.mpad = s->mpad;
@@ -583,7 +615,5 @@ int mixed_solve_block(gwas_ctx* c, const double* dY, int j0, int tb, int64_t i0,
     a.singular = c->d_status + 1;
     rc = launch_fused(c, a, s->G, s->A2, B1, B2);
   }
-  cudaStreamSynchronize(c->stream);
-  for (void* q : tmp) ctx_free(c, q);
   return rc;
 }

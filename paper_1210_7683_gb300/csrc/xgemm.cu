@@ -24,10 +24,12 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 64;
+constexpr int BM = 128, BK = 64;
 
 template <int SA, int SB, int L>
 struct XCfg {
+  // wider N when A has a single slice: (L+1) accumulators of BN columns fit TMEM
+  static constexpr int BN = (SA == 1 && (L + 1) * 128 <= 512) ? 128 : 64;
   static constexpr int A_BYTES = BM * BK * 2;            // one slice plane tile
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE = SA * A_BYTES + SB * B_BYTES;
@@ -40,6 +42,7 @@ template <int SA, int SB, int L>
 __global__ void __launch_bounds__(192, 1) xgemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                        const __grid_constant__ CUtensorMap mapB, XgemmArgs g) {
   using Cfg = XCfg<SA, SB, L>;
+  constexpr int BN = Cfg::BN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + Cfg::STAGES * Cfg::STAGE);
@@ -120,16 +123,29 @@ __global__ void __launch_bounds__(192, 1) xgemm_kernel(const __grid_constant__ C
 #pragma unroll
       for (int l = 0; l <= L; ++l) tc::reg_fence(v[l]);
       if (!ok || r >= g.rows) continue;
+      if (g.out64) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int c = c0 + cc + j;
-        if (c >= g.cols) break;
-        double acc = (double)__uint_as_float(v[L][j]);
+        for (int j = 0; j < 8; ++j) {
+          const int c = c0 + cc + j;
+          if (c >= g.cols) break;
+          double acc = (double)__uint_as_float(v[L][j]);
 #pragma unroll
-        for (int l = L - 1; l >= 0; --l) acc = fma(acc, g.level_scale, (double)__uint_as_float(v[l][j]));
-        const double val = acc * sa * g.scaleB[c];
-        if (g.out64) g.out64[(size_t)r * g.ldo + c] = val;
-        else g.out32[(size_t)r * g.ldo + c] = (float)val;
+          for (int l = L - 1; l >= 0; --l) acc = fma(acc, g.level_scale, (double)__uint_as_float(v[l][j]));
+          g.out64[(size_t)r * g.ldo + c] = acc * sa * g.scaleB[c];
+        }
+      } else {
+        // FP32 result: each level sum is an exact integer below 2^24, so combining the
+        // levels in FP32 (smallest first) costs no more than the final rounding
+        const float ls = (float)g.level_scale, saf = (float)sa;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int c = c0 + cc + j;
+          if (c >= g.cols) break;
+          float acc = __uint_as_float(v[L][j]);
+#pragma unroll
+          for (int l = L - 1; l >= 0; --l) acc = fmaf(acc, ls, __uint_as_float(v[l][j]));
+          g.out32[(size_t)r * g.ldo + c] = acc * (saf * (float)g.scaleB[c]);
+        }
       }
     }
   }
@@ -205,14 +221,16 @@ static int run_xgemm(gwas_ctx* c, const XgemmArgs& g, const __nv_bfloat16* A, co
   using Cfg = XCfg<SA, SB, L>;
   CUtensorMap ma, mb;
   if (!make_bf16_map(&ma, A, (uint64_t)SA * g.rowsA_pad, g.Kpad, BM) ||
-      !make_bf16_map(&mb, B, (uint64_t)SB * g.rowsB_pad, g.Kpad, BN))
+      !make_bf16_map(&mb, B, (uint64_t)SB * g.rowsB_pad, g.Kpad, Cfg::BN))
     return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(xgemm_kernel<SA, SB, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     attr = true;
   }
-  dim3 grid(g.rowsA_pad / BM, g.rowsB_pad / BN);
+  // a last partial column tile reads past its plane (the next plane, or TMA zero fill
+  // after the last one); those columns are >= g.cols and never stored
+  dim3 grid(g.rowsA_pad / BM, (g.rowsB_pad + Cfg::BN - 1) / Cfg::BN);
   ProfScope ps(c, g.name ? g.name : "xgemm");
   xgemm_kernel<SA, SB, L><<<grid, 192, Cfg::SMEM, c->stream>>>(ma, mb, g);
   c->launches++;
@@ -221,7 +239,7 @@ static int run_xgemm(gwas_ctx* c, const XgemmArgs& g, const __nv_bfloat16* A, co
 
 int launch_xgemm(gwas_ctx* c, int SA, int SB, int L, const XgemmArgs& g, const __nv_bfloat16* A,
                  const __nv_bfloat16* B) {
-  if (g.rowsA_pad % BM || g.rowsB_pad % BN || g.Kpad % BK)
+  if (g.rowsA_pad % BM || g.rowsB_pad % 64 || g.Kpad % BK)
     return ctx_fail(c, GWAS_ERR_ARG, "xgemm: padded sizes are not tile multiples");
   if (SA == 4 && SB == 4 && L == 3) return run_xgemm<4, 4, 3>(c, g, A, B);
   if (SA == 1 && SB == 4 && L == 3) return run_xgemm<1, 4, 3>(c, g, A, B);
