@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=400,
+                    help="requests of the serving run (the full serving workload has 2000; 0 skips it)")
+    ap.add_argument("--serving-load", type=float, default=0.8, help="offered load as a fraction of saturation")
     return ap.parse_args()
 
 
@@ -165,6 +168,77 @@ def cpu_baseline(n, inp, m_s=8192, t_s=128):
             "seconds": t_solve + t_eig}, (b, se, m_s, t_s)
 
 
+def serving_run(g, torch, dev, local, count, load, seed_offset=0):
+    """Serving workload: n=2000, m=1e6 resident SNPs, Poisson stream of requests with
+    t_k ~ log-uniform[1, 2000] traits and SNP ranges of log-uniform length in [1e4, 1e6].
+
+    First all requests are submitted at once (saturation throughput); then the same
+    stream is replayed with Poisson arrivals at `load` x that throughput, and the
+    latency (submit -> done) percentiles are measured on the host clock.
+    """
+    from synth import BASE_SEED, serving_requests
+    n, m = 2000, 1_000_000
+    phi, XL = kinship(n), covariates(n, PM1)
+    XR = torch.from_numpy(genotypes(n, m, BASE_SEED + 100 + seed_offset)).to(dev)
+    reqs = serving_requests(count, m, BASE_SEED + seed_offset)
+    rng = np.random.default_rng(BASE_SEED + 7)
+    ypool = rng.standard_normal((4096, n))
+    hpool = rng.uniform(0.1, 0.9, 4096)
+    o = g.gwas_default_opts(precision=g.GWAS_MIXED, output=g.GWAS_OUT_LAST_SE, device=local)
+    ctx = g.gwas_setup(n, PM1, phi, XL, 1, hpool[:1], o)
+    try:
+        g.gwas_load_snps(ctx, m, XR, n)
+        del XR
+
+        def inputs(r):
+            off = r["seed"] % (4096 - r["t"])
+            return ypool[off:off + r["t"]], np.ascontiguousarray(hpool[off:off + r["t"]])
+
+        def run(arrivals, cap=32):
+            # at most `cap` requests outstanding (their outputs live in HBM); a request that
+            # arrives while the cap is reached waits on the client, and its latency counts
+            # from its arrival, not from its submission
+            t0 = time.perf_counter()
+            pending, lat, pairs = {}, [], 0
+            k = 0
+            while k < len(reqs) or pending:
+                now = time.perf_counter() - t0
+                while k < len(reqs) and arrivals[k] <= now and len(pending) < cap:
+                    r = reqs[k]
+                    Y, h2 = inputs(r)
+                    out = torch.empty((2, r["t"], r["i1"] - r["i0"]), dtype=torch.float32, device=dev)
+                    late = time.perf_counter() - t0 - arrivals[k]
+                    rid = g.gwas_submit(ctx, Y, r["t"], h2, r["i0"], r["i1"], out)
+                    pending[rid] = (out, r["t"] * (r["i1"] - r["i0"]), late)
+                    k += 1
+                for rid in list(pending):
+                    done, rc = g.gwas_poll(ctx, rid)
+                    if done:
+                        if rc not in (g.GWAS_OK, g.GWAS_ERR_SINGULAR_PAIRS):
+                            raise RuntimeError(f"request failed: {rc}")
+                        ts, _, td = g.gwas_request_times(ctx, rid)
+                        _, np_, late = pending.pop(rid)
+                        lat.append(td - ts + late)
+                        pairs += np_
+                nxt = arrivals[k] - (time.perf_counter() - t0) if k < len(reqs) else 0.0
+                time.sleep(min(max(nxt, 0.0), 0.0005))
+            return time.perf_counter() - t0, np.array(lat), pairs
+
+        span, _, total_pairs = run(np.zeros(len(reqs)))          # saturation: all at once
+        sat = total_pairs / span
+        mean_pairs = total_pairs / len(reqs)
+        rate = load * sat / mean_pairs                            # requests per second
+        gaps = np.random.default_rng(BASE_SEED + 9).exponential(1.0 / rate, len(reqs))
+        span2, lat, pairs2 = run(np.cumsum(gaps))
+    finally:
+        g.gwas_destroy(ctx)
+    return {"workload": f"n={n} p=4 m={m} resident, {len(reqs)} requests, t_k log-uniform[1,2000], "
+                        f"SNP ranges log-uniform[1e4,1e6], Poisson arrivals at {load:.2f} of saturation",
+            "saturated_pairs_per_s": sat, "pairs_per_s": pairs2 / span2, "offered_load": load,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "requests": len(reqs), "pairs": int(total_pairs)}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle, timed as it stands on the host cores."""
     if rank != 0:
@@ -250,6 +324,7 @@ def main():
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
+    last_sample = out[:, :128, :8192].cpu().numpy()
     ms_step = ev0.elapsed_time(ev1) / args.steps
     if world > 1:
         tt = torch.tensor([ms_step], device=dev)
@@ -338,11 +413,18 @@ def main():
                              "note": out_note + "; inputs from pinned host memory; wall clock around the C calls"}
             del hout
 
+    # ---------------------------------------------------------------- serving (continuous batching)
+    if args.serving_requests > 0 and rank == 0:
+        del inp_d, out
+        torch.cuda.empty_cache()
+        result["serving"] = serving_run(g, torch, dev, local, args.serving_requests, args.serving_load)
+        out = None
+
     # ---------------------------------------------------------------- CPU oracle and sampled error
     if not args.no_cpu and rank == 0:
         cb, (b, se, m_s, t_s) = cpu_baseline(n, inp_h)
         result["cpu_baseline"] = cb
-        got = out[:, :t_s, :m_s].cpu().numpy()
+        got = last_sample
         beta, s = got[0].T.astype(np.float64), got[1].T.astype(np.float64)
         bl = b[..., -1]
         err = np.abs(beta - bl) / np.maximum(np.abs(bl), se)

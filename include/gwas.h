@@ -155,6 +155,29 @@ typedef void (*gwas_block_fn)(void* user, int j0, int nb, const void* host_block
 GWAS_API int gwas_solve_stream(gwas_ctx* ctx, const double* Y, int64_t i0, int64_t i1, int block_traits,
                                void* host_buf0, void* host_buf1, gwas_block_fn fn, void* user);
 
+/*
+ * Serving (continuous batching).  gwas_submit queues a request: tk traits Y
+ * (n x tk, FP64) with their own heritabilities h2k, solved against the resident
+ * SNPs [i0, i1).  A scheduler thread of the context admits queued requests while
+ * their operands fit the serving arena in HBM, prepares them, and runs rounds of
+ * the fused kernel over work units of every admitted request, so requests that
+ * arrive while others run join the next round.  Results are the same as a
+ * separate gwas_solve of the request (the mixed path).  The caller's Y and h2k
+ * are copied before gwas_submit returns.  `out` (same layout as gwas_solve for
+ * tk traits and i1-i0 SNPs) must be device memory or page-locked host memory and
+ * must stay valid until the request has finished.  Requires GWAS_MIXED and
+ * loaded genotypes.  gwas_submit, gwas_poll and gwas_wait are safe to call from
+ * one host thread.
+ */
+GWAS_API int gwas_submit(gwas_ctx* ctx, const double* Y, int tk, const double* h2k, int64_t i0, int64_t i1, void* out,
+                         uint64_t* req_id);
+/* *done = 1 once the request has finished; returns its status (GWAS_OK, a warning or an error). */
+GWAS_API int gwas_poll(gwas_ctx* ctx, uint64_t req_id, int* done);
+/* Blocks until the request finishes or timeout_s (seconds; < 0: no limit) passes (GWAS_ERR_TIMEOUT). */
+GWAS_API int gwas_wait(gwas_ctx* ctx, uint64_t req_id, double timeout_s);
+/* Host steady-clock times (seconds) of a request's submission, admission and completion. */
+GWAS_API int gwas_request_times(gwas_ctx* ctx, uint64_t req_id, double* t_submit, double* t_admit, double* t_done);
+
 /* Replace the t heritabilities given at setup (same t). */
 GWAS_API int gwas_set_h2(gwas_ctx* ctx, int t, const double* h2);
 

@@ -81,6 +81,15 @@ def _load():
     lib.gwas_solve_fp64_noalloc.restype = ci
     lib.gwas_solve_stream.argtypes = [vp, vp, i64, i64, ci, vp, vp, GWAS_BLOCK_FN, vp]
     lib.gwas_solve_stream.restype = ci
+    lib.gwas_submit.argtypes = [vp, vp, ci, vp, i64, i64, vp, C.POINTER(C.c_uint64)]
+    lib.gwas_submit.restype = ci
+    lib.gwas_poll.argtypes = [vp, C.c_uint64, C.POINTER(ci)]
+    lib.gwas_poll.restype = ci
+    lib.gwas_wait.argtypes = [vp, C.c_uint64, C.c_double]
+    lib.gwas_wait.restype = ci
+    lib.gwas_request_times.argtypes = [vp, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]
+    lib.gwas_request_times.restype = ci
     lib.gwas_destroy.argtypes = [vp]
     lib.gwas_destroy.restype = None
     return lib
@@ -179,6 +188,32 @@ def gwas_solve_stream(ctx, Y, i0, i1, block_traits, buf0, buf1, fn):
     rc = lib.gwas_solve_stream(ctx, _addr(Y, np.float64, None, "Y"), int(i0), int(i1), int(block_traits),
                                _addr(buf0, dt, None, "buf0"), _addr(buf1, dt, None, "buf1"), cb, None)
     return _check(rc, ctx, allow=(GWAS_ERR_SINGULAR_PAIRS,))
+
+
+def gwas_submit(ctx, Y, tk, h2k, i0, i1, out) -> int:
+    """Queue a serving request (see include/gwas.h); returns its id."""
+    rid = C.c_uint64()
+    dt = np.float64 if getattr(out, "dtype", None) in (np.float64, getattr(_torch(), "float64", None)) else np.float32
+    _check(lib.gwas_submit(ctx, _addr(Y, np.float64, None, "Y"), int(tk), _addr(h2k, np.float64, (tk,), "h2k"),
+                           int(i0), int(i1), _addr(out, dt, None, "out"), C.byref(rid)), ctx)
+    return rid.value
+
+
+def gwas_poll(ctx, req_id):
+    """(done, status) of a serving request."""
+    done = C.c_int()
+    rc = lib.gwas_poll(ctx, req_id, C.byref(done))
+    return bool(done.value), rc
+
+
+def gwas_wait(ctx, req_id, timeout_s=-1.0) -> int:
+    return _check(lib.gwas_wait(ctx, req_id, float(timeout_s)), ctx, allow=(GWAS_ERR_SINGULAR_PAIRS,))
+
+
+def gwas_request_times(ctx, req_id):
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(lib.gwas_request_times(ctx, req_id, C.byref(a), C.byref(b), C.byref(c)), ctx)
+    return a.value, b.value, c.value
 
 
 def gwas_set_h2(ctx, t, h2):

@@ -169,6 +169,7 @@ static void destroy_impl(gwas_ctx* c) {
   int dev;
   bool have = cudaGetDevice(&dev) == cudaSuccess;
   cudaSetDevice(c->device);
+  serve_shutdown(c);
   if (c->stream) cudaStreamSynchronize(c->stream);
   prof_flush(c);
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
@@ -373,6 +374,8 @@ extern "C" int gwas_load_snps(gwas_ctx* c, int64_t m, const int8_t* XR) {
   if (m < 1 || !XR) return ctx_fail(c, GWAS_ERR_ARG, "m must be >= 1 and XR non-NULL");
   DeviceGuard guard(c->device);
   int rc = GWAS_OK;
+  if (serve_busy(c)) return ctx_fail(c, GWAS_ERR_STATE, "gwas_load_snps while serving requests are pending");
+  serve_shutdown(c);
   // drop previous genotypes
   ctx_free(c, c->Xt);
   c->Xt = nullptr;

@@ -38,15 +38,19 @@
 
 namespace {
 
+// K extent of one stage: 64 bf16 = one 128-byte swizzled row.  (32-wide stages with
+// the 64-byte swizzle and a 6-slot ring measured 1.6x slower: twice the TMA boxes
+// and barrier round trips per MMA.)
 constexpr int BM = 128, TT = 32, BK = 64;
+constexpr int ROWB = BK * 2;                         // bytes per operand row of a stage
 constexpr int PM1 = 3;
-constexpr int G_BYTES = BM * BK * 2;                 // 16 KB: one A tile
+constexpr int G_BYTES = BM * ROWB;                   // 8 KB: one A tile
 constexpr int B1_ROWS = 10 * TT, B2_ROWS = 4 * TT;   // 320 and 128 rows per trait tile
 constexpr int BBOX = 32;                             // rows per TMA box of the trait operands
 constexpr int SLOT = 64 * 1024;                      // a ring slot holds either half-stage
 constexpr int SLOTS = 3;
-constexpr int H1_BYTES = G_BYTES + B1_ROWS * BK * 2; // 57344
-constexpr int H2_BYTES = 3 * G_BYTES + B2_ROWS * BK * 2;  // 65536
+constexpr int H1_BYTES = G_BYTES + B1_ROWS * ROWB;   // 57344
+constexpr int H2_BYTES = 3 * G_BYTES + B2_ROWS * ROWB;  // 65536
 constexpr int CST_BYTES = TT * FUSED_CST * 4;          // per-trait constants of one tile
 constexpr int SMEM_BYTES = SLOTS * SLOT + 2 * CST_BYTES + 1024 + 512;
 constexpr int TMEM_COLS = 512;
@@ -64,7 +68,7 @@ __device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us,
   us = g0 + w % gs;
 }
 
-template <int CS, int CT, int EPW>
+template <int CS, int CT, int EPW, bool SERVE>
 __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     fused_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapA2,
                  const __grid_constant__ CUtensorMap mapB1, const __grid_constant__ CUtensorMap mapB2, FusedArgs a) {
@@ -94,7 +98,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   for (int k = 0; k < CT; ++k) maskA |= (uint16_t)(1u << (sr + CS * k));
 #pragma unroll
   for (int k = 0; k < CS; ++k) maskB |= (uint16_t)(1u << (CS * tr + k));
-  const int nsuper = ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
+  const int nsuper = SERVE ? a.nunits : ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
   const int nkb = a.Kpad / BK;
   if (threadIdx.x == 0) {
     for (int s = 0; s < SLOTS; ++s) {
@@ -123,10 +127,17 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       uint32_t h = 0;  // half-stage counter
       bool ok = true;
       for (int u = cid; u < nsuper && ok; u += ncl) {
-        int us, ut;
-        super_coords<CS, CT>(u, a, us, ut);
-        const int row = (int)a.row0 + (us * CS + sr) * BM + tr * AROWS;
-        const int tt = ut * CT + tr;
+        int row, tt;
+        if (SERVE) {
+          const int4 w = a.units[u];
+          row = w.x + tr * AROWS;
+          tt = w.y;
+        } else {
+          int us, ut;
+          super_coords<CS, CT>(u, a, us, ut);
+          row = (int)a.row0 + (us * CS + sr) * BM + tr * AROWS;
+          tt = ut * CT + tr;
+        }
         for (int kb = 0; kb < nkb && ok; ++kb) {
           for (int half = 0; half < 2; ++half, ++h) {
             const uint32_t s = h % SLOTS;
@@ -135,12 +146,12 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             const int x = kb * BK;
             if (half == 0) {
               tc::mbar_expect_tx(&full[s], H1_BYTES);
-              if (CT > 1) tc::tma_load_2d_mc(buf + tr * AROWS * 128, &mapG, &full[s], x, row, maskA);
+              if (CT > 1) tc::tma_load_2d_mc(buf + tr * AROWS * ROWB, &mapG, &full[s], x, row, maskA);
               else tc::tma_load_2d(buf, &mapG, &full[s], x, row);
 #pragma unroll
               for (int q = 0; q < B1_BOXES; ++q) {
                 const int r = (sr * B1_BOXES + q) * BBOX;
-                uint8_t* dst = buf + G_BYTES + r * 128;
+                uint8_t* dst = buf + G_BYTES + r * ROWB;
                 if (CS > 1) tc::tma_load_2d_mc(dst, &mapB1, &full[s], x, tt * B1_ROWS + r, maskB);
                 else tc::tma_load_2d(dst, &mapB1, &full[s], x, tt * B1_ROWS + r);
               }
@@ -148,14 +159,14 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               tc::mbar_expect_tx(&full[s], H2_BYTES);
 #pragma unroll
               for (int p = 0; p < 3; ++p) {
-                uint8_t* dst = buf + p * G_BYTES + tr * AROWS * 128;
+                uint8_t* dst = buf + p * G_BYTES + tr * AROWS * ROWB;
                 if (CT > 1) tc::tma_load_2d_mc(dst, &mapA2, &full[s], x, (int)(p * a.mpad) + row, maskA);
                 else tc::tma_load_2d(dst, &mapA2, &full[s], x, (int)(p * a.mpad) + row);
               }
 #pragma unroll
               for (int q = 0; q < B2_BOXES; ++q) {
                 const int r = (sr * B2_BOXES + q) * BBOX;
-                uint8_t* dst = buf + 3 * G_BYTES + r * 128;
+                uint8_t* dst = buf + 3 * G_BYTES + r * ROWB;
                 if (CS > 1) tc::tma_load_2d_mc(dst, &mapB2, &full[s], x, tt * B2_ROWS + r, maskB);
                 else tc::tma_load_2d(dst, &mapB2, &full[s], x, tt * B2_ROWS + r);
               }
@@ -193,7 +204,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               for (int k = 0; k < BK / 16; ++k) {
                 const uint32_t acc = (kb | k) ? 1u : 0u;
                 tc::mma_bf16(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), id256, acc);
-                tc::mma_bf16(tbase + 8 * TT, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, 8 * TT * 128 + k * 32),
+                tc::mma_bf16(tbase + 8 * TT, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, 8 * TT * ROWB + k * 32),
                              id64, acc);
               }
             } else {
@@ -203,11 +214,11 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               for (int k = 0; k < BK / 16; ++k) {
                 const uint32_t acc = (kb | k) ? 1u : 0u;
                 // A1 x [E1 | E2 | E3s] -> [level 0 | a | b]
-                tc::mma_bf16(tbase + 10 * TT, tc::sdesc_add(d1, k * 32), tc::sdesc_add(de, TT * 128 + k * 32), id96, acc);
+                tc::mma_bf16(tbase + 10 * TT, tc::sdesc_add(d1, k * 32), tc::sdesc_add(de, TT * ROWB + k * 32), id96, acc);
                 // A2 x [E2s | E1] -> [a | b]
                 tc::mma_bf16(tbase + 11 * TT, tc::sdesc_add(d2, k * 32), tc::sdesc_add(de, k * 32), id64, 1u);
                 // A3s x E1 -> a
-                tc::mma_bf16(tbase + 11 * TT, tc::sdesc_add(d3, k * 32), tc::sdesc_add(de, TT * 128 + k * 32), id32, 1u);
+                tc::mma_bf16(tbase + 11 * TT, tc::sdesc_add(d3, k * 32), tc::sdesc_add(de, TT * ROWB + k * 32), id32, 1u);
               }
             }
             if (NC > 1) tc::mma_commit_mc(&empty[s], release);
@@ -228,27 +239,45 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     uint32_t tcount = 0;
     unsigned long long nsing = 0;
     for (int u = cid; u < nsuper; u += ncl, ++tcount) {
-      int us, ut;
-      super_coords<CS, CT>(u, a, us, ut);
-      const int st = us * CS + sr, tt = ut * CT + tr;
+      // this tile's SNPs [snp0, snp0+128) (valid below snp_end), output origin and stride,
+      // first trait (jbase) within its request, constants and output arrays
+      int64_t snp0, snp_end, oi0, ldo;
+      int ntrait, jbase, full_b;
+      const float* cst_tile;
+      float *obeta, *ose;
+      double* ob64;
+      unsigned long long* sing_ctr;
+      if (SERVE) {
+        const int4 w = a.units[u];
+        const ServeDesc rd = a.reqs[w.z];
+        snp0 = w.x; snp_end = rd.i1; oi0 = rd.i0; ldo = rd.ldo; ntrait = rd.ntrait; jbase = w.w * TT;
+        full_b = rd.full_b; cst_tile = a.cst + (size_t)w.y * TT * FUSED_CST;
+        obeta = rd.beta; ose = rd.se; ob64 = rd.b64; sing_ctr = rd.singular;
+      } else {
+        int us, ut;
+        super_coords<CS, CT>(u, a, us, ut);
+        const int st = us * CS + sr, tt = ut * CT + tr;
+        snp0 = a.row0 + (int64_t)st * BM; snp_end = a.row0 + a.nsnp; oi0 = a.i0; ldo = a.ldo; ntrait = a.ntrait;
+        jbase = tt * TT; full_b = a.full_b; cst_tile = a.cst + (size_t)jbase * FUSED_CST;
+        obeta = a.out_beta; ose = a.out_se; ob64 = a.out_b64; sing_ctr = nullptr;
+      }
       // stage this tile's per-trait constants (double buffer: the barrier of the previous
       // tile guarantees every epilogue warp has finished reading this buffer)
       float* cs = cst_smem + (tcount & 1) * TT * FUSED_CST;
-      for (int e = ew * 32 + lane; e < TT * FUSED_CST; e += EPW * 32) {
-        const int jj = tt * TT + e / FUSED_CST;
-        cs[e] = jj < a.ntrait ? a.cst[(size_t)jj * FUSED_CST + e % FUSED_CST] : 0.f;
-      }
+      for (int e = ew * 32 + lane; e < TT * FUSED_CST; e += EPW * 32)
+        cs[e] = jbase + e / FUSED_CST < ntrait ? cst_tile[e] : 0.f;
       tc::named_sync(1, EPW * 32);
       const bool ok = tc::mbar_wait(acc_full, tcount & 1, a.status, abort);
       tc::fence_after();
-      const int64_t i = (int64_t)st * BM + q * 32 + lane;   // SNP index relative to row0
-      const bool valid_i = ok && st < a.n_stiles && i < a.nsnp;
-      const float sA = valid_i ? a.sA[a.row0 + i] : 0.f;
+      const int64_t snp = snp0 + q * 32 + lane;
+      const bool valid_i = ok && snp < snp_end;
+      const float sA = valid_i ? a.sA[snp] : 0.f;
       float ac[PM1] = {0.f, 0.f, 0.f};
-      if (valid_i && a.full_b) {
+      if (valid_i && full_b) {
 #pragma unroll
-        for (int c = 0; c < PM1; ++c) ac[c] = a.acoef[(a.row0 + i) * PM1 + c];
+        for (int c = 0; c < PM1; ++c) ac[c] = a.acoef[snp * PM1 + c];
       }
+      unsigned long long tsing = 0;
       for (int j0 = jbeg; j0 < jbeg + JPW; j0 += 4) {
         uint32_t hw[4], hz[3][4], lw[4], lz[3][4], w3[4], w4[4], d0[4], da[4], db[4];
         tc::tmem_ld4(lane_base + 0 * TT + j0, hw);
@@ -277,8 +306,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int jl = j0 + v;
-          const int jj = tt * TT + jl;          // trait index within the block
-          if (jj >= a.ntrait) break;
+          const int jj = jbase + jl;            // trait index within the block (request)
+          if (jj >= ntrait) break;
           const float* cj = cs + jl * FUSED_CST;
           const float F = 1.f / 256.f;
           const float num = cj[0] * fmaf(F, fmaf(F, fmaf(F, __uint_as_float(w4[v]), __uint_as_float(w3[v])),
@@ -295,16 +324,16 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
           const bool sing = !(delta > 1e-6f * s) || !(sA > 0.f);
           if (sing) {
             beta = se = __int_as_float(0x7fc00000);
-            ++nsing;
+            ++tsing;
           } else {
             const float inv = __frcp_rn(delta);
             beta = num * inv;
             const float rss = fmaxf(fmaf(-num, beta, cj[5]), 0.f);
             se = __fsqrt_rn(rss * inv * inv_dof);
           }
-          const int64_t o = (int64_t)jj * a.ldo + (a.row0 + i - a.i0);
-          if (a.full_b) {
-            double* ob = a.out_b64 + o * (PM1 + 1);
+          const int64_t o = (int64_t)jj * ldo + (snp - oi0);
+          if (full_b) {
+            double* ob = ob64 + o * (PM1 + 1);
 #pragma unroll
             for (int c = 0; c < PM1; ++c) {
               // beta_L = g - L^-T z beta - a_i beta
@@ -316,11 +345,17 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             }
             ob[PM1] = (double)beta;
           } else {
-            a.out_beta[o] = beta;
-            a.out_se[o] = se;
+            obeta[o] = beta;
+            ose[o] = se;
           }
         }
       }
+      if (SERVE && sing_ctr) {
+        unsigned long long v = tsing;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && v) atomicAdd(sing_ctr, v);
+      }
+      nsing += tsing;
     }
     // warp-aggregated count of singular pairs
     for (int o = 16; o > 0; o >>= 1) nsing += __shfl_xor_sync(0xffffffffu, nsing, o);
@@ -345,11 +380,11 @@ Shape shape_from_env() {
   return sh;
 }
 
-template <int CS, int CT, int EPW>
+template <int CS, int CT, int EPW, bool SERVE = false>
 int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const CUtensorMap& ma,
                  const CUtensorMap& m1, const CUtensorMap& m2) {
   constexpr int NC = CS * CT;
-  auto kern = fused_kernel<CS, CT, EPW>;
+  auto kern = fused_kernel<CS, CT, EPW, SERVE>;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
@@ -373,11 +408,11 @@ int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const C
   int maxc = 0;
   if (cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg) == cudaSuccess && maxc > 0) nclusters = maxc;
   cudaGetLastError();
-  const int nsuper = ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
+  const int nsuper = SERVE ? a.nunits : ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
   nclusters = std::min(nclusters, nsuper);
   if (a.max_ctas > 0) nclusters = std::max(1, std::min(nclusters, a.max_ctas / NC));
   cfg.gridDim = dim3(nclusters * NC);
-  ProfScope ps(c, "fused");
+  ProfScope ps(c, SERVE ? "fused_serve" : "fused");
   cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mg, ma, m1, m2, a);
   c->launches++;
   if (e != cudaSuccess) {
@@ -398,9 +433,10 @@ int launch_fused(gwas_ctx* c, const FusedArgs& args, const __nv_bfloat16* G, con
   const Shape sh = shape_from_env();
   const int ttiles_pad = (a.n_ttiles + 3) / 4 * 4;   // trait operands are allocated for a multiple of 4 tiles
   CUtensorMap mg, ma, m1, m2;
-  if (!make_bf16_map(&mg, G, a.mpad, a.Kpad, BM / sh.ct) || !make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM / sh.ct) ||
-      !make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * B1_ROWS, a.Kpad, BBOX) ||
-      !make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * B2_ROWS, a.Kpad, BBOX))
+  if (!make_bf16_map(&mg, G, a.mpad, a.Kpad, BM / sh.ct, BK) ||
+      !make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM / sh.ct, BK) ||
+      !make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * B1_ROWS, a.Kpad, BBOX, BK) ||
+      !make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * B2_ROWS, a.Kpad, BBOX, BK))
     return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
 #define GWAS_SHAPE(CS, CT, EPW) \
   if (sh.cs == CS && sh.ct == CT && sh.epw == EPW) return launch_shape<CS, CT, EPW>(c, a, mg, ma, m1, m2);
@@ -413,4 +449,15 @@ int launch_fused(gwas_ctx* c, const FusedArgs& args, const __nv_bfloat16* G, con
   GWAS_SHAPE(2, 2, 16)
 #undef GWAS_SHAPE
   return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: cluster shape not instantiated");
+}
+
+int launch_fused_serve(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
+                       const __nv_bfloat16* B1, const __nv_bfloat16* B2, int b_tiles) {
+  if (a.nunits == 0) return GWAS_OK;
+  CUtensorMap mg, ma, m1, m2;
+  if (!make_bf16_map(&mg, G, a.mpad, a.Kpad, BM) || !make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM) ||
+      !make_bf16_map(&m1, B1, (uint64_t)b_tiles * B1_ROWS, a.Kpad, BBOX) ||
+      !make_bf16_map(&m2, B2, (uint64_t)b_tiles * B2_ROWS, a.Kpad, BBOX))
+    return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
+  return launch_shape<1, 1, 16, true>(c, a, mg, ma, m1, m2);
 }

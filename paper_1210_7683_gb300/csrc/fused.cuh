@@ -11,6 +11,18 @@ struct gwas_ctx;
 //   [6..8] g = S_TL^-1 b_T, [9..17] L^-T (row-major), used for the full coefficient vector.
 #define FUSED_CST 20
 
+// Serving mode: one request of the work list (fused.cu, serve.cu).
+struct ServeDesc {
+  int64_t i0, i1;     // SNP range of the request
+  int64_t ldo;        // output stride between traits (= i1 - i0)
+  int ntrait;         // traits of the request
+  int full_b;
+  float* beta;        // LAST_SE outputs (device or page-locked host memory)
+  float* se;
+  double* b64;        // FULL_B output
+  unsigned long long* singular;  // per-request singular-pair counter
+};
+
 struct FusedArgs {
   int64_t row0;       // first SNP (row of G and of the x'_c^2 planes) of the range
   int64_t i0;         // SNP index that maps to output column 0
@@ -33,6 +45,10 @@ struct FusedArgs {
   unsigned long long* status;    // [0] <- 1 when a bounded wait expires
   unsigned long long* singular;  // singular-pair counter
   int max_ctas;       // 0 = one CTA per SM
+  // serving mode: work units {first SNP row of the tile, trait-tile slot, request, request-local trait tile}
+  const int4* units;
+  int nunits;
+  const ServeDesc* reqs;
 };
 
 // Trait operands (B1, B2) must be allocated (and zeroed) for a multiple of this many trait tiles.
@@ -40,3 +56,7 @@ int fused_trait_tile_multiple();
 
 int launch_fused(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2);
+// Serving mode: processes a.units (a.cst indexed by trait-tile slot) with per-request outputs.
+// b_tiles = trait-tile slots of the B1/B2 arena.
+int launch_fused_serve(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
+                       const __nv_bfloat16* B1, const __nv_bfloat16* B2, int b_tiles);

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of the GWAS library.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <map>
@@ -18,6 +19,7 @@ struct DevBuf {
 };
 
 struct MixedState;  // mixed-precision resident data (mixed.cu)
+struct ServeState;  // serving scheduler (serve.cu)
 
 // A kernel launch bracketed by two events on the context's stream (profiling mode).
 struct ProfPending {
@@ -49,6 +51,7 @@ struct gwas_ctx {
   int64_t m = 0;
   double* Xt = nullptr;        // FP64 path: [m][n] rotated genotypes
   MixedState* mixed = nullptr; // mixed path state
+  ServeState* serve = nullptr; // serving scheduler, started by the first gwas_submit
 
   // device status words: [0] timeout flag, [1..2] singular-pair counter (u64)
   unsigned long long* d_status = nullptr;
@@ -101,7 +104,21 @@ int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m);  // genotypes already
 struct MixedWs;  // work buffers of one gwas_solve call (mixed.cu)
 int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** ws);
 void mixed_ws_free(gwas_ctx* c, MixedWs* ws);
+// Enqueues the per-trait operands of traits [0, tb) of dY (heritabilities h2, device) into
+// trait tiles slot[j/32] (identity when slot is NULL) of the operand arrays B1, B2, cst.
+int mixed_prep_traits(gwas_ctx* c, MixedWs* ws, const double* dY, const double* h2, int tb, __nv_bfloat16* B1,
+                      __nv_bfloat16* B2, float* cst, const int* slot);
 // Enqueues (no synchronisation) the solve of traits [j0, j0+tb) x SNPs [i0, i1) into dout.
 int mixed_solve_block(gwas_ctx* c, MixedWs* ws, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
                       void* dout);
 void mixed_free(gwas_ctx* c);
+// resident mixed-path data (for the serving kernel launches)
+int64_t mixed_mpad(gwas_ctx* c);
+const float* mixed_sA(gwas_ctx* c);
+const float* mixed_acoef(gwas_ctx* c);
+const __nv_bfloat16* mixed_G(gwas_ctx* c);
+const __nv_bfloat16* mixed_A2(gwas_ctx* c);
+
+// ---------------------------------------------------------------- serving (serve.cu)
+void serve_shutdown(gwas_ctx* c);  // stops the scheduler thread and frees its memory
+int serve_busy(gwas_ctx* c);       // requests queued or running

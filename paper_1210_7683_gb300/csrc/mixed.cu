@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
                                                          const double* __restrict__ h2, const double* __restrict__ lam,
                                                          const double* __restrict__ XLt, int n, int Kpad,
                                                          double* __restrict__ Wt, __nv_bfloat16* __restrict__ B2,
-                                                         float* __restrict__ cst) {
+                                                         float* __restrict__ cst, const int* __restrict__ slot) {
   const int j = blockIdx.x;
   const double h = h2[j];
   const double* y = Yt + (size_t)j * ldy;
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
   const double se = sh_se, inv_se = 1.0 / se;
   double rr = 0;
   const int p = PM1 + 1;
-  const int tile = j / TT, jj = j % TT;
+  const int tile = slot ? slot[j / TT] : j / TT, jj = j % TT;
   __nv_bfloat16* b2 = B2 + (size_t)tile * B2_ROWS * Kpad;
   for (int k = threadIdx.x; k < Kpad; k += blockDim.x) {
     double w = 0, v[PM1] = {0, 0, 0};
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
   if (threadIdx.x == 0) {
     double v = 0;
     for (int w = 0; w < nw; ++w) v += red[w][0];
-    float* cj = cst + (size_t)j * FUSED_CST;
+    float* cj = cst + ((size_t)tile * TT + jj) * FUSED_CST;
     cj[4] = (float)se;
     cj[5] = (float)v;
     for (int a = 0; a < PM1; ++a) cj[6 + a] = (float)sh_g[a];
@@ -297,13 +297,14 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
 // fixed-point slices in the C1 operand layout (w: 4 slices, v: 2 slices).
 __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__ W, const double* __restrict__ XL,
                                                       const double* __restrict__ XtXinv, int n, int Kpad,
-                                                      __nv_bfloat16* __restrict__ B1, float* __restrict__ cst) {
+                                                      __nv_bfloat16* __restrict__ B1, float* __restrict__ cst,
+                                                      const int* __restrict__ slot) {
   const int j = blockIdx.x;
   const int p = PM1 + 1;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   __shared__ double red[8][PM1 + 1];
   __shared__ double coef[PM1], smax;
-  const int tile = j / TT, jj = j % TT;
+  const int tile = slot ? slot[j / TT] : j / TT, jj = j % TT;
   __nv_bfloat16* b1 = B1 + (size_t)tile * B1_ROWS * Kpad;
   for (int c = 0; c < p; ++c) {
     const double* col = W + ((size_t)j * p + c) * Kpad;
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__
       double v = 0;
       for (int w = 0; w < nw; ++w) v = fmax(v, red[w][PM1]);
       smax = v > 0 ? v / 256.0 : 1.0;
-      cst[(size_t)j * FUSED_CST + (c == 0 ? 0 : c)] = (float)smax;
+      cst[((size_t)tile * TT + jj) * FUSED_CST + (c == 0 ? 0 : c)] = (float)smax;
     }
     __syncthreads();
     const double inv = 1.0 / smax;
@@ -366,6 +367,12 @@ __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__
 }
 
 }  // namespace
+
+int64_t mixed_mpad(gwas_ctx* c) { return c->mixed ? c->mixed->mpad : 0; }
+const float* mixed_sA(gwas_ctx* c) { return c->mixed ? c->mixed->sA : nullptr; }
+const float* mixed_acoef(gwas_ctx* c) { return c->mixed ? c->mixed->acoef : nullptr; }
+const __nv_bfloat16* mixed_G(gwas_ctx* c) { return c->mixed ? c->mixed->G : nullptr; }
+const __nv_bfloat16* mixed_A2(gwas_ctx* c) { return c->mixed ? c->mixed->A2 : nullptr; }
 
 void mixed_free(gwas_ctx* c) {
   MixedState* s = c->mixed;
@@ -535,22 +542,16 @@ int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** out) {
   return GWAS_OK;
 }
 
-int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
-                      void* out) {
+int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h2, int tb, __nv_bfloat16* B1,
+                      __nv_bfloat16* B2, float* cst, const int* slot) {
   MixedState* s = c->mixed;
   if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
   if (tb > w->tb_max) return ctx_fail(c, GWAS_ERR_ARG, "trait block larger than its workspace");
   const int n = c->n, p = PM1 + 1, Kpad = s->Kpad;
-  const int nt_tiles = (tb + TT - 1) / TT;
-  const int nt_alloc = (nt_tiles + fused_trait_tile_multiple() - 1) / fused_trait_tile_multiple() *
-                       fused_trait_tile_multiple();
   const int rowsY = (int)rup(tb, 128), rowsW = (int)rup((int64_t)tb * p, 128);
   int rc = GWAS_OK;
-  __nv_bfloat16 *Ysl = w->Ysl, *Wsl = w->Wsl, *B1 = w->B1, *B2 = w->B2;
+  __nv_bfloat16 *Ysl = w->Ysl, *Wsl = w->Wsl;
   double *sY = w->sY, *Yt = w->Yt, *Wt = w->Wt, *sW = w->sW;
-  float* cst = w->cst;
-  cudaMemsetAsync(B1, 0, 2ull * nt_alloc * B1_ROWS * Kpad, c->stream);
-  cudaMemsetAsync(B2, 0, 2ull * nt_alloc * B2_ROWS * Kpad, c->stream);
   // Y' := Z^T Y (Algorithm 5, gemm) as an exact sliced GEMM
   launch_slice_rows(c, dY, n, tb, n, rowsY, Kpad, 4, s->bits, Ysl, sY);
   XgemmArgs g{};
@@ -569,7 +570,7 @@ int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb,
   if ((rc = launch_xgemm(c, 4, 4, 3, g, Ysl, s->Bzt)) == GWAS_OK) {
     // per-trait algebra and the C2 operand
     ProfScope ps(c, "prep_traits");
-    prep_mixed_kernel<<<tb, 256, 0, c->stream>>>(Yt, Kpad, c->h2 + j0, c->lam, c->XLt, n, Kpad, Wt, B2, cst);
+    prep_mixed_kernel<<<tb, 256, 0, c->stream>>>(Yt, Kpad, h2, c->lam, c->XLt, n, Kpad, Wt, B2, cst, slot);
     c->launches++;
     // back-rotation [w | v] = Z [e.r' | (e.X'_L) L^-T]
     launch_slice_rows(c, Wt, Kpad, tb * p, n, rowsW, Kpad, 4, s->bits, Wsl, sW);
@@ -584,9 +585,29 @@ int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb,
     rc = launch_xgemm(c, 4, 4, 3, b, Wsl, s->Bz);
   }
   if (rc == GWAS_OK) {
-    { ProfScope ps(c, "pack_trait_columns");
-    pack_c1_kernel<<<tb, 256, 0, c->stream>>>(Wt, c->XL, s->XtXinv, n, Kpad, B1, cst);
-    c->launches++; }
+    ProfScope ps(c, "pack_trait_columns");
+    pack_c1_kernel<<<tb, 256, 0, c->stream>>>(Wt, c->XL, s->XtXinv, n, Kpad, B1, cst, slot);
+    c->launches++;
+  }
+  return rc;
+}
+
+int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
+                      void* out) {
+  MixedState* s = c->mixed;
+  if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
+  if (tb > w->tb_max) return ctx_fail(c, GWAS_ERR_ARG, "trait block larger than its workspace");
+  const int n = c->n, p = PM1 + 1, Kpad = s->Kpad;
+  const int nt_tiles = (tb + TT - 1) / TT;
+  const int nt_alloc = (nt_tiles + fused_trait_tile_multiple() - 1) / fused_trait_tile_multiple() *
+                       fused_trait_tile_multiple();
+  int rc = GWAS_OK;
+  __nv_bfloat16 *B1 = w->B1, *B2 = w->B2;
+  float* cst = w->cst;
+  cudaMemsetAsync(B1, 0, 2ull * nt_alloc * B1_ROWS * Kpad, c->stream);
+  cudaMemsetAsync(B2, 0, 2ull * nt_alloc * B2_ROWS * Kpad, c->stream);
+  rc = mixed_prep_traits(c, w, dY, c->h2 + j0, tb, B1, B2, cst, nullptr);
+  if (rc == GWAS_OK) {
     FusedArgs a{};
     a.row0 = i0;
     a.i0 = i0;
@@ -599,6 +620,7 @@ int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb,
     a.Kpad = Kpad;
     a.mpad = s->mpad;
     a.dof = (float)(n - p);
+    (void)n;
     a.sA = s->sA;
     a.acoef = s->acoef;
     a.cst = cst;

@@ -96,6 +96,16 @@ __device__ __forceinline__ uint64_t sdesc_sw128(const void* p) {
   d |= (uint64_t)2 << 61;                  // 128-byte swizzle
   return d;
 }
+// Same for a tile with the 64-byte swizzle (rows of 32 bf16): 8-row groups of 8 x 64 B.
+__device__ __forceinline__ uint64_t sdesc_sw64(const void* p) {
+  const uint64_t a = smem_u32(p);
+  uint64_t d = (a & 0x3FFFFull) >> 4;
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;                  // 64-byte swizzle
+  return d;
+}
 // Advance a descriptor by `bytes` along K inside the swizzle atom (multiple of 32 B).
 __device__ __forceinline__ uint64_t sdesc_add(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
 
@@ -185,5 +195,6 @@ __device__ __forceinline__ void reg_fence(uint32_t (&r)[8]) {
 }  // namespace tc
 
 // Host: build a 2-D tensor map of a row-major bf16 matrix [rows][cols] (cols contiguous)
-// with a box of box_rows x 64 elements and the 128-byte swizzle.  Returns false on failure.
-bool make_bf16_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows);
+// with a box of box_rows x box_cols elements (64: 128-byte swizzle, 32: 64-byte swizzle).
+bool make_bf16_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows,
+                   uint32_t box_cols = 64);
