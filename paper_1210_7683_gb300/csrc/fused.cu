@@ -46,6 +46,7 @@ constexpr int ROWB = BK * 2;                         // bytes per operand row of
 constexpr int PM1 = 3;
 constexpr int G_BYTES = BM * ROWB;                   // 8 KB: one A tile
 constexpr int B1_ROWS = 10 * TT, B2_ROWS = 4 * TT;   // 320 and 128 rows per trait tile
+constexpr int B2_ROWS_PAIR = 6 * TT;                  // 192: C2 rows of a trait tile in the pair layout
 constexpr int BBOX = 32;                             // rows per TMA box of the trait operands
 constexpr int SLOT = 64 * 1024;                      // a ring slot holds either half-stage
 constexpr int SLOTS = 3;
@@ -68,14 +69,24 @@ __device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us,
   us = g0 + w % gs;
 }
 
-template <int CS, int CT, int EPW, bool SERVE>
+// PAIR: the two CTAs of a cluster issue one M = 256 MMA (cta_group::2); each holds its
+// own 128 SNP rows and half of every MMA's trait rows (B2_ROWS_PAIR layout), the leader
+// (rank 0) issues the MMAs, and both CTAs' loads complete on the leader's barriers.
+template <int CS, int CT, int EPW, bool SERVE, bool PAIR>
 __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     fused_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapA2,
                  const __grid_constant__ CUtensorMap mapB1, const __grid_constant__ CUtensorMap mapB2, FusedArgs a) {
   constexpr int NC = CS * CT;
   constexpr int AROWS = BM / CT;                    // genotype rows this CTA loads per plane
-  constexpr int B1_BOXES = B1_ROWS / BBOX / CS, B2_BOXES = B2_ROWS / BBOX / CS;
+  static_assert(!PAIR || (CS == 2 && CT == 1 && !SERVE), "pair mode is a 2 x 1 cluster");
+  constexpr int C1_ROWS = PAIR ? B1_ROWS / 2 : B1_ROWS;       // trait rows in this CTA's C1 region
+  constexpr int C2_ROWS = PAIR ? B2_ROWS_PAIR / 2 : B2_ROWS;  // and in its C2 region
+  constexpr int B2_TILE = PAIR ? B2_ROWS_PAIR : B2_ROWS;      // rows per trait tile of the B2 layout
+  constexpr int B1_BOXES = PAIR ? C1_ROWS / BBOX : B1_ROWS / BBOX / CS;
+  constexpr int B2_BOXES = PAIR ? C2_ROWS / BBOX : B2_ROWS / BBOX / CS;
+  constexpr uint32_t H1 = G_BYTES + C1_ROWS * ROWB, H2 = 3 * G_BYTES + C2_ROWS * ROWB;
   static_assert(B1_ROWS % (BBOX * CS) == 0 && B2_ROWS % (BBOX * CS) == 0 && BM % (8 * CT) == 0, "cluster shape");
+  static_assert(C1_ROWS % BBOX == 0 && C2_ROWS % BBOX == 0, "pair layout");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* cst_smem = (float*)(smem + SLOTS * SLOT);      // [2][TT][FUSED_CST], double-buffered by tile
@@ -103,19 +114,23 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < SLOTS; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], CS + CT - 1);
+      tc::mbar_init(&empty[s], PAIR ? 1 : CS + CT - 1);
     }
     tc::mbar_init(acc_full, 1);
-    tc::mbar_init(acc_empty, EPW);
+    tc::mbar_init(acc_empty, PAIR ? 2 * EPW : EPW);
     *abort = 0;
     tc::fence_mbar_init();
   }
-  if (warp == 1) tc::tmem_alloc(tslot, TMEM_COLS);
+  if (warp == 1) {
+    if (PAIR) tc::tmem_alloc_pair(tslot, TMEM_COLS);
+    else tc::tmem_alloc(tslot, TMEM_COLS);
+  }
   tc::fence_before();
   __syncthreads();
   if (NC > 1) tc::cluster_sync();
   tc::fence_after();
   const uint32_t tbase = *tslot;
+  const bool leader = !PAIR || crank == 0;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -144,6 +159,27 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             if (h >= SLOTS && !tc::mbar_wait(&empty[s], ((h / SLOTS) - 1) & 1, a.status, abort)) { ok = false; break; }
             uint8_t* buf = smem + s * SLOT;
             const int x = kb * BK;
+            if (PAIR) {
+              // own SNP rows and own half of the trait rows, completing on the leader's barrier
+              const uint32_t fb = tc::mapa(&full[s], 0);
+              if (leader) tc::mbar_expect_tx(&full[s], 2 * (half == 0 ? H1 : H2));
+              if (half == 0) {
+                tc::tma_load_2d_pair(buf, &mapG, fb, x, row);
+#pragma unroll
+                for (int q = 0; q < B1_BOXES; ++q)
+                  tc::tma_load_2d_pair(buf + G_BYTES + q * BBOX * ROWB, &mapB1, fb, x,
+                                       tt * B1_ROWS + (int)crank * C1_ROWS + q * BBOX);
+              } else {
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+                  tc::tma_load_2d_pair(buf + p * G_BYTES, &mapA2, fb, x, (int)(p * a.mpad) + row);
+#pragma unroll
+                for (int q = 0; q < B2_BOXES; ++q)
+                  tc::tma_load_2d_pair(buf + 3 * G_BYTES + q * BBOX * ROWB, &mapB2, fb, x,
+                                       tt * B2_TILE + (int)crank * C2_ROWS + q * BBOX);
+              }
+              continue;
+            }
             if (half == 0) {
               tc::mbar_expect_tx(&full[s], H1_BYTES);
               if (CT > 1) tc::tma_load_2d_mc(buf + tr * AROWS * ROWB, &mapG, &full[s], x, row, maskA);
@@ -182,7 +218,49 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
+    if (PAIR && lane == 0 && leader) {
+      constexpr uint32_t id256 = tc::idesc_bf16(2 * BM, 8 * TT), id64 = tc::idesc_bf16(2 * BM, 2 * TT);
+      constexpr uint32_t id96 = tc::idesc_bf16(2 * BM, 3 * TT), id32 = tc::idesc_bf16(2 * BM, TT);
+      uint32_t h = 0, tcount = 0;
+      bool ok = true;
+      for (int u = cid; u < nsuper && ok; u += ncl, ++tcount) {
+        if (tcount > 0 && !tc::mbar_wait(acc_empty, (tcount - 1) & 1, a.status, abort)) { ok = false; break; }
+        tc::fence_after();
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+          for (int half = 0; half < 2; ++half, ++h) {
+            const uint32_t s = h % SLOTS;
+            if (!tc::mbar_wait(&full[s], (h / SLOTS) & 1, a.status, abort)) { ok = false; break; }
+            tc::fence_after();
+            uint8_t* buf = smem + s * SLOT;
+            if (half == 0) {
+              const uint64_t dg = tc::sdesc_sw128(buf), db = tc::sdesc_sw128(buf + G_BYTES);
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k) {
+                const uint32_t acc = (kb | k) ? 1u : 0u;
+                // [Q1 | Q2] -> levels 0 and 1 of [w v1 v2 v3]; [Q3 | Q4] -> slices 3, 4 of w
+                tc::mma_bf16_pair(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), id256, acc);
+                tc::mma_bf16_pair(tbase + 8 * TT, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, 4 * TT * ROWB + k * 32),
+                                  id64, acc);
+              }
+            } else {
+              const uint64_t d1 = tc::sdesc_sw128(buf), d2 = tc::sdesc_sw128(buf + G_BYTES);
+              const uint64_t d3 = tc::sdesc_sw128(buf + 2 * G_BYTES), de = tc::sdesc_sw128(buf + 3 * G_BYTES);
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k) {
+                const uint32_t acc = (kb | k) ? 1u : 0u;
+                tc::mma_bf16_pair(tbase + 10 * TT, tc::sdesc_add(d1, k * 32), tc::sdesc_add(de, k * 32), id96, acc);
+                tc::mma_bf16_pair(tbase + 11 * TT, tc::sdesc_add(d2, k * 32),
+                                  tc::sdesc_add(de, (3 * TT / 2) * ROWB + k * 32), id64, 1u);
+                tc::mma_bf16_pair(tbase + 11 * TT, tc::sdesc_add(d3, k * 32),
+                                  tc::sdesc_add(de, (5 * TT / 2) * ROWB + k * 32), id32, 1u);
+              }
+            }
+            tc::mma_commit_pair(&empty[s], (uint16_t)3);
+          }
+        }
+        if (ok) tc::mma_commit_pair(acc_full, (uint16_t)3);
+      }
+    } else if (!PAIR && lane == 0) {
       constexpr uint32_t id256 = tc::idesc_bf16(BM, 8 * TT), id64 = tc::idesc_bf16(BM, 2 * TT);
       constexpr uint32_t id96 = tc::idesc_bf16(BM, 3 * TT), id32 = tc::idesc_bf16(BM, TT);
       const uint16_t release = maskA | maskB;
@@ -300,7 +378,10 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
           // every TMEM read of this warp for this tile is complete: release the accumulators
           tc::fence_before();
           __syncwarp();
-          if (lane == 0) tc::mbar_arrive(acc_empty);
+          if (lane == 0) {
+            if (PAIR) tc::mbar_arrive_cluster(tc::mapa(acc_empty, 0));
+            else tc::mbar_arrive(acc_empty);
+          }
         }
         if (!valid_i) continue;
 #pragma unroll
@@ -364,27 +445,31 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   tc::fence_before();
   __syncthreads();
   if (NC > 1) tc::cluster_sync();
-  if (warp == 1) tc::tmem_dealloc(tbase, TMEM_COLS);
+  if (warp == 1) {
+    if (PAIR) tc::tmem_dealloc_pair(tbase, TMEM_COLS);
+    else tc::tmem_dealloc(tbase, TMEM_COLS);
+  }
 }
 
 struct Shape {
-  int cs, ct, epw;
+  int cs, ct, epw, pair;
 };
 
 Shape shape_from_env() {
-  Shape sh{1, 1, 16};
+  Shape sh{1, 1, 16, 0};
   if (const char* e = getenv("GWAS_FUSED_SHAPE")) {
-    int cs = 0, ct = 0, epw = 0;
-    if (sscanf(e, "%dx%dx%d", &cs, &ct, &epw) == 3) sh = {cs, ct, epw};
+    int cs = 0, ct = 0, epw = 0, pr = 0;
+    const int k = sscanf(e, "%dx%dx%dx%d", &cs, &ct, &epw, &pr);
+    if (k >= 3) sh = {cs, ct, epw, k == 4 ? pr : 0};
   }
   return sh;
 }
 
-template <int CS, int CT, int EPW, bool SERVE = false>
+template <int CS, int CT, int EPW, bool SERVE = false, bool PAIR = false>
 int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const CUtensorMap& ma,
                  const CUtensorMap& m1, const CUtensorMap& m2) {
   constexpr int NC = CS * CT;
-  auto kern = fused_kernel<CS, CT, EPW, SERVE>;
+  auto kern = fused_kernel<CS, CT, EPW, SERVE, PAIR>;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
@@ -426,6 +511,8 @@ int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const C
 
 int fused_trait_tile_multiple() { return 4; }
 
+int fused_pair_layout() { return shape_from_env().pair; }
+
 int launch_fused(gwas_ctx* c, const FusedArgs& args, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2) {
   FusedArgs a = args;
@@ -436,10 +523,10 @@ int launch_fused(gwas_ctx* c, const FusedArgs& args, const __nv_bfloat16* G, con
   if (!make_bf16_map(&mg, G, a.mpad, a.Kpad, BM / sh.ct, BK) ||
       !make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM / sh.ct, BK) ||
       !make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * B1_ROWS, a.Kpad, BBOX, BK) ||
-      !make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * B2_ROWS, a.Kpad, BBOX, BK))
+      !make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * (sh.pair ? B2_ROWS_PAIR : B2_ROWS), a.Kpad, BBOX, BK))
     return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
 #define GWAS_SHAPE(CS, CT, EPW) \
-  if (sh.cs == CS && sh.ct == CT && sh.epw == EPW) return launch_shape<CS, CT, EPW>(c, a, mg, ma, m1, m2);
+  if (sh.cs == CS && sh.ct == CT && sh.epw == EPW && !sh.pair) return launch_shape<CS, CT, EPW>(c, a, mg, ma, m1, m2);
   GWAS_SHAPE(1, 1, 4)
   GWAS_SHAPE(1, 1, 8)
   GWAS_SHAPE(1, 1, 16)
@@ -447,6 +534,7 @@ int launch_fused(gwas_ctx* c, const FusedArgs& args, const __nv_bfloat16* G, con
   GWAS_SHAPE(1, 2, 16)
   GWAS_SHAPE(2, 1, 16)
   GWAS_SHAPE(2, 2, 16)
+  if (sh.cs == 2 && sh.ct == 1 && sh.epw == 16 && sh.pair) return launch_shape<2, 1, 16, false, true>(c, a, mg, ma, m1, m2);
 #undef GWAS_SHAPE
   return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: cluster shape not instantiated");
 }

@@ -51,8 +51,11 @@ struct FusedArgs {
   const ServeDesc* reqs;
 };
 
-// Trait operands (B1, B2) must be allocated (and zeroed) for a multiple of this many trait tiles.
+// Trait operands (B1, B2) must be allocated (and zeroed) for a multiple of this many trait tiles,
+// with 320 B1 rows and 192 B2 rows per trait tile.
 int fused_trait_tile_multiple();
+// 1 when the selected kernel shape is the CTA-pair one, whose trait operands use the pair layout.
+int fused_pair_layout();
 
 int launch_fused(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2);

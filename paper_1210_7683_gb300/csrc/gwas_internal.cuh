@@ -105,9 +105,10 @@ struct MixedWs;  // work buffers of one gwas_solve call (mixed.cu)
 int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** ws);
 void mixed_ws_free(gwas_ctx* c, MixedWs* ws);
 // Enqueues the per-trait operands of traits [0, tb) of dY (heritabilities h2, device) into
-// trait tiles slot[j/32] (identity when slot is NULL) of the operand arrays B1, B2, cst.
+// trait tiles slot[j/32] (identity when slot is NULL) of the operand arrays B1, B2, cst, in the
+// one-CTA layout or (pair != 0) the CTA-pair layout of the fused kernel.
 int mixed_prep_traits(gwas_ctx* c, MixedWs* ws, const double* dY, const double* h2, int tb, __nv_bfloat16* B1,
-                      __nv_bfloat16* B2, float* cst, const int* slot);
+                      __nv_bfloat16* B2, float* cst, const int* slot, int pair);
 // Enqueues (no synchronisation) the solve of traits [j0, j0+tb) x SNPs [i0, i1) into dout.
 int mixed_solve_block(gwas_ctx* c, MixedWs* ws, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
                       void* dout);

@@ -35,6 +35,7 @@ namespace {
 constexpr int PM1 = 3;
 constexpr int TT = 32;
 constexpr int B1_ROWS = 10 * TT, B2_ROWS = 4 * TT;
+constexpr int B2_ALLOC = 6 * TT;  // B2 rows allocated per trait tile (the CTA-pair layout needs 192)
 
 inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
@@ -169,7 +170,8 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
                                                          const double* __restrict__ h2, const double* __restrict__ lam,
                                                          const double* __restrict__ XLt, int n, int Kpad,
                                                          double* __restrict__ Wt, __nv_bfloat16* __restrict__ B2,
-                                                         float* __restrict__ cst, const int* __restrict__ slot) {
+                                                         float* __restrict__ cst, const int* __restrict__ slot,
+                                                         int pair) {
   const int j = blockIdx.x;
   const double h = h2[j];
   const double* y = Yt + (size_t)j * ldy;
@@ -246,7 +248,18 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
   double rr = 0;
   const int p = PM1 + 1;
   const int tile = slot ? slot[j / TT] : j / TT, jj = j % TT;
-  __nv_bfloat16* b2 = B2 + (size_t)tile * B2_ROWS * Kpad;
+  __nv_bfloat16* b2 = B2 + (size_t)tile * (pair ? B2_ALLOC : B2_ROWS) * Kpad;
+  // rows of the four slices of e in the C2 operand of the tile:
+  //   one CTA:   [E2s | E1 | E2 | E3s], 32 rows each;
+  //   CTA pair:  each MMA's rows split between the two CTAs (E1 appears three times)
+  int r_e2s, r_e1a, r_e1b, r_e1c, r_e2, r_e3s;
+  if (!pair) {
+    r_e2s = jj; r_e1a = TT + jj; r_e2 = 2 * TT + jj; r_e3s = 3 * TT + jj; r_e1b = r_e1c = -1;
+  } else {
+    r_e1a = jj; r_e2 = jj < TT / 2 ? TT + jj : 3 * TT + (jj - TT / 2);
+    r_e2s = 3 * TT / 2 + jj; r_e1c = jj < TT / 2 ? 5 * TT / 2 + jj : 11 * TT / 2 + (jj - TT / 2);
+    r_e3s = 7 * TT / 2 + jj; r_e1b = 9 * TT / 2 + jj;
+  }
   for (int k = threadIdx.x; k < Kpad; k += blockDim.x) {
     double w = 0, v[PM1] = {0, 0, 0};
     float q0 = 0, q1 = 0, q2 = 0;
@@ -273,10 +286,14 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
     }
     Wt[((size_t)j * p + 0) * Kpad + k] = w;
     for (int c = 0; c < PM1; ++c) Wt[((size_t)j * p + 1 + c) * Kpad + k] = v[c];
-    b2[(size_t)(0 * TT + jj) * Kpad + k] = __float2bfloat16(q1 * (1.f / 256.f));
-    b2[(size_t)(1 * TT + jj) * Kpad + k] = __float2bfloat16(q0);
-    b2[(size_t)(2 * TT + jj) * Kpad + k] = __float2bfloat16(q1);
-    b2[(size_t)(3 * TT + jj) * Kpad + k] = __float2bfloat16(q2 * (1.f / 256.f));
+    b2[(size_t)r_e2s * Kpad + k] = __float2bfloat16(q1 * (1.f / 256.f));
+    b2[(size_t)r_e1a * Kpad + k] = __float2bfloat16(q0);
+    if (r_e1b >= 0) {
+      b2[(size_t)r_e1b * Kpad + k] = __float2bfloat16(q0);
+      b2[(size_t)r_e1c * Kpad + k] = __float2bfloat16(q0);
+    }
+    b2[(size_t)r_e2 * Kpad + k] = __float2bfloat16(q1);
+    b2[(size_t)r_e3s * Kpad + k] = __float2bfloat16(q2 * (1.f / 256.f));
   }
   for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
   __syncthreads();
@@ -298,7 +315,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
 __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__ W, const double* __restrict__ XL,
                                                       const double* __restrict__ XtXinv, int n, int Kpad,
                                                       __nv_bfloat16* __restrict__ B1, float* __restrict__ cst,
-                                                      const int* __restrict__ slot) {
+                                                      const int* __restrict__ slot, int pair) {
   const int j = blockIdx.x;
   const int p = PM1 + 1;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
@@ -355,9 +372,10 @@ __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__
       }
       for (int s = 0; s < nsl; ++s) {
         const double q = rint(t);
+        // one CTA: [Q1 | Q2 | Q3 | Q4]; CTA pair: [Q1 | Q3] for the first CTA, [Q2 | Q4] for the second
         int row;
-        if (s < 2) row = s * 128 + c * TT + jj;
-        else row = (s == 2 ? 256 : 288) + jj;
+        if (!pair) row = s < 2 ? s * 4 * TT + c * TT + jj : (s == 2 ? 8 * TT : 9 * TT) + jj;
+        else row = (s == 0 ? 0 : s == 1 ? 5 * TT : s == 2 ? 4 * TT : 9 * TT) + (s < 2 ? c * TT : 0) + jj;
         b1[(size_t)row * Kpad + l] = __float2bfloat16((float)q);
         t = (t - q) * 256.0;
       }
@@ -533,7 +551,7 @@ int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** out) {
       (rc = ctx_alloc(c, 2ull * 4 * rowsW * Kpad, (void**)&w->Wsl)) ||
       (rc = ctx_alloc(c, sizeof(double) * rowsW, (void**)&w->sW)) ||
       (rc = ctx_alloc(c, 2ull * (size_t)nt_alloc * B1_ROWS * Kpad, (void**)&w->B1)) ||
-      (rc = ctx_alloc(c, 2ull * (size_t)nt_alloc * B2_ROWS * Kpad, (void**)&w->B2)) ||
+      (rc = ctx_alloc(c, 2ull * (size_t)nt_alloc * B2_ALLOC * Kpad, (void**)&w->B2)) ||
       (rc = ctx_alloc(c, sizeof(float) * (size_t)nt_tiles * TT * FUSED_CST, (void**)&w->cst))) {
     mixed_ws_free(c, w);
     return rc;
@@ -543,7 +561,7 @@ int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** out) {
 }
 
 int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h2, int tb, __nv_bfloat16* B1,
-                      __nv_bfloat16* B2, float* cst, const int* slot) {
+                      __nv_bfloat16* B2, float* cst, const int* slot, int pair) {
   MixedState* s = c->mixed;
   if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
   if (tb > w->tb_max) return ctx_fail(c, GWAS_ERR_ARG, "trait block larger than its workspace");
@@ -570,7 +588,7 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h
   if ((rc = launch_xgemm(c, 4, 4, 3, g, Ysl, s->Bzt)) == GWAS_OK) {
     // per-trait algebra and the C2 operand
     ProfScope ps(c, "prep_traits");
-    prep_mixed_kernel<<<tb, 256, 0, c->stream>>>(Yt, Kpad, h2, c->lam, c->XLt, n, Kpad, Wt, B2, cst, slot);
+    prep_mixed_kernel<<<tb, 256, 0, c->stream>>>(Yt, Kpad, h2, c->lam, c->XLt, n, Kpad, Wt, B2, cst, slot, pair);
     c->launches++;
     // back-rotation [w | v] = Z [e.r' | (e.X'_L) L^-T]
     launch_slice_rows(c, Wt, Kpad, tb * p, n, rowsW, Kpad, 4, s->bits, Wsl, sW);
@@ -586,7 +604,7 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h
   }
   if (rc == GWAS_OK) {
     ProfScope ps(c, "pack_trait_columns");
-    pack_c1_kernel<<<tb, 256, 0, c->stream>>>(Wt, c->XL, s->XtXinv, n, Kpad, B1, cst, slot);
+    pack_c1_kernel<<<tb, 256, 0, c->stream>>>(Wt, c->XL, s->XtXinv, n, Kpad, B1, cst, slot, pair);
     c->launches++;
   }
   return rc;
@@ -605,8 +623,8 @@ int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb,
   __nv_bfloat16 *B1 = w->B1, *B2 = w->B2;
   float* cst = w->cst;
   cudaMemsetAsync(B1, 0, 2ull * nt_alloc * B1_ROWS * Kpad, c->stream);
-  cudaMemsetAsync(B2, 0, 2ull * nt_alloc * B2_ROWS * Kpad, c->stream);
-  rc = mixed_prep_traits(c, w, dY, c->h2 + j0, tb, B1, B2, cst, nullptr);
+  cudaMemsetAsync(B2, 0, 2ull * nt_alloc * B2_ALLOC * Kpad, c->stream);
+  rc = mixed_prep_traits(c, w, dY, c->h2 + j0, tb, B1, B2, cst, nullptr, fused_pair_layout());
   if (rc == GWAS_OK) {
     FusedArgs a{};
     a.row0 = i0;

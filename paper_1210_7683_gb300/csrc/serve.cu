@@ -199,7 +199,7 @@ void serve_loop(gwas_ctx* c) {
         cudaMemcpyAsync(S->d_Y, S->h_Y, sizeof(double) * rows * n, cudaMemcpyHostToDevice, c->stream);
         cudaMemcpyAsync(S->d_h2, S->h_h2, sizeof(double) * rows, cudaMemcpyHostToDevice, c->stream);
         cudaMemcpyAsync(S->d_slot, S->h_slot, sizeof(int) * tiles, cudaMemcpyHostToDevice, c->stream);
-        rc = mixed_prep_traits(c, S->ws, S->d_Y, S->d_h2, rows, S->B1, S->B2, S->cst, S->d_slot);
+        rc = mixed_prep_traits(c, S->ws, S->d_Y, S->d_h2, rows, S->B1, S->B2, S->cst, S->d_slot, 0);
       }
       for (uint64_t id : admitted) {
         std::lock_guard<std::mutex> lk(S->mu);
