@@ -325,12 +325,9 @@ def main():
     barrier()
     clk = clocks.stop()
     last_sample = out[:, :128, :8192].cpu().numpy()
-    ms_step = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(tt.item())
-    value = world * pairs / (ms_step / 1e3)
+    from paper_1210_7683_gb300.sharding import max_over_ranks, weak_scaling_rate
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+    value = weak_scaling_rate(pairs, world, ms_step)
 
     # ---------------------------------------------------------------- roofline of the fused kernel
     pk, pk_src = peaks()

@@ -229,6 +229,15 @@ GWAS_API int gwas_solve_fp64_noalloc(int n, int pm1, const double* lam, const do
                                      int64_t m, const double* Yt, const double* h2, int t, int output, void* out,
                                      void* stream, int64_t* singular);
 
+/*
+ * Self-test of failure detection: launches one kernel that waits on a barrier that
+ * nothing completes, with the same bounded-wait code every kernel of the library
+ * uses but a limit of limit_s seconds (0 < limit_s <= 10).  Returns GWAS_ERR_TIMEOUT
+ * (the expected outcome: the wait gave up and reported it) with *waited_s the time it
+ * waited, GWAS_OK if the barrier completed, or GWAS_ERR_CUDA.  The device stays usable.
+ */
+GWAS_API int gwas_check_bounded_wait(int device, double limit_s, double* waited_s);
+
 /* One-line description of the last failure on ctx (or of the last failed
  * gwas_setup when ctx is NULL).  Owned by the library. */
 GWAS_API const char* gwas_last_error(const gwas_ctx* ctx);

@@ -90,6 +90,8 @@ def _load():
     lib.gwas_request_times.argtypes = [vp, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                        C.POINTER(C.c_double)]
     lib.gwas_request_times.restype = ci
+    lib.gwas_check_bounded_wait.argtypes = [ci, C.c_double, C.POINTER(C.c_double)]
+    lib.gwas_check_bounded_wait.restype = ci
     lib.gwas_destroy.argtypes = [vp]
     lib.gwas_destroy.restype = None
     return lib
@@ -255,6 +257,13 @@ def gwas_solve_fp64_noalloc(n, pm1, lam, XLt, Xt, m, Yt, h2, t, output, out, str
     if rc not in (GWAS_OK, GWAS_ERR_SINGULAR_PAIRS):
         raise GwasError(rc, "gwas_solve_fp64_noalloc failed")
     return rc, sing.value
+
+
+def gwas_check_bounded_wait(device=0, limit_s=0.05):
+    """(status, waited seconds) of the bounded-wait self-test (expected: GWAS_ERR_TIMEOUT)."""
+    w = C.c_double()
+    rc = lib.gwas_check_bounded_wait(int(device), float(limit_s), C.byref(w))
+    return rc, w.value
 
 
 def gwas_last_error(ctx=None) -> str:

@@ -26,7 +26,11 @@
 //   [0,128)   C1 level 0  (slice 1 of w, v1, v2, v3; 32 traits each)
 //   [128,256) C1 level 1  (slice 2)
 //   [256,288) w slice 3   [288,320) w slice 4
-//   [320,352) C2 level 0  [352,384) C2 level-1 units (a)  [384,416) (b)
+//   [320,416) A1 x [E1 | E2 | E3s]: C2 level 0, then two groups in level-1 units
+//   [416,480) A2 x [E2s | E1]       [480,512) A3s x E1   (level-1 units)
+// Every MMA of a K step writes its own columns, so consecutive small MMAs do not wait
+// on one another's accumulator (a chain of dependent N <= 128 MMAs runs at the MMA
+// latency, not at the tensor-core rate); the epilogue adds the level-1 groups.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -249,10 +253,10 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               for (int k = 0; k < BK / 16; ++k) {
                 const uint32_t acc = (kb | k) ? 1u : 0u;
                 tc::mma_bf16_pair(tbase + 10 * TT, tc::sdesc_add(d1, k * 32), tc::sdesc_add(de, k * 32), id96, acc);
-                tc::mma_bf16_pair(tbase + 11 * TT, tc::sdesc_add(d2, k * 32),
-                                  tc::sdesc_add(de, (3 * TT / 2) * ROWB + k * 32), id64, 1u);
-                tc::mma_bf16_pair(tbase + 11 * TT, tc::sdesc_add(d3, k * 32),
-                                  tc::sdesc_add(de, (5 * TT / 2) * ROWB + k * 32), id32, 1u);
+                tc::mma_bf16_pair(tbase + 13 * TT, tc::sdesc_add(d2, k * 32),
+                                  tc::sdesc_add(de, (3 * TT / 2) * ROWB + k * 32), id64, acc);
+                tc::mma_bf16_pair(tbase + 15 * TT, tc::sdesc_add(d3, k * 32),
+                                  tc::sdesc_add(de, (5 * TT / 2) * ROWB + k * 32), id32, acc);
               }
             }
             tc::mma_commit_pair(&empty[s], (uint16_t)3);
@@ -293,10 +297,10 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                 const uint32_t acc = (kb | k) ? 1u : 0u;
                 // A1 x [E1 | E2 | E3s] -> [level 0 | a | b]
                 tc::mma_bf16(tbase + 10 * TT, tc::sdesc_add(d1, k * 32), tc::sdesc_add(de, TT * ROWB + k * 32), id96, acc);
-                // A2 x [E2s | E1] -> [a | b]
-                tc::mma_bf16(tbase + 11 * TT, tc::sdesc_add(d2, k * 32), tc::sdesc_add(de, k * 32), id64, 1u);
-                // A3s x E1 -> a
-                tc::mma_bf16(tbase + 11 * TT, tc::sdesc_add(d3, k * 32), tc::sdesc_add(de, TT * ROWB + k * 32), id32, 1u);
+                // A2 x [E2s | E1] -> its own two groups
+                tc::mma_bf16(tbase + 13 * TT, tc::sdesc_add(d2, k * 32), tc::sdesc_add(de, k * 32), id64, acc);
+                // A3s x E1 -> its own group
+                tc::mma_bf16(tbase + 15 * TT, tc::sdesc_add(d3, k * 32), tc::sdesc_add(de, TT * ROWB + k * 32), id32, acc);
               }
             }
             if (NC > 1) tc::mma_commit_mc(&empty[s], release);
@@ -357,23 +361,55 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       }
       unsigned long long tsing = 0;
       for (int j0 = jbeg; j0 < jbeg + JPW; j0 += 4) {
-        uint32_t hw[4], hz[3][4], lw[4], lz[3][4], w3[4], w4[4], d0[4], da[4], db[4];
-        tc::tmem_ld4(lane_base + 0 * TT + j0, hw);
+        // C1 accumulators first: reduce them to num and z before reading C2 (register pressure)
+        float num4[4], z4[4][PM1], zz4[4];
+        {
+          uint32_t hw[4], hz[3][4], lw[4], lz[3][4], w3[4], w4[4];
+          tc::tmem_ld4(lane_base + 0 * TT + j0, hw);
 #pragma unroll
-        for (int c = 0; c < PM1; ++c) tc::tmem_ld4(lane_base + (1 + c) * TT + j0, hz[c]);
-        tc::tmem_ld4(lane_base + 4 * TT + j0, lw);
+          for (int c = 0; c < PM1; ++c) tc::tmem_ld4(lane_base + (1 + c) * TT + j0, hz[c]);
+          tc::tmem_ld4(lane_base + 4 * TT + j0, lw);
 #pragma unroll
-        for (int c = 0; c < PM1; ++c) tc::tmem_ld4(lane_base + (5 + c) * TT + j0, lz[c]);
-        tc::tmem_ld4(lane_base + 8 * TT + j0, w3);
-        tc::tmem_ld4(lane_base + 9 * TT + j0, w4);
-        tc::tmem_ld4(lane_base + 10 * TT + j0, d0);
-        tc::tmem_ld4(lane_base + 11 * TT + j0, da);
-        tc::tmem_ld4(lane_base + 12 * TT + j0, db);
-        tc::tmem_ld_wait();
-        tc::reg_fence(hw); tc::reg_fence(lw); tc::reg_fence(w3); tc::reg_fence(w4);
-        tc::reg_fence(d0); tc::reg_fence(da); tc::reg_fence(db);
+          for (int c = 0; c < PM1; ++c) tc::tmem_ld4(lane_base + (5 + c) * TT + j0, lz[c]);
+          tc::tmem_ld4(lane_base + 8 * TT + j0, w3);
+          tc::tmem_ld4(lane_base + 9 * TT + j0, w4);
+          tc::tmem_ld_wait();
+          tc::reg_fence(hw); tc::reg_fence(lw); tc::reg_fence(w3); tc::reg_fence(w4);
 #pragma unroll
-        for (int c = 0; c < PM1; ++c) { tc::reg_fence(hz[c]); tc::reg_fence(lz[c]); }
+          for (int c = 0; c < PM1; ++c) { tc::reg_fence(hz[c]); tc::reg_fence(lz[c]); }
+          const float F = 1.f / 256.f;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const float* cj = cs + (j0 + v) * FUSED_CST;
+            num4[v] = cj[0] * fmaf(F, fmaf(F, fmaf(F, __uint_as_float(w4[v]), __uint_as_float(w3[v])),
+                                         __uint_as_float(lw[v])), __uint_as_float(hw[v]));
+            zz4[v] = 0.f;
+#pragma unroll
+            for (int c = 0; c < PM1; ++c) {
+              z4[v][c] = cj[1 + c] * fmaf(F, __uint_as_float(lz[c][v]), __uint_as_float(hz[c][v]));
+              zz4[v] = fmaf(z4[v][c], z4[v][c], zz4[v]);
+            }
+          }
+        }
+        float lvl0[4], lvl1[4];
+        {
+          uint32_t d0[4], da[4], db[4], ea[4], eb[4], ec[4];
+          tc::tmem_ld4(lane_base + 10 * TT + j0, d0);
+          tc::tmem_ld4(lane_base + 11 * TT + j0, da);
+          tc::tmem_ld4(lane_base + 12 * TT + j0, db);
+          tc::tmem_ld4(lane_base + 13 * TT + j0, ea);
+          tc::tmem_ld4(lane_base + 14 * TT + j0, eb);
+          tc::tmem_ld4(lane_base + 15 * TT + j0, ec);
+          tc::tmem_ld_wait();
+          tc::reg_fence(d0); tc::reg_fence(da); tc::reg_fence(db);
+          tc::reg_fence(ea); tc::reg_fence(eb); tc::reg_fence(ec);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            lvl0[v] = __uint_as_float(d0[v]);
+            lvl1[v] = (__uint_as_float(da[v]) + __uint_as_float(db[v])) +
+                      (__uint_as_float(ea[v]) + __uint_as_float(eb[v])) + __uint_as_float(ec[v]);
+          }
+        }
         if (j0 + 4 == jbeg + JPW) {
           // every TMEM read of this warp for this tile is complete: release the accumulators
           tc::fence_before();
@@ -390,16 +426,11 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
           const int jj = jbase + jl;            // trait index within the block (request)
           if (jj >= ntrait) break;
           const float* cj = cs + jl * FUSED_CST;
-          const float F = 1.f / 256.f;
-          const float num = cj[0] * fmaf(F, fmaf(F, fmaf(F, __uint_as_float(w4[v]), __uint_as_float(w3[v])),
-                                                 __uint_as_float(lw[v])), __uint_as_float(hw[v]));
-          float z[PM1], zz = 0.f;
+          const float num = num4[v], zz = zz4[v];
+          float z[PM1];
 #pragma unroll
-          for (int c = 0; c < PM1; ++c) {
-            z[c] = cj[1 + c] * fmaf(F, __uint_as_float(lz[c][v]), __uint_as_float(hz[c][v]));
-            zz = fmaf(z[c], z[c], zz);
-          }
-          const float s = (sA * cj[4]) * fmaf(F, __uint_as_float(da[v]) + __uint_as_float(db[v]), __uint_as_float(d0[v]));
+          for (int c = 0; c < PM1; ++c) z[c] = z4[v][c];
+          const float s = (sA * cj[4]) * fmaf(1.f / 256.f, lvl1[v], lvl0[v]);
           const float delta = s - zz;
           float beta, se;
           const bool sing = !(delta > 1e-6f * s) || !(sA > 0.f);

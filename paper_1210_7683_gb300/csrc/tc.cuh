@@ -38,8 +38,8 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 
 // Bounded wait for the phase with the given parity to complete.  On expiry (or when
 // another thread of the CTA has set *abort) sets status[0] and *abort and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, unsigned long long* status,
-                                          volatile int* abort) {
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* b, uint32_t parity, unsigned long long* status,
+                                                volatile int* abort, uint64_t limit_ns) {
   const uint32_t addr = smem_u32(b);
   uint64_t t0 = 0;
   for (uint32_t it = 0; it < kMaxPolls; ++it) {
@@ -54,12 +54,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, unsigned
       if (abort && *abort) return false;
       const uint64_t now = globaltimer_ns();
       if (it == 0) t0 = now;
-      else if (now - t0 > kMaxWaitNs) break;
+      else if (now - t0 > limit_ns) break;
     }
   }
   if (status) atomicExch(status, 1ull);
   if (abort) *abort = 1;
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, unsigned long long* status,
+                                          volatile int* abort) {
+  return mbar_wait_limit(b, parity, status, abort, kMaxWaitNs);
 }
 
 // 2-D TMA tile load (x = innermost coordinate in elements, y = row) into shared
