@@ -43,23 +43,33 @@
 namespace {
 
 // K extent of one stage: 64 bf16 = one 128-byte swizzled row.  (32-wide stages with
-// the 64-byte swizzle and a 6-slot ring measured 1.6x slower: twice the TMA boxes
-// and barrier round trips per MMA.)
+// the 64-byte swizzle and 32-row boxes measured 1.6x slower: the TMA unit's cost per box.)
 constexpr int BM = 128, TT = 32, BK = 64;
 constexpr int ROWB = BK * 2;                         // bytes per operand row of a stage
 constexpr int PM1 = 3;
-constexpr int G_BYTES = BM * ROWB;                   // 8 KB: one A tile
+constexpr int G_BYTES = BM * ROWB;                   // 16 KB: one A tile
 constexpr int B1_ROWS = 10 * TT, B2_ROWS = 4 * TT;   // 320 and 128 rows per trait tile
 constexpr int B2_ROWS_PAIR = 6 * TT;                  // 192: C2 rows of a trait tile in the pair layout
 constexpr int BBOX = 32;                             // rows per TMA box of the trait operands
-constexpr int SLOT = 64 * 1024;                      // a ring slot holds either half-stage
+constexpr int SLOT = 64 * 1024;                      // one-CTA shapes: a ring slot holds either half-stage
 constexpr int SLOTS = 3;
+// CTA pair: each CTA stages its own SNP rows and half of the trait rows, in three items per
+// K block (G + C1 half: 36 KB; C2 half + A1: 28 KB; A2 + A3s: 32 KB) and a ring of six
+// 36 KB slots, i.e. two K blocks in flight.
+constexpr int PSLOT = 36 * 1024, PSLOTS = 6;
+constexpr int PC1_ROWS = B1_ROWS / 2, PC2_ROWS = B2_ROWS_PAIR / 2;  // 160 and 96 trait rows per CTA
+constexpr int PI0_BYTES = G_BYTES + PC1_ROWS * ROWB;   // G + this CTA's C1 trait rows
+constexpr int PI1_BYTES = PC2_ROWS * ROWB + G_BYTES;   // this CTA's C2 trait rows + A1
+constexpr int PI2_BYTES = 2 * G_BYTES;                 // A2 + A3s
 constexpr int H1_BYTES = G_BYTES + B1_ROWS * ROWB;   // 57344
 constexpr int H2_BYTES = 3 * G_BYTES + B2_ROWS * ROWB;  // 65536
 constexpr int CST_BYTES = TT * FUSED_CST * 4;          // per-trait constants of one tile
-constexpr int SMEM_BYTES = SLOTS * SLOT + 2 * CST_BYTES + 1024 + 512;
+__host__ __device__ constexpr int ring_bytes(bool pair) { return pair ? PSLOTS * PSLOT : SLOTS * SLOT; }
+__host__ __device__ constexpr int smem_bytes(bool pair) { return ring_bytes(pair) + 2 * CST_BYTES + 1024 + 512; }
 constexpr int TMEM_COLS = 512;
 static_assert(H1_BYTES <= SLOT && H2_BYTES <= SLOT, "half-stage does not fit a slot");
+static_assert(PI0_BYTES <= PSLOT && PI1_BYTES <= PSLOT && PI2_BYTES <= PSLOT, "pair item does not fit a slot");
+static_assert(smem_bytes(true) <= 227 * 1024 && smem_bytes(false) <= 227 * 1024, "shared memory");
 
 template <int CS, int CT>
 __device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us, int& ut) {
@@ -83,20 +93,22 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   constexpr int NC = CS * CT;
   constexpr int AROWS = BM / CT;                    // genotype rows this CTA loads per plane
   static_assert(!PAIR || (CS == 2 && CT == 1 && !SERVE), "pair mode is a 2 x 1 cluster");
-  constexpr int C1_ROWS = PAIR ? B1_ROWS / 2 : B1_ROWS;       // trait rows in this CTA's C1 region
-  constexpr int C2_ROWS = PAIR ? B2_ROWS_PAIR / 2 : B2_ROWS;  // and in its C2 region
-  constexpr int B2_TILE = PAIR ? B2_ROWS_PAIR : B2_ROWS;      // rows per trait tile of the B2 layout
-  constexpr int B1_BOXES = PAIR ? C1_ROWS / BBOX : B1_ROWS / BBOX / CS;
-  constexpr int B2_BOXES = PAIR ? C2_ROWS / BBOX : B2_ROWS / BBOX / CS;
-  constexpr uint32_t H1 = G_BYTES + C1_ROWS * ROWB, H2 = 3 * G_BYTES + C2_ROWS * ROWB;
+  // multicast cluster shapes: each CTA loads 1/CS of the trait rows in 32-row boxes
+  constexpr int B1_BOXES = B1_ROWS / BBOX / CS, B2_BOXES = B2_ROWS / BBOX / CS;
   static_assert(B1_ROWS % (BBOX * CS) == 0 && B2_ROWS % (BBOX * CS) == 0 && BM % (8 * CT) == 0, "cluster shape");
-  static_assert(C1_ROWS % BBOX == 0 && C2_ROWS % BBOX == 0, "pair layout");
+  // One CTA per tile: every half-stage is three TMA boxes of 128 to 192 rows (the genotype
+  // tile and the C1 trait rows in two halves; the three x'^2 planes, stored next to one
+  // another, in two halves and the C2 trait rows).  The TMA unit pays a fixed cost per box
+  // of the order of 50 cycles, so the 32-row boxes of the cluster shapes cap the load rate.
+  constexpr bool BIG = CS == 1 && CT == 1 && !PAIR;
+  constexpr int NSL = PAIR ? PSLOTS : SLOTS, SLB = PAIR ? PSLOT : SLOT;  // ring slots and their size
+  constexpr int NI = PAIR ? 3 : 2;                                        // ring items per K block
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* cst_smem = (float*)(smem + SLOTS * SLOT);      // [2][TT][FUSED_CST], double-buffered by tile
-  uint64_t* full = (uint64_t*)(smem + SLOTS * SLOT + 2 * CST_BYTES);
-  uint64_t* empty = full + SLOTS;
-  uint64_t* acc_full = empty + SLOTS;
+  float* cst_smem = (float*)(smem + ring_bytes(PAIR));  // [2][TT][FUSED_CST], double-buffered by tile
+  uint64_t* full = (uint64_t*)(smem + ring_bytes(PAIR) + 2 * CST_BYTES);
+  uint64_t* empty = full + NSL;
+  uint64_t* acc_full = empty + NSL;
   uint64_t* acc_empty = acc_full + 1;
   uint32_t* tslot = (uint32_t*)(acc_empty + 1);
   volatile int* abort = (volatile int*)(tslot + 1);
@@ -116,7 +128,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   const int nsuper = SERVE ? a.nunits : ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
   const int nkb = a.Kpad / BK;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < SLOTS; ++s) {
+    for (int s = 0; s < NSL; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], PAIR ? 1 : CS + CT - 1);
     }
@@ -143,7 +155,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       tc::prefetch_map(&mapA2);
       tc::prefetch_map(&mapB1);
       tc::prefetch_map(&mapB2);
-      uint32_t h = 0;  // half-stage counter
+      uint32_t h = 0;  // ring item counter
       bool ok = true;
       for (int u = cid; u < nsuper && ok; u += ncl) {
         int row, tt;
@@ -158,29 +170,40 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
           tt = ut * CT + tr;
         }
         for (int kb = 0; kb < nkb && ok; ++kb) {
-          for (int half = 0; half < 2; ++half, ++h) {
-            const uint32_t s = h % SLOTS;
-            if (h >= SLOTS && !tc::mbar_wait(&empty[s], ((h / SLOTS) - 1) & 1, a.status, abort)) { ok = false; break; }
-            uint8_t* buf = smem + s * SLOT;
+          for (int it = 0; it < NI; ++it, ++h) {
+            const uint32_t s = h % NSL;
+            if (h >= NSL && !tc::mbar_wait(&empty[s], ((h / NSL) - 1) & 1, a.status, abort)) { ok = false; break; }
+            uint8_t* buf = smem + s * SLB;
             const int x = kb * BK;
+            const int half = it;
             if (PAIR) {
               // own SNP rows and own half of the trait rows, completing on the leader's barrier
               const uint32_t fb = tc::mapa(&full[s], 0);
-              if (leader) tc::mbar_expect_tx(&full[s], 2 * (half == 0 ? H1 : H2));
-              if (half == 0) {
+              if (leader) tc::mbar_expect_tx(&full[s], 2 * (it == 0 ? PI0_BYTES : it == 1 ? PI1_BYTES : PI2_BYTES));
+              if (it == 0) {
                 tc::tma_load_2d_pair(buf, &mapG, fb, x, row);
-#pragma unroll
-                for (int q = 0; q < B1_BOXES; ++q)
-                  tc::tma_load_2d_pair(buf + G_BYTES + q * BBOX * ROWB, &mapB1, fb, x,
-                                       tt * B1_ROWS + (int)crank * C1_ROWS + q * BBOX);
+                tc::tma_load_2d_pair(buf + G_BYTES, &mapB1, fb, x, tt * B1_ROWS + (int)crank * PC1_ROWS);
+              } else if (it == 1) {
+                tc::tma_load_2d_pair(buf, &mapB2, fb, x, tt * B2_ROWS_PAIR + (int)crank * PC2_ROWS);
+                tc::tma_load_2d_pair(buf + PC2_ROWS * ROWB, &mapA2, fb, x, (int)a2_row(0, row));
               } else {
-#pragma unroll
-                for (int p = 0; p < 3; ++p)
-                  tc::tma_load_2d_pair(buf + p * G_BYTES, &mapA2, fb, x, (int)(p * a.mpad) + row);
-#pragma unroll
-                for (int q = 0; q < B2_BOXES; ++q)
-                  tc::tma_load_2d_pair(buf + 3 * G_BYTES + q * BBOX * ROWB, &mapB2, fb, x,
-                                       tt * B2_TILE + (int)crank * C2_ROWS + q * BBOX);
+                tc::tma_load_2d_pair(buf, &mapA2, fb, x, (int)a2_row(1, row));
+                tc::tma_load_2d_pair(buf + G_BYTES, &mapA2, fb, x, (int)a2_row(2, row));
+              }
+              continue;
+            }
+            if (BIG) {
+              if (half == 0) {
+                tc::mbar_expect_tx(&full[s], H1_BYTES);
+                tc::tma_load_2d(buf, &mapG, &full[s], x, row);
+                tc::tma_load_2d(buf + G_BYTES, &mapB1, &full[s], x, tt * B1_ROWS);
+                tc::tma_load_2d(buf + G_BYTES + B1_ROWS / 2 * ROWB, &mapB1, &full[s], x, tt * B1_ROWS + B1_ROWS / 2);
+              } else {
+                const int y = (int)a2_row(0, row);
+                tc::mbar_expect_tx(&full[s], H2_BYTES);
+                tc::tma_load_2d(buf, &mapA2, &full[s], x, y);
+                tc::tma_load_2d(buf + 3 * BM / 2 * ROWB, &mapA2, &full[s], x, y + 3 * BM / 2);
+                tc::tma_load_2d(buf + 3 * G_BYTES, &mapB2, &full[s], x, tt * B2_ROWS);
               }
               continue;
             }
@@ -200,8 +223,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
               for (int p = 0; p < 3; ++p) {
                 uint8_t* dst = buf + p * G_BYTES + tr * AROWS * ROWB;
-                if (CT > 1) tc::tma_load_2d_mc(dst, &mapA2, &full[s], x, (int)(p * a.mpad) + row, maskA);
-                else tc::tma_load_2d(dst, &mapA2, &full[s], x, (int)(p * a.mpad) + row);
+                if (CT > 1) tc::tma_load_2d_mc(dst, &mapA2, &full[s], x, (int)a2_row(p, row), maskA);
+                else tc::tma_load_2d(dst, &mapA2, &full[s], x, (int)a2_row(p, row));
               }
 #pragma unroll
               for (int q = 0; q < B2_BOXES; ++q) {
@@ -215,8 +238,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         }
       }
       // the last release of every slot (ours and the peers') must land before we exit
-      for (uint32_t s = 0; s < SLOTS && h > s; ++s) {
-        const uint32_t uses = (h - s + SLOTS - 1) / SLOTS;
+      for (uint32_t s = 0; s < NSL && h > s; ++s) {
+        const uint32_t uses = (h - s + NSL - 1) / NSL;
         tc::mbar_wait(&empty[s], (uses - 1) & 1, a.status, abort);
       }
     }
@@ -231,35 +254,49 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         if (tcount > 0 && !tc::mbar_wait(acc_empty, (tcount - 1) & 1, a.status, abort)) { ok = false; break; }
         tc::fence_after();
         for (int kb = 0; kb < nkb && ok; ++kb) {
-          for (int half = 0; half < 2; ++half, ++h) {
-            const uint32_t s = h % SLOTS;
-            if (!tc::mbar_wait(&full[s], (h / SLOTS) & 1, a.status, abort)) { ok = false; break; }
+          {
+            // item 0: G and the C1 trait rows
+            const uint32_t s = h % NSL;
+            if (!tc::mbar_wait(&full[s], (h / NSL) & 1, a.status, abort)) { ok = false; break; }
             tc::fence_after();
-            uint8_t* buf = smem + s * SLOT;
-            if (half == 0) {
-              const uint64_t dg = tc::sdesc_sw128(buf), db = tc::sdesc_sw128(buf + G_BYTES);
+            uint8_t* buf = smem + s * SLB;
+            const uint64_t dg = tc::sdesc_sw128(buf), db = tc::sdesc_sw128(buf + G_BYTES);
 #pragma unroll
-              for (int k = 0; k < BK / 16; ++k) {
-                const uint32_t acc = (kb | k) ? 1u : 0u;
-                // [Q1 | Q2] -> levels 0 and 1 of [w v1 v2 v3]; [Q3 | Q4] -> slices 3, 4 of w
-                tc::mma_bf16_pair(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), id256, acc);
-                tc::mma_bf16_pair(tbase + 8 * TT, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, 4 * TT * ROWB + k * 32),
-                                  id64, acc);
-              }
-            } else {
-              const uint64_t d1 = tc::sdesc_sw128(buf), d2 = tc::sdesc_sw128(buf + G_BYTES);
-              const uint64_t d3 = tc::sdesc_sw128(buf + 2 * G_BYTES), de = tc::sdesc_sw128(buf + 3 * G_BYTES);
-#pragma unroll
-              for (int k = 0; k < BK / 16; ++k) {
-                const uint32_t acc = (kb | k) ? 1u : 0u;
-                tc::mma_bf16_pair(tbase + 10 * TT, tc::sdesc_add(d1, k * 32), tc::sdesc_add(de, k * 32), id96, acc);
-                tc::mma_bf16_pair(tbase + 13 * TT, tc::sdesc_add(d2, k * 32),
-                                  tc::sdesc_add(de, (3 * TT / 2) * ROWB + k * 32), id64, acc);
-                tc::mma_bf16_pair(tbase + 15 * TT, tc::sdesc_add(d3, k * 32),
-                                  tc::sdesc_add(de, (5 * TT / 2) * ROWB + k * 32), id32, acc);
-              }
+            for (int k = 0; k < BK / 16; ++k) {
+              const uint32_t acc = (kb | k) ? 1u : 0u;
+              // [Q1 | Q2] -> levels 0 and 1 of [w v1 v2 v3]; [Q3 | Q4] -> slices 3, 4 of w
+              tc::mma_bf16_pair(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), id256, acc);
+              tc::mma_bf16_pair(tbase + 8 * TT, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, 4 * TT * ROWB + k * 32),
+                                id64, acc);
             }
             tc::mma_commit_pair(&empty[s], (uint16_t)3);
+            ++h;
+          }
+          {
+            // items 1 and 2: the C2 trait rows and A1; A2 and A3s
+            const uint32_t s1 = h % NSL, s2 = (h + 1) % NSL;
+            if (!tc::mbar_wait(&full[s1], (h / NSL) & 1, a.status, abort) ||
+                !tc::mbar_wait(&full[s2], ((h + 1) / NSL) & 1, a.status, abort)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after();
+            uint8_t* b1 = smem + s1 * SLB;
+            uint8_t* b2 = smem + s2 * SLB;
+            const uint64_t de = tc::sdesc_sw128(b1), d1 = tc::sdesc_sw128(b1 + PC2_ROWS * ROWB);
+            const uint64_t d2 = tc::sdesc_sw128(b2), d3 = tc::sdesc_sw128(b2 + G_BYTES);
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k) {
+              const uint32_t acc = (kb | k) ? 1u : 0u;
+              tc::mma_bf16_pair(tbase + 10 * TT, tc::sdesc_add(d1, k * 32), tc::sdesc_add(de, k * 32), id96, acc);
+              tc::mma_bf16_pair(tbase + 13 * TT, tc::sdesc_add(d2, k * 32),
+                                tc::sdesc_add(de, (3 * TT / 2) * ROWB + k * 32), id64, acc);
+              tc::mma_bf16_pair(tbase + 15 * TT, tc::sdesc_add(d3, k * 32),
+                                tc::sdesc_add(de, (5 * TT / 2) * ROWB + k * 32), id32, acc);
+            }
+            tc::mma_commit_pair(&empty[s1], (uint16_t)3);
+            tc::mma_commit_pair(&empty[s2], (uint16_t)3);
+            h += 2;
           }
         }
         if (ok) tc::mma_commit_pair(acc_full, (uint16_t)3);
@@ -275,10 +312,10 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         tc::fence_after();
         for (int kb = 0; kb < nkb && ok; ++kb) {
           for (int half = 0; half < 2; ++half, ++h) {
-            const uint32_t s = h % SLOTS;
-            if (!tc::mbar_wait(&full[s], (h / SLOTS) & 1, a.status, abort)) { ok = false; break; }
+            const uint32_t s = h % NSL;
+            if (!tc::mbar_wait(&full[s], (h / NSL) & 1, a.status, abort)) { ok = false; break; }
             tc::fence_after();
-            uint8_t* buf = smem + s * SLOT;
+            uint8_t* buf = smem + s * SLB;
             if (half == 0) {
               const uint64_t dg = tc::sdesc_sw128(buf);
               const uint64_t db = tc::sdesc_sw128(buf + G_BYTES);
@@ -321,9 +358,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     uint32_t tcount = 0;
     unsigned long long nsing = 0;
     for (int u = cid; u < nsuper; u += ncl, ++tcount) {
-      // this tile's SNPs [snp0, snp0+128) (valid below snp_end), output origin and stride,
+      // this tile's SNPs [snp0, snp0+128) (valid in [snp_lo, snp_end)), output origin and stride,
       // first trait (jbase) within its request, constants and output arrays
-      int64_t snp0, snp_end, oi0, ldo;
+      int64_t snp0, snp_lo, snp_end, oi0, ldo;
       int ntrait, jbase, full_b;
       const float* cst_tile;
       float *obeta, *ose;
@@ -332,14 +369,14 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       if (SERVE) {
         const int4 w = a.units[u];
         const ServeDesc rd = a.reqs[w.z];
-        snp0 = w.x; snp_end = rd.i1; oi0 = rd.i0; ldo = rd.ldo; ntrait = rd.ntrait; jbase = w.w * TT;
+        snp0 = w.x; snp_lo = rd.i0; snp_end = rd.i1; oi0 = rd.i0; ldo = rd.ldo; ntrait = rd.ntrait; jbase = w.w * TT;
         full_b = rd.full_b; cst_tile = a.cst + (size_t)w.y * TT * FUSED_CST;
         obeta = rd.beta; ose = rd.se; ob64 = rd.b64; sing_ctr = rd.singular;
       } else {
         int us, ut;
         super_coords<CS, CT>(u, a, us, ut);
         const int st = us * CS + sr, tt = ut * CT + tr;
-        snp0 = a.row0 + (int64_t)st * BM; snp_end = a.row0 + a.nsnp; oi0 = a.i0; ldo = a.ldo; ntrait = a.ntrait;
+        snp0 = a.row0 + (int64_t)st * BM; snp_lo = a.snp_lo; snp_end = a.row0 + a.nsnp; oi0 = a.i0; ldo = a.ldo; ntrait = a.ntrait;
         jbase = tt * TT; full_b = a.full_b; cst_tile = a.cst + (size_t)jbase * FUSED_CST;
         obeta = a.out_beta; ose = a.out_se; ob64 = a.out_b64; sing_ctr = nullptr;
       }
@@ -352,7 +389,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       const bool ok = tc::mbar_wait(acc_full, tcount & 1, a.status, abort);
       tc::fence_after();
       const int64_t snp = snp0 + q * 32 + lane;
-      const bool valid_i = ok && snp < snp_end;
+      const bool valid_i = ok && snp >= snp_lo && snp < snp_end;
       const float sA = valid_i ? a.sA[snp] : 0.f;
       float ac[PM1] = {0.f, 0.f, 0.f};
       if (valid_i && full_b) {
@@ -360,10 +397,16 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         for (int c = 0; c < PM1; ++c) ac[c] = a.acoef[snp * PM1 + c];
       }
       unsigned long long tsing = 0;
-      for (int j0 = jbeg; j0 < jbeg + JPW; j0 += 4) {
-        // C1 accumulators first: reduce them to num and z before reading C2 (register pressure)
-        float num4[4], z4[4][PM1], zz4[4];
+      // All TMEM reads of this warp's JPW traits come first, reduced at once to the few
+      // per-pair values the solve needs; the accumulators are released before any of the
+      // per-pair arithmetic and output stores, so the next tile's MMAs wait only for the reads.
+      static_assert(JPW % 4 == 0, "epilogue reads traits in groups of 4");
+      float num_r[JPW], zz_r[JPW], s_r[JPW], z_r[JPW][PM1];
+#pragma unroll
+      for (int g = 0; g < JPW / 4; ++g) {
+        const int j0 = jbeg + 4 * g;
         {
+          // C1: levels of [w | v1 v2 v3] -> num and z
           uint32_t hw[4], hz[3][4], lw[4], lz[3][4], w3[4], w4[4];
           tc::tmem_ld4(lane_base + 0 * TT + j0, hw);
 #pragma unroll
@@ -381,18 +424,19 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             const float* cj = cs + (j0 + v) * FUSED_CST;
-            num4[v] = cj[0] * fmaf(F, fmaf(F, fmaf(F, __uint_as_float(w4[v]), __uint_as_float(w3[v])),
-                                         __uint_as_float(lw[v])), __uint_as_float(hw[v]));
-            zz4[v] = 0.f;
+            const int r = 4 * g + v;
+            num_r[r] = cj[0] * fmaf(F, fmaf(F, fmaf(F, __uint_as_float(w4[v]), __uint_as_float(w3[v])),
+                                          __uint_as_float(lw[v])), __uint_as_float(hw[v]));
+            zz_r[r] = 0.f;
 #pragma unroll
             for (int c = 0; c < PM1; ++c) {
-              z4[v][c] = cj[1 + c] * fmaf(F, __uint_as_float(lz[c][v]), __uint_as_float(hz[c][v]));
-              zz4[v] = fmaf(z4[v][c], z4[v][c], zz4[v]);
+              z_r[r][c] = cj[1 + c] * fmaf(F, __uint_as_float(lz[c][v]), __uint_as_float(hz[c][v]));
+              zz_r[r] = fmaf(z_r[r][c], z_r[r][c], zz_r[r]);
             }
           }
         }
-        float lvl0[4], lvl1[4];
         {
+          // C2: level 0 and the five level-1 groups -> s
           uint32_t d0[4], da[4], db[4], ea[4], eb[4], ec[4];
           tc::tmem_ld4(lane_base + 10 * TT + j0, d0);
           tc::tmem_ld4(lane_base + 11 * TT + j0, da);
@@ -405,32 +449,27 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
           tc::reg_fence(ea); tc::reg_fence(eb); tc::reg_fence(ec);
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
-            lvl0[v] = __uint_as_float(d0[v]);
-            lvl1[v] = (__uint_as_float(da[v]) + __uint_as_float(db[v])) +
-                      (__uint_as_float(ea[v]) + __uint_as_float(eb[v])) + __uint_as_float(ec[v]);
+            const float lvl1 = (__uint_as_float(da[v]) + __uint_as_float(db[v])) +
+                               (__uint_as_float(ea[v]) + __uint_as_float(eb[v])) + __uint_as_float(ec[v]);
+            s_r[4 * g + v] = (sA * cs[(j0 + v) * FUSED_CST + 4]) * fmaf(1.f / 256.f, lvl1, __uint_as_float(d0[v]));
           }
         }
-        if (j0 + 4 == jbeg + JPW) {
-          // every TMEM read of this warp for this tile is complete: release the accumulators
-          tc::fence_before();
-          __syncwarp();
-          if (lane == 0) {
-            if (PAIR) tc::mbar_arrive_cluster(tc::mapa(acc_empty, 0));
-            else tc::mbar_arrive(acc_empty);
-          }
-        }
-        if (!valid_i) continue;
+      }
+      // every TMEM read of this warp for this tile is complete: release the accumulators
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (PAIR) tc::mbar_arrive_cluster(tc::mapa(acc_empty, 0));
+        else tc::mbar_arrive(acc_empty);
+      }
+      if (valid_i) {
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const int jl = j0 + v;
+        for (int r = 0; r < JPW; ++r) {
+          const int jl = jbeg + r;
           const int jj = jbase + jl;            // trait index within the block (request)
           if (jj >= ntrait) break;
           const float* cj = cs + jl * FUSED_CST;
-          const float num = num4[v], zz = zz4[v];
-          float z[PM1];
-#pragma unroll
-          for (int c = 0; c < PM1; ++c) z[c] = z4[v][c];
-          const float s = (sA * cj[4]) * fmaf(1.f / 256.f, lvl1[v], lvl0[v]);
+          const float num = num_r[r], zz = zz_r[r], s = s_r[r];
           const float delta = s - zz;
           float beta, se;
           const bool sing = !(delta > 1e-6f * s) || !(sA > 0.f);
@@ -451,7 +490,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               // beta_L = g - L^-T z beta - a_i beta
               float t = cj[6 + c];
 #pragma unroll
-              for (int d = 0; d < PM1; ++d) t = fmaf(-cj[9 + c * PM1 + d] * z[d], beta, t);
+              for (int d = 0; d < PM1; ++d) t = fmaf(-cj[9 + c * PM1 + d] * z_r[r][d], beta, t);
               t = fmaf(-ac[c], beta, t);
               ob[c] = sing ? (double)beta : (double)t;
             }
@@ -503,7 +542,7 @@ int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const C
   auto kern = fused_kernel<CS, CT, EPW, SERVE, PAIR>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(PAIR));
     attr = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -513,7 +552,7 @@ int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const C
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.blockDim = dim3(64 + 32 * EPW);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.dynamicSmemBytes = smem_bytes(PAIR);
   cfg.stream = c->stream;
   cfg.attrs = at;
   cfg.numAttrs = 1;
@@ -538,6 +577,17 @@ int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const C
   return GWAS_OK;
 }
 
+
+// Tensor maps of the one-CTA-per-tile shapes: boxes of 128 genotype rows, 192 rows of
+// x'^2 planes, 160 C1 trait rows and 128 C2 trait rows.
+bool make_big_maps(CUtensorMap* mg, CUtensorMap* ma, CUtensorMap* m1, CUtensorMap* m2, const FusedArgs& a,
+                   const __nv_bfloat16* G, const __nv_bfloat16* A2, const __nv_bfloat16* B1, const __nv_bfloat16* B2,
+                   int ttiles) {
+  return make_bf16_map(mg, G, a.mpad, a.Kpad, BM, BK) && make_bf16_map(ma, A2, 3ull * a.mpad, a.Kpad, 3 * BM / 2, BK) &&
+         make_bf16_map(m1, B1, (uint64_t)ttiles * B1_ROWS, a.Kpad, B1_ROWS / 2, BK) &&
+         make_bf16_map(m2, B2, (uint64_t)ttiles * B2_ROWS, a.Kpad, B2_ROWS, BK);
+}
+
 }  // namespace
 
 int fused_trait_tile_multiple() { return 4; }
@@ -551,11 +601,19 @@ int launch_fused(gwas_ctx* c, const FusedArgs& args, const __nv_bfloat16* G, con
   const Shape sh = shape_from_env();
   const int ttiles_pad = (a.n_ttiles + 3) / 4 * 4;   // trait operands are allocated for a multiple of 4 tiles
   CUtensorMap mg, ma, m1, m2;
-  if (!make_bf16_map(&mg, G, a.mpad, a.Kpad, BM / sh.ct, BK) ||
-      !make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM / sh.ct, BK) ||
-      !make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * B1_ROWS, a.Kpad, BBOX, BK) ||
-      !make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * (sh.pair ? B2_ROWS_PAIR : B2_ROWS), a.Kpad, BBOX, BK))
-    return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
+  bool maps_ok;
+  if (sh.pair)  // boxes of 128 SNP rows, 160 C1 and 96 C2 trait rows (one CTA's half)
+    maps_ok = make_bf16_map(&mg, G, a.mpad, a.Kpad, BM, BK) && make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM, BK) &&
+              make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * B1_ROWS, a.Kpad, PC1_ROWS, BK) &&
+              make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * B2_ROWS_PAIR, a.Kpad, PC2_ROWS, BK);
+  else if (sh.cs == 1 && sh.ct == 1)
+    maps_ok = make_big_maps(&mg, &ma, &m1, &m2, a, G, A2, B1, B2, ttiles_pad);
+  else
+    maps_ok = make_bf16_map(&mg, G, a.mpad, a.Kpad, BM / sh.ct, BK) &&
+              make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM / sh.ct, BK) &&
+              make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * B1_ROWS, a.Kpad, BBOX, BK) &&
+              make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * B2_ROWS, a.Kpad, BBOX, BK);
+  if (!maps_ok) return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
 #define GWAS_SHAPE(CS, CT, EPW) \
   if (sh.cs == CS && sh.ct == CT && sh.epw == EPW && !sh.pair) return launch_shape<CS, CT, EPW>(c, a, mg, ma, m1, m2);
   GWAS_SHAPE(1, 1, 4)
@@ -574,9 +632,7 @@ int launch_fused_serve(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, 
                        const __nv_bfloat16* B1, const __nv_bfloat16* B2, int b_tiles) {
   if (a.nunits == 0) return GWAS_OK;
   CUtensorMap mg, ma, m1, m2;
-  if (!make_bf16_map(&mg, G, a.mpad, a.Kpad, BM) || !make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM) ||
-      !make_bf16_map(&m1, B1, (uint64_t)b_tiles * B1_ROWS, a.Kpad, BBOX) ||
-      !make_bf16_map(&m2, B2, (uint64_t)b_tiles * B2_ROWS, a.Kpad, BBOX))
+  if (!make_big_maps(&mg, &ma, &m1, &m2, a, G, A2, B1, B2, b_tiles))
     return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
   return launch_shape<1, 1, 16, true>(c, a, mg, ma, m1, m2);
 }

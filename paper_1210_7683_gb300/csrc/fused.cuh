@@ -11,6 +11,11 @@ struct gwas_ctx;
 //   [6..8] g = S_TL^-1 b_T, [9..17] L^-T (row-major), used for the full coefficient vector.
 #define FUSED_CST 20
 
+// Row of plane p (0..2) of SNP i in the x'_c^2 slice array: the three planes of each
+// 128-SNP tile are stored next to one another ([tile][plane][128 rows][Kpad]), so that
+// one tile's planes are 384 consecutive rows and load as two large TMA boxes.
+__host__ __device__ __forceinline__ int64_t a2_row(int p, int64_t i) { return ((i >> 7) * 3 + p) * 128 + (i & 127); }
+
 // Serving mode: one request of the work list (fused.cu, serve.cu).
 struct ServeDesc {
   int64_t i0, i1;     // SNP range of the request
@@ -24,9 +29,10 @@ struct ServeDesc {
 };
 
 struct FusedArgs {
-  int64_t row0;       // first SNP (row of G and of the x'_c^2 planes) of the range
+  int64_t row0;       // first SNP of the first tile (a multiple of 128)
+  int64_t snp_lo;     // first SNP of the range (row0 <= snp_lo < row0 + 128); SNPs below it are not written
   int64_t i0;         // SNP index that maps to output column 0
-  int64_t nsnp;       // SNPs in the range
+  int64_t nsnp;       // SNPs from row0 to the end of the range
   int n_stiles;       // ceil(nsnp / 128)
   int n_ttiles;       // ceil(ntrait / 32)
   int group;          // cluster-wide SNP super-tiles per traversal group (L2 reuse of genotype tiles)

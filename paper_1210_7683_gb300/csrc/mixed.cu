@@ -4,7 +4,7 @@
 //
 // Resident data (per loaded genotype set):
 //   G   [mpad][Kpad] bf16  exact genotypes x_i
-//   A2  [3][mpad][Kpad] bf16  slices of x'_c^2, x'_c = Z^T P_c x_i (P_c: projector onto
+//   A2  [mpad/128][3][128][Kpad] bf16  slices of x'_c^2 (a2_row), x'_c = Z^T P_c x_i (P_c: projector onto
 //                             the complement of span(X_L), applied through the B operand)
 //   sA  [m] float            per-SNP scale of the slices (0 for SNPs in span(X_L))
 //   acoef [m][p-1] float     a_i with P_c x_i = x_i - X_L a_i (full coefficient output)
@@ -153,9 +153,9 @@ __global__ void a2_slice_kernel(const float* __restrict__ Xc, int ldx, const int
       q1 = rintf(r1);
       q2 = rintf((r1 - q1) * 256.f);
     }
-    A2[(0 * mpad + i) * Kpad + k] = __float2bfloat16(q0);
-    A2[(1 * mpad + i) * Kpad + k] = __float2bfloat16(q1);
-    A2[(2 * mpad + i) * Kpad + k] = __float2bfloat16(q2 * (1.f / 256.f));
+    A2[a2_row(0, i) * Kpad + k] = __float2bfloat16(q0);
+    A2[a2_row(1, i) * Kpad + k] = __float2bfloat16(q1);
+    A2[a2_row(2, i) * Kpad + k] = __float2bfloat16(q2 * (1.f / 256.f));
   }
   if (lane == 0) sA[i] = singular ? 0.f : s;
   if (lane < PM1) acoef[i * PM1 + lane] = x[n + lane];
@@ -627,9 +627,11 @@ int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb,
   rc = mixed_prep_traits(c, w, dY, c->h2 + j0, tb, B1, B2, cst, nullptr, fused_pair_layout());
   if (rc == GWAS_OK) {
     FusedArgs a{};
-    a.row0 = i0;
+    // tiles start on multiples of 128 SNPs; those below i0 are not written
+    a.row0 = i0 & ~(int64_t)127;
+    a.snp_lo = i0;
     a.i0 = i0;
-    a.nsnp = i1 - i0;
+    a.nsnp = i1 - a.row0;
     a.n_stiles = (int)((a.nsnp + 127) / 128);
     a.n_ttiles = nt_tiles;
     a.group = 16;

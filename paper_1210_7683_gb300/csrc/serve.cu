@@ -228,7 +228,7 @@ void serve_loop(gwas_ctx* c) {
           for (int64_t u = 0; u < take; ++u) {
             int st, tt;
             unit_coords(r, r.next_unit + u, st, tt);
-            S->h_units[nu++] = make_int4((int)(r.i0 + (int64_t)st * 128), r.slots[tt], r.desc, tt);
+            S->h_units[nu++] = make_int4((int)((r.i0 & ~(int64_t)127) + (int64_t)st * 128), r.slots[tt], r.desc, tt);
           }
           if (take > 0) took.push_back({id, take});
           r.next_unit += take;
@@ -422,7 +422,9 @@ extern "C" int gwas_submit(gwas_ctx* c, const double* Y, int tk, const double* h
     if (!(dmin > 1e-12 * dmax)) return ctx_fail(c, GWAS_ERR_NOT_SPD, "M_j not positive definite");
   }
   r.nt = (tk + TT - 1) / TT;
-  r.ns = (int)((i1 - i0 + 127) / 128);
+  // SNP tiles start on multiples of 128 (the x'^2 planes are stored by 128-SNP tile);
+  // the SNPs of the first tile below i0 are computed and not written
+  r.ns = (int)((i1 - (i0 & ~(int64_t)127) + 127) / 128);
   r.units = (int64_t)r.nt * r.ns;
   r.t_submit = now_s();
   {
