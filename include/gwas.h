@@ -64,7 +64,10 @@ extern "C" {
 /* precision modes */
 #define GWAS_FP64  0  /* every step in FP64 (the paper's arithmetic, Section 6) */
 #define GWAS_MIXED 1  /* bf16 tensor-core contractions on exact fixed-point slices with
-                         FP32 accumulation; FP64 eigendecomposition and per-trait algebra */
+                         FP32 accumulation; FP64 eigendecomposition and per-trait algebra.
+                         Any 0 <= p-1 <= 7; traits are processed in tiles of 32 for
+                         p-1 <= 3 and of 16 above (the accumulators of a tile take
+                         (10 + 2(p-1)) x tile TMEM columns of 512). */
 
 /* output modes */
 #define GWAS_OUT_FULL_B  0  /* double b[t][i1-i0][p]: every coefficient, SNP coefficient last */

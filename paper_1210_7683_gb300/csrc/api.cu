@@ -227,8 +227,6 @@ extern "C" int gwas_setup(gwas_ctx** out, int n, int pm1, const double* phi, con
   if (!phi || !h2 || (pm1 > 0 && !XL)) return ctx_fail(nullptr, GWAS_ERR_ARG, "NULL input array");
   if (o.precision != GWAS_FP64 && o.precision != GWAS_MIXED) return ctx_fail(nullptr, GWAS_ERR_ARG, "bad precision mode");
   if (o.output != GWAS_OUT_FULL_B && o.output != GWAS_OUT_LAST_SE) return ctx_fail(nullptr, GWAS_ERR_ARG, "bad output mode");
-  if (o.precision == GWAS_MIXED && pm1 != 3)
-    return ctx_fail(nullptr, GWAS_ERR_UNSUPPORTED, "the mixed-precision path is built for p-1 = 3 covariates");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     cudaGetLastError();

@@ -44,32 +44,35 @@ namespace {
 
 // K extent of one stage: 64 bf16 = one 128-byte swizzled row.  (32-wide stages with
 // the 64-byte swizzle and 32-row boxes measured 1.6x slower: the TMA unit's cost per box.)
-constexpr int BM = 128, TT = 32, BK = 64;
+constexpr int BM = 128, BK = 64;
 constexpr int ROWB = BK * 2;                         // bytes per operand row of a stage
-constexpr int PM1 = 3;
 constexpr int G_BYTES = BM * ROWB;                   // 16 KB: one A tile
-constexpr int B1_ROWS = 10 * TT, B2_ROWS = 4 * TT;   // 320 and 128 rows per trait tile
-constexpr int B2_ROWS_PAIR = 6 * TT;                  // 192: C2 rows of a trait tile in the pair layout
-constexpr int BBOX = 32;                             // rows per TMA box of the trait operands
+constexpr int BBOX = 32;                             // rows per TMA box of the trait operands (cluster shapes)
 constexpr int SLOT = 64 * 1024;                      // one-CTA shapes: a ring slot holds either half-stage
 constexpr int SLOTS = 3;
-// CTA pair: each CTA stages its own SNP rows and half of the trait rows, in three items per
-// K block (G + C1 half: 36 KB; C2 half + A1: 28 KB; A2 + A3s: 32 KB) and a ring of six
+// half-stages of the one-CTA shapes: G + the C1 trait rows; the three x'^2 planes + the C2 trait rows
+__host__ __device__ constexpr int h1_bytes(int q) { return G_BYTES + c1_rows(q) * ROWB; }
+__host__ __device__ constexpr int h2_bytes(int q) { return 3 * G_BYTES + c2_rows(q) * ROWB; }
+// CTA pair (q = 3): each CTA stages its own SNP rows and half of the trait rows, in three items
+// per K block (G + C1 half: 36 KB; C2 half + A1: 28 KB; A2 + A3s: 32 KB) and a ring of six
 // 36 KB slots, i.e. two K blocks in flight.
 constexpr int PSLOT = 36 * 1024, PSLOTS = 6;
-constexpr int PC1_ROWS = B1_ROWS / 2, PC2_ROWS = B2_ROWS_PAIR / 2;  // 160 and 96 trait rows per CTA
+constexpr int PC1_ROWS = c1_rows(3) / 2, PC2_ROWS = c2_alloc(3) / 2;  // 160 and 96 trait rows per CTA
 constexpr int PI0_BYTES = G_BYTES + PC1_ROWS * ROWB;   // G + this CTA's C1 trait rows
 constexpr int PI1_BYTES = PC2_ROWS * ROWB + G_BYTES;   // this CTA's C2 trait rows + A1
 constexpr int PI2_BYTES = 2 * G_BYTES;                 // A2 + A3s
-constexpr int H1_BYTES = G_BYTES + B1_ROWS * ROWB;   // 57344
-constexpr int H2_BYTES = 3 * G_BYTES + B2_ROWS * ROWB;  // 65536
-constexpr int CST_BYTES = TT * FUSED_CST * 4;          // per-trait constants of one tile
+__host__ __device__ constexpr int cst_bytes(int q) { return mixed_tt(q) * cst_stride(q) * 4; }  // one tile's constants
 __host__ __device__ constexpr int ring_bytes(bool pair) { return pair ? PSLOTS * PSLOT : SLOTS * SLOT; }
-__host__ __device__ constexpr int smem_bytes(bool pair) { return ring_bytes(pair) + 2 * CST_BYTES + 1024 + 512; }
+__host__ __device__ constexpr int smem_bytes(bool pair, int q) { return ring_bytes(pair) + 2 * cst_bytes(q) + 1024 + 512; }
 constexpr int TMEM_COLS = 512;
-static_assert(H1_BYTES <= SLOT && H2_BYTES <= SLOT, "half-stage does not fit a slot");
+constexpr bool fits_all_q() {
+  for (int q = 0; q <= 7; ++q)
+    if (h1_bytes(q) > SLOT || h2_bytes(q) > SLOT || smem_bytes(false, q) > 227 * 1024) return false;
+  return true;
+}
+static_assert(fits_all_q(), "half-stage does not fit a slot");
 static_assert(PI0_BYTES <= PSLOT && PI1_BYTES <= PSLOT && PI2_BYTES <= PSLOT, "pair item does not fit a slot");
-static_assert(smem_bytes(true) <= 227 * 1024 && smem_bytes(false) <= 227 * 1024, "shared memory");
+static_assert(smem_bytes(true, 3) <= 227 * 1024, "shared memory");
 
 template <int CS, int CT>
 __device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us, int& ut) {
@@ -83,16 +86,27 @@ __device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us,
   us = g0 + w % gs;
 }
 
-// PAIR: the two CTAs of a cluster issue one M = 256 MMA (cta_group::2); each holds its
-// own 128 SNP rows and half of every MMA's trait rows (B2_ROWS_PAIR layout), the leader
-// (rank 0) issues the MMAs, and both CTAs' loads complete on the leader's barriers.
-template <int CS, int CT, int EPW, bool SERVE, bool PAIR>
+// Q = p - 1 covariates.  PAIR: the two CTAs of a cluster issue one M = 256 MMA
+// (cta_group::2); each holds its own 128 SNP rows and half of every MMA's trait rows (the
+// pair layout of the C2 operand, c2_alloc rows per tile), the leader (rank 0) issues the
+// MMAs, and both CTAs' loads complete on the leader's barriers.
+template <int CS, int CT, int EPW, bool SERVE, bool PAIR, int Q>
 __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     fused_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapA2,
                  const __grid_constant__ CUtensorMap mapB1, const __grid_constant__ CUtensorMap mapB2, FusedArgs a) {
   constexpr int NC = CS * CT;
   constexpr int AROWS = BM / CT;                    // genotype rows this CTA loads per plane
   static_assert(!PAIR || (CS == 2 && CT == 1 && !SERVE), "pair mode is a 2 x 1 cluster");
+  static_assert(NC == 1 || Q == 3, "cluster and pair shapes are built for q = 3");
+  constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = mixed_tt(Q), CSTR = cst_stride(Q);
+  constexpr int B1_ROWS = c1_rows(Q), B2_ROWS = c2_rows(Q), B2_ROWS_PAIR = c2_alloc(Q);
+  constexpr int C2B = c1_groups(Q) * TT;            // first TMEM column of the C2 accumulators
+  constexpr int H1_BYTES = h1_bytes(Q), H2_BYTES = h2_bytes(Q);
+  // C1 MMAs of the one-CTA shapes: the C1 trait rows in chunks of at most 256 (N <= 256)
+  constexpr int N0 = B1_ROWS < 256 ? B1_ROWS : 256, N1 = B1_ROWS - N0;
+  // TMA boxes of the C1 trait rows in the one-CTA shapes (at most 256 rows per box)
+  constexpr int B1_NBOX = B1_ROWS <= 256 ? 1 : 2, B1_BOX = B1_ROWS / B1_NBOX;
+  static_assert(N1 >= 0 && N1 <= 256 && N0 % 16 == 0 && N1 % 16 == 0 && B1_BOX % 8 == 0, "C1 geometry");
   // multicast cluster shapes: each CTA loads 1/CS of the trait rows in 32-row boxes
   constexpr int B1_BOXES = B1_ROWS / BBOX / CS, B2_BOXES = B2_ROWS / BBOX / CS;
   static_assert(B1_ROWS % (BBOX * CS) == 0 && B2_ROWS % (BBOX * CS) == 0 && BM % (8 * CT) == 0, "cluster shape");
@@ -105,8 +119,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   constexpr int NI = PAIR ? 3 : 2;                                        // ring items per K block
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* cst_smem = (float*)(smem + ring_bytes(PAIR));  // [2][TT][FUSED_CST], double-buffered by tile
-  uint64_t* full = (uint64_t*)(smem + ring_bytes(PAIR) + 2 * CST_BYTES);
+  float* cst_smem = (float*)(smem + ring_bytes(PAIR));  // [2][TT][CSTR], double-buffered by tile
+  uint64_t* full = (uint64_t*)(smem + ring_bytes(PAIR) + 2 * cst_bytes(Q));
   uint64_t* empty = full + NSL;
   uint64_t* acc_full = empty + NSL;
   uint64_t* acc_empty = acc_full + 1;
@@ -196,8 +210,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               if (half == 0) {
                 tc::mbar_expect_tx(&full[s], H1_BYTES);
                 tc::tma_load_2d(buf, &mapG, &full[s], x, row);
-                tc::tma_load_2d(buf + G_BYTES, &mapB1, &full[s], x, tt * B1_ROWS);
-                tc::tma_load_2d(buf + G_BYTES + B1_ROWS / 2 * ROWB, &mapB1, &full[s], x, tt * B1_ROWS + B1_ROWS / 2);
+#pragma unroll
+                for (int b = 0; b < B1_NBOX; ++b)
+                  tc::tma_load_2d(buf + G_BYTES + b * B1_BOX * ROWB, &mapB1, &full[s], x, tt * B1_ROWS + b * B1_BOX);
               } else {
                 const int y = (int)a2_row(0, row);
                 tc::mbar_expect_tx(&full[s], H2_BYTES);
@@ -302,8 +317,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         if (ok) tc::mma_commit_pair(acc_full, (uint16_t)3);
       }
     } else if (!PAIR && lane == 0) {
-      constexpr uint32_t id256 = tc::idesc_bf16(BM, 8 * TT), id64 = tc::idesc_bf16(BM, 2 * TT);
-      constexpr uint32_t id96 = tc::idesc_bf16(BM, 3 * TT), id32 = tc::idesc_bf16(BM, TT);
+      constexpr uint32_t idN0 = tc::idesc_bf16(BM, N0), idN1 = tc::idesc_bf16(BM, N1 > 0 ? N1 : 16);
+      constexpr uint32_t id3 = tc::idesc_bf16(BM, 3 * TT), id2 = tc::idesc_bf16(BM, 2 * TT), id1 = tc::idesc_bf16(BM, TT);
       const uint16_t release = maskA | maskB;
       uint32_t h = 0, tcount = 0;
       bool ok = true;
@@ -322,9 +337,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
               for (int k = 0; k < BK / 16; ++k) {
                 const uint32_t acc = (kb | k) ? 1u : 0u;
-                tc::mma_bf16(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), id256, acc);
-                tc::mma_bf16(tbase + 8 * TT, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, 8 * TT * ROWB + k * 32),
-                             id64, acc);
+                tc::mma_bf16(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), idN0, acc);
+                if (N1 > 0)
+                  tc::mma_bf16(tbase + N0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, N0 * ROWB + k * 32), idN1, acc);
               }
             } else {
               const uint64_t d1 = tc::sdesc_sw128(buf), d2 = tc::sdesc_sw128(buf + G_BYTES);
@@ -333,11 +348,12 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               for (int k = 0; k < BK / 16; ++k) {
                 const uint32_t acc = (kb | k) ? 1u : 0u;
                 // A1 x [E1 | E2 | E3s] -> [level 0 | a | b]
-                tc::mma_bf16(tbase + 10 * TT, tc::sdesc_add(d1, k * 32), tc::sdesc_add(de, TT * ROWB + k * 32), id96, acc);
+                tc::mma_bf16(tbase + C2B, tc::sdesc_add(d1, k * 32), tc::sdesc_add(de, TT * ROWB + k * 32), id3, acc);
                 // A2 x [E2s | E1] -> its own two groups
-                tc::mma_bf16(tbase + 13 * TT, tc::sdesc_add(d2, k * 32), tc::sdesc_add(de, k * 32), id64, acc);
+                tc::mma_bf16(tbase + C2B + 3 * TT, tc::sdesc_add(d2, k * 32), tc::sdesc_add(de, k * 32), id2, acc);
                 // A3s x E1 -> its own group
-                tc::mma_bf16(tbase + 15 * TT, tc::sdesc_add(d3, k * 32), tc::sdesc_add(de, TT * ROWB + k * 32), id32, acc);
+                tc::mma_bf16(tbase + C2B + 5 * TT, tc::sdesc_add(d3, k * 32), tc::sdesc_add(de, TT * ROWB + k * 32), id1,
+                             acc);
               }
             }
             if (NC > 1) tc::mma_commit_mc(&empty[s], release);
@@ -370,28 +386,28 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         const int4 w = a.units[u];
         const ServeDesc rd = a.reqs[w.z];
         snp0 = w.x; snp_lo = rd.i0; snp_end = rd.i1; oi0 = rd.i0; ldo = rd.ldo; ntrait = rd.ntrait; jbase = w.w * TT;
-        full_b = rd.full_b; cst_tile = a.cst + (size_t)w.y * TT * FUSED_CST;
+        full_b = rd.full_b; cst_tile = a.cst + (size_t)w.y * TT * CSTR;
         obeta = rd.beta; ose = rd.se; ob64 = rd.b64; sing_ctr = rd.singular;
       } else {
         int us, ut;
         super_coords<CS, CT>(u, a, us, ut);
         const int st = us * CS + sr, tt = ut * CT + tr;
         snp0 = a.row0 + (int64_t)st * BM; snp_lo = a.snp_lo; snp_end = a.row0 + a.nsnp; oi0 = a.i0; ldo = a.ldo; ntrait = a.ntrait;
-        jbase = tt * TT; full_b = a.full_b; cst_tile = a.cst + (size_t)jbase * FUSED_CST;
+        jbase = tt * TT; full_b = a.full_b; cst_tile = a.cst + (size_t)jbase * CSTR;
         obeta = a.out_beta; ose = a.out_se; ob64 = a.out_b64; sing_ctr = nullptr;
       }
       // stage this tile's per-trait constants (double buffer: the barrier of the previous
       // tile guarantees every epilogue warp has finished reading this buffer)
-      float* cs = cst_smem + (tcount & 1) * TT * FUSED_CST;
-      for (int e = ew * 32 + lane; e < TT * FUSED_CST; e += EPW * 32)
-        cs[e] = jbase + e / FUSED_CST < ntrait ? cst_tile[e] : 0.f;
+      float* cs = cst_smem + (tcount & 1) * TT * CSTR;
+      for (int e = ew * 32 + lane; e < TT * CSTR; e += EPW * 32)
+        cs[e] = jbase + e / CSTR < ntrait ? cst_tile[e] : 0.f;
       tc::named_sync(1, EPW * 32);
       const bool ok = tc::mbar_wait(acc_full, tcount & 1, a.status, abort);
       tc::fence_after();
       const int64_t snp = snp0 + q * 32 + lane;
       const bool valid_i = ok && snp >= snp_lo && snp < snp_end;
       const float sA = valid_i ? a.sA[snp] : 0.f;
-      float ac[PM1] = {0.f, 0.f, 0.f};
+      float ac[Q1] = {};
       if (valid_i && full_b) {
 #pragma unroll
         for (int c = 0; c < PM1; ++c) ac[c] = a.acoef[snp * PM1 + c];
@@ -401,49 +417,62 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       // per-pair values the solve needs; the accumulators are released before any of the
       // per-pair arithmetic and output stores, so the next tile's MMAs wait only for the reads.
       static_assert(JPW % 4 == 0, "epilogue reads traits in groups of 4");
-      float num_r[JPW], zz_r[JPW], s_r[JPW], z_r[JPW][PM1];
+      float num_r[JPW], zz_r[JPW], s_r[JPW], z_r[JPW][Q1];
+      const float F = 1.f / 256.f;
 #pragma unroll
       for (int g = 0; g < JPW / 4; ++g) {
         const int j0 = jbeg + 4 * g;
         {
-          // C1: levels of [w | v1 v2 v3] -> num and z
-          uint32_t hw[4], hz[3][4], lw[4], lz[3][4], w3[4], w4[4];
+          // C1, w: slices 1 and 2 (groups 0 and 1 + q) and the groups of slices 3 and 4 -> num
+          uint32_t hw[4], lw[4], w3[4], w4[4];
           tc::tmem_ld4(lane_base + 0 * TT + j0, hw);
-#pragma unroll
-          for (int c = 0; c < PM1; ++c) tc::tmem_ld4(lane_base + (1 + c) * TT + j0, hz[c]);
-          tc::tmem_ld4(lane_base + 4 * TT + j0, lw);
-#pragma unroll
-          for (int c = 0; c < PM1; ++c) tc::tmem_ld4(lane_base + (5 + c) * TT + j0, lz[c]);
-          tc::tmem_ld4(lane_base + 8 * TT + j0, w3);
-          tc::tmem_ld4(lane_base + 9 * TT + j0, w4);
+          tc::tmem_ld4(lane_base + (1 + PM1) * TT + j0, lw);
+          tc::tmem_ld4(lane_base + (2 + 2 * PM1) * TT + j0, w3);
+          tc::tmem_ld4(lane_base + (3 + 2 * PM1) * TT + j0, w4);
           tc::tmem_ld_wait();
           tc::reg_fence(hw); tc::reg_fence(lw); tc::reg_fence(w3); tc::reg_fence(w4);
 #pragma unroll
-          for (int c = 0; c < PM1; ++c) { tc::reg_fence(hz[c]); tc::reg_fence(lz[c]); }
-          const float F = 1.f / 256.f;
-#pragma unroll
           for (int v = 0; v < 4; ++v) {
-            const float* cj = cs + (j0 + v) * FUSED_CST;
-            const int r = 4 * g + v;
-            num_r[r] = cj[0] * fmaf(F, fmaf(F, fmaf(F, __uint_as_float(w4[v]), __uint_as_float(w3[v])),
-                                          __uint_as_float(lw[v])), __uint_as_float(hw[v]));
-            zz_r[r] = 0.f;
-#pragma unroll
-            for (int c = 0; c < PM1; ++c) {
-              z_r[r][c] = cj[1 + c] * fmaf(F, __uint_as_float(lz[c][v]), __uint_as_float(hz[c][v]));
-              zz_r[r] = fmaf(z_r[r][c], z_r[r][c], zz_r[r]);
-            }
+            num_r[4 * g + v] = cs[(j0 + v) * CSTR] *
+                               fmaf(F, fmaf(F, fmaf(F, __uint_as_float(w4[v]), __uint_as_float(w3[v])),
+                                            __uint_as_float(lw[v])), __uint_as_float(hw[v]));
+            zz_r[4 * g + v] = 0.f;
           }
+        }
+        // C1, v_c: slices 1 and 2 (groups 1 + c and 2 + q + c) -> z_c, three covariates per wait
+#pragma unroll
+        for (int c0 = 0; c0 < PM1; c0 += 3) {
+          constexpr int CB = 3;
+          uint32_t hz[CB][4], lz[CB][4];
+#pragma unroll
+          for (int c = 0; c < CB; ++c)
+            if (c0 + c < PM1) {
+              tc::tmem_ld4(lane_base + (1 + c0 + c) * TT + j0, hz[c]);
+              tc::tmem_ld4(lane_base + (2 + PM1 + c0 + c) * TT + j0, lz[c]);
+            }
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int c = 0; c < CB; ++c)
+            if (c0 + c < PM1) { tc::reg_fence(hz[c]); tc::reg_fence(lz[c]); }
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int c = 0; c < CB; ++c)
+              if (c0 + c < PM1) {
+                const float z = cs[(j0 + v) * CSTR + 1 + c0 + c] * fmaf(F, __uint_as_float(lz[c][v]), __uint_as_float(hz[c][v]));
+                z_r[4 * g + v][c0 + c] = z;
+                zz_r[4 * g + v] = fmaf(z, z, zz_r[4 * g + v]);
+              }
         }
         {
           // C2: level 0 and the five level-1 groups -> s
           uint32_t d0[4], da[4], db[4], ea[4], eb[4], ec[4];
-          tc::tmem_ld4(lane_base + 10 * TT + j0, d0);
-          tc::tmem_ld4(lane_base + 11 * TT + j0, da);
-          tc::tmem_ld4(lane_base + 12 * TT + j0, db);
-          tc::tmem_ld4(lane_base + 13 * TT + j0, ea);
-          tc::tmem_ld4(lane_base + 14 * TT + j0, eb);
-          tc::tmem_ld4(lane_base + 15 * TT + j0, ec);
+          tc::tmem_ld4(lane_base + C2B + 0 * TT + j0, d0);
+          tc::tmem_ld4(lane_base + C2B + 1 * TT + j0, da);
+          tc::tmem_ld4(lane_base + C2B + 2 * TT + j0, db);
+          tc::tmem_ld4(lane_base + C2B + 3 * TT + j0, ea);
+          tc::tmem_ld4(lane_base + C2B + 4 * TT + j0, eb);
+          tc::tmem_ld4(lane_base + C2B + 5 * TT + j0, ec);
           tc::tmem_ld_wait();
           tc::reg_fence(d0); tc::reg_fence(da); tc::reg_fence(db);
           tc::reg_fence(ea); tc::reg_fence(eb); tc::reg_fence(ec);
@@ -451,7 +480,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
           for (int v = 0; v < 4; ++v) {
             const float lvl1 = (__uint_as_float(da[v]) + __uint_as_float(db[v])) +
                                (__uint_as_float(ea[v]) + __uint_as_float(eb[v])) + __uint_as_float(ec[v]);
-            s_r[4 * g + v] = (sA * cs[(j0 + v) * FUSED_CST + 4]) * fmaf(1.f / 256.f, lvl1, __uint_as_float(d0[v]));
+            s_r[4 * g + v] = (sA * cs[(j0 + v) * CSTR + cst_escale(Q)]) * fmaf(F, lvl1, __uint_as_float(d0[v]));
           }
         }
       }
@@ -468,7 +497,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
           const int jl = jbeg + r;
           const int jj = jbase + jl;            // trait index within the block (request)
           if (jj >= ntrait) break;
-          const float* cj = cs + jl * FUSED_CST;
+          const float* cj = cs + jl * CSTR;
           const float num = num_r[r], zz = zz_r[r], s = s_r[r];
           const float delta = s - zz;
           float beta, se;
@@ -479,7 +508,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
           } else {
             const float inv = __frcp_rn(delta);
             beta = num * inv;
-            const float rss = fmaxf(fmaf(-num, beta, cj[5]), 0.f);
+            const float rss = fmaxf(fmaf(-num, beta, cj[cst_rr(Q)]), 0.f);
             se = __fsqrt_rn(rss * inv * inv_dof);
           }
           const int64_t o = (int64_t)jj * ldo + (snp - oi0);
@@ -488,9 +517,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
             for (int c = 0; c < PM1; ++c) {
               // beta_L = g - L^-T z beta - a_i beta
-              float t = cj[6 + c];
+              float t = cj[cst_g(Q) + c];
 #pragma unroll
-              for (int d = 0; d < PM1; ++d) t = fmaf(-cj[9 + c * PM1 + d] * z_r[r][d], beta, t);
+              for (int d = 0; d < PM1; ++d) t = fmaf(-cj[cst_lit(Q) + c * PM1 + d] * z_r[r][d], beta, t);
               t = fmaf(-ac[c], beta, t);
               ob[c] = sing ? (double)beta : (double)t;
             }
@@ -525,9 +554,12 @@ struct Shape {
   int cs, ct, epw, pair;
 };
 
-Shape shape_from_env() {
+// Kernel shape "CSxCTxEPW[xPAIR]" from GWAS_FUSED_SHAPE (q = 3 only; every other q runs the
+// default one-CTA shape).
+Shape shape_from_env(int q) {
   Shape sh{1, 1, 16, 0};
-  if (const char* e = getenv("GWAS_FUSED_SHAPE")) {
+  const char* e = getenv("GWAS_FUSED_SHAPE");
+  if (e && q == 3) {
     int cs = 0, ct = 0, epw = 0, pr = 0;
     const int k = sscanf(e, "%dx%dx%dx%d", &cs, &ct, &epw, &pr);
     if (k >= 3) sh = {cs, ct, epw, k == 4 ? pr : 0};
@@ -535,14 +567,14 @@ Shape shape_from_env() {
   return sh;
 }
 
-template <int CS, int CT, int EPW, bool SERVE = false, bool PAIR = false>
+template <int CS, int CT, int EPW, bool SERVE, bool PAIR, int Q>
 int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const CUtensorMap& ma,
                  const CUtensorMap& m1, const CUtensorMap& m2) {
   constexpr int NC = CS * CT;
-  auto kern = fused_kernel<CS, CT, EPW, SERVE, PAIR>;
+  auto kern = fused_kernel<CS, CT, EPW, SERVE, PAIR, Q>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(PAIR));
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(PAIR, Q));
     attr = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -552,7 +584,7 @@ int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const C
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.blockDim = dim3(64 + 32 * EPW);
-  cfg.dynamicSmemBytes = smem_bytes(PAIR);
+  cfg.dynamicSmemBytes = smem_bytes(PAIR, Q);
   cfg.stream = c->stream;
   cfg.attrs = at;
   cfg.numAttrs = 1;
@@ -577,62 +609,66 @@ int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const C
   return GWAS_OK;
 }
 
-
 // Tensor maps of the one-CTA-per-tile shapes: boxes of 128 genotype rows, 192 rows of
-// x'^2 planes, 160 C1 trait rows and 128 C2 trait rows.
-bool make_big_maps(CUtensorMap* mg, CUtensorMap* ma, CUtensorMap* m1, CUtensorMap* m2, const FusedArgs& a,
+// x'^2 planes, the C1 trait rows in one or two boxes of at most 256 rows, and the C2 trait rows.
+bool make_big_maps(int q, CUtensorMap* mg, CUtensorMap* ma, CUtensorMap* m1, CUtensorMap* m2, const FusedArgs& a,
                    const __nv_bfloat16* G, const __nv_bfloat16* A2, const __nv_bfloat16* B1, const __nv_bfloat16* B2,
                    int ttiles) {
+  const int r1 = c1_rows(q), r2 = c2_rows(q), b1box = r1 <= 256 ? r1 : r1 / 2;
   return make_bf16_map(mg, G, a.mpad, a.Kpad, BM, BK) && make_bf16_map(ma, A2, 3ull * a.mpad, a.Kpad, 3 * BM / 2, BK) &&
-         make_bf16_map(m1, B1, (uint64_t)ttiles * B1_ROWS, a.Kpad, B1_ROWS / 2, BK) &&
-         make_bf16_map(m2, B2, (uint64_t)ttiles * B2_ROWS, a.Kpad, B2_ROWS, BK);
+         make_bf16_map(m1, B1, (uint64_t)ttiles * r1, a.Kpad, b1box, BK) &&
+         make_bf16_map(m2, B2, (uint64_t)ttiles * r2, a.Kpad, r2, BK);
 }
 
 }  // namespace
 
 int fused_trait_tile_multiple() { return 4; }
 
-int fused_pair_layout() { return shape_from_env().pair; }
+int fused_pair_layout(int q) { return shape_from_env(q).pair; }
 
-int launch_fused(gwas_ctx* c, const FusedArgs& args, const __nv_bfloat16* G, const __nv_bfloat16* A2,
+int launch_fused(gwas_ctx* c, int q, const FusedArgs& args, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2) {
   FusedArgs a = args;
   if (a.n_stiles == 0 || a.n_ttiles == 0) return GWAS_OK;
-  const Shape sh = shape_from_env();
+  if (q < 0 || q > 7) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: p-1 outside [0, 7]");
+  const Shape sh = shape_from_env(q);
   const int ttiles_pad = (a.n_ttiles + 3) / 4 * 4;   // trait operands are allocated for a multiple of 4 tiles
   CUtensorMap mg, ma, m1, m2;
   bool maps_ok;
   if (sh.pair)  // boxes of 128 SNP rows, 160 C1 and 96 C2 trait rows (one CTA's half)
     maps_ok = make_bf16_map(&mg, G, a.mpad, a.Kpad, BM, BK) && make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM, BK) &&
-              make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * B1_ROWS, a.Kpad, PC1_ROWS, BK) &&
-              make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * B2_ROWS_PAIR, a.Kpad, PC2_ROWS, BK);
+              make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * c1_rows(3), a.Kpad, PC1_ROWS, BK) &&
+              make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * c2_alloc(3), a.Kpad, PC2_ROWS, BK);
   else if (sh.cs == 1 && sh.ct == 1)
-    maps_ok = make_big_maps(&mg, &ma, &m1, &m2, a, G, A2, B1, B2, ttiles_pad);
+    maps_ok = make_big_maps(q, &mg, &ma, &m1, &m2, a, G, A2, B1, B2, ttiles_pad);
   else
     maps_ok = make_bf16_map(&mg, G, a.mpad, a.Kpad, BM / sh.ct, BK) &&
               make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM / sh.ct, BK) &&
-              make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * B1_ROWS, a.Kpad, BBOX, BK) &&
-              make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * B2_ROWS, a.Kpad, BBOX, BK);
+              make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * c1_rows(3), a.Kpad, BBOX, BK) &&
+              make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * c2_rows(3), a.Kpad, BBOX, BK);
   if (!maps_ok) return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
+  if (sh.cs == 1 && sh.ct == 1 && sh.epw == 16 && !sh.pair) {
+    Q_DISPATCH(q, return launch_shape<1, 1, 16, false, false, Q>(c, a, mg, ma, m1, m2));
+  }
+  // optional cluster shapes (q = 3): TMA multicast of shared operands, or the CTA pair
 #define GWAS_SHAPE(CS, CT, EPW) \
-  if (sh.cs == CS && sh.ct == CT && sh.epw == EPW && !sh.pair) return launch_shape<CS, CT, EPW>(c, a, mg, ma, m1, m2);
-  GWAS_SHAPE(1, 1, 4)
-  GWAS_SHAPE(1, 1, 8)
-  GWAS_SHAPE(1, 1, 16)
-  GWAS_SHAPE(1, 2, 8)
+  if (sh.cs == CS && sh.ct == CT && sh.epw == EPW && !sh.pair) return launch_shape<CS, CT, EPW, false, false, 3>(c, a, mg, ma, m1, m2);
   GWAS_SHAPE(1, 2, 16)
   GWAS_SHAPE(2, 1, 16)
   GWAS_SHAPE(2, 2, 16)
-  if (sh.cs == 2 && sh.ct == 1 && sh.epw == 16 && sh.pair) return launch_shape<2, 1, 16, false, true>(c, a, mg, ma, m1, m2);
+  if (sh.cs == 2 && sh.ct == 1 && sh.epw == 16 && sh.pair)
+    return launch_shape<2, 1, 16, false, true, 3>(c, a, mg, ma, m1, m2);
 #undef GWAS_SHAPE
   return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: cluster shape not instantiated");
 }
 
-int launch_fused_serve(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
+int launch_fused_serve(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                        const __nv_bfloat16* B1, const __nv_bfloat16* B2, int b_tiles) {
   if (a.nunits == 0) return GWAS_OK;
+  if (q < 0 || q > 7) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: p-1 outside [0, 7]");
   CUtensorMap mg, ma, m1, m2;
-  if (!make_big_maps(&mg, &ma, &m1, &m2, a, G, A2, B1, B2, b_tiles))
+  if (!make_big_maps(q, &mg, &ma, &m1, &m2, a, G, A2, B1, B2, b_tiles))
     return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
-  return launch_shape<1, 1, 16, true>(c, a, mg, ma, m1, m2);
+  Q_DISPATCH(q, return launch_shape<1, 1, 16, true, false, Q>(c, a, mg, ma, m1, m2));
+  return GWAS_OK;
 }

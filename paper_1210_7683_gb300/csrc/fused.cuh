@@ -6,10 +6,43 @@
 
 struct gwas_ctx;
 
-// Per-trait FP32 constants of the epilogue (stride FUSED_CST):
-//   [0] scale of w, [1..3] scales of v'_1..3, [4] scale of e, [5] r^T M^-1 r,
-//   [6..8] g = S_TL^-1 b_T, [9..17] L^-T (row-major), used for the full coefficient vector.
-#define FUSED_CST 20
+// Geometry of the mixed path for q = p - 1 covariates (0 <= q <= 7).
+//   A trait tile holds mixed_tt(q) traits.  Its C1 operand has c1_groups(q) groups of
+//   mixed_tt(q) rows: [w1 | v_1..v_q] (slice 1), [w2 | v_1..v_q] (slice 2), w3, w4.  Its
+//   C2 operand has 4 groups [E2s | E1 | E2 | E3s].  The accumulators of a tile take
+//   (c1_groups(q) + 6) * mixed_tt(q) <= 512 TMEM columns.
+__host__ __device__ constexpr int mixed_tt(int q) { return q <= 3 ? 32 : 16; }
+__host__ __device__ constexpr int c1_groups(int q) { return 4 + 2 * q; }
+__host__ __device__ constexpr int c1_rows(int q) { return c1_groups(q) * mixed_tt(q); }
+__host__ __device__ constexpr int c2_rows(int q) { return 4 * mixed_tt(q); }
+// C2 rows allocated per trait tile (the CTA-pair layout, q = 3 only, needs 6 groups)
+__host__ __device__ constexpr int c2_alloc(int q) { return 6 * mixed_tt(q); }
+
+// Runs the statement in the variadic arguments with the compile-time constant Q = q (0..7,
+// larger values run as 7).
+#define Q_DISPATCH(q, ...)                                   \
+  switch (q) {                                               \
+    case 0: { constexpr int Q = 0; __VA_ARGS__; } break;     \
+    case 1: { constexpr int Q = 1; __VA_ARGS__; } break;     \
+    case 2: { constexpr int Q = 2; __VA_ARGS__; } break;     \
+    case 3: { constexpr int Q = 3; __VA_ARGS__; } break;     \
+    case 4: { constexpr int Q = 4; __VA_ARGS__; } break;     \
+    case 5: { constexpr int Q = 5; __VA_ARGS__; } break;     \
+    case 6: { constexpr int Q = 6; __VA_ARGS__; } break;     \
+    default: { constexpr int Q = 7; __VA_ARGS__; } break;    \
+  }
+
+// Per-trait FP32 constants of the epilogue, cst_stride(q) floats per trait:
+//   [0] scale of w, [1..q] scales of v'_1..q, [q+1] scale of e, [q+2] r^T M^-1 r,
+//   [q+3 .. 2q+2] g = S_TL^-1 b_T, [2q+3 ..] L^-T (q x q, row-major), used for the full
+//   coefficient vector.
+__host__ __device__ constexpr int cst_stride(int q) { return (3 + 2 * q + q * q + 3) / 4 * 4; }
+__host__ __device__ constexpr int cst_escale(int q) { return q + 1; }
+__host__ __device__ constexpr int cst_rr(int q) { return q + 2; }
+__host__ __device__ constexpr int cst_g(int q) { return q + 3; }
+__host__ __device__ constexpr int cst_lit(int q) { return 2 * q + 3; }
+static_assert(cst_stride(3) == 20 && (c1_groups(3) + 6) * mixed_tt(3) == 512, "p = 4 geometry");
+static_assert((c1_groups(7) + 6) * mixed_tt(7) <= 512, "TMEM columns");
 
 // Row of plane p (0..2) of SNP i in the x'_c^2 slice array: the three planes of each
 // 128-SNP tile are stored next to one another ([tile][plane][128 rows][Kpad]), so that
@@ -34,16 +67,16 @@ struct FusedArgs {
   int64_t i0;         // SNP index that maps to output column 0
   int64_t nsnp;       // SNPs from row0 to the end of the range
   int n_stiles;       // ceil(nsnp / 128)
-  int n_ttiles;       // ceil(ntrait / 32)
+  int n_ttiles;       // ceil(ntrait / mixed_tt(q))
   int group;          // cluster-wide SNP super-tiles per traversal group (L2 reuse of genotype tiles)
   int ntrait;         // traits in this block
   int Kpad;           // padded n (multiple of 64)
   int64_t mpad;       // rows per plane of G and of the x'_c^2 planes
   float dof;          // n - p
   const float* sA;    // [m] scale of the x'_c^2 slices of each SNP (0 marks a singular SNP)
-  const float* acoef; // [m][3] centring coefficients a_i (full output only)
-  const float* cst;   // [ntrait][FUSED_CST]
-  int full_b;         // 1: double b[ntrait][ldo][4]; 0: float beta/se [ntrait][ldo]
+  const float* acoef; // [m][q] centring coefficients a_i (full output only)
+  const float* cst;   // [trait tiles * mixed_tt(q)][cst_stride(q)]
+  int full_b;         // 1: double b[ntrait][ldo][q + 1]; 0: float beta/se [ntrait][ldo]
   int64_t ldo;        // output stride between traits (SNPs)
   float* out_beta;
   float* out_se;
@@ -58,14 +91,16 @@ struct FusedArgs {
 };
 
 // Trait operands (B1, B2) must be allocated (and zeroed) for a multiple of this many trait tiles,
-// with 320 B1 rows and 192 B2 rows per trait tile.
+// with c1_rows(q) B1 rows and c2_alloc(q) B2 rows per trait tile.
 int fused_trait_tile_multiple();
 // 1 when the selected kernel shape is the CTA-pair one, whose trait operands use the pair layout.
-int fused_pair_layout();
+int fused_pair_layout(int q);
 
-int launch_fused(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
+// q = p - 1 selects the kernel's geometry; shapes other than the default one-CTA shape
+// are built for q = 3 only.
+int launch_fused(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2);
 // Serving mode: processes a.units (a.cst indexed by trait-tile slot) with per-request outputs.
 // b_tiles = trait-tile slots of the B1/B2 arena.
-int launch_fused_serve(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
+int launch_fused_serve(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                        const __nv_bfloat16* B1, const __nv_bfloat16* B2, int b_tiles);

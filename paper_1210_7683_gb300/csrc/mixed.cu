@@ -7,7 +7,7 @@
 //   A2  [mpad/128][3][128][Kpad] bf16  slices of x'_c^2 (a2_row), x'_c = Z^T P_c x_i (P_c: projector onto
 //                             the complement of span(X_L), applied through the B operand)
 //   sA  [m] float            per-SNP scale of the slices (0 for SNPs in span(X_L))
-//   acoef [m][p-1] float     a_i with P_c x_i = x_i - X_L a_i (full coefficient output)
+//   acoef [m][q] float       a_i with P_c x_i = x_i - X_L a_i (full coefficient output), q = p - 1
 // Per gwas_solve trait block: Y' = Z^T Y and the back-rotated per-trait columns
 //   w_j = M_j^-1 r_j and v'_j = P_c M_j^-1 X_L L_j^-T, both by exact sliced GEMMs.
 #include <algorithm>
@@ -32,24 +32,22 @@ struct MixedState {
 
 namespace {
 
-constexpr int PM1 = 3;
-constexpr int TT = 32;
-constexpr int B1_ROWS = 10 * TT, B2_ROWS = 4 * TT;
-constexpr int B2_ALLOC = 6 * TT;  // B2 rows allocated per trait tile (the CTA-pair layout needs 192)
-
 inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
 
 // Rows of the FP64 B operand of the genotype rotation: row k < n is P_c z_k (so that
 // (P_c Z)^T x = Z^T P_c x); row n + a holds the map x -> a_i[a] = ((X_L^T X_L)^-1 X_L^T x)[a].
+template <int Q>
 __global__ void rot_b_kernel(const double* __restrict__ Zc, const double* __restrict__ XL,
                              const double* __restrict__ XtXinv, int n, double* __restrict__ out) {
+  constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1;
   const int k = blockIdx.x;
-  __shared__ double red[PM1][8];
-  __shared__ double coef[PM1];
+  __shared__ double red[Q1][8];
+  __shared__ double coef[Q1];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (k < n) {
     const double* z = Zc + (size_t)k * n;
-    double u[PM1] = {0, 0, 0};
+    double u[Q1] = {};
     for (int l = threadIdx.x; l < n; l += blockDim.x)
       for (int a = 0; a < PM1; ++a) u[a] += XL[(size_t)a * n + l] * z[l];
     for (int a = 0; a < PM1; ++a) {
@@ -59,7 +57,7 @@ __global__ void rot_b_kernel(const double* __restrict__ Zc, const double* __rest
     }
     __syncthreads();
     if (threadIdx.x < PM1) {
-      double s[PM1];
+      double s[Q1];
       for (int a = 0; a < PM1; ++a) {
         s[a] = 0;
         for (int w = 0; w < (int)blockDim.x / 32; ++w) s[a] += red[a][w];
@@ -111,7 +109,7 @@ __global__ void geno_bf16_kernel(const int8_t* __restrict__ X, int64_t m, int n,
 // doubled while the level-0 partial sums could reach 2^24) and the centring coefficients.
 __global__ void a2_slice_kernel(const float* __restrict__ Xc, int ldx, const int8_t* __restrict__ X, int64_t row0,
                                 int64_t rows, int n, int64_t mpad, int Kpad, __nv_bfloat16* __restrict__ A2,
-                                float* __restrict__ sA, float* __restrict__ acoef) {
+                                float* __restrict__ sA, float* __restrict__ acoef, int q) {
   const int warps = blockDim.x / 32;
   const int64_t r = blockIdx.x * (int64_t)warps + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
@@ -158,7 +156,7 @@ __global__ void a2_slice_kernel(const float* __restrict__ Xc, int ldx, const int
     A2[a2_row(2, i) * Kpad + k] = __float2bfloat16(q2 * (1.f / 256.f));
   }
   if (lane == 0) sA[i] = singular ? 0.f : s;
-  if (lane < PM1) acoef[i * PM1 + lane] = x[n + lane];
+  if (lane < q) acoef[i * q + lane] = x[n + lane];
 }
 
 // Per-trait FP64 algebra (Algorithm 5, per-trait lines) with e_j = diag(D_j^-1):
@@ -166,23 +164,25 @@ __global__ void a2_slice_kernel(const float* __restrict__ Xc, int ldx, const int
 //   r' = y' - X'_L g,  rr = r'^T diag(e) r',
 //   rows of Wt: [e . r' | (e . X'_L) L^-T]  (rotated basis; back-rotated by Z later),
 //   slices of e in the C2 operand layout [E2s | E1 | E2 | E3s].
+template <int Q>
 __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restrict__ Yt, int ldy,
                                                          const double* __restrict__ h2, const double* __restrict__ lam,
                                                          const double* __restrict__ XLt, int n, int Kpad,
                                                          double* __restrict__ Wt, __nv_bfloat16* __restrict__ B2,
                                                          float* __restrict__ cst, const int* __restrict__ slot,
                                                          int pair) {
+  constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = mixed_tt(Q);
   const int j = blockIdx.x;
   const double h = h2[j];
   const double* y = Yt + (size_t)j * ldy;
   __shared__ double red[8][PM1 * PM1 + PM1 + 1];
-  __shared__ double sh_g[PM1], sh_Lit[PM1 * PM1], sh_se;
+  __shared__ double sh_g[Q1], sh_Lit[Q1 * Q1], sh_se;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   double part[PM1 * PM1 + PM1 + 1];
   for (int q = 0; q < PM1 * PM1 + PM1 + 1; ++q) part[q] = 0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const double e = 1.0 / (h * lam[k] + (1.0 - h));
-    double xl[PM1];
+    double xl[Q1];
     for (int a = 0; a < PM1; ++a) xl[a] = XLt[(size_t)a * n + k];
     for (int a = 0; a < PM1; ++a) {
       for (int b = 0; b < PM1; ++b) part[a * PM1 + b] += e * xl[a] * xl[b];
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double S[PM1][PM1], bT[PM1], emax = 0;
+    double S[Q1][Q1], bT[Q1], emax = 0;
     for (int a = 0; a < PM1; ++a) {
       for (int b = 0; b < PM1; ++b) {
         double v = 0;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
       bT[a] = v;
     }
     for (int w = 0; w < nw; ++w) emax = fmax(emax, red[w][PM1 * PM1 + PM1]);
-    double L[PM1][PM1] = {};
+    double L[Q1][Q1] = {};
     for (int a = 0; a < PM1; ++a)
       for (int b = 0; b <= a; ++b) {
         double v = S[a][b];
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
         L[a][b] = (a == b) ? sqrt(fmax(v, 1e-300)) : v / L[b][b];
       }
     // Linv = L^-1 (lower)
-    double Li[PM1][PM1] = {};
+    double Li[Q1][Q1] = {};
     for (int c = 0; c < PM1; ++c)
       for (int a = 0; a < PM1; ++a) {
         double v = (a == c) ? 1.0 : 0.0;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
         Li[a][c] = v / L[a][a];
       }
     // g = L^-T L^-1 b_T
-    double zt[PM1];
+    double zt[Q1];
     for (int a = 0; a < PM1; ++a) {
       double v = 0;
       for (int k = 0; k <= a; ++k) v += Li[a][k] * bT[k];
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
   double rr = 0;
   const int p = PM1 + 1;
   const int tile = slot ? slot[j / TT] : j / TT, jj = j % TT;
-  __nv_bfloat16* b2 = B2 + (size_t)tile * (pair ? B2_ALLOC : B2_ROWS) * Kpad;
+  __nv_bfloat16* b2 = B2 + (size_t)tile * (pair ? c2_alloc(Q) : c2_rows(Q)) * Kpad;
   // rows of the four slices of e in the C2 operand of the tile:
   //   one CTA:   [E2s | E1 | E2 | E3s], 32 rows each;
   //   CTA pair:  each MMA's rows split between the two CTAs (E1 appears three times)
@@ -261,11 +261,11 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
     r_e3s = 7 * TT / 2 + jj; r_e1b = 9 * TT / 2 + jj;
   }
   for (int k = threadIdx.x; k < Kpad; k += blockDim.x) {
-    double w = 0, v[PM1] = {0, 0, 0};
+    double w = 0, v[Q1] = {};
     float q0 = 0, q1 = 0, q2 = 0;
     if (k < n) {
       const double e = 1.0 / (h * lam[k] + (1.0 - h));
-      double xl[PM1];
+      double xl[Q1];
       for (int a = 0; a < PM1; ++a) xl[a] = XLt[(size_t)a * n + k];
       double r = y[k];
       for (int a = 0; a < PM1; ++a) r -= xl[a] * sh_g[a];
@@ -302,30 +302,32 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
   if (threadIdx.x == 0) {
     double v = 0;
     for (int w = 0; w < nw; ++w) v += red[w][0];
-    float* cj = cst + ((size_t)tile * TT + jj) * FUSED_CST;
-    cj[4] = (float)se;
-    cj[5] = (float)v;
-    for (int a = 0; a < PM1; ++a) cj[6 + a] = (float)sh_g[a];
-    for (int q = 0; q < PM1 * PM1; ++q) cj[9 + q] = (float)sh_Lit[q];
+    float* cj = cst + ((size_t)tile * TT + jj) * cst_stride(Q);
+    cj[cst_escale(Q)] = (float)se;
+    cj[cst_rr(Q)] = (float)v;
+    for (int a = 0; a < PM1; ++a) cj[cst_g(Q) + a] = (float)sh_g[a];
+    for (int q = 0; q < PM1 * PM1; ++q) cj[cst_lit(Q) + q] = (float)sh_Lit[q];
   }
 }
 
-// Per trait: project the back-rotated columns [w | v_1..3] with P_c and write their
+// Per trait: project the back-rotated columns [w | v_1..q] with P_c and write their
 // fixed-point slices in the C1 operand layout (w: 4 slices, v: 2 slices).
+template <int Q>
 __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__ W, const double* __restrict__ XL,
                                                       const double* __restrict__ XtXinv, int n, int Kpad,
                                                       __nv_bfloat16* __restrict__ B1, float* __restrict__ cst,
                                                       const int* __restrict__ slot, int pair) {
+  constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = mixed_tt(Q);
   const int j = blockIdx.x;
   const int p = PM1 + 1;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   __shared__ double red[8][PM1 + 1];
-  __shared__ double coef[PM1], smax;
+  __shared__ double coef[Q1], smax;
   const int tile = slot ? slot[j / TT] : j / TT, jj = j % TT;
-  __nv_bfloat16* b1 = B1 + (size_t)tile * B1_ROWS * Kpad;
+  __nv_bfloat16* b1 = B1 + (size_t)tile * c1_rows(Q) * Kpad;
   for (int c = 0; c < p; ++c) {
     const double* col = W + ((size_t)j * p + c) * Kpad;
-    double u[PM1] = {0, 0, 0};
+    double u[Q1] = {};
     for (int l = threadIdx.x; l < n; l += blockDim.x)
       for (int a = 0; a < PM1; ++a) u[a] += XL[(size_t)a * n + l] * col[l];
     for (int a = 0; a < PM1; ++a) {
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__
     }
     __syncthreads();
     if (threadIdx.x < PM1) {
-      double s[PM1];
+      double s[Q1];
       for (int a = 0; a < PM1; ++a) {
         s[a] = 0;
         for (int w = 0; w < nw; ++w) s[a] += red[w][a];
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__
       double v = 0;
       for (int w = 0; w < nw; ++w) v = fmax(v, red[w][PM1]);
       smax = v > 0 ? v / 256.0 : 1.0;
-      cst[((size_t)tile * TT + jj) * FUSED_CST + (c == 0 ? 0 : c)] = (float)smax;
+      cst[((size_t)tile * TT + jj) * cst_stride(Q) + c] = (float)smax;
     }
     __syncthreads();
     const double inv = 1.0 / smax;
@@ -372,9 +374,10 @@ __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__
       }
       for (int s = 0; s < nsl; ++s) {
         const double q = rint(t);
-        // one CTA: [Q1 | Q2 | Q3 | Q4]; CTA pair: [Q1 | Q3] for the first CTA, [Q2 | Q4] for the second
+        // one CTA: groups [slice 1 of w, v_1..q | slice 2 of w, v_1..q | w3 | w4];
+        // CTA pair (q = 3): [Q1 | Q3] for the first CTA, [Q2 | Q4] for the second
         int row;
-        if (!pair) row = s < 2 ? s * 4 * TT + c * TT + jj : (s == 2 ? 8 * TT : 9 * TT) + jj;
+        if (!pair) row = (s < 2 ? s * (1 + Q) + c : 2 * Q + s) * TT + jj;
         else row = (s == 0 ? 0 : s == 1 ? 5 * TT : s == 2 ? 4 * TT : 9 * TT) + (s < 2 ? c * TT : 0) + jj;
         b1[(size_t)row * Kpad + l] = __float2bfloat16((float)q);
         t = (t - q) * 256.0;
@@ -415,17 +418,17 @@ static void mixed_destroy_setup(gwas_ctx* c) {
 // One-time preparation of the B operands of the three rotations.
 static int mixed_setup(gwas_ctx* c) {
   if (c->mixed && c->mixed->Brot) return GWAS_OK;
-  if (c->pm1 != PM1) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "mixed path needs p-1 = 3");
+  if (c->pm1 < 0 || c->pm1 > 7) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "mixed path needs 0 <= p-1 <= 7");
   if (!c->mixed) c->mixed = new MixedState;
   MixedState* s = c->mixed;
-  const int n = c->n;
+  const int n = c->n, PM1 = c->pm1;
   s->Kpad = (int)rup(n, 64);
   s->bits = xgemm_bits(s->Kpad);
   s->ldx = (int)rup(n + PM1, 64);
   int rc;
   double *rot = nullptr, *zr = nullptr;
   const size_t plane_rows_rot = (size_t)s->ldx, plane_rows_z = (size_t)s->Kpad;
-  if ((rc = ctx_alloc(c, sizeof(double) * PM1 * PM1, (void**)&s->XtXinv)) ||
+  if ((rc = ctx_alloc(c, sizeof(double) * std::max(1, PM1 * PM1), (void**)&s->XtXinv)) ||
       (rc = ctx_alloc(c, sizeof(double) * (size_t)(n + PM1) * n, (void**)&rot)) ||
       (rc = ctx_alloc(c, sizeof(double) * (size_t)n * n, (void**)&zr)) ||
       (rc = ctx_alloc(c, 2ull * 4 * plane_rows_rot * s->Kpad, (void**)&s->Brot)) ||
@@ -439,9 +442,10 @@ static int mixed_setup(gwas_ctx* c) {
     mixed_destroy_setup(c);
     return rc;
   }
-  cudaMemcpyAsync(s->XtXinv, c->h_XtXinv.data(), sizeof(double) * PM1 * PM1, cudaMemcpyHostToDevice, c->stream);
+  if (PM1 > 0)
+    cudaMemcpyAsync(s->XtXinv, c->h_XtXinv.data(), sizeof(double) * PM1 * PM1, cudaMemcpyHostToDevice, c->stream);
   { ProfScope ps(c, "setup_rotation_operands");
-  rot_b_kernel<<<n + PM1, 256, 0, c->stream>>>(c->Z, c->XL, s->XtXinv, n, rot);
+  Q_DISPATCH(PM1, rot_b_kernel<Q><<<n + PM1, 256, 0, c->stream>>>(c->Z, c->XL, s->XtXinv, n, rot));
   c->launches++;
   dim3 tb(32, 8), tg((n + 31) / 32, (n + 31) / 32);
   transpose_kernel<<<tg, tb, 0, c->stream>>>(c->Z, n, zr);
@@ -463,12 +467,12 @@ int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m) {
   int rc = mixed_setup(c);
   if (rc) return rc;
   MixedState* s = c->mixed;
-  const int n = c->n;
+  const int n = c->n, PM1 = c->pm1;
   s->mpad = rup(m, 128);
   if ((rc = ctx_alloc(c, 2ull * s->mpad * s->Kpad, (void**)&s->G)) ||
       (rc = ctx_alloc(c, 2ull * 3 * s->mpad * s->Kpad, (void**)&s->A2)) ||
       (rc = ctx_alloc(c, sizeof(float) * m, (void**)&s->sA)) ||
-      (rc = ctx_alloc(c, sizeof(float) * m * PM1, (void**)&s->acoef))) {
+      (rc = ctx_alloc(c, sizeof(float) * m * std::max(1, PM1), (void**)&s->acoef))) {
     mixed_free(c);
     return rc;
   }
@@ -503,7 +507,7 @@ int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m) {
       const int warps = 8;
       ProfScope ps(c, "slice_snp_squares");
       a2_slice_kernel<<<(unsigned)((rows + warps - 1) / warps), warps * 32, 0, c->stream>>>(
-          Xc, s->ldx, dXR, r0, rows, n, s->mpad, s->Kpad, s->A2, s->sA, s->acoef);
+          Xc, s->ldx, dXR, r0, rows, n, s->mpad, s->Kpad, s->A2, s->sA, s->acoef, PM1);
       c->launches++;
     }
   }
@@ -536,7 +540,7 @@ int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** out) {
   *out = nullptr;
   MixedState* s = c->mixed;
   if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
-  const int p = PM1 + 1, Kpad = s->Kpad;
+  const int q = c->pm1, p = q + 1, Kpad = s->Kpad, TT = mixed_tt(q);
   const int nt_tiles = (tb_max + TT - 1) / TT;
   const int nt_alloc = (nt_tiles + fused_trait_tile_multiple() - 1) / fused_trait_tile_multiple() *
                        fused_trait_tile_multiple();
@@ -550,9 +554,9 @@ int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** out) {
       (rc = ctx_alloc(c, sizeof(double) * (size_t)tb_max * p * Kpad, (void**)&w->Wt)) ||
       (rc = ctx_alloc(c, 2ull * 4 * rowsW * Kpad, (void**)&w->Wsl)) ||
       (rc = ctx_alloc(c, sizeof(double) * rowsW, (void**)&w->sW)) ||
-      (rc = ctx_alloc(c, 2ull * (size_t)nt_alloc * B1_ROWS * Kpad, (void**)&w->B1)) ||
-      (rc = ctx_alloc(c, 2ull * (size_t)nt_alloc * B2_ALLOC * Kpad, (void**)&w->B2)) ||
-      (rc = ctx_alloc(c, sizeof(float) * (size_t)nt_tiles * TT * FUSED_CST, (void**)&w->cst))) {
+      (rc = ctx_alloc(c, 2ull * (size_t)nt_alloc * c1_rows(q) * Kpad, (void**)&w->B1)) ||
+      (rc = ctx_alloc(c, 2ull * (size_t)nt_alloc * c2_alloc(q) * Kpad, (void**)&w->B2)) ||
+      (rc = ctx_alloc(c, sizeof(float) * (size_t)nt_tiles * TT * cst_stride(q), (void**)&w->cst))) {
     mixed_ws_free(c, w);
     return rc;
   }
@@ -565,7 +569,7 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h
   MixedState* s = c->mixed;
   if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
   if (tb > w->tb_max) return ctx_fail(c, GWAS_ERR_ARG, "trait block larger than its workspace");
-  const int n = c->n, p = PM1 + 1, Kpad = s->Kpad;
+  const int n = c->n, q = c->pm1, p = q + 1, Kpad = s->Kpad;
   const int rowsY = (int)rup(tb, 128), rowsW = (int)rup((int64_t)tb * p, 128);
   int rc = GWAS_OK;
   __nv_bfloat16 *Ysl = w->Ysl, *Wsl = w->Wsl;
@@ -588,7 +592,8 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h
   if ((rc = launch_xgemm(c, 4, 4, 3, g, Ysl, s->Bzt)) == GWAS_OK) {
     // per-trait algebra and the C2 operand
     ProfScope ps(c, "prep_traits");
-    prep_mixed_kernel<<<tb, 256, 0, c->stream>>>(Yt, Kpad, h2, c->lam, c->XLt, n, Kpad, Wt, B2, cst, slot, pair);
+    Q_DISPATCH(q, prep_mixed_kernel<Q><<<tb, 256, 0, c->stream>>>(Yt, Kpad, h2, c->lam, c->XLt, n, Kpad, Wt, B2, cst,
+                                                                  slot, pair));
     c->launches++;
     // back-rotation [w | v] = Z [e.r' | (e.X'_L) L^-T]
     launch_slice_rows(c, Wt, Kpad, tb * p, n, rowsW, Kpad, 4, s->bits, Wsl, sW);
@@ -604,7 +609,7 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h
   }
   if (rc == GWAS_OK) {
     ProfScope ps(c, "pack_trait_columns");
-    pack_c1_kernel<<<tb, 256, 0, c->stream>>>(Wt, c->XL, s->XtXinv, n, Kpad, B1, cst, slot, pair);
+    Q_DISPATCH(q, pack_c1_kernel<Q><<<tb, 256, 0, c->stream>>>(Wt, c->XL, s->XtXinv, n, Kpad, B1, cst, slot, pair));
     c->launches++;
   }
   return rc;
@@ -615,16 +620,16 @@ int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb,
   MixedState* s = c->mixed;
   if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
   if (tb > w->tb_max) return ctx_fail(c, GWAS_ERR_ARG, "trait block larger than its workspace");
-  const int n = c->n, p = PM1 + 1, Kpad = s->Kpad;
+  const int n = c->n, q = c->pm1, p = q + 1, Kpad = s->Kpad, TT = mixed_tt(q);
   const int nt_tiles = (tb + TT - 1) / TT;
   const int nt_alloc = (nt_tiles + fused_trait_tile_multiple() - 1) / fused_trait_tile_multiple() *
                        fused_trait_tile_multiple();
   int rc = GWAS_OK;
   __nv_bfloat16 *B1 = w->B1, *B2 = w->B2;
   float* cst = w->cst;
-  cudaMemsetAsync(B1, 0, 2ull * nt_alloc * B1_ROWS * Kpad, c->stream);
-  cudaMemsetAsync(B2, 0, 2ull * nt_alloc * B2_ALLOC * Kpad, c->stream);
-  rc = mixed_prep_traits(c, w, dY, c->h2 + j0, tb, B1, B2, cst, nullptr, fused_pair_layout());
+  cudaMemsetAsync(B1, 0, 2ull * nt_alloc * c1_rows(q) * Kpad, c->stream);
+  cudaMemsetAsync(B2, 0, 2ull * nt_alloc * c2_alloc(q) * Kpad, c->stream);
+  rc = mixed_prep_traits(c, w, dY, c->h2 + j0, tb, B1, B2, cst, nullptr, fused_pair_layout(q));
   if (rc == GWAS_OK) {
     FusedArgs a{};
     // tiles start on multiples of 128 SNPs; those below i0 are not written
@@ -655,7 +660,7 @@ int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb,
     }
     a.status = c->d_status;
     a.singular = c->d_status + 1;
-    rc = launch_fused(c, a, s->G, s->A2, B1, B2);
+    rc = launch_fused(c, q, a, s->G, s->A2, B1, B2);
   }
   return rc;
 }

@@ -28,8 +28,6 @@
 
 namespace {
 
-constexpr int TT = 32;
-constexpr int B1_ROWS = 10 * TT, B2_ROWS = 4 * TT;
 constexpr int GROUP = 16;  // SNP tiles per traversal group of a request
 
 double now_s() {
@@ -66,6 +64,7 @@ struct ServeState {
   std::thread thread;
   // device resources
   int slots = 0, max_prep = 0, round_units = 0, max_reqs = 0;
+  int tt = 0, b1_rows = 0, b2_rows = 0, cstr = 0;  // trait-tile geometry for q = p - 1 (mixed_tt, c1_rows, ...)
   std::vector<int> free_slots;
   std::vector<int> free_desc;
   __nv_bfloat16 *B1 = nullptr, *B2 = nullptr;
@@ -173,6 +172,7 @@ void serve_loop(gwas_ctx* c) {
       while (k < todo.size() && rc == GWAS_OK) {
         int rows = 0, tiles = 0;
         cudaStreamSynchronize(c->stream);  // the pinned staging is reused by every batch
+        const int TT = S->tt;
         while (k < todo.size() && rows + TT <= S->max_prep) {
           Request* r;
           {
@@ -250,7 +250,7 @@ void serve_loop(gwas_ctx* c) {
       a.units = S->d_units;
       a.nunits = nu;
       a.reqs = S->d_desc;
-      rc = launch_fused_serve(c, a, mixed_G(c), mixed_A2(c), S->B1, S->B2, S->slots);
+      rc = launch_fused_serve(c, c->pm1, a, mixed_G(c), mixed_A2(c), S->B1, S->B2, S->slots);
       cudaError_t e = cudaStreamSynchronize(c->stream);
       unsigned long long st0 = 0;
       if (rc == GWAS_OK && e == cudaSuccess) {
@@ -313,6 +313,11 @@ int serve_init(gwas_ctx* c) {
   S->max_reqs = 4096;
   if (const char* e = getenv("GWAS_SERVE_SLOTS")) S->slots = std::max(8, atoi(e));
   if (const char* e = getenv("GWAS_SERVE_ROUND")) S->round_units = std::max(152, atoi(e));
+  const int q = c->pm1, TT = mixed_tt(q);
+  S->tt = TT;
+  S->b1_rows = c1_rows(q);
+  S->b2_rows = c2_rows(q);
+  S->cstr = cst_stride(q);
   int rc;
   auto fail = [&](int code) {
     ctx_free(c, S->B1); ctx_free(c, S->B2); ctx_free(c, S->cst); ctx_free(c, S->d_desc); ctx_free(c, S->d_sing);
@@ -325,9 +330,9 @@ int serve_init(gwas_ctx* c) {
     delete S;
     return code;
   };
-  if ((rc = ctx_alloc(c, 2ull * S->slots * B1_ROWS * Kpad, (void**)&S->B1)) ||
-      (rc = ctx_alloc(c, 2ull * S->slots * B2_ROWS * Kpad, (void**)&S->B2)) ||
-      (rc = ctx_alloc(c, sizeof(float) * S->slots * TT * FUSED_CST, (void**)&S->cst)) ||
+  if ((rc = ctx_alloc(c, 2ull * S->slots * S->b1_rows * Kpad, (void**)&S->B1)) ||
+      (rc = ctx_alloc(c, 2ull * S->slots * S->b2_rows * Kpad, (void**)&S->B2)) ||
+      (rc = ctx_alloc(c, sizeof(float) * S->slots * TT * S->cstr, (void**)&S->cst)) ||
       (rc = ctx_alloc(c, sizeof(ServeDesc) * S->max_reqs, (void**)&S->d_desc)) ||
       (rc = ctx_alloc(c, sizeof(unsigned long long) * S->max_reqs, (void**)&S->d_sing)) ||
       (rc = ctx_alloc(c, sizeof(int4) * S->round_units, (void**)&S->d_units)) ||
@@ -343,8 +348,8 @@ int serve_init(gwas_ctx* c) {
     cudaGetLastError();
     return fail(ctx_fail(c, GWAS_ERR_OOM, "pinned host staging for serving"));
   }
-  cudaMemsetAsync(S->B1, 0, 2ull * S->slots * B1_ROWS * Kpad, c->stream);
-  cudaMemsetAsync(S->B2, 0, 2ull * S->slots * B2_ROWS * Kpad, c->stream);
+  cudaMemsetAsync(S->B1, 0, 2ull * S->slots * S->b1_rows * Kpad, c->stream);
+  cudaMemsetAsync(S->B2, 0, 2ull * S->slots * S->b2_rows * Kpad, c->stream);
   cudaMemsetAsync(c->d_status, 0, 32, c->stream);
   cudaStreamSynchronize(c->stream);
   for (int i = S->slots - 1; i >= 0; --i) S->free_slots.push_back(i);
@@ -389,6 +394,7 @@ extern "C" int gwas_submit(gwas_ctx* c, const double* Y, int tk, const double* h
   cudaSetDevice(dev0);
   if (rc) return rc;
   ServeState* S = c->serve;
+  const int TT = S->tt;
   if ((tk + TT - 1) / TT > S->slots)
     return ctx_fail(c, GWAS_ERR_OOM, "request has more traits than the serving operand arena holds");
   // output: device memory or page-locked host memory (the kernel writes it directly)

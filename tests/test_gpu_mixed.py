@@ -111,3 +111,25 @@ def test_sampled_pairs_at_full_mixed_workload(gw):
     assert finite
     b, se = EigOracle(phi, XL).solve(XR[idx], Y[tj], h2[tj])
     check_last(got, b, se)
+
+
+# Any number of covariates: q = p - 1 from 0 to 7.  Tiles hold 32 traits for q <= 3 and 16
+# above; the trait and SNP counts leave ragged last tiles.
+@pytest.mark.parametrize("pm1,n,m,t", [(0, 200, 300, 40), (1, 256, 257, 33), (2, 300, 200, 17), (4, 256, 300, 20),
+                                       (5, 130, 129, 45), (6, 200, 256, 19), (7, 97, 300, 35)])
+def test_general_p_last_se(gw, pm1, n, m, t):
+    P = make_problem(n, m, t, pm1=pm1, seed=101 * pm1 + n)
+    out, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE)
+    assert rc == gw.GWAS_OK
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    check_last(out, b, se)
+
+
+@pytest.mark.parametrize("pm1", [0, 2, 5, 7])
+def test_general_p_full_b(gw, pm1):
+    P = make_problem(160, 290, 37, pm1=pm1, seed=7 + pm1)
+    out, rc, _ = solve(gw, P, gw.GWAS_OUT_FULL_B)
+    assert rc == gw.GWAS_OK
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    err = full_b_err(out.transpose(1, 0, 2), b, se)
+    assert err <= TOL, err

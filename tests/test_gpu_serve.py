@@ -96,3 +96,35 @@ def test_poll_and_singular_request(gw):
             gw.gwas_submit(ctx, Y, 40, h2, 0, 10, np.empty((2, 40, 10), np.float32))  # pageable output
     finally:
         gw.gwas_destroy(ctx)
+
+
+@pytest.mark.parametrize("pm1", [0, 5])
+def test_serving_general_p(gw, pm1):
+    """Serving with q = p - 1 other than 3 (tiles of 16 traits for q = 5): a mix of
+    requests equals gwas_solve of each request and the oracle."""
+    P = make_problem(160, 1200, 2, pm1=pm1, seed=43 + pm1)
+    reqs = requests(P, 6, 11 + pm1)
+    ctx = new_ctx(gw, P)
+    try:
+        outs, ids = [], []
+        for k, (Y, h2, i0, i1) in enumerate(reqs):
+            out = alloc_out(len(h2), i1 - i0, k)
+            outs.append(out)
+            ids.append(gw.gwas_submit(ctx, Y, len(h2), h2, i0, i1, out))
+        for rid in ids:
+            assert gw.gwas_wait(ctx, rid, 120.0) == gw.GWAS_OK
+        mix = [o.cpu().numpy() for o in outs]
+    finally:
+        gw.gwas_destroy(ctx)
+    for k in (0, 2, 5):
+        Y, h2, i0, i1 = reqs[k]
+        ctx = new_ctx(gw, P, t=len(h2), h2=h2)
+        try:
+            out = np.empty((2, len(h2), i1 - i0), np.float32)
+            gw.gwas_solve(ctx, Y, i0, i1, out)
+        finally:
+            gw.gwas_destroy(ctx)
+        np.testing.assert_array_equal(out, mix[k])
+        b, se = EigOracle(P.phi, P.XL).solve(P.XR[i0:i1], Y, h2)
+        assert last_coef_err(out[0].T.astype(np.float64), out[1].T.astype(np.float64), b, se) <= 1e-6
+        assert se_err(out[1].T.astype(np.float64), se) <= 1e-6
