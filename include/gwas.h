@@ -159,6 +159,38 @@ GWAS_API int gwas_solve_stream(gwas_ctx* ctx, const double* Y, int64_t i0, int64
                                void* host_buf0, void* host_buf1, gwas_block_fn fn, void* user);
 
 /*
+ * gwas_solve_ooc -- Algorithm 5 for genotype sets larger than device memory: the
+ * out-of-core setting of Section 4, in which slabs of X_R are streamed through two
+ * buffers (double buffering) while the previous slab is processed.  Here the slabs come
+ * from host memory; each is uploaded on a side stream while the previous one is computed,
+ * converted and rotated on the device exactly as gwas_load_snps does (the preloop of
+ * Section 4.1, fused into the loop instead of written back), and solved against every
+ * trait.  Results leave through the caller's two host buffers, one (slab, trait block)
+ * piece at a time.
+ *
+ *   m, XR         SNPs and their int8 genotypes, n x m column-major (SNP i at XR + i*n),
+ *                 host memory (pageable or page-locked) or device memory
+ *   slab          SNPs per slab, >= 0 (0 = 2^20); rounded up to a multiple of 128
+ *   Y             n x t traits, FP64 (host or device)
+ *   block_traits  traits per piece, >= 1
+ *   host_buf0/1   host buffers, each large enough for one piece of slab x block_traits
+ *                 pairs in gwas_solve's layout (for nb traits and i1-i0 SNPs)
+ *   fn            called on the calling thread for every piece, in order:
+ *                 fn(user, i0, i1, j0, nb, host_block) for SNPs [i0, i1) x traits
+ *                 [j0, j0+nb); host_block stays valid until fn returns
+ *
+ * Pieces arrive trait block by trait block, slab by slab within a block.  The results
+ * equal those of gwas_load_snps(m, XR) followed by gwas_solve, bit for bit.  Genotypes of
+ * an earlier gwas_load_snps are released first; the context holds none afterwards.
+ * Fails with GWAS_ERR_STATE while serving requests are pending.  Device memory: the slab
+ * arrays (about 8 bytes per SNP and individual on the mixed path, 8 on the FP64 path),
+ * two int8 slabs and two output staging pieces.
+ */
+typedef void (*gwas_slab_fn)(void* user, int64_t i0, int64_t i1, int j0, int nb, const void* host_block);
+GWAS_API int gwas_solve_ooc(gwas_ctx* ctx, int64_t m, const int8_t* XR, int64_t slab, const double* Y,
+                            int block_traits, void* host_buf0, void* host_buf1, gwas_slab_fn fn, void* user);
+
+/*
  * Serving (continuous batching).  gwas_submit queues a request: tk traits Y
  * (n x tk, FP64) with their own heritabilities h2k, solved against the resident
  * SNPs [i0, i1).  A scheduler thread of the context admits queued requests while

@@ -50,6 +50,7 @@ class gwas_opts(C.Structure):
 
 # void (*)(void* user, int j0, int nb, const void* host_block)
 GWAS_BLOCK_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int, C.c_int, C.c_void_p)
+GWAS_SLAB_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_int, C.c_void_p)
 
 
 def _load():
@@ -81,6 +82,8 @@ def _load():
     lib.gwas_solve_fp64_noalloc.restype = ci
     lib.gwas_solve_stream.argtypes = [vp, vp, i64, i64, ci, vp, vp, GWAS_BLOCK_FN, vp]
     lib.gwas_solve_stream.restype = ci
+    lib.gwas_solve_ooc.argtypes = [vp, i64, vp, i64, vp, ci, vp, vp, GWAS_SLAB_FN, vp]
+    lib.gwas_solve_ooc.restype = ci
     lib.gwas_submit.argtypes = [vp, vp, ci, vp, i64, i64, vp, C.POINTER(C.c_uint64)]
     lib.gwas_submit.restype = ci
     lib.gwas_poll.argtypes = [vp, C.c_uint64, C.POINTER(ci)]
@@ -189,6 +192,20 @@ def gwas_solve_stream(ctx, Y, i0, i1, block_traits, buf0, buf1, fn):
     dt = np.float64 if getattr(buf0, "dtype", None) in (np.float64, getattr(_torch(), "float64", None)) else np.float32
     rc = lib.gwas_solve_stream(ctx, _addr(Y, np.float64, None, "Y"), int(i0), int(i1), int(block_traits),
                                _addr(buf0, dt, None, "buf0"), _addr(buf1, dt, None, "buf1"), cb, None)
+    return _check(rc, ctx, allow=(GWAS_ERR_SINGULAR_PAIRS,))
+
+
+def gwas_solve_ooc(ctx, m, XR, slab, Y, block_traits, buf0, buf1, fn, n=None):
+    """Out-of-core solve: XR (m, n) int8 SNP-major in host (or device) memory is streamed in
+    slabs of `slab` SNPs; fn(i0, i1, j0, nb, address) is called per finished piece of SNPs
+    [i0, i1) x traits [j0, j0+nb), the piece in gwas_solve's layout at `address` (one of the
+    two host buffers).  Returns GWAS_OK or GWAS_ERR_SINGULAR_PAIRS; raises otherwise.
+    """
+    cb = GWAS_SLAB_FN(lambda user, i0, i1, j0, nb, ptr: fn(i0, i1, j0, nb, ptr))
+    dt = np.float64 if getattr(buf0, "dtype", None) in (np.float64, getattr(_torch(), "float64", None)) else np.float32
+    shape = None if n is None else (m, n)
+    rc = lib.gwas_solve_ooc(ctx, int(m), _addr(XR, np.int8, shape, "XR"), int(slab), _addr(Y, np.float64, None, "Y"),
+                            int(block_traits), _addr(buf0, dt, None, "buf0"), _addr(buf1, dt, None, "buf1"), cb, None)
     return _check(rc, ctx, allow=(GWAS_ERR_SINGULAR_PAIRS,))
 
 

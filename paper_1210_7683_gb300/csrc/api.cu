@@ -7,6 +7,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "gwas_internal.cuh"
 
@@ -26,6 +28,19 @@ struct DeviceGuard {
     if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
   }
 };
+
+// One cuSOLVER handle per device for the whole process, created on first use: creating a
+// handle and its first eigensolver call cost several milliseconds that every gwas_setup
+// would otherwise pay.  The mutex serialises contexts of different host threads that run
+// their eigendecompositions at the same time (a handle is bound to one stream at a time).
+struct SolverCache {
+  std::mutex mu;
+  std::map<int, cusolverDnHandle_t> handles;
+};
+SolverCache& solver_cache() {
+  static SolverCache* s = new SolverCache;  // never destroyed: handles outlive every context
+  return *s;
+}
 
 std::string fmt(const char* f, ...) {
   char buf[512];
@@ -185,7 +200,6 @@ static void destroy_impl(gwas_ctx* c) {
   c->mixed = nullptr;
   for (auto& b : c->bufs) cudaFree(b.ptr);
   c->bufs.clear();
-  if (c->solver) cusolverDnDestroy((cusolverDnHandle_t)c->solver);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   if (have) cudaSetDevice(dev);
   delete c;
@@ -254,9 +268,13 @@ extern "C" int gwas_setup(gwas_ctx** out, int n, int pm1, const double* phi, con
   if ((rc = ctx_alloc(c, sizeof(double) * n * n, (void**)&c->Z))) return fail(rc);
   if ((rc = ctx_alloc(c, sizeof(double) * n, (void**)&c->lam))) return fail(rc);
   if ((rc = ctx_upload(c, phi, sizeof(double) * n * n, c->Z))) return fail(rc);
-  cusolverDnHandle_t h;
-  if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) return fail(ctx_fail(c, GWAS_ERR_CUDA, "cusolverDnCreate failed"));
-  c->solver = h;
+  SolverCache& sc = solver_cache();
+  std::unique_lock<std::mutex> solver_lock(sc.mu);
+  cusolverDnHandle_t h = sc.handles.count(c->device) ? sc.handles[c->device] : nullptr;
+  if (!h) {
+    if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) return fail(ctx_fail(c, GWAS_ERR_CUDA, "cusolverDnCreate failed"));
+    sc.handles[c->device] = h;
+  }
   cusolverDnSetStream(h, c->stream);
   int lwork = 0;
   if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, c->Z, n, c->lam, &lwork) !=
@@ -279,6 +297,7 @@ extern "C" int gwas_setup(gwas_ctx** out, int n, int pm1, const double* phi, con
                    "lambda", &rc))
     return fail(rc);
   if (!ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "eigendecomposition", &rc)) return fail(rc);
+  solver_lock.unlock();
   ctx_free(c, work);
   ctx_free(c, info);
   if (hinfo != 0) return fail(ctx_fail(c, GWAS_ERR_NOT_SPD, fmt("eigensolver did not converge (info %d)", hinfo)));
@@ -620,4 +639,201 @@ extern "C" int gwas_solve_stream(gwas_ctx* c, const double* Y, int64_t i0, int64
   sink.fn = fn;
   sink.user = user;
   return solve_impl(c, Y, i0, i1, std::min(block_traits, c->t), sink);
+}
+
+// Out-of-core solve (Section 4: slabs of X_R through two buffers while the previous slab is
+// processed).  Units u = (trait block b, slab s), b-major.  Per unit, on the compute stream:
+// the block's per-trait operands (first slab of a block), the slab's conversion and rotation
+// (gwas_load_snps' work, into slab-sized arrays), the fused kernel into output staging k = u&1.
+// On the copy stream: the upload of the next unit's slab into int8 buffer (u+1)&1, and the
+// download of the finished piece, after which the host calls fn.
+extern "C" int gwas_solve_ooc(gwas_ctx* c, int64_t m, const int8_t* XR, int64_t slab, const double* Y,
+                              int block_traits, void* host_buf0, void* host_buf1, gwas_slab_fn fn, void* user) {
+  if (!c) return GWAS_ERR_ARG;
+  if (m < 1 || slab < 0 || block_traits < 1 || !XR || !Y || !host_buf0 || !host_buf1 || !fn)
+    return ctx_fail(c, GWAS_ERR_ARG, "gwas_solve_ooc needs m >= 1, slab >= 0, block_traits >= 1 and non-NULL arguments");
+  DeviceGuard guard(c->device);
+  if (serve_busy(c)) return ctx_fail(c, GWAS_ERR_STATE, "gwas_solve_ooc while serving requests are pending");
+  serve_shutdown(c);
+  int rc;
+  bool xdev, ydev, d0, d1;
+  if ((rc = ptr_kind(c, XR, &xdev)) || (rc = ptr_kind(c, Y, &ydev)) || (rc = ptr_kind(c, host_buf0, &d0)) ||
+      (rc = ptr_kind(c, host_buf1, &d1)))
+    return rc;
+  if (d0 || d1) return ctx_fail(c, GWAS_ERR_ARG, "gwas_solve_ooc buffers must be host memory");
+  bool xpinned = false;
+  if (!xdev) {
+    cudaPointerAttributes at;
+    xpinned = cudaPointerGetAttributes(&at, XR) == cudaSuccess && at.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+  }
+  // the slabs take the place of a resident genotype set
+  ctx_free(c, c->Xt);
+  c->Xt = nullptr;
+  mixed_free(c);
+  c->m = 0;
+  c->singular = 0;
+  const int n = c->n, t = c->t, p = c->p;
+  if (slab == 0) slab = 1 << 20;
+  slab = std::min<int64_t>((slab + 127) / 128 * 128, (m + 127) / 128 * 128);
+  const int tb = std::min(block_traits, t);
+  const int nblocks = (t + tb - 1) / tb;
+  const int64_t nslabs = (m + slab - 1) / slab, U = nblocks * nslabs;
+  const bool lastse = c->output == GWAS_OUT_LAST_SE;
+  const size_t pair_bytes = lastse ? 2 * sizeof(float) : sizeof(double) * p;
+  std::vector<void*> tmp;
+  auto talloc = [&](size_t b, void** q) {
+    int r = ctx_alloc(c, b, q);
+    if (r == GWAS_OK) tmp.push_back(*q);
+    return r;
+  };
+  MixedWs* ws = nullptr;
+  int8_t* hX[2] = {nullptr, nullptr};
+  int8_t* dX[2] = {nullptr, nullptr};
+  double *dY = (double*)Y, *Yt = nullptr, *R = nullptr, *cst = nullptr;
+  void* stage[2] = {nullptr, nullptr};
+  void* ring[2] = {host_buf0, host_buf1};
+  cudaEvent_t ev_up[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(c->stream);
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+    if (ws) mixed_ws_free(c, ws);
+    for (void* q : tmp) ctx_free(c, q);
+    for (int k = 0; k < 2; ++k) {
+      if (hX[k]) cudaFreeHost(hX[k]);
+      if (ev_up[k]) cudaEventDestroy(ev_up[k]);
+      if (ev_used[k]) cudaEventDestroy(ev_used[k]);
+    }
+    ctx_free(c, c->Xt);
+    c->Xt = nullptr;
+    mixed_free(c);
+    c->m = 0;
+  };
+  cudaMemsetAsync(c->d_status, 0, 32, c->stream);
+  if (!ydev) {
+    if ((rc = talloc(sizeof(double) * t * n, (void**)&dY)) || (rc = ctx_upload(c, Y, sizeof(double) * t * n, dY))) {
+      cleanup();
+      return rc;
+    }
+  }
+  if ((rc = ensure_copy_stream(c)) || (rc = talloc(pair_bytes * (size_t)tb * slab, &stage[0])) ||
+      (rc = talloc(pair_bytes * (size_t)tb * slab, &stage[1]))) {
+    cleanup();
+    return rc;
+  }
+  for (int k = 0; k < 2 && rc == GWAS_OK; ++k) {
+    ctx_cuda_ok(c, cudaEventCreateWithFlags(&ev_up[k], cudaEventDisableTiming), "event", &rc);
+    if (rc == GWAS_OK) ctx_cuda_ok(c, cudaEventCreateWithFlags(&ev_used[k], cudaEventDisableTiming), "event", &rc);
+    if (rc == GWAS_OK && !xdev) rc = talloc((size_t)slab * n, (void**)&dX[k]);
+    if (rc == GWAS_OK && !xdev && !xpinned &&
+        cudaHostAlloc((void**)&hX[k], (size_t)slab * n, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      hX[k] = nullptr;
+      rc = ctx_fail(c, GWAS_ERR_OOM, "pinned staging of the genotype slabs");
+    }
+  }
+  if (rc == GWAS_OK) {
+    if (c->precision == GWAS_FP64) {
+      if ((rc = talloc(sizeof(double) * tb * n, (void**)&Yt)) == GWAS_OK &&
+          (rc = talloc(sizeof(double) * tb * (p + 1) * n, (void**)&R)) == GWAS_OK &&
+          (rc = talloc(sizeof(double) * tb * consts_stride(c->pm1), (void**)&cst)) == GWAS_OK)
+        rc = ctx_alloc(c, sizeof(double) * slab * n, (void**)&c->Xt);
+    } else {
+      rc = mixed_ws_alloc(c, tb, &ws);
+    }
+  }
+  if (rc) {
+    cleanup();
+    return rc;
+  }
+  auto unit = [&](int64_t u, int64_t* i0, int64_t* rows, int* j0, int* nb) {
+    const int64_t b = u / nslabs, s = u % nslabs;
+    *i0 = s * slab;
+    *rows = std::min<int64_t>(slab, m - *i0);
+    *j0 = (int)(b * tb);
+    *nb = std::min(tb, t - *j0);
+  };
+  auto upload = [&](int64_t u) -> int {
+    int64_t i0, rows;
+    int j0, nb, r = GWAS_OK;
+    unit(u, &i0, &rows, &j0, &nb);
+    const int k = (int)(u & 1);
+    // int8 buffer k was last read by the conversion of unit u - 2
+    if (u >= 2 && !ctx_cuda_ok(c, cudaStreamWaitEvent(c->copy_stream, ev_used[k], 0), "event wait", &r)) return r;
+    const int8_t* src = XR + (size_t)i0 * n;
+    if (!xpinned) {
+      // pinned staging k was last read by the upload of unit u - 2
+      if (u >= 2 && !ctx_cuda_ok(c, cudaEventSynchronize(ev_up[k]), "slab upload", &r)) return r;
+      std::memcpy(hX[k], src, (size_t)rows * n);
+      src = hX[k];
+    }
+    if (!ctx_cuda_ok(c, cudaMemcpyAsync(dX[k], src, (size_t)rows * n, cudaMemcpyHostToDevice, c->copy_stream),
+                     "slab upload", &r))
+      return r;
+    ctx_cuda_ok(c, cudaEventRecord(ev_up[k], c->copy_stream), "event", &r);
+    return r;
+  };
+  auto compute = [&](int64_t u) -> int {
+    int64_t i0, rows;
+    int j0, nb, r = GWAS_OK;
+    unit(u, &i0, &rows, &j0, &nb);
+    const int k = (int)(u & 1);
+    if (i0 == 0) {
+      // a new trait block: its per-trait operands, used by every slab
+      if (c->precision == GWAS_FP64) {
+        launch_rotate_fp64_f64(c, dY + (size_t)j0 * n, nb, n, Yt);
+        launch_prep_fp64(c, Yt, nb, c->h2 + j0, R, cst);
+      } else if ((r = mixed_prep_block(c, ws, dY + (size_t)j0 * n, j0, nb))) {
+        return r;
+      }
+    }
+    const int8_t* xs = xdev ? XR + (size_t)i0 * n : dX[k];
+    if (!xdev && !ctx_cuda_ok(c, cudaStreamWaitEvent(c->stream, ev_up[k], 0), "event wait", &r)) return r;
+    if (c->precision == GWAS_FP64) launch_rotate_fp64_i8(c, xs, rows, n, c->Xt);
+    else if ((r = mixed_load(c, xs, rows, true))) return r;
+    if (!xdev && !ctx_cuda_ok(c, cudaEventRecord(ev_used[k], c->stream), "event", &r)) return r;
+    // output staging k was last read by the download of unit u - 2
+    if (u >= 2 && !ctx_cuda_ok(c, cudaStreamWaitEvent(c->stream, c->ev_copy[k], 0), "event wait", &r)) return r;
+    void* ob = stage[k];
+    void* pair[2] = {stage[k], (float*)stage[k] + (size_t)nb * rows};
+    void* out = lastse ? (void*)pair : ob;
+    if (c->precision == GWAS_FP64) launch_fused_fp64(c, 0, rows, j0, nb, rows, R, cst, out);
+    else r = mixed_fused_block(c, ws, nb, 0, rows, rows, out);
+    return r;
+  };
+  auto deliver = [&](int64_t u) -> int {
+    int64_t i0, rows;
+    int j0, nb, r = GWAS_OK;
+    unit(u, &i0, &rows, &j0, &nb);
+    const int k = (int)(u & 1);
+    if (!ctx_cuda_ok(c, cudaEventRecord(c->ev_compute[k], c->stream), "event", &r) ||
+        !ctx_cuda_ok(c, cudaStreamWaitEvent(c->copy_stream, c->ev_compute[k], 0), "event wait", &r) ||
+        !ctx_cuda_ok(c, cudaMemcpyAsync(ring[k], stage[k], pair_bytes * (size_t)nb * rows, cudaMemcpyDeviceToHost,
+                                        c->copy_stream), "piece download", &r) ||
+        !ctx_cuda_ok(c, cudaEventRecord(c->ev_copy[k], c->copy_stream), "event", &r) ||
+        !ctx_cuda_ok(c, cudaEventSynchronize(c->ev_copy[k]), "piece download", &r))
+      return r;
+    fn(user, i0, i0 + rows, j0, nb, ring[k]);
+    return GWAS_OK;
+  };
+  if (!xdev) rc = upload(0);
+  for (int64_t u = 0; u <= U && rc == GWAS_OK; ++u) {
+    if (u < U) {
+      rc = compute(u);
+      if (rc == GWAS_OK && !xdev && u + 1 < U) rc = upload(u + 1);
+    }
+    // the previous piece's download waits for its kernels, which were enqueued before this unit's
+    if (rc == GWAS_OK && u >= 1) rc = deliver(u - 1);
+  }
+  unsigned long long st[2] = {0, 0};
+  if (rc == GWAS_OK) ctx_cuda_ok(c, cudaGetLastError(), "solve kernels", &rc);
+  if (rc == GWAS_OK) ctx_cuda_ok(c, cudaMemcpyAsync(st, c->d_status, 16, cudaMemcpyDeviceToHost, c->stream), "status", &rc);
+  if (rc == GWAS_OK) ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "solve", &rc);
+  if (rc == GWAS_OK) prof_flush(c);
+  cleanup();
+  if (rc) return rc;
+  if (st[0]) return ctx_fail(c, GWAS_ERR_TIMEOUT, "a bounded wait inside a kernel ran out");
+  c->singular = (int64_t)st[1];
+  if (c->singular) return ctx_fail(c, GWAS_ERR_SINGULAR_PAIRS, fmt("%lld pairs with a singular system", (long long)st[1]));
+  return GWAS_OK;
 }

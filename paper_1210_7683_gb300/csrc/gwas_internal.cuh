@@ -33,7 +33,6 @@ struct gwas_ctx {
   size_t budget = 0, allocated = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  void* solver = nullptr;  // cusolverDnHandle_t
   std::string err;
   std::vector<DevBuf> bufs;
 
@@ -100,7 +99,10 @@ void launch_fused_fp64(gwas_ctx* c, int64_t i0, int64_t i1, int j0, int tb, int6
 int consts_stride(int pm1);
 
 // ---------------------------------------------------------------- mixed path (mixed.cu)
-int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m);  // genotypes already on the device
+// Genotypes already on the device -> resident mixed-path arrays.  reuse: keep the arrays and
+// the rotation scratch when they are large enough (out-of-core slabs), with no final
+// synchronisation.
+int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m, bool reuse = false);
 struct MixedWs;  // work buffers of one gwas_solve call (mixed.cu)
 int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** ws);
 void mixed_ws_free(gwas_ctx* c, MixedWs* ws);
@@ -109,6 +111,10 @@ void mixed_ws_free(gwas_ctx* c, MixedWs* ws);
 // one-CTA layout or (pair != 0) the CTA-pair layout of the fused kernel.
 int mixed_prep_traits(gwas_ctx* c, MixedWs* ws, const double* dY, const double* h2, int tb, __nv_bfloat16* B1,
                       __nv_bfloat16* B2, float* cst, const int* slot, int pair);
+// Enqueues (no synchronisation) the per-trait operands of traits [j0, j0+tb) into the workspace.
+int mixed_prep_block(gwas_ctx* c, MixedWs* ws, const double* dY, int j0, int tb);
+// Enqueues the fused kernel for the workspace's tb traits x SNPs [i0, i1) into dout.
+int mixed_fused_block(gwas_ctx* c, MixedWs* ws, int tb, int64_t i0, int64_t i1, int64_t ldo, void* dout);
 // Enqueues (no synchronisation) the solve of traits [j0, j0+tb) x SNPs [i0, i1) into dout.
 int mixed_solve_block(gwas_ctx* c, MixedWs* ws, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
                       void* dout);

@@ -28,6 +28,8 @@ struct MixedState {
   int64_t m = 0, mpad = 0;
   __nv_bfloat16 *G = nullptr, *A2 = nullptr;
   float *sA = nullptr, *acoef = nullptr;
+  float* Xc = nullptr;     // FP32 scratch of the rotation, kept while slabs are reloaded
+  int64_t xc_rows = 0;
 };
 
 namespace {
@@ -402,9 +404,10 @@ void mixed_free(gwas_ctx* c) {
   ctx_free(c, s->A2);
   ctx_free(c, s->sA);
   ctx_free(c, s->acoef);
+  ctx_free(c, s->Xc);
   s->G = s->A2 = nullptr;
-  s->sA = s->acoef = nullptr;
-  s->m = s->mpad = 0;
+  s->sA = s->acoef = s->Xc = nullptr;
+  s->m = s->mpad = s->xc_rows = 0;
 }
 
 static void mixed_destroy_setup(gwas_ctx* c) {
@@ -463,29 +466,40 @@ static int mixed_setup(gwas_ctx* c) {
   return GWAS_OK;
 }
 
-int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m) {
+int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m, bool reuse) {
   int rc = mixed_setup(c);
   if (rc) return rc;
   MixedState* s = c->mixed;
   const int n = c->n, PM1 = c->pm1;
-  s->mpad = rup(m, 128);
-  if ((rc = ctx_alloc(c, 2ull * s->mpad * s->Kpad, (void**)&s->G)) ||
-      (rc = ctx_alloc(c, 2ull * 3 * s->mpad * s->Kpad, (void**)&s->A2)) ||
-      (rc = ctx_alloc(c, sizeof(float) * m, (void**)&s->sA)) ||
-      (rc = ctx_alloc(c, sizeof(float) * m * std::max(1, PM1), (void**)&s->acoef))) {
+  // a slab reuses the arrays when they hold enough rows (rows past m keep stale values,
+  // which the fused kernel never writes out)
+  if (!reuse || !s->G || s->mpad < rup(m, 128)) {
     mixed_free(c);
-    return rc;
+    s->mpad = rup(m, 128);
+    if ((rc = ctx_alloc(c, 2ull * s->mpad * s->Kpad, (void**)&s->G)) ||
+        (rc = ctx_alloc(c, 2ull * 3 * s->mpad * s->Kpad, (void**)&s->A2)) ||
+        (rc = ctx_alloc(c, sizeof(float) * s->mpad, (void**)&s->sA)) ||
+        (rc = ctx_alloc(c, sizeof(float) * s->mpad * std::max(1, PM1), (void**)&s->acoef))) {
+      mixed_free(c);
+      return rc;
+    }
   }
   { ProfScope ps(c, "genotypes_bf16");
   geno_bf16_kernel<<<4 * 152, 256, 0, c->stream>>>(dXR, m, n, s->mpad, s->Kpad, s->G);
   c->launches++; }
   // rotate in chunks of SNPs to bound the FP32 scratch
   const int64_t chunk = std::min<int64_t>(s->mpad, 1 << 18);
-  float* Xc = nullptr;
-  if ((rc = ctx_alloc(c, sizeof(float) * chunk * s->ldx, (void**)&Xc))) {
-    mixed_free(c);
-    return rc;
+  if (s->xc_rows < chunk) {
+    ctx_free(c, s->Xc);
+    s->Xc = nullptr;
+    s->xc_rows = 0;
+    if ((rc = ctx_alloc(c, sizeof(float) * chunk * s->ldx, (void**)&s->Xc))) {
+      mixed_free(c);
+      return rc;
+    }
+    s->xc_rows = chunk;
   }
+  float* Xc = s->Xc;
   for (int64_t r0 = 0; r0 < m && rc == GWAS_OK; r0 += chunk) {
     const int64_t rows = std::min<int64_t>(chunk, m - r0);
     XgemmArgs g{};
@@ -511,11 +525,17 @@ int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m) {
       c->launches++;
     }
   }
-  cudaStreamSynchronize(c->stream);
-  ctx_free(c, Xc);
   if (rc) {
+    cudaStreamSynchronize(c->stream);
     mixed_free(c);
     return rc;
+  }
+  if (!reuse) {
+    // a one-time load gives its scratch back
+    cudaStreamSynchronize(c->stream);
+    ctx_free(c, s->Xc);
+    s->Xc = nullptr;
+    s->xc_rows = 0;
   }
   s->m = m;
   return GWAS_OK;
@@ -538,8 +558,9 @@ void mixed_ws_free(gwas_ctx* c, MixedWs* w) {
 // Work buffers of a trait block of up to tb_max traits, allocated once per gwas_solve.
 int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** out) {
   *out = nullptr;
+  int rc = mixed_setup(c);  // the rotation operands (one-time); no genotypes needed
+  if (rc) return rc;
   MixedState* s = c->mixed;
-  if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
   const int q = c->pm1, p = q + 1, Kpad = s->Kpad, TT = mixed_tt(q);
   const int nt_tiles = (tb_max + TT - 1) / TT;
   const int nt_alloc = (nt_tiles + fused_trait_tile_multiple() - 1) / fused_trait_tile_multiple() *
@@ -547,7 +568,6 @@ int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** out) {
   const int rowsY = (int)rup(tb_max, 128), rowsW = (int)rup((int64_t)tb_max * p, 128);
   MixedWs* w = new MixedWs;
   w->tb_max = tb_max;
-  int rc;
   if ((rc = ctx_alloc(c, 2ull * 4 * rowsY * Kpad, (void**)&w->Ysl)) ||
       (rc = ctx_alloc(c, sizeof(double) * rowsY, (void**)&w->sY)) ||
       (rc = ctx_alloc(c, sizeof(double) * (size_t)tb_max * Kpad, (void**)&w->Yt)) ||
@@ -567,7 +587,7 @@ int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** out) {
 int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h2, int tb, __nv_bfloat16* B1,
                       __nv_bfloat16* B2, float* cst, const int* slot, int pair) {
   MixedState* s = c->mixed;
-  if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
+  if (!s || !s->Brot) return ctx_fail(c, GWAS_ERR_STATE, "mixed path not set up");
   if (tb > w->tb_max) return ctx_fail(c, GWAS_ERR_ARG, "trait block larger than its workspace");
   const int n = c->n, q = c->pm1, p = q + 1, Kpad = s->Kpad;
   const int rowsY = (int)rup(tb, 128), rowsW = (int)rup((int64_t)tb * p, 128);
@@ -615,22 +635,28 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h
   return rc;
 }
 
-int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
-                      void* out) {
+int mixed_prep_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb) {
   MixedState* s = c->mixed;
-  if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
+  if (!s || !s->Brot) return ctx_fail(c, GWAS_ERR_STATE, "mixed path not set up");
   if (tb > w->tb_max) return ctx_fail(c, GWAS_ERR_ARG, "trait block larger than its workspace");
-  const int n = c->n, q = c->pm1, p = q + 1, Kpad = s->Kpad, TT = mixed_tt(q);
+  const int q = c->pm1, Kpad = s->Kpad, TT = mixed_tt(q);
   const int nt_tiles = (tb + TT - 1) / TT;
   const int nt_alloc = (nt_tiles + fused_trait_tile_multiple() - 1) / fused_trait_tile_multiple() *
                        fused_trait_tile_multiple();
-  int rc = GWAS_OK;
+  cudaMemsetAsync(w->B1, 0, 2ull * nt_alloc * c1_rows(q) * Kpad, c->stream);
+  cudaMemsetAsync(w->B2, 0, 2ull * nt_alloc * c2_alloc(q) * Kpad, c->stream);
+  return mixed_prep_traits(c, w, dY, c->h2 + j0, tb, w->B1, w->B2, w->cst, nullptr, fused_pair_layout(q));
+}
+
+int mixed_fused_block(gwas_ctx* c, MixedWs* w, int tb, int64_t i0, int64_t i1, int64_t ldo, void* out) {
+  MixedState* s = c->mixed;
+  if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
+  const int n = c->n, q = c->pm1, p = q + 1, Kpad = s->Kpad, TT = mixed_tt(q);
+  const int nt_tiles = (tb + TT - 1) / TT;
   __nv_bfloat16 *B1 = w->B1, *B2 = w->B2;
   float* cst = w->cst;
-  cudaMemsetAsync(B1, 0, 2ull * nt_alloc * c1_rows(q) * Kpad, c->stream);
-  cudaMemsetAsync(B2, 0, 2ull * nt_alloc * c2_alloc(q) * Kpad, c->stream);
-  rc = mixed_prep_traits(c, w, dY, c->h2 + j0, tb, B1, B2, cst, nullptr, fused_pair_layout(q));
-  if (rc == GWAS_OK) {
+  int rc = GWAS_OK;
+  {
     FusedArgs a{};
     // tiles start on multiples of 128 SNPs; those below i0 are not written
     a.row0 = i0 & ~(int64_t)127;
@@ -663,4 +689,10 @@ int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb,
     rc = launch_fused(c, q, a, s->G, s->A2, B1, B2);
   }
   return rc;
+}
+
+int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
+                      void* out) {
+  int rc = mixed_prep_block(c, w, dY, j0, tb);
+  return rc ? rc : mixed_fused_block(c, w, tb, i0, i1, ldo, out);
 }
