@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-ooc", action="store_true", help="skip the out-of-core measurement")
     ap.add_argument("--serving-requests", type=int, default=400,
                     help="requests of the serving run (the full serving workload has 2000; 0 skips it)")
     ap.add_argument("--serving-load", type=float, default=0.8, help="offered load as a fraction of saturation")
@@ -396,7 +397,7 @@ def main():
             h2d = sum(v.numel() * v.element_size() for v in pin.values())
             d2h = hout.numel() * hout.element_size()
             opts_h = g.gwas_default_opts(precision=g.GWAS_MIXED, output=g.GWAS_OUT_LAST_SE, device=local,
-                                         stream=stream.cuda_stream, trait_block=2500)
+                                         stream=stream.cuda_stream, trait_block=1250)
             step(g, opts_h, n, m, t, pin, hout)
             barrier()
             e_steps = max(1, min(args.steps, 3))
@@ -409,6 +410,40 @@ def main():
                              "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": e_steps,
                              "note": out_note + "; inputs from pinned host memory; wall clock around the C calls"}
             del hout
+
+    # ---------------------------------------------------------------- out of core: genotype slabs from host memory
+    if not args.no_ooc and not args.no_e2e and rank == 0:
+        slab, block = 1 << 18, 1250
+        try:
+            bufs = [torch.empty(2 * slab * block, dtype=torch.float32).pin_memory() for _ in range(2)]
+        except RuntimeError:
+            bufs = None
+        if bufs is not None:
+            opts_o = g.gwas_default_opts(precision=g.GWAS_MIXED, output=g.GWAS_OUT_LAST_SE, device=local,
+                                         stream=stream.cuda_stream)
+            pieces = []
+
+            def run_ooc():
+                ctx = g.gwas_setup(n, PM1, pin["phi"], pin["XL"], t, pin["h2"], opts_o)
+                try:
+                    g.gwas_solve_ooc(ctx, m, pin["XR"], slab, pin["Y"], block, bufs[0], bufs[1],
+                                     lambda i0, i1, j0, nb, ptr: pieces.append((i1 - i0) * nb), n=n)
+                finally:
+                    g.gwas_destroy(ctx)
+
+            run_ooc()
+            pieces.clear()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            run_ooc()
+            o_ms = (time.perf_counter() - t0) * 1e3
+            result["ooc"] = {"value": sum(pieces) / (o_ms / 1e3), "unit": "pairs/s", "ms": o_ms,
+                             "slab_snps": slab, "block_traits": block, "pieces": len(pieces),
+                             "h2d_bytes": m * n + t * n * 8, "d2h_bytes": 8 * m * t,
+                             "note": "gwas_setup + gwas_solve_ooc: int8 genotype slabs streamed once from pinned "
+                                     "host memory, converted and rotated per slab; every (slab, trait block) "
+                                     "piece downloaded to pinned host buffers; wall clock"}
+            del bufs
 
     # ---------------------------------------------------------------- serving (continuous batching)
     if args.serving_requests > 0 and rank == 0:

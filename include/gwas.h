@@ -179,12 +179,14 @@ GWAS_API int gwas_solve_stream(gwas_ctx* ctx, const double* Y, int64_t i0, int64
  *                 fn(user, i0, i1, j0, nb, host_block) for SNPs [i0, i1) x traits
  *                 [j0, j0+nb); host_block stays valid until fn returns
  *
- * Pieces arrive trait block by trait block, slab by slab within a block.  The results
- * equal those of gwas_load_snps(m, XR) followed by gwas_solve, bit for bit.  Genotypes of
- * an earlier gwas_load_snps are released first; the context holds none afterwards.
- * Fails with GWAS_ERR_STATE while serving requests are pending.  Device memory: the slab
- * arrays (about 8 bytes per SNP and individual on the mixed path, 8 on the FP64 path),
- * two int8 slabs and two output staging pieces.
+ * The per-trait operands of all t traits are prepared once; each slab is uploaded,
+ * converted and rotated once.  Pieces arrive slab by slab, trait blocks in order within a
+ * slab.  The results equal those of gwas_load_snps(m, XR) followed by gwas_solve, bit for
+ * bit.  Genotypes of an earlier gwas_load_snps are released first; the context holds none
+ * afterwards.  Fails with GWAS_ERR_STATE while serving requests are pending.  Device
+ * memory: the slab arrays (about 8 bytes per SNP and individual on either path), two int8
+ * slabs, two output staging pieces and the operands of all traits (about 32 KB per trait
+ * and 1000 individuals on the mixed path).
  */
 typedef void (*gwas_slab_fn)(void* user, int64_t i0, int64_t i1, int j0, int nb, const void* host_block);
 GWAS_API int gwas_solve_ooc(gwas_ctx* ctx, int64_t m, const int8_t* XR, int64_t slab, const double* Y,

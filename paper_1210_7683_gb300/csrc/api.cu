@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 
+#include "fused.cuh"
 #include "gwas_internal.cuh"
 
 static thread_local std::string g_setup_err;
@@ -531,7 +532,7 @@ int run_blocks(gwas_ctx* c, const double* dY, int64_t i0, int64_t i1, int tb, co
     const int j0 = b * tb, nb = std::min(tb, t - j0);
     const int k = b & 1;
     int r = GWAS_OK;
-    if (!ctx_cuda_ok(c, cudaEventRecord(c->ev_compute[k], c->stream), "event", &r)) return r;
+    // ev_compute[k] was recorded right after block b's kernels, so the download overlaps block b+1
     if (!ctx_cuda_ok(c, cudaStreamWaitEvent(c->copy_stream, c->ev_compute[k], 0), "event wait", &r)) return r;
     if (sink.kind == 2) {
       ctx_cuda_ok(c, cudaMemcpyAsync(sink.ring[k], stage[k], pair_bytes * (size_t)nb * M, cudaMemcpyDeviceToHost,
@@ -560,6 +561,8 @@ int run_blocks(gwas_ctx* c, const double* dY, int64_t i0, int64_t i1, int tb, co
       if (sink.kind != 0 && b >= 2)
         ctx_cuda_ok(c, cudaStreamWaitEvent(c->stream, c->ev_copy[b & 1], 0), "event wait", &rc);
       if (rc == GWAS_OK) rc = compute(b);
+      if (rc == GWAS_OK && sink.kind != 0)
+        ctx_cuda_ok(c, cudaEventRecord(c->ev_compute[b & 1], c->stream), "event", &rc);
     }
     if (rc == GWAS_OK && sink.kind != 0 && b >= 1) rc = copy_out(b - 1);
   }
@@ -642,11 +645,11 @@ extern "C" int gwas_solve_stream(gwas_ctx* c, const double* Y, int64_t i0, int64
 }
 
 // Out-of-core solve (Section 4: slabs of X_R through two buffers while the previous slab is
-// processed).  Units u = (trait block b, slab s), b-major.  Per unit, on the compute stream:
-// the block's per-trait operands (first slab of a block), the slab's conversion and rotation
-// (gwas_load_snps' work, into slab-sized arrays), the fused kernel into output staging k = u&1.
-// On the copy stream: the upload of the next unit's slab into int8 buffer (u+1)&1, and the
-// download of the finished piece, after which the host calls fn.
+// processed).  The per-trait operands of every trait block are prepared once, up front.  Then
+// units u = (slab s, trait block b), slab-major: the slab's conversion and rotation
+// (gwas_load_snps' work, into slab-sized arrays) before its first block, and the fused kernel
+// of every block into output staging k = u & 1.  Uploads of the next slab run on a stream of
+// their own, downloads of finished pieces on the copy stream; the host calls fn per piece.
 extern "C" int gwas_solve_ooc(gwas_ctx* c, int64_t m, const int8_t* XR, int64_t slab, const double* Y,
                               int block_traits, void* host_buf0, void* host_buf1, gwas_slab_fn fn, void* user) {
   if (!c) return GWAS_ERR_ARG;
@@ -673,32 +676,39 @@ extern "C" int gwas_solve_ooc(gwas_ctx* c, int64_t m, const int8_t* XR, int64_t 
   mixed_free(c);
   c->m = 0;
   c->singular = 0;
-  const int n = c->n, t = c->t, p = c->p;
+  const int n = c->n, t = c->t, p = c->p, q = c->pm1;
   if (slab == 0) slab = 1 << 20;
   slab = std::min<int64_t>((slab + 127) / 128 * 128, (m + 127) / 128 * 128);
   const int tb = std::min(block_traits, t);
   const int nblocks = (t + tb - 1) / tb;
-  const int64_t nslabs = (m + slab - 1) / slab, U = nblocks * nslabs;
-  const bool lastse = c->output == GWAS_OUT_LAST_SE;
+  const int64_t nslabs = (m + slab - 1) / slab, U = nslabs * nblocks;
+  const bool lastse = c->output == GWAS_OUT_LAST_SE, mixed = c->precision == GWAS_MIXED;
   const size_t pair_bytes = lastse ? 2 * sizeof(float) : sizeof(double) * p;
   std::vector<void*> tmp;
-  auto talloc = [&](size_t b, void** q) {
-    int r = ctx_alloc(c, b, q);
-    if (r == GWAS_OK) tmp.push_back(*q);
+  auto talloc = [&](size_t b, void** ptr) {
+    int r = ctx_alloc(c, b, ptr);
+    if (r == GWAS_OK) tmp.push_back(*ptr);
     return r;
   };
   MixedWs* ws = nullptr;
   int8_t* hX[2] = {nullptr, nullptr};
   int8_t* dX[2] = {nullptr, nullptr};
   double *dY = (double*)Y, *Yt = nullptr, *R = nullptr, *cst = nullptr;
+  __nv_bfloat16 *B1 = nullptr, *B2 = nullptr;
+  float* cst32 = nullptr;
   void* stage[2] = {nullptr, nullptr};
   void* ring[2] = {host_buf0, host_buf1};
   cudaEvent_t ev_up[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+  cudaStream_t up = nullptr;
   auto cleanup = [&]() {
     cudaStreamSynchronize(c->stream);
     if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+    if (up) {
+      cudaStreamSynchronize(up);
+      cudaStreamDestroy(up);
+    }
     if (ws) mixed_ws_free(c, ws);
-    for (void* q : tmp) ctx_free(c, q);
+    for (void* ptr : tmp) ctx_free(c, ptr);
     for (int k = 0; k < 2; ++k) {
       if (hX[k]) cudaFreeHost(hX[k]);
       if (ev_up[k]) cudaEventDestroy(ev_up[k]);
@@ -709,120 +719,125 @@ extern "C" int gwas_solve_ooc(gwas_ctx* c, int64_t m, const int8_t* XR, int64_t 
     mixed_free(c);
     c->m = 0;
   };
-  cudaMemsetAsync(c->d_status, 0, 32, c->stream);
-  if (!ydev) {
-    if ((rc = talloc(sizeof(double) * t * n, (void**)&dY)) || (rc = ctx_upload(c, Y, sizeof(double) * t * n, dY))) {
-      cleanup();
-      return rc;
-    }
-  }
-  if ((rc = ensure_copy_stream(c)) || (rc = talloc(pair_bytes * (size_t)tb * slab, &stage[0])) ||
-      (rc = talloc(pair_bytes * (size_t)tb * slab, &stage[1]))) {
+  auto fail = [&](int r) {
     cleanup();
-    return rc;
-  }
-  for (int k = 0; k < 2 && rc == GWAS_OK; ++k) {
-    ctx_cuda_ok(c, cudaEventCreateWithFlags(&ev_up[k], cudaEventDisableTiming), "event", &rc);
-    if (rc == GWAS_OK) ctx_cuda_ok(c, cudaEventCreateWithFlags(&ev_used[k], cudaEventDisableTiming), "event", &rc);
-    if (rc == GWAS_OK && !xdev) rc = talloc((size_t)slab * n, (void**)&dX[k]);
-    if (rc == GWAS_OK && !xdev && !xpinned &&
-        cudaHostAlloc((void**)&hX[k], (size_t)slab * n, cudaHostAllocDefault) != cudaSuccess) {
+    return r;
+  };
+  cudaMemsetAsync(c->d_status, 0, 32, c->stream);
+  if (!ydev && ((rc = talloc(sizeof(double) * t * n, (void**)&dY)) || (rc = ctx_upload(c, Y, sizeof(double) * t * n, dY))))
+    return fail(rc);
+  if ((rc = ensure_copy_stream(c)) || (rc = talloc(pair_bytes * (size_t)tb * slab, &stage[0])) ||
+      (rc = talloc(pair_bytes * (size_t)tb * slab, &stage[1])))
+    return fail(rc);
+  if (!ctx_cuda_ok(c, cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking), "upload stream", &rc)) return fail(rc);
+  for (int k = 0; k < 2; ++k) {
+    if (!ctx_cuda_ok(c, cudaEventCreateWithFlags(&ev_up[k], cudaEventDisableTiming), "event", &rc) ||
+        !ctx_cuda_ok(c, cudaEventCreateWithFlags(&ev_used[k], cudaEventDisableTiming), "event", &rc))
+      return fail(rc);
+    if (!xdev && (rc = talloc((size_t)slab * n, (void**)&dX[k]))) return fail(rc);
+    if (!xdev && !xpinned && cudaHostAlloc((void**)&hX[k], (size_t)slab * n, cudaHostAllocDefault) != cudaSuccess) {
       cudaGetLastError();
       hX[k] = nullptr;
-      rc = ctx_fail(c, GWAS_ERR_OOM, "pinned staging of the genotype slabs");
+      return fail(ctx_fail(c, GWAS_ERR_OOM, "pinned staging of the genotype slabs"));
     }
   }
-  if (rc == GWAS_OK) {
-    if (c->precision == GWAS_FP64) {
-      if ((rc = talloc(sizeof(double) * tb * n, (void**)&Yt)) == GWAS_OK &&
-          (rc = talloc(sizeof(double) * tb * (p + 1) * n, (void**)&R)) == GWAS_OK &&
-          (rc = talloc(sizeof(double) * tb * consts_stride(c->pm1), (void**)&cst)) == GWAS_OK)
-        rc = ctx_alloc(c, sizeof(double) * slab * n, (void**)&c->Xt);
+  // ---- the per-trait operands of every trait block, prepared once
+  const int TT = mixed_tt(q), tm = fused_trait_tile_multiple();
+  const int tpb = ((tb + TT - 1) / TT + tm - 1) / tm * tm;  // trait tiles allocated per block
+  const int pair = mixed ? fused_pair_layout(q) : 0;
+  int64_t kp = 0;
+  if (mixed) {
+    if ((rc = mixed_ws_alloc(c, tb, &ws))) return fail(rc);
+    kp = mixed_kpad(c);
+    if ((rc = talloc(2ull * nblocks * tpb * c1_rows(q) * kp, (void**)&B1)) ||
+        (rc = talloc(2ull * nblocks * tpb * c2_alloc(q) * kp, (void**)&B2)) ||
+        (rc = talloc(sizeof(float) * nblocks * tpb * TT * cst_stride(q), (void**)&cst32)))
+      return fail(rc);
+    cudaMemsetAsync(B1, 0, 2ull * nblocks * tpb * c1_rows(q) * kp, c->stream);
+    cudaMemsetAsync(B2, 0, 2ull * nblocks * tpb * c2_alloc(q) * kp, c->stream);
+  } else if ((rc = talloc(sizeof(double) * tb * n, (void**)&Yt)) ||
+             (rc = talloc(sizeof(double) * t * (p + 1) * n, (void**)&R)) ||
+             (rc = talloc(sizeof(double) * t * consts_stride(q), (void**)&cst)) ||
+             (rc = ctx_alloc(c, sizeof(double) * slab * n, (void**)&c->Xt))) {
+    return fail(rc);
+  }
+  auto b1_of = [&](int b) { return B1 + (size_t)b * tpb * c1_rows(q) * kp; };
+  auto b2_of = [&](int b) { return B2 + (size_t)b * tpb * c2_alloc(q) * kp; };
+  auto cst_of = [&](int b) { return cst32 + (size_t)b * tpb * TT * cst_stride(q); };
+  for (int b = 0; b < nblocks && rc == GWAS_OK; ++b) {
+    const int j0 = b * tb, nb = std::min(tb, t - j0);
+    if (mixed) {
+      rc = mixed_prep_traits(c, ws, dY + (size_t)j0 * n, c->h2 + j0, nb, b1_of(b), b2_of(b), cst_of(b), nullptr, pair);
     } else {
-      rc = mixed_ws_alloc(c, tb, &ws);
+      launch_rotate_fp64_f64(c, dY + (size_t)j0 * n, nb, n, Yt);
+      launch_prep_fp64(c, Yt, nb, c->h2 + j0, R + (size_t)j0 * (p + 1) * n, cst + (size_t)j0 * consts_stride(q));
     }
   }
-  if (rc) {
-    cleanup();
-    return rc;
-  }
-  auto unit = [&](int64_t u, int64_t* i0, int64_t* rows, int* j0, int* nb) {
-    const int64_t b = u / nslabs, s = u % nslabs;
-    *i0 = s * slab;
-    *rows = std::min<int64_t>(slab, m - *i0);
-    *j0 = (int)(b * tb);
-    *nb = std::min(tb, t - *j0);
-  };
-  auto upload = [&](int64_t u) -> int {
-    int64_t i0, rows;
-    int j0, nb, r = GWAS_OK;
-    unit(u, &i0, &rows, &j0, &nb);
-    const int k = (int)(u & 1);
-    // int8 buffer k was last read by the conversion of unit u - 2
-    if (u >= 2 && !ctx_cuda_ok(c, cudaStreamWaitEvent(c->copy_stream, ev_used[k], 0), "event wait", &r)) return r;
-    const int8_t* src = XR + (size_t)i0 * n;
+  if (rc) return fail(rc);
+  // ---- slabs
+  auto slab_rows = [&](int64_t s) { return std::min<int64_t>(slab, m - s * slab); };
+  auto upload = [&](int64_t s) -> int {
+    const int64_t rows = slab_rows(s);
+    const int k = (int)(s & 1);
+    int r = GWAS_OK;
+    // int8 buffer k was last read by the conversion of slab s - 2
+    if (s >= 2 && !ctx_cuda_ok(c, cudaStreamWaitEvent(up, ev_used[k], 0), "event wait", &r)) return r;
+    const int8_t* src = XR + (size_t)(s * slab) * n;
     if (!xpinned) {
-      // pinned staging k was last read by the upload of unit u - 2
-      if (u >= 2 && !ctx_cuda_ok(c, cudaEventSynchronize(ev_up[k]), "slab upload", &r)) return r;
+      // pinned staging k was last read by the upload of slab s - 2
+      if (s >= 2 && !ctx_cuda_ok(c, cudaEventSynchronize(ev_up[k]), "slab upload", &r)) return r;
       std::memcpy(hX[k], src, (size_t)rows * n);
       src = hX[k];
     }
-    if (!ctx_cuda_ok(c, cudaMemcpyAsync(dX[k], src, (size_t)rows * n, cudaMemcpyHostToDevice, c->copy_stream),
-                     "slab upload", &r))
-      return r;
-    ctx_cuda_ok(c, cudaEventRecord(ev_up[k], c->copy_stream), "event", &r);
+    if (ctx_cuda_ok(c, cudaMemcpyAsync(dX[k], src, (size_t)rows * n, cudaMemcpyHostToDevice, up), "slab upload", &r))
+      ctx_cuda_ok(c, cudaEventRecord(ev_up[k], up), "event", &r);
     return r;
   };
   auto compute = [&](int64_t u) -> int {
-    int64_t i0, rows;
-    int j0, nb, r = GWAS_OK;
-    unit(u, &i0, &rows, &j0, &nb);
-    const int k = (int)(u & 1);
-    if (i0 == 0) {
-      // a new trait block: its per-trait operands, used by every slab
-      if (c->precision == GWAS_FP64) {
-        launch_rotate_fp64_f64(c, dY + (size_t)j0 * n, nb, n, Yt);
-        launch_prep_fp64(c, Yt, nb, c->h2 + j0, R, cst);
-      } else if ((r = mixed_prep_block(c, ws, dY + (size_t)j0 * n, j0, nb))) {
-        return r;
+    const int64_t s = u / nblocks, rows = slab_rows(s);
+    const int b = (int)(u % nblocks), j0 = b * tb, nb = std::min(tb, t - j0), k = (int)(u & 1);
+    int r = GWAS_OK;
+    if (b == 0) {
+      // the slab's conversion and rotation, then the next slab's upload
+      const int ks = (int)(s & 1);
+      const int8_t* xs = xdev ? XR + (size_t)(s * slab) * n : dX[ks];
+      if (!xdev && !ctx_cuda_ok(c, cudaStreamWaitEvent(c->stream, ev_up[ks], 0), "event wait", &r)) return r;
+      if (mixed) {
+        if ((r = mixed_load(c, xs, rows, true))) return r;
+      } else {
+        launch_rotate_fp64_i8(c, xs, rows, n, c->Xt);
       }
+      if (!xdev && !ctx_cuda_ok(c, cudaEventRecord(ev_used[ks], c->stream), "event", &r)) return r;
+      if (!xdev && s + 1 < nslabs && (r = upload(s + 1))) return r;
     }
-    const int8_t* xs = xdev ? XR + (size_t)i0 * n : dX[k];
-    if (!xdev && !ctx_cuda_ok(c, cudaStreamWaitEvent(c->stream, ev_up[k], 0), "event wait", &r)) return r;
-    if (c->precision == GWAS_FP64) launch_rotate_fp64_i8(c, xs, rows, n, c->Xt);
-    else if ((r = mixed_load(c, xs, rows, true))) return r;
-    if (!xdev && !ctx_cuda_ok(c, cudaEventRecord(ev_used[k], c->stream), "event", &r)) return r;
     // output staging k was last read by the download of unit u - 2
     if (u >= 2 && !ctx_cuda_ok(c, cudaStreamWaitEvent(c->stream, c->ev_copy[k], 0), "event wait", &r)) return r;
-    void* ob = stage[k];
-    void* pair[2] = {stage[k], (float*)stage[k] + (size_t)nb * rows};
-    void* out = lastse ? (void*)pair : ob;
-    if (c->precision == GWAS_FP64) launch_fused_fp64(c, 0, rows, j0, nb, rows, R, cst, out);
-    else r = mixed_fused_block(c, ws, nb, 0, rows, rows, out);
+    void* pieces[2] = {stage[k], (float*)stage[k] + (size_t)nb * rows};
+    void* out = lastse ? (void*)pieces : stage[k];
+    if (mixed)
+      r = mixed_fused_ops(c, b1_of(b), b2_of(b), cst_of(b), nb, 0, rows, rows, out);
+    else
+      launch_fused_fp64(c, 0, rows, j0, nb, rows, R + (size_t)j0 * (p + 1) * n, cst + (size_t)j0 * consts_stride(q), out);
+    // recorded here, not at delivery, so that the piece's download overlaps the next unit
+    if (r == GWAS_OK) ctx_cuda_ok(c, cudaEventRecord(c->ev_compute[k], c->stream), "event", &r);
     return r;
   };
   auto deliver = [&](int64_t u) -> int {
-    int64_t i0, rows;
-    int j0, nb, r = GWAS_OK;
-    unit(u, &i0, &rows, &j0, &nb);
-    const int k = (int)(u & 1);
-    if (!ctx_cuda_ok(c, cudaEventRecord(c->ev_compute[k], c->stream), "event", &r) ||
-        !ctx_cuda_ok(c, cudaStreamWaitEvent(c->copy_stream, c->ev_compute[k], 0), "event wait", &r) ||
+    const int64_t s = u / nblocks, rows = slab_rows(s);
+    const int b = (int)(u % nblocks), j0 = b * tb, nb = std::min(tb, t - j0), k = (int)(u & 1);
+    int r = GWAS_OK;
+    if (!ctx_cuda_ok(c, cudaStreamWaitEvent(c->copy_stream, c->ev_compute[k], 0), "event wait", &r) ||
         !ctx_cuda_ok(c, cudaMemcpyAsync(ring[k], stage[k], pair_bytes * (size_t)nb * rows, cudaMemcpyDeviceToHost,
                                         c->copy_stream), "piece download", &r) ||
         !ctx_cuda_ok(c, cudaEventRecord(c->ev_copy[k], c->copy_stream), "event", &r) ||
         !ctx_cuda_ok(c, cudaEventSynchronize(c->ev_copy[k]), "piece download", &r))
       return r;
-    fn(user, i0, i0 + rows, j0, nb, ring[k]);
+    fn(user, s * slab, s * slab + rows, j0, nb, ring[k]);
     return GWAS_OK;
   };
   if (!xdev) rc = upload(0);
   for (int64_t u = 0; u <= U && rc == GWAS_OK; ++u) {
-    if (u < U) {
-      rc = compute(u);
-      if (rc == GWAS_OK && !xdev && u + 1 < U) rc = upload(u + 1);
-    }
-    // the previous piece's download waits for its kernels, which were enqueued before this unit's
+    if (u < U) rc = compute(u);
     if (rc == GWAS_OK && u >= 1) rc = deliver(u - 1);
   }
   unsigned long long st[2] = {0, 0};

@@ -115,12 +115,16 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* ws, const double* dY, const double* 
 int mixed_prep_block(gwas_ctx* c, MixedWs* ws, const double* dY, int j0, int tb);
 // Enqueues the fused kernel for the workspace's tb traits x SNPs [i0, i1) into dout.
 int mixed_fused_block(gwas_ctx* c, MixedWs* ws, int tb, int64_t i0, int64_t i1, int64_t ldo, void* dout);
+// The same for trait operands prepared elsewhere (mixed_prep_traits into B1, B2, cst).
+int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B2, const float* cst, int tb, int64_t i0,
+                    int64_t i1, int64_t ldo, void* dout);
 // Enqueues (no synchronisation) the solve of traits [j0, j0+tb) x SNPs [i0, i1) into dout.
 int mixed_solve_block(gwas_ctx* c, MixedWs* ws, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
                       void* dout);
 void mixed_free(gwas_ctx* c);
 // resident mixed-path data (for the serving kernel launches)
 int64_t mixed_mpad(gwas_ctx* c);
+int mixed_kpad(gwas_ctx* c);  // padded n of the mixed path's operands (after mixed setup)
 const float* mixed_sA(gwas_ctx* c);
 const float* mixed_acoef(gwas_ctx* c);
 const __nv_bfloat16* mixed_G(gwas_ctx* c);

@@ -392,6 +392,7 @@ __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__
 }  // namespace
 
 int64_t mixed_mpad(gwas_ctx* c) { return c->mixed ? c->mixed->mpad : 0; }
+int mixed_kpad(gwas_ctx* c) { return c->mixed ? c->mixed->Kpad : 0; }
 const float* mixed_sA(gwas_ctx* c) { return c->mixed ? c->mixed->sA : nullptr; }
 const float* mixed_acoef(gwas_ctx* c) { return c->mixed ? c->mixed->acoef : nullptr; }
 const __nv_bfloat16* mixed_G(gwas_ctx* c) { return c->mixed ? c->mixed->G : nullptr; }
@@ -648,13 +649,12 @@ int mixed_prep_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb) 
   return mixed_prep_traits(c, w, dY, c->h2 + j0, tb, w->B1, w->B2, w->cst, nullptr, fused_pair_layout(q));
 }
 
-int mixed_fused_block(gwas_ctx* c, MixedWs* w, int tb, int64_t i0, int64_t i1, int64_t ldo, void* out) {
+int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B2, const float* cst, int tb, int64_t i0,
+                    int64_t i1, int64_t ldo, void* out) {
   MixedState* s = c->mixed;
   if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
   const int n = c->n, q = c->pm1, p = q + 1, Kpad = s->Kpad, TT = mixed_tt(q);
   const int nt_tiles = (tb + TT - 1) / TT;
-  __nv_bfloat16 *B1 = w->B1, *B2 = w->B2;
-  float* cst = w->cst;
   int rc = GWAS_OK;
   {
     FusedArgs a{};
@@ -689,6 +689,10 @@ int mixed_fused_block(gwas_ctx* c, MixedWs* w, int tb, int64_t i0, int64_t i1, i
     rc = launch_fused(c, q, a, s->G, s->A2, B1, B2);
   }
   return rc;
+}
+
+int mixed_fused_block(gwas_ctx* c, MixedWs* w, int tb, int64_t i0, int64_t i1, int64_t ldo, void* out) {
+  return mixed_fused_ops(c, w->B1, w->B2, w->cst, tb, i0, i1, ldo, out);
 }
 
 int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,

@@ -63,8 +63,8 @@ def test_ooc_equals_in_core(gw, precision_name, pm1, output_name):
     ref = in_core(gw, P, precision, output)
     out, seen = out_of_core(gw, P, precision, output, slab=300, block=24)
     # slabs of 384 SNPs (300 rounded up to 128): [0,384) [384,768) [768,1000); trait blocks [0,24) [24,40)
-    assert seen == [(0, 384, 0, 24), (384, 768, 0, 24), (768, 1000, 0, 24),
-                    (0, 384, 24, 16), (384, 768, 24, 16), (768, 1000, 24, 16)]
+    assert seen == [(0, 384, 0, 24), (0, 384, 24, 16), (384, 768, 0, 24), (384, 768, 24, 16),
+                    (768, 1000, 0, 24), (768, 1000, 24, 16)]
     np.testing.assert_array_equal(out, ref)
 
 
