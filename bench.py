@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-ooc", action="store_true", help="skip the out-of-core measurement")
+    ap.add_argument("--no-t1", action="store_true", help="skip the single-trait measurement")
     ap.add_argument("--serving-requests", type=int, default=400,
                     help="requests of the serving run (the full serving workload has 2000; 0 skips it)")
     ap.add_argument("--serving-load", type=float, default=0.8, help="offered load as a fraction of saturation")
@@ -384,6 +385,40 @@ def main():
                               "step_ms": e0.elapsed_time(e1), "kernel_ms": {k: v[0] for k, v in kt64.items()}}
         result["mixed_over_fp64"] = (pairs / (fused_ms / 1e3)) / (m64 * t / fused64)
         del out64, y_part, s64
+
+    # ---------------------------------------------------------------- one trait: the HBM-bound single-trait kernel
+    if not args.no_t1 and rank == 0:
+        o1 = g.gwas_default_opts(precision=g.GWAS_MIXED, output=g.GWAS_OUT_LAST_SE, device=local, profile=1,
+                                 stream=stream.cuda_stream)
+        out1 = torch.empty((2, 1, m), dtype=torch.float32, device=dev)
+        ctx = g.gwas_setup(n, PM1, inp_d["phi"], inp_d["XL"], 1, inp_d["h2"][:1], o1)
+        try:
+            g.gwas_load_snps(ctx, m, inp_d["XR"], n)
+            y1 = inp_d["Y"][:1].contiguous()
+            for _ in range(3):
+                g.gwas_solve(ctx, y1, 0, m, out1)
+            g.gwas_reset_timers(ctx)
+            reps = 10
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                g.gwas_solve(ctx, y1, 0, m, out1)
+            torch.cuda.synchronize()
+            wall = (time.perf_counter() - t0) * 1e3 / reps
+            k_ms, k_n = g.gwas_kernel_time(ctx, "gemv1")
+        finally:
+            g.gwas_destroy(ctx)
+        kpad = (n + 63) // 64 * 64
+        bytes1 = m * 8 * kpad + m * 8        # G + three x'^2 planes (bf16) per SNP, beta + SE out
+        k_ms = k_ms / max(k_n, 1)
+        result["t1"] = {"value": m / (wall / 1e3), "unit": "pairs/s", "solve_ms": wall, "kernel_ms": k_ms,
+                        "roofline": {"bound": "hbm", "achieved": bytes1 / (k_ms / 1e3) / 1e9,
+                                     "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                     "frac": bytes1 / (k_ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                                     "algorithmic_bytes_per_launch": bytes1},
+                        "note": "gwas_solve with t = 1 on the resident SNPs (device output): per-trait prep + the "
+                                "single-trait kernel, which streams 8 B per SNP and individual once"}
+        del out1
 
     # ---------------------------------------------------------------- end to end from pinned host buffers
     if not args.no_e2e:

@@ -686,7 +686,9 @@ int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B
     }
     a.status = c->d_status;
     a.singular = c->d_status + 1;
-    rc = launch_fused(c, q, a, s->G, s->A2, B1, B2);
+    // one trait: the contractions are matrix-vector products, bound by HBM (gemv.cu)
+    if (tb == 1 && gemv1_supported(q, Kpad) && !fused_pair_layout(q)) rc = launch_gemv1(c, q, a, s->G, s->A2, B1, B2);
+    else rc = launch_fused(c, q, a, s->G, s->A2, B1, B2);
   }
   return rc;
 }

@@ -133,3 +133,39 @@ def test_general_p_full_b(gw, pm1):
     b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
     err = full_b_err(out.transpose(1, 0, 2), b, se)
     assert err <= TOL, err
+
+
+# One trait: the single-trait (GEMV-shaped, HBM-bound) kernel instead of the fused one.
+@pytest.mark.parametrize("pm1", [0, 3, 7])
+def test_single_trait(gw, pm1):
+    P = make_problem(300, 1500, 1, pm1=pm1, seed=83 + pm1)
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    out, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE)
+    assert rc == gw.GWAS_OK
+    check_last(out, b, se)
+    full, rc, _ = solve(gw, P, gw.GWAS_OUT_FULL_B)
+    assert full_b_err(full.transpose(1, 0, 2), b, se) <= TOL
+    # an unaligned SNP range
+    part, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE, 77, 1333)
+    check_last(part, b[77:1333], se[77:1333])
+
+
+def test_single_trait_blocks_match_the_oracle(gw):
+    # trait blocks of one trait: every block runs the single-trait kernel
+    P = make_problem(256, 900, 9, seed=84)
+    out, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE, trait_block=1)
+    assert rc == gw.GWAS_OK
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    check_last(out, b, se)
+
+
+def test_single_trait_singular_snp(gw):
+    P = make_problem(128, 300, 1, seed=85)
+    P.XR[40] = 1
+    out, rc, cnt = solve(gw, P, gw.GWAS_OUT_LAST_SE)
+    assert rc == gw.GWAS_ERR_SINGULAR_PAIRS and cnt == 1
+    assert np.isnan(out[0, 0, 40]) and np.isnan(out[1, 0, 40])
+    ok = np.ones(P.m, bool)
+    ok[40] = False
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR[ok], P.Y, P.h2)
+    check_last(out[:, :, ok], b, se)
