@@ -101,7 +101,7 @@ int fused_pair_layout(int q);
 int launch_fused(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2);
 // Single-trait kernel (gemv.cu): the same solve for a.ntrait == 1, streaming the SNPs'
-// operands once (HBM-bound); for Kpad <= 2048 and the one-CTA operand layout.
+// operands once through a TMA ring (HBM-bound); for the one-CTA operand layout.
 bool gemv1_supported(int q, int Kpad);
 int launch_gemv1(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2);

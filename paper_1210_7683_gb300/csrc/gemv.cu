@@ -1,24 +1,43 @@
 // Single-trait path of the mixed precision solve (t = 1): the contractions of Algorithm 5
 // for one trait are matrix-vector products, so the pass is bound by HBM, not by the
-// tensor cores.  One thread per SNP streams the SNP's resident operands (the exact
-// genotypes and the three fixed-point slices of x'_c^2, 8 bytes per individual) once,
-// 32 bytes per load, and forms the same exact-slice sums as the fused kernel's MMAs:
+// tensor cores.  Every SNP's resident operands (the exact genotypes and the three
+// fixed-point slices of x'_c^2, 8 bytes per individual) are streamed once, and the same
+// exact-slice sums as the fused kernel's MMAs are formed on the CUDA cores:
 //   C1: x_i . [w1 | v_1..q | w2 | v_1..q | w3 | w4]  (slices of the trait's columns),
 //   C2: [A1 A1 A1 A2 A2 A3s] . [E1 E2 E3s E2s E1 E1]  (slices of x'^2 against slices of e).
 // Level-0 partial sums are integers below 2^24, so they are exact in FP32 in any order.
-// The trait's slices (from the fused kernel's C1/C2 operands, trait 0 of tile 0) are held in
-// shared memory as FP32 and read by broadcast.  The per-pair solve is the fused epilogue's.
+// The per-pair solve is the fused epilogue's.
+//
+// One persistent CTA per SM: a TMA producer warp and 8 consumer warps, one thread per SNP,
+// 256 SNPs (two 128-SNP tiles) per unit.  A stage holds 32 values of k: eight 8 KB boxes
+// (genotypes and the three planes, two tiles; 64-byte swizzle, so that the row-per-thread
+// reads are free of bank conflicts) and the trait's 32-wide slices (two strided boxes that
+// pick trait 0's row of every group).  A ring of three stages keeps ~200 KB per SM in flight.
 #include <algorithm>
 #include <cstdio>
 #include <string>
 
 #include "fused.cuh"
 #include "gwas_internal.cuh"
+#include "tc.cuh"
 
 namespace {
 
-constexpr int GEMV_THREADS = 512;
-constexpr int GEMV_KMAX = 2048;  // Kpad up to which the trait's rows fit shared memory
+constexpr int GK = 32;                   // values of k per stage
+constexpr int GNS = 3;                   // ring stages
+constexpr int GCONS = 8;                 // consumer warps
+constexpr int GUNIT = GCONS * 32;        // SNPs per unit (two tiles)
+constexpr int GBOX = 128 * GK * 2;       // one box: 128 rows x 32 bf16 = 8 KB
+constexpr int GDATA = 8 * GBOX;          // G + three planes, two tiles
+
+template <int Q>
+struct GemvGeo {
+  static constexpr int G1 = c1_groups(Q), NR = G1 + 4, NRP = (NR + 3) / 4 * 4;
+  static constexpr int TRAW = (NR * GK * 2 + 1023) / 1024 * 1024;  // bf16 trait rows of a stage
+  static constexpr int STAGE = GDATA + TRAW;
+  static constexpr int TF32 = GK * NRP * 4;                         // the same rows, FP32, [k][row]
+  static constexpr int SMEM = GNS * STAGE + GNS * TF32 + 1024 + 256;
+};
 
 __device__ __forceinline__ void bf16x8(const uint4& v, float* f) {
   const uint32_t w[4] = {v.x, v.y, v.z, v.w};
@@ -30,67 +49,119 @@ __device__ __forceinline__ void bf16x8(const uint4& v, float* f) {
 }
 
 template <int Q>
-__global__ void __launch_bounds__(GEMV_THREADS, 1)
-    gemv1_kernel(const __nv_bfloat16* __restrict__ G, const __nv_bfloat16* __restrict__ A2,
-                 const __nv_bfloat16* __restrict__ B1, const __nv_bfloat16* __restrict__ B2, FusedArgs a) {
-  constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = mixed_tt(Q), G1 = c1_groups(Q), NR = G1 + 4, CSTR = cst_stride(Q);
-  constexpr int NRP = (NR + 3) / 4 * 4;  // row pitch: 16-byte aligned rows for vector loads
-  extern __shared__ float4 trow4[];
-  float* trow = (float*)trow4;  // [Kpad][NRP]: the trait's C1 groups, then E2s, E1, E2, E3s
+__global__ void __launch_bounds__(32 + GUNIT, 1)
+    gemv1_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapA,
+                 const __grid_constant__ CUtensorMap mapT1, const __grid_constant__ CUtensorMap mapT2, FusedArgs a) {
+  using Geo = GemvGeo<Q>;
+  constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, G1 = Geo::G1, NR = Geo::NR, NRP = Geo::NRP, CSTR = cst_stride(Q);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* tf = (float*)(smem + GNS * Geo::STAGE);  // [GNS][GK][NRP]
+  uint64_t* full = (uint64_t*)(smem + GNS * Geo::STAGE + GNS * Geo::TF32);
+  uint64_t* empty = full + GNS;
+  volatile int* abort = (volatile int*)(empty + GNS);
   __shared__ float cj[CSTR];
-  const int Kpad = a.Kpad;
-  for (int idx = threadIdx.x; idx < NR * Kpad; idx += blockDim.x) {
-    const int r = idx / Kpad, k = idx % Kpad;
-    const __nv_bfloat16 v = r < G1 ? B1[(size_t)(r * TT) * Kpad + k] : B2[(size_t)((r - G1) * TT) * Kpad + k];
-    trow[k * NRP + r] = __bfloat162float(v);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < GNS; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], GCONS);
+    }
+    *abort = 0;
+    tc::fence_mbar_init();
   }
   for (int e = threadIdx.x; e < CSTR; e += blockDim.x) cj[e] = a.cst[e];
   __syncthreads();
-  const float inv_dof = 1.f / a.dof, F = 1.f / 256.f;
+  const int nkb = a.Kpad / GK;
   const int64_t snp_end = a.row0 + a.nsnp;
-  const int full_b = a.full_b;
-  unsigned long long nsing = 0;
-  for (int64_t base = a.row0 + (int64_t)blockIdx.x * blockDim.x; base < snp_end; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t snp = base + threadIdx.x;
-    const bool valid = snp >= a.snp_lo && snp < snp_end;
-    float acc[G1], c2[6];
+  const int64_t nunits = (a.nsnp + GUNIT - 1) / GUNIT;
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      tc::prefetch_map(&mapG);
+      tc::prefetch_map(&mapA);
+      tc::prefetch_map(&mapT1);
+      tc::prefetch_map(&mapT2);
+      uint32_t h = 0;
+      bool ok = true;
+      for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const int row = (int)(a.row0 + u * GUNIT);
+        for (int kb = 0; kb < nkb; ++kb, ++h) {
+          const uint32_t s = h % GNS;
+          if (h >= GNS && !tc::mbar_wait(&empty[s], ((h / GNS) - 1) & 1, a.status, abort)) { ok = false; break; }
+          uint8_t* buf = smem + s * Geo::STAGE;
+          const int x = kb * GK;
+          tc::mbar_expect_tx(&full[s], GDATA + NR * GK * 2);
 #pragma unroll
-    for (int r = 0; r < G1; ++r) acc[r] = 0.f;
+          for (int t = 0; t < 2; ++t) tc::tma_load_2d(buf + t * GBOX, &mapG, &full[s], x, row + 128 * t);
 #pragma unroll
-    for (int r = 0; r < 6; ++r) c2[r] = 0.f;
-    if (valid) {
-      const uint4* g = (const uint4*)(G + (size_t)snp * Kpad);
-      const uint4* p0 = (const uint4*)(A2 + (size_t)a2_row(0, snp) * Kpad);
-      const uint4* p1 = (const uint4*)(A2 + (size_t)a2_row(1, snp) * Kpad);
-      const uint4* p2 = (const uint4*)(A2 + (size_t)a2_row(2, snp) * Kpad);
-      for (int k8 = 0; k8 < Kpad / 8; k8 += 2) {
-        const uint4 gv[2] = {__ldg(g + k8), __ldg(g + k8 + 1)};
-        const uint4 v0[2] = {__ldg(p0 + k8), __ldg(p0 + k8 + 1)};
-        const uint4 v1[2] = {__ldg(p1 + k8), __ldg(p1 + k8 + 1)};
-        const uint4 v2[2] = {__ldg(p2 + k8), __ldg(p2 + k8 + 1)};
+          for (int p = 0; p < 3; ++p)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float xg[8], xa1[8], xa2[8], xa3[8];
-          bf16x8(gv[h], xg);
-          bf16x8(v0[h], xa1);
-          bf16x8(v1[h], xa2);
-          bf16x8(v2[h], xa3);
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const float* tr = trow + (size_t)(8 * (k8 + h) + e) * NRP;
-#pragma unroll
-            for (int r = 0; r < G1; ++r) acc[r] = fmaf(xg[e], tr[r], acc[r]);
-            const float e2s = tr[G1], e1 = tr[G1 + 1], e2 = tr[G1 + 2], e3s = tr[G1 + 3];
-            c2[0] = fmaf(xa1[e], e1, c2[0]);   // A1 x E1   (level 0)
-            c2[1] = fmaf(xa1[e], e2, c2[1]);   // A1 x E2
-            c2[2] = fmaf(xa1[e], e3s, c2[2]);  // A1 x E3s
-            c2[3] = fmaf(xa2[e], e2s, c2[3]);  // A2 x E2s
-            c2[4] = fmaf(xa2[e], e1, c2[4]);   // A2 x E1
-            c2[5] = fmaf(xa3[e], e1, c2[5]);   // A3s x E1
-          }
+            for (int t = 0; t < 2; ++t)
+              tc::tma_load_2d(buf + (2 + 2 * p + t) * GBOX, &mapA, &full[s], x, (int)a2_row(p, row + 128 * t));
+          tc::tma_load_2d(buf + GDATA, &mapT1, &full[s], x, 0);
+          tc::tma_load_2d(buf + GDATA + G1 * GK * 2, &mapT2, &full[s], x, 0);
         }
       }
+      // every stage's last release must land before the CTA exits
+      for (uint32_t s = 0; s < GNS && h > s; ++s) {
+        const uint32_t uses = (h - s + GNS - 1) / GNS;
+        tc::mbar_wait(&empty[s], (uses - 1) & 1, a.status, abort);
+      }
     }
+    return;
+  }
+  // -------------------------------------------------------------- consumers: one SNP per thread
+  const int ct = threadIdx.x - 32, tile = ct / 128, r = ct % 128;
+  const float inv_dof = 1.f / a.dof, F = 1.f / 256.f;
+  const int full_b = a.full_b;
+  unsigned long long nsing = 0;
+  uint32_t h = 0;
+  bool ok = true;
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int64_t snp = a.row0 + u * GUNIT + ct;
+    float acc[G1], c2[6];
+#pragma unroll
+    for (int i = 0; i < G1; ++i) acc[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) c2[i] = 0.f;
+    for (int kb = 0; kb < nkb; ++kb, ++h) {
+      const uint32_t s = h % GNS;
+      if (ok && !tc::mbar_wait(&full[s], (h / GNS) & 1, a.status, abort)) ok = false;
+      const uint8_t* buf = smem + s * Geo::STAGE;
+      float* tfs = tf + s * GK * NRP;
+      // the stage's trait slices, bf16 [NR][GK] -> FP32 [GK][NRP]
+      const __nv_bfloat16* traw = (const __nv_bfloat16*)(buf + GDATA);
+      for (int idx = ct; idx < NR * GK; idx += GUNIT) tfs[(idx % GK) * NRP + idx / GK] = __bfloat162float(traw[idx]);
+      tc::named_sync(1, GUNIT);
+      const uint32_t sw = (uint32_t)((r >> 1) & 3);
+#pragma unroll
+      for (int c = 0; c < GK / 8; ++c) {
+        const uint32_t off = (uint32_t)r * (GK * 2) + ((c ^ sw) << 4);
+        float xg[8], xa1[8], xa2[8], xa3[8];
+        bf16x8(*(const uint4*)(buf + tile * GBOX + off), xg);
+        bf16x8(*(const uint4*)(buf + (2 + tile) * GBOX + off), xa1);
+        bf16x8(*(const uint4*)(buf + (4 + tile) * GBOX + off), xa2);
+        bf16x8(*(const uint4*)(buf + (6 + tile) * GBOX + off), xa3);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float* tr = tfs + (8 * c + e) * NRP;
+#pragma unroll
+          for (int i = 0; i < G1; ++i) acc[i] = fmaf(xg[e], tr[i], acc[i]);
+          const float e2s = tr[G1], e1 = tr[G1 + 1], e2 = tr[G1 + 2], e3s = tr[G1 + 3];
+          c2[0] = fmaf(xa1[e], e1, c2[0]);   // A1 x E1   (level 0)
+          c2[1] = fmaf(xa1[e], e2, c2[1]);   // A1 x E2
+          c2[2] = fmaf(xa1[e], e3s, c2[2]);  // A1 x E3s
+          c2[3] = fmaf(xa2[e], e2s, c2[3]);  // A2 x E2s
+          c2[4] = fmaf(xa2[e], e1, c2[4]);   // A2 x E1
+          c2[5] = fmaf(xa3[e], e1, c2[5]);   // A3s x E1
+        }
+      }
+      // release the stage: one arrival per warp once all its lanes have read it
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&empty[s]);
+    }
+    const bool valid = ok && snp >= a.snp_lo && snp < snp_end;
     if (!valid) continue;
     // the fused kernel's epilogue for pair (snp, trait 0)
     const float sA = a.sA[snp];
@@ -102,10 +173,10 @@ __global__ void __launch_bounds__(GEMV_THREADS, 1)
       zz = fmaf(z[c], z[c], zz);
     }
     const float lvl1 = (c2[1] + c2[2]) + (c2[3] + c2[4]) + c2[5];
-    const float s = (sA * cj[cst_escale(Q)]) * fmaf(F, lvl1, c2[0]);
-    const float delta = s - zz;
+    const float sv = (sA * cj[cst_escale(Q)]) * fmaf(F, lvl1, c2[0]);
+    const float delta = sv - zz;
     float beta, se;
-    const bool sing = !(delta > 1e-6f * s) || !(sA > 0.f);
+    const bool sing = !(delta > 1e-6f * sv) || !(sA > 0.f);
     if (sing) {
       beta = se = __int_as_float(0x7fc00000);
       ++nsing;
@@ -134,27 +205,35 @@ __global__ void __launch_bounds__(GEMV_THREADS, 1)
     }
   }
   for (int o = 16; o > 0; o >>= 1) nsing += __shfl_xor_sync(0xffffffffu, nsing, o);
-  if ((threadIdx.x & 31) == 0 && nsing) atomicAdd(a.singular, nsing);
+  if (lane == 0 && nsing) atomicAdd(a.singular, nsing);
 }
 
 }  // namespace
 
-bool gemv1_supported(int q, int Kpad) { return q >= 0 && q <= 7 && Kpad <= GEMV_KMAX; }
+bool gemv1_supported(int q, int Kpad) { return q >= 0 && q <= 7 && Kpad % GK == 0; }
 
 int launch_gemv1(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2) {
   if (a.nsnp <= 0) return GWAS_OK;
-  if (!gemv1_supported(q, a.Kpad)) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "single-trait kernel: p-1 or n out of range");
+  if (!gemv1_supported(q, a.Kpad)) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "single-trait kernel: p-1 out of range");
+  const int TT = mixed_tt(q);
+  CUtensorMap mg, ma, m1, m2;
+  if (!make_bf16_map(&mg, G, a.mpad, a.Kpad, 128, GK) || !make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, 128, GK) ||
+      !make_bf16_map_strided(&m1, B1, c1_groups(q), a.Kpad, (uint64_t)TT * a.Kpad, c1_groups(q), GK) ||
+      !make_bf16_map_strided(&m2, B2, 4, a.Kpad, (uint64_t)TT * a.Kpad, 4, GK))
+    return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-  const int64_t blocks = std::min<int64_t>(nsm, (a.nsnp + GEMV_THREADS - 1) / GEMV_THREADS);
+  const int64_t units = (a.nsnp + GUNIT - 1) / GUNIT;
+  const unsigned blocks = (unsigned)std::min<int64_t>(nsm, units);
   cudaError_t e = cudaSuccess;
   ProfScope ps(c, "gemv1");
   Q_DISPATCH(q, {
     auto kern = gemv1_kernel<Q>;
-    const size_t smem = sizeof(float) * ((c1_groups(Q) + 4 + 3) / 4 * 4) * a.Kpad;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<(unsigned)blocks, GEMV_THREADS, smem, c->stream>>>(G, A2, B1, B2, a);
+    constexpr int smem = GemvGeo<Q>::SMEM;
+    static_assert(smem <= 227 * 1024, "single-trait kernel shared memory");
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    kern<<<blocks, 32 + GUNIT, smem, c->stream>>>(mg, ma, m1, m2, a);
     e = cudaGetLastError();
   });
   c->launches++;

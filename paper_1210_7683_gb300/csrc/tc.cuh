@@ -244,3 +244,7 @@ __device__ __forceinline__ void reg_fence(uint32_t (&r)[8]) {
 // with a box of box_rows x box_cols elements (64: 128-byte swizzle, 32: 64-byte swizzle).
 bool make_bf16_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows,
                    uint32_t box_cols = 64);
+// Host: 2-D tensor map of `rows` bf16 rows of `cols` elements, row r at base + r * row_stride
+// elements, box of box_rows x box_cols, no swizzle.
+bool make_bf16_map_strided(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t row_stride,
+                           uint32_t box_rows, uint32_t box_cols);
