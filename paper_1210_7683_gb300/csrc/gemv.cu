@@ -8,8 +8,9 @@
 // Level-0 partial sums are integers below 2^24, so they are exact in FP32 in any order.
 // The per-pair solve is the fused epilogue's.
 //
-// One persistent CTA per SM: a TMA producer warp and 8 consumer warps, one thread per SNP,
-// 256 SNPs (two 128-SNP tiles) per unit.  A stage holds 32 values of k: eight 8 KB boxes
+// One persistent CTA per SM: a TMA producer warp and 4 consumer warps, 256 SNPs (two 128-SNP
+// tiles) per unit, two SNPs per thread (row r of each tile), so that each read of the trait's
+// slices from shared memory serves two SNPs.  A stage holds 32 values of k: eight 8 KB boxes
 // (genotypes and the three planes, two tiles; 64-byte swizzle, so that the row-per-thread
 // reads are free of bank conflicts) and the trait's 32-wide slices (two strided boxes that
 // pick trait 0's row of every group).  A ring of three stages keeps ~200 KB per SM in flight.
@@ -25,8 +26,9 @@ namespace {
 
 constexpr int GK = 32;                   // values of k per stage
 constexpr int GNS = 3;                   // ring stages
-constexpr int GCONS = 8;                 // consumer warps
-constexpr int GUNIT = GCONS * 32;        // SNPs per unit (two tiles)
+constexpr int GCONS = 4;                 // consumer warps
+constexpr int GTHR = GCONS * 32;         // consumer threads
+constexpr int GUNIT = 2 * GTHR;          // SNPs per unit: two tiles, two SNPs per thread
 constexpr int GBOX = 128 * GK * 2;       // one box: 128 rows x 32 bf16 = 8 KB
 constexpr int GDATA = 8 * GBOX;          // G + three planes, two tiles
 
@@ -49,7 +51,7 @@ __device__ __forceinline__ void bf16x8(const uint4& v, float* f) {
 }
 
 template <int Q>
-__global__ void __launch_bounds__(32 + GUNIT, 1)
+__global__ void __launch_bounds__(32 + GTHR, 1)
     gemv1_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapA,
                  const __grid_constant__ CUtensorMap mapT1, const __grid_constant__ CUtensorMap mapT2, FusedArgs a) {
   using Geo = GemvGeo<Q>;
@@ -111,20 +113,22 @@ __global__ void __launch_bounds__(32 + GUNIT, 1)
     }
     return;
   }
-  // -------------------------------------------------------------- consumers: one SNP per thread
-  const int ct = threadIdx.x - 32, tile = ct / 128, r = ct % 128;
+  // -------------------------------------------------------------- consumers: two SNPs per thread
+  const int ct = threadIdx.x - 32, r = ct;  // row r of both tiles
   const float inv_dof = 1.f / a.dof, F = 1.f / 256.f;
   const int full_b = a.full_b;
   unsigned long long nsing = 0;
   uint32_t h = 0;
   bool ok = true;
   for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const int64_t snp = a.row0 + u * GUNIT + ct;
-    float acc[G1], c2[6];
+    float acc[2][G1], c2[2][6];
 #pragma unroll
-    for (int i = 0; i < G1; ++i) acc[i] = 0.f;
+    for (int t = 0; t < 2; ++t) {
 #pragma unroll
-    for (int i = 0; i < 6; ++i) c2[i] = 0.f;
+      for (int i = 0; i < G1; ++i) acc[t][i] = 0.f;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) c2[t][i] = 0.f;
+    }
     for (int kb = 0; kb < nkb; ++kb, ++h) {
       const uint32_t s = h % GNS;
       if (ok && !tc::mbar_wait(&full[s], (h / GNS) & 1, a.status, abort)) ok = false;
@@ -132,76 +136,92 @@ __global__ void __launch_bounds__(32 + GUNIT, 1)
       float* tfs = tf + s * GK * NRP;
       // the stage's trait slices, bf16 [NR][GK] -> FP32 [GK][NRP]
       const __nv_bfloat16* traw = (const __nv_bfloat16*)(buf + GDATA);
-      for (int idx = ct; idx < NR * GK; idx += GUNIT) tfs[(idx % GK) * NRP + idx / GK] = __bfloat162float(traw[idx]);
-      tc::named_sync(1, GUNIT);
+      for (int idx = ct; idx < NR * GK; idx += GTHR) tfs[(idx % GK) * NRP + idx / GK] = __bfloat162float(traw[idx]);
+      tc::named_sync(1, GTHR);
       const uint32_t sw = (uint32_t)((r >> 1) & 3);
 #pragma unroll
       for (int c = 0; c < GK / 8; ++c) {
         const uint32_t off = (uint32_t)r * (GK * 2) + ((c ^ sw) << 4);
-        float xg[8], xa1[8], xa2[8], xa3[8];
-        bf16x8(*(const uint4*)(buf + tile * GBOX + off), xg);
-        bf16x8(*(const uint4*)(buf + (2 + tile) * GBOX + off), xa1);
-        bf16x8(*(const uint4*)(buf + (4 + tile) * GBOX + off), xa2);
-        bf16x8(*(const uint4*)(buf + (6 + tile) * GBOX + off), xa3);
+        float xg[2][8], xa1[2][8], xa2[2][8], xa3[2][8];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          bf16x8(*(const uint4*)(buf + t * GBOX + off), xg[t]);
+          bf16x8(*(const uint4*)(buf + (2 + t) * GBOX + off), xa1[t]);
+          bf16x8(*(const uint4*)(buf + (4 + t) * GBOX + off), xa2[t]);
+          bf16x8(*(const uint4*)(buf + (6 + t) * GBOX + off), xa3[t]);
+        }
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const float* tr = tfs + (8 * c + e) * NRP;
+          float tv[NR];
 #pragma unroll
-          for (int i = 0; i < G1; ++i) acc[i] = fmaf(xg[e], tr[i], acc[i]);
-          const float e2s = tr[G1], e1 = tr[G1 + 1], e2 = tr[G1 + 2], e3s = tr[G1 + 3];
-          c2[0] = fmaf(xa1[e], e1, c2[0]);   // A1 x E1   (level 0)
-          c2[1] = fmaf(xa1[e], e2, c2[1]);   // A1 x E2
-          c2[2] = fmaf(xa1[e], e3s, c2[2]);  // A1 x E3s
-          c2[3] = fmaf(xa2[e], e2s, c2[3]);  // A2 x E2s
-          c2[4] = fmaf(xa2[e], e1, c2[4]);   // A2 x E1
-          c2[5] = fmaf(xa3[e], e1, c2[5]);   // A3s x E1
+          for (int i = 0; i < NR; ++i) tv[i] = tr[i];
+          const float e2s = tv[G1], e1 = tv[G1 + 1], e2 = tv[G1 + 2], e3s = tv[G1 + 3];
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+#pragma unroll
+            for (int i = 0; i < G1; ++i) acc[t][i] = fmaf(xg[t][e], tv[i], acc[t][i]);
+            c2[t][0] = fmaf(xa1[t][e], e1, c2[t][0]);   // A1 x E1   (level 0)
+            c2[t][1] = fmaf(xa1[t][e], e2, c2[t][1]);   // A1 x E2
+            c2[t][2] = fmaf(xa1[t][e], e3s, c2[t][2]);  // A1 x E3s
+            c2[t][3] = fmaf(xa2[t][e], e2s, c2[t][3]);  // A2 x E2s
+            c2[t][4] = fmaf(xa2[t][e], e1, c2[t][4]);   // A2 x E1
+            c2[t][5] = fmaf(xa3[t][e], e1, c2[t][5]);   // A3s x E1
+          }
         }
       }
       // release the stage: one arrival per warp once all its lanes have read it
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&empty[s]);
     }
-    const bool valid = ok && snp >= a.snp_lo && snp < snp_end;
-    if (!valid) continue;
-    // the fused kernel's epilogue for pair (snp, trait 0)
-    const float sA = a.sA[snp];
-    const float num = cj[0] * fmaf(F, fmaf(F, fmaf(F, acc[3 + 2 * PM1], acc[2 + 2 * PM1]), acc[1 + PM1]), acc[0]);
-    float z[Q1], zz = 0.f;
 #pragma unroll
-    for (int c = 0; c < PM1; ++c) {
-      z[c] = cj[1 + c] * fmaf(F, acc[2 + PM1 + c], acc[1 + c]);
-      zz = fmaf(z[c], z[c], zz);
-    }
-    const float lvl1 = (c2[1] + c2[2]) + (c2[3] + c2[4]) + c2[5];
-    const float sv = (sA * cj[cst_escale(Q)]) * fmaf(F, lvl1, c2[0]);
-    const float delta = sv - zz;
-    float beta, se;
-    const bool sing = !(delta > 1e-6f * sv) || !(sA > 0.f);
-    if (sing) {
-      beta = se = __int_as_float(0x7fc00000);
-      ++nsing;
-    } else {
-      const float inv = __frcp_rn(delta);
-      beta = num * inv;
-      const float rss = fmaxf(fmaf(-num, beta, cj[cst_rr(Q)]), 0.f);
-      se = __fsqrt_rn(rss * inv * inv_dof);
-    }
-    const int64_t o = snp - a.i0;
-    if (full_b) {
-      double* ob = a.out_b64 + o * (PM1 + 1);
-#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int64_t snp = a.row0 + u * GUNIT + 128 * t + r;
+      const bool valid = ok && snp >= a.snp_lo && snp < snp_end;
+      if (!valid) continue;
+      const float* acc_t = acc[t];
+      const float* c2t = c2[t];
+      // the fused kernel's epilogue for pair (snp, trait 0)
+      const float sA = a.sA[snp];
+      const float num =
+          cj[0] * fmaf(F, fmaf(F, fmaf(F, acc_t[3 + 2 * PM1], acc_t[2 + 2 * PM1]), acc_t[1 + PM1]), acc_t[0]);
+      float z[Q1], zz = 0.f;
+  #pragma unroll
       for (int c = 0; c < PM1; ++c) {
-        // beta_L = g - L^-T z beta - a_i beta
-        float t = cj[cst_g(Q) + c];
-#pragma unroll
-        for (int d = 0; d < PM1; ++d) t = fmaf(-cj[cst_lit(Q) + c * PM1 + d] * z[d], beta, t);
-        t = fmaf(-a.acoef[snp * PM1 + c], beta, t);
-        ob[c] = sing ? (double)beta : (double)t;
+        z[c] = cj[1 + c] * fmaf(F, acc_t[2 + PM1 + c], acc_t[1 + c]);
+        zz = fmaf(z[c], z[c], zz);
       }
-      ob[PM1] = (double)beta;
-    } else {
-      a.out_beta[o] = beta;
-      a.out_se[o] = se;
+      const float lvl1 = (c2t[1] + c2t[2]) + (c2t[3] + c2t[4]) + c2t[5];
+      const float sv = (sA * cj[cst_escale(Q)]) * fmaf(F, lvl1, c2t[0]);
+      const float delta = sv - zz;
+      float beta, se;
+      const bool sing = !(delta > 1e-6f * sv) || !(sA > 0.f);
+      if (sing) {
+        beta = se = __int_as_float(0x7fc00000);
+        ++nsing;
+      } else {
+        const float inv = __frcp_rn(delta);
+        beta = num * inv;
+        const float rss = fmaxf(fmaf(-num, beta, cj[cst_rr(Q)]), 0.f);
+        se = __fsqrt_rn(rss * inv * inv_dof);
+      }
+      const int64_t o = snp - a.i0;
+      if (full_b) {
+        double* ob = a.out_b64 + o * (PM1 + 1);
+  #pragma unroll
+        for (int c = 0; c < PM1; ++c) {
+          // beta_L = g - L^-T z beta - a_i beta
+          float t = cj[cst_g(Q) + c];
+  #pragma unroll
+          for (int d = 0; d < PM1; ++d) t = fmaf(-cj[cst_lit(Q) + c * PM1 + d] * z[d], beta, t);
+          t = fmaf(-a.acoef[snp * PM1 + c], beta, t);
+          ob[c] = sing ? (double)beta : (double)t;
+        }
+        ob[PM1] = (double)beta;
+      } else {
+        a.out_beta[o] = beta;
+        a.out_se[o] = se;
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) nsing += __shfl_xor_sync(0xffffffffu, nsing, o);
@@ -233,7 +253,7 @@ int launch_gemv1(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G,
     constexpr int smem = GemvGeo<Q>::SMEM;
     static_assert(smem <= 227 * 1024, "single-trait kernel shared memory");
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    kern<<<blocks, 32 + GUNIT, smem, c->stream>>>(mg, ma, m1, m2, a);
+    kern<<<blocks, 32 + GTHR, smem, c->stream>>>(mg, ma, m1, m2, a);
     e = cudaGetLastError();
   });
   c->launches++;
