@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(32 + GTHR, 1)
       const float num =
           cj[0] * fmaf(F, fmaf(F, fmaf(F, acc_t[3 + 2 * PM1], acc_t[2 + 2 * PM1]), acc_t[1 + PM1]), acc_t[0]);
       float z[Q1], zz = 0.f;
-  #pragma unroll
+#pragma unroll
       for (int c = 0; c < PM1; ++c) {
         z[c] = cj[1 + c] * fmaf(F, acc_t[2 + PM1 + c], acc_t[1 + c]);
         zz = fmaf(z[c], z[c], zz);
@@ -208,11 +208,11 @@ __global__ void __launch_bounds__(32 + GTHR, 1)
       const int64_t o = snp - a.i0;
       if (full_b) {
         double* ob = a.out_b64 + o * (PM1 + 1);
-  #pragma unroll
+#pragma unroll
         for (int c = 0; c < PM1; ++c) {
           // beta_L = g - L^-T z beta - a_i beta
           float t = cj[cst_g(Q) + c];
-  #pragma unroll
+#pragma unroll
           for (int d = 0; d < PM1; ++d) t = fmaf(-cj[cst_lit(Q) + c * PM1 + d] * z[d], beta, t);
           t = fmaf(-a.acoef[snp * PM1 + c], beta, t);
           ob[c] = sing ? (double)beta : (double)t;
