@@ -488,7 +488,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       tc::fence_before();
       __syncwarp();
       if (lane == 0) {
-        if (PAIR) tc::mbar_arrive_cluster(tc::mapa(acc_empty, 0));
+        // relaxed: the TMEM loads are complete (tcgen05.wait::ld); nothing else is ordered
+        if (PAIR) tc::mbar_arrive_cluster_relaxed(tc::mapa(acc_empty, 0));
         else tc::mbar_arrive(acc_empty);
       }
       if (valid_i) {

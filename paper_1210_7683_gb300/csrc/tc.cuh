@@ -93,6 +93,12 @@ __device__ __forceinline__ uint32_t mapa(const void* p, uint32_t rank) {
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
+// Relaxed arrival on another CTA's mbarrier: no cluster-scope release fence.  For signals
+// that order no memory writes of the caller (e.g. "my TMEM reads have completed", after
+// tcgen05.wait::ld).  The release form measured ~2 us per arrival on this GPU.
+__device__ __forceinline__ void mbar_arrive_cluster_relaxed(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
 // MMA of a CTA pair (M = 256: 128 rows of A and N/2 rows of B from each CTA), issued by one CTA.
 __device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                               uint32_t accumulate) {
