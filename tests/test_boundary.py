@@ -56,3 +56,11 @@ def test_argument_errors_without_gpu(libpath):
     assert rc == 8  # GWAS_ERR_UNSUPPORTED
     rc = lib.gwas_solve(None, None, 0, 0, None)
     assert rc == 1
+    # the streaming entry points reject a missing context before any device work
+    lib.gwas_solve_ooc.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.gwas_solve_ooc(None, 10, None, 0, None, 1, None, None, None, None) == 1
+    lib.gwas_solve_stream.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.gwas_solve_stream(None, None, 0, 0, 1, None, None, None, None) == 1
+
