@@ -526,8 +526,10 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             }
             ob[PM1] = (double)beta;
           } else {
-            obeta[o] = beta;
-            ose[o] = se;
+            // streaming stores: the grid is never re-read here, so it should not push the
+            // genotype and trait tiles out of L2
+            __stcs(obeta + o, beta);
+            __stcs(ose + o, se);
           }
         }
       }
