@@ -43,7 +43,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # single-pass ncu captures of dram__bytes_read.sum + dram__bytes_write.sum.  Valid only while
 # the kernel's sources hash to the value the captures were taken on: a changed kernel reports
 # null traffic.
-FUSED_TRAFFIC = {"sources": ["fused.cu", "fused.cuh", "tc.cuh", "mixed.cu"],
+FUSED_TRAFFIC = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "tc.cuh", "mixed.cu"],
                  "sha256": "6abdc04ad2ff27987cd1d6c72d0895f6df4f03c7a268e981dd7c20e45c7ff9cd",
                  "workload": (1000, 3, 1_000_000, 10_000), "read": 204.23e9, "write": 80.01e9}
 

@@ -65,9 +65,11 @@ extern "C" {
 #define GWAS_FP64  0  /* every step in FP64 (the paper's arithmetic, Section 6) */
 #define GWAS_MIXED 1  /* bf16 tensor-core contractions on exact fixed-point slices with
                          FP32 accumulation; FP64 eigendecomposition and per-trait algebra.
-                         Any 0 <= p-1 <= 7; traits are processed in tiles of 32 for
-                         p-1 <= 3 and of 16 above (the accumulators of a tile take
-                         (10 + 2(p-1)) x tile TMEM columns of 512). */
+                         Any 0 <= p-1 <= 19 (the paper's 2 <= p <= 20, Section 3);
+                         traits are processed in tiles of 32 for p-1 <= 3, 16 for
+                         p-1 <= 10 and 8 above (the accumulators of a tile take
+                         (4 + 2(p-1)) x tile + 6 x tile TMEM columns of 512, 8 x tile for
+                         the C2 part of 8-trait tiles). */
 
 /* output modes */
 #define GWAS_OUT_FULL_B  0  /* double b[t][i1-i0][p]: every coefficient, SNP coefficient last */
@@ -96,7 +98,8 @@ GWAS_API void gwas_default_opts(gwas_opts* opts);
  *
  *   ctx   out: the new context (NULL on failure)
  *   n     number of individuals, 1 <= n <= 16384
- *   pm1   number of covariates p-1 (columns of X_L), 0 <= pm1 <= 7
+ *   pm1   number of covariates p-1 (columns of X_L), 0 <= pm1 <= 19 (Section 3 states
+ *         2 <= p <= 20; p = 1, no covariates, is also accepted)
  *   phi   n x n symmetric kinship matrix Phi, FP64 (only the lower triangle is read)
  *   XL    n x pm1 covariates X_L, FP64 column-major (may be NULL when pm1 == 0)
  *   t     number of traits, t >= 1

@@ -236,7 +236,7 @@ extern "C" int gwas_setup(gwas_ctx** out, int n, int pm1, const double* phi, con
   gwas_default_opts(&o);
   if (opts) o = *opts;
   if (n < 1 || n > 16384) return ctx_fail(nullptr, GWAS_ERR_ARG, fmt("n = %d outside [1, 16384]", n));
-  if (pm1 < 0 || pm1 > GWAS_MAX_PM1) return ctx_fail(nullptr, GWAS_ERR_UNSUPPORTED, fmt("p-1 = %d outside [0, 7]", pm1));
+  if (pm1 < 0 || pm1 > GWAS_MAX_PM1) return ctx_fail(nullptr, GWAS_ERR_UNSUPPORTED, fmt("p-1 = %d outside [0, 19]", pm1));
   if (n <= pm1 + 1) return ctx_fail(nullptr, GWAS_ERR_ARG, "need n > p");
   if (t < 1) return ctx_fail(nullptr, GWAS_ERR_ARG, "t must be >= 1");
   if (!phi || !h2 || (pm1 > 0 && !XL)) return ctx_fail(nullptr, GWAS_ERR_ARG, "NULL input array");

@@ -1,557 +1,9 @@
-// Fused contraction + per-pair Schur-complement solve on the tensor cores (the loop
-// body of Algorithm 5: S_BL, S_BR, b_B for every SNP x trait pair, then the p x p
-// solve, with the blocks of Algorithm 2).
-//
-// Per pair (i, j), with x_c = P_c x_i the SNP centred against span(X_L) (an exact
-// reparametrisation: the SNP coefficient and its standard error do not change, the
-// covariate coefficients move by a_i * beta), r_j the GLS residual of y_j on X_L,
-// L_j the Cholesky factor of S_TL,j and e_j = diag(D_j^-1):
-//   num  = x_i^T M_j^-1 r_j                  = x_i . w_j       (C1, column w)
-//   z    = L_j^-1 X_L^T M_j^-1 x_c           = x_i . v'_j,c    (C1, columns v)
-//   s    = x_c^T M_j^-1 x_c = sum_k e_jk x'_ck^2                (C2)
-//   delta = s - z^T z  (Schur complement of S_TL in S),  beta = num / delta,
-//   RSS = r_j^T M_j^-1 r_j - num * beta,  SE = sqrt(RSS / ((n - p) delta)).
-// C1 contracts the exact int8 genotypes (as bf16) against fixed-point slices of
-// the per-trait columns [w | v'_1..3]; C2 contracts slices of x'_c^2 against slices
-// of e_j.  Level-0 slice products are exact in FP32 (bounded partial sums), the
-// lower levels go to separate accumulators, and the levels are recombined in the
-// epilogue.
-//
-// Work is split into tiles of 128 SNPs x 32 traits.  A thread-block cluster of
-// CS x CT CTAs works on CS SNP tiles x CT trait tiles at once: the CTAs on the same
-// SNP tile share its genotype operands through TMA multicast (each loads 1/CT of
-// the rows for all of them), those on the same trait tile share the trait
-// operands (1/CS each), and every CTA releases a ring slot to all CTAs that write
-// into it.  TMEM columns of each CTA:
-//   [0,128)   C1 level 0  (slice 1 of w, v1, v2, v3; 32 traits each)
-//   [128,256) C1 level 1  (slice 2)
-//   [256,288) w slice 3   [288,320) w slice 4
-//   [320,416) A1 x [E1 | E2 | E3s]: C2 level 0, then two groups in level-1 units
-//   [416,480) A2 x [E2s | E1]       [480,512) A3s x E1   (level-1 units)
-// Every MMA of a K step writes its own columns, so consecutive small MMAs do not wait
-// on one another's accumulator (a chain of dependent N <= 128 MMAs runs at the MMA
-// latency, not at the tensor-core rate); the epilogue adds the level-1 groups.
-#include <algorithm>
-#include <cstdio>
-#include <cstdlib>
-#include <string>
-
-#include "fused.cuh"
-#include "gwas_internal.cuh"
-#include "tc.cuh"
+// Launches of the fused contraction + Schur solve kernel (fused_impl.cuh) for 0 <= p - 1 <= 7,
+// with the optional cluster and CTA-pair shapes of p = 4; 8 <= p - 1 <= 19 is instantiated
+// in fused_wide.cu.
+#include "fused_impl.cuh"
 
 namespace {
-
-// K extent of one stage: 64 bf16 = one 128-byte swizzled row.  (32-wide stages with
-// the 64-byte swizzle and 32-row boxes measured 1.6x slower: the TMA unit's cost per box.)
-constexpr int BM = 128, BK = 64;
-constexpr int ROWB = BK * 2;                         // bytes per operand row of a stage
-constexpr int G_BYTES = BM * ROWB;                   // 16 KB: one A tile
-constexpr int BBOX = 32;                             // rows per TMA box of the trait operands (cluster shapes)
-constexpr int SLOT = 64 * 1024;                      // one-CTA shapes: a ring slot holds either half-stage
-constexpr int SLOTS = 3;
-// half-stages of the one-CTA shapes: G + the C1 trait rows; the three x'^2 planes + the C2 trait rows
-__host__ __device__ constexpr int h1_bytes(int q) { return G_BYTES + c1_rows(q) * ROWB; }
-__host__ __device__ constexpr int h2_bytes(int q) { return 3 * G_BYTES + c2_rows(q) * ROWB; }
-// CTA pair (q = 3): each CTA stages its own SNP rows and half of the trait rows, in three items
-// per K block (G + C1 half: 36 KB; C2 half + A1: 28 KB; A2 + A3s: 32 KB) and a ring of six
-// 36 KB slots, i.e. two K blocks in flight.
-constexpr int PSLOT = 36 * 1024, PSLOTS = 6;
-constexpr int PC1_ROWS = c1_rows(3) / 2, PC2_ROWS = c2_alloc(3) / 2;  // 160 and 96 trait rows per CTA
-constexpr int PI0_BYTES = G_BYTES + PC1_ROWS * ROWB;   // G + this CTA's C1 trait rows
-constexpr int PI1_BYTES = PC2_ROWS * ROWB + G_BYTES;   // this CTA's C2 trait rows + A1
-constexpr int PI2_BYTES = 2 * G_BYTES;                 // A2 + A3s
-__host__ __device__ constexpr int cst_bytes(int q) { return mixed_tt(q) * cst_stride(q) * 4; }  // one tile's constants
-__host__ __device__ constexpr int ring_bytes(bool pair) { return pair ? PSLOTS * PSLOT : SLOTS * SLOT; }
-__host__ __device__ constexpr int smem_bytes(bool pair, int q) { return ring_bytes(pair) + 2 * cst_bytes(q) + 1024 + 512; }
-constexpr int TMEM_COLS = 512;
-constexpr bool fits_all_q() {
-  for (int q = 0; q <= 7; ++q)
-    if (h1_bytes(q) > SLOT || h2_bytes(q) > SLOT || smem_bytes(false, q) > 227 * 1024) return false;
-  return true;
-}
-static_assert(fits_all_q(), "half-stage does not fit a slot");
-static_assert(PI0_BYTES <= PSLOT && PI1_BYTES <= PSLOT && PI2_BYTES <= PSLOT, "pair item does not fit a slot");
-static_assert(smem_bytes(true, 3) <= 227 * 1024, "shared memory");
-
-template <int CS, int CT>
-__device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us, int& ut) {
-  const int nss = (a.n_stiles + CS - 1) / CS, nst = (a.n_ttiles + CT - 1) / CT;
-  const int per_group = a.group * nst;
-  const int g = u / per_group;
-  const int w = u % per_group;
-  const int g0 = g * a.group;
-  const int gs = min(a.group, nss - g0);
-  ut = w / gs;
-  us = g0 + w % gs;
-}
-
-// Q = p - 1 covariates.  PAIR: the two CTAs of a cluster issue one M = 256 MMA
-// (cta_group::2); each holds its own 128 SNP rows and half of every MMA's trait rows (the
-// pair layout of the C2 operand, c2_alloc rows per tile), the leader (rank 0) issues the
-// MMAs, and both CTAs' loads complete on the leader's barriers.
-template <int CS, int CT, int EPW, bool SERVE, bool PAIR, int Q>
-__global__ void __launch_bounds__(64 + 32 * EPW, 1)
-    fused_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapA2,
-                 const __grid_constant__ CUtensorMap mapB1, const __grid_constant__ CUtensorMap mapB2, FusedArgs a) {
-  constexpr int NC = CS * CT;
-  constexpr int AROWS = BM / CT;                    // genotype rows this CTA loads per plane
-  static_assert(!PAIR || (CS == 2 && CT == 1 && !SERVE), "pair mode is a 2 x 1 cluster");
-  static_assert(NC == 1 || Q == 3, "cluster and pair shapes are built for q = 3");
-  constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = mixed_tt(Q), CSTR = cst_stride(Q);
-  constexpr int B1_ROWS = c1_rows(Q), B2_ROWS = c2_rows(Q), B2_ROWS_PAIR = c2_alloc(Q);
-  constexpr int C2B = c1_groups(Q) * TT;            // first TMEM column of the C2 accumulators
-  constexpr int H1_BYTES = h1_bytes(Q), H2_BYTES = h2_bytes(Q);
-  // C1 MMAs of the one-CTA shapes: the C1 trait rows in chunks of at most 256 (N <= 256)
-  constexpr int N0 = B1_ROWS < 256 ? B1_ROWS : 256, N1 = B1_ROWS - N0;
-  // TMA boxes of the C1 trait rows in the one-CTA shapes (at most 256 rows per box)
-  constexpr int B1_NBOX = B1_ROWS <= 256 ? 1 : 2, B1_BOX = B1_ROWS / B1_NBOX;
-  static_assert(N1 >= 0 && N1 <= 256 && N0 % 16 == 0 && N1 % 16 == 0 && B1_BOX % 8 == 0, "C1 geometry");
-  // multicast cluster shapes: each CTA loads 1/CS of the trait rows in 32-row boxes
-  constexpr int B1_BOXES = B1_ROWS / BBOX / CS, B2_BOXES = B2_ROWS / BBOX / CS;
-  static_assert(B1_ROWS % (BBOX * CS) == 0 && B2_ROWS % (BBOX * CS) == 0 && BM % (8 * CT) == 0, "cluster shape");
-  // One CTA per tile: every half-stage is three TMA boxes of 128 to 192 rows (the genotype
-  // tile and the C1 trait rows in two halves; the three x'^2 planes, stored next to one
-  // another, in two halves and the C2 trait rows).  The TMA unit pays a fixed cost per box
-  // of the order of 50 cycles, so the 32-row boxes of the cluster shapes cap the load rate.
-  constexpr bool BIG = CS == 1 && CT == 1 && !PAIR;
-  constexpr int NSL = PAIR ? PSLOTS : SLOTS, SLB = PAIR ? PSLOT : SLOT;  // ring slots and their size
-  constexpr int NI = PAIR ? 3 : 2;                                        // ring items per K block
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* cst_smem = (float*)(smem + ring_bytes(PAIR));  // [2][TT][CSTR], double-buffered by tile
-  uint64_t* full = (uint64_t*)(smem + ring_bytes(PAIR) + 2 * cst_bytes(Q));
-  uint64_t* empty = full + NSL;
-  uint64_t* acc_full = empty + NSL;
-  uint64_t* acc_empty = acc_full + 1;
-  uint32_t* tslot = (uint32_t*)(acc_empty + 1);
-  volatile int* abort = (volatile int*)(tslot + 1);
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  uint32_t crank = 0, cid = blockIdx.x, ncl = gridDim.x;
-  if (NC > 1) {
-    crank = tc::cluster_ctarank();
-    cid = tc::cluster_id_x();
-    ncl = tc::cluster_count_x();
-  }
-  const int sr = crank % CS, tr = crank / CS;
-  uint16_t maskA = 0, maskB = 0;   // CTAs sharing this CTA's genotype / trait operands
-#pragma unroll
-  for (int k = 0; k < CT; ++k) maskA |= (uint16_t)(1u << (sr + CS * k));
-#pragma unroll
-  for (int k = 0; k < CS; ++k) maskB |= (uint16_t)(1u << (CS * tr + k));
-  const int nsuper = SERVE ? a.nunits : ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
-  const int nkb = a.Kpad / BK;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < NSL; ++s) {
-      tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], PAIR ? 1 : CS + CT - 1);
-    }
-    tc::mbar_init(acc_full, 1);
-    tc::mbar_init(acc_empty, PAIR ? 2 * EPW : EPW);
-    *abort = 0;
-    tc::fence_mbar_init();
-  }
-  if (warp == 1) {
-    if (PAIR) tc::tmem_alloc_pair(tslot, TMEM_COLS);
-    else tc::tmem_alloc(tslot, TMEM_COLS);
-  }
-  tc::fence_before();
-  __syncthreads();
-  if (NC > 1) tc::cluster_sync();
-  tc::fence_after();
-  const uint32_t tbase = *tslot;
-  const bool leader = !PAIR || crank == 0;
-
-  if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      tc::prefetch_map(&mapG);
-      tc::prefetch_map(&mapA2);
-      tc::prefetch_map(&mapB1);
-      tc::prefetch_map(&mapB2);
-      uint32_t h = 0;  // ring item counter
-      bool ok = true;
-      for (int u = cid; u < nsuper && ok; u += ncl) {
-        int row, tt;
-        if (SERVE) {
-          const int4 w = a.units[u];
-          row = w.x + tr * AROWS;
-          tt = w.y;
-        } else {
-          int us, ut;
-          super_coords<CS, CT>(u, a, us, ut);
-          row = (int)a.row0 + (us * CS + sr) * BM + tr * AROWS;
-          tt = ut * CT + tr;
-        }
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-          for (int it = 0; it < NI; ++it, ++h) {
-            const uint32_t s = h % NSL;
-            if (h >= NSL && !tc::mbar_wait(&empty[s], ((h / NSL) - 1) & 1, a.status, abort)) { ok = false; break; }
-            uint8_t* buf = smem + s * SLB;
-            const int x = kb * BK;
-            const int half = it;
-            if (PAIR) {
-              // own SNP rows and own half of the trait rows, completing on the leader's barrier
-              const uint32_t fb = tc::mapa(&full[s], 0);
-              if (leader) tc::mbar_expect_tx(&full[s], 2 * (it == 0 ? PI0_BYTES : it == 1 ? PI1_BYTES : PI2_BYTES));
-              if (it == 0) {
-                tc::tma_load_2d_pair(buf, &mapG, fb, x, row);
-                tc::tma_load_2d_pair(buf + G_BYTES, &mapB1, fb, x, tt * B1_ROWS + (int)crank * PC1_ROWS);
-              } else if (it == 1) {
-                tc::tma_load_2d_pair(buf, &mapB2, fb, x, tt * B2_ROWS_PAIR + (int)crank * PC2_ROWS);
-                tc::tma_load_2d_pair(buf + PC2_ROWS * ROWB, &mapA2, fb, x, (int)a2_row(0, row));
-              } else {
-                tc::tma_load_2d_pair(buf, &mapA2, fb, x, (int)a2_row(1, row));
-                tc::tma_load_2d_pair(buf + G_BYTES, &mapA2, fb, x, (int)a2_row(2, row));
-              }
-              continue;
-            }
-            if (BIG) {
-              if (half == 0) {
-                tc::mbar_expect_tx(&full[s], H1_BYTES);
-                tc::tma_load_2d(buf, &mapG, &full[s], x, row);
-#pragma unroll
-                for (int b = 0; b < B1_NBOX; ++b)
-                  tc::tma_load_2d(buf + G_BYTES + b * B1_BOX * ROWB, &mapB1, &full[s], x, tt * B1_ROWS + b * B1_BOX);
-              } else {
-                const int y = (int)a2_row(0, row);
-                tc::mbar_expect_tx(&full[s], H2_BYTES);
-                tc::tma_load_2d(buf, &mapA2, &full[s], x, y);
-                tc::tma_load_2d(buf + 3 * BM / 2 * ROWB, &mapA2, &full[s], x, y + 3 * BM / 2);
-                tc::tma_load_2d(buf + 3 * G_BYTES, &mapB2, &full[s], x, tt * B2_ROWS);
-              }
-              continue;
-            }
-            if (half == 0) {
-              tc::mbar_expect_tx(&full[s], H1_BYTES);
-              if (CT > 1) tc::tma_load_2d_mc(buf + tr * AROWS * ROWB, &mapG, &full[s], x, row, maskA);
-              else tc::tma_load_2d(buf, &mapG, &full[s], x, row);
-#pragma unroll
-              for (int q = 0; q < B1_BOXES; ++q) {
-                const int r = (sr * B1_BOXES + q) * BBOX;
-                uint8_t* dst = buf + G_BYTES + r * ROWB;
-                if (CS > 1) tc::tma_load_2d_mc(dst, &mapB1, &full[s], x, tt * B1_ROWS + r, maskB);
-                else tc::tma_load_2d(dst, &mapB1, &full[s], x, tt * B1_ROWS + r);
-              }
-            } else {
-              tc::mbar_expect_tx(&full[s], H2_BYTES);
-#pragma unroll
-              for (int p = 0; p < 3; ++p) {
-                uint8_t* dst = buf + p * G_BYTES + tr * AROWS * ROWB;
-                if (CT > 1) tc::tma_load_2d_mc(dst, &mapA2, &full[s], x, (int)a2_row(p, row), maskA);
-                else tc::tma_load_2d(dst, &mapA2, &full[s], x, (int)a2_row(p, row));
-              }
-#pragma unroll
-              for (int q = 0; q < B2_BOXES; ++q) {
-                const int r = (sr * B2_BOXES + q) * BBOX;
-                uint8_t* dst = buf + 3 * G_BYTES + r * ROWB;
-                if (CS > 1) tc::tma_load_2d_mc(dst, &mapB2, &full[s], x, tt * B2_ROWS + r, maskB);
-                else tc::tma_load_2d(dst, &mapB2, &full[s], x, tt * B2_ROWS + r);
-              }
-            }
-          }
-        }
-      }
-      // the last release of every slot (ours and the peers') must land before we exit
-      for (uint32_t s = 0; s < NSL && h > s; ++s) {
-        const uint32_t uses = (h - s + NSL - 1) / NSL;
-        tc::mbar_wait(&empty[s], (uses - 1) & 1, a.status, abort);
-      }
-    }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
-    if (PAIR && lane == 0 && leader) {
-      constexpr uint32_t id256 = tc::idesc_bf16(2 * BM, 8 * TT), id64 = tc::idesc_bf16(2 * BM, 2 * TT);
-      constexpr uint32_t id96 = tc::idesc_bf16(2 * BM, 3 * TT), id32 = tc::idesc_bf16(2 * BM, TT);
-      uint32_t h = 0, tcount = 0;
-      bool ok = true;
-      for (int u = cid; u < nsuper && ok; u += ncl, ++tcount) {
-        if (tcount > 0 && !tc::mbar_wait(acc_empty, (tcount - 1) & 1, a.status, abort)) { ok = false; break; }
-        tc::fence_after();
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-          {
-            // item 0: G and the C1 trait rows
-            const uint32_t s = h % NSL;
-            if (!tc::mbar_wait(&full[s], (h / NSL) & 1, a.status, abort)) { ok = false; break; }
-            tc::fence_after();
-            uint8_t* buf = smem + s * SLB;
-            const uint64_t dg = tc::sdesc_sw128(buf), db = tc::sdesc_sw128(buf + G_BYTES);
-#pragma unroll
-            for (int k = 0; k < BK / 16; ++k) {
-              const uint32_t acc = (kb | k) ? 1u : 0u;
-              // [Q1 | Q2] -> levels 0 and 1 of [w v1 v2 v3]; [Q3 | Q4] -> slices 3, 4 of w
-              tc::mma_bf16_pair(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), id256, acc);
-              tc::mma_bf16_pair(tbase + 8 * TT, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, 4 * TT * ROWB + k * 32),
-                                id64, acc);
-            }
-            tc::mma_commit_pair(&empty[s], (uint16_t)3);
-            ++h;
-          }
-          {
-            // items 1 and 2: the C2 trait rows and A1; A2 and A3s
-            const uint32_t s1 = h % NSL, s2 = (h + 1) % NSL;
-            if (!tc::mbar_wait(&full[s1], (h / NSL) & 1, a.status, abort) ||
-                !tc::mbar_wait(&full[s2], ((h + 1) / NSL) & 1, a.status, abort)) {
-              ok = false;
-              break;
-            }
-            tc::fence_after();
-            uint8_t* b1 = smem + s1 * SLB;
-            uint8_t* b2 = smem + s2 * SLB;
-            const uint64_t de = tc::sdesc_sw128(b1), d1 = tc::sdesc_sw128(b1 + PC2_ROWS * ROWB);
-            const uint64_t d2 = tc::sdesc_sw128(b2), d3 = tc::sdesc_sw128(b2 + G_BYTES);
-#pragma unroll
-            for (int k = 0; k < BK / 16; ++k) {
-              const uint32_t acc = (kb | k) ? 1u : 0u;
-              tc::mma_bf16_pair(tbase + 10 * TT, tc::sdesc_add(d1, k * 32), tc::sdesc_add(de, k * 32), id96, acc);
-              tc::mma_bf16_pair(tbase + 13 * TT, tc::sdesc_add(d2, k * 32),
-                                tc::sdesc_add(de, (3 * TT / 2) * ROWB + k * 32), id64, acc);
-              tc::mma_bf16_pair(tbase + 15 * TT, tc::sdesc_add(d3, k * 32),
-                                tc::sdesc_add(de, (5 * TT / 2) * ROWB + k * 32), id32, acc);
-            }
-            tc::mma_commit_pair(&empty[s1], (uint16_t)3);
-            tc::mma_commit_pair(&empty[s2], (uint16_t)3);
-            h += 2;
-          }
-        }
-        if (ok) tc::mma_commit_pair(acc_full, (uint16_t)3);
-      }
-    } else if (!PAIR && lane == 0) {
-      constexpr uint32_t idN0 = tc::idesc_bf16(BM, N0), idN1 = tc::idesc_bf16(BM, N1 > 0 ? N1 : 16);
-      constexpr uint32_t id3 = tc::idesc_bf16(BM, 3 * TT), id2 = tc::idesc_bf16(BM, 2 * TT), id1 = tc::idesc_bf16(BM, TT);
-      const uint16_t release = maskA | maskB;
-      uint32_t h = 0, tcount = 0;
-      bool ok = true;
-      for (int u = cid; u < nsuper && ok; u += ncl, ++tcount) {
-        if (tcount > 0 && !tc::mbar_wait(acc_empty, (tcount - 1) & 1, a.status, abort)) { ok = false; break; }
-        tc::fence_after();
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-          for (int half = 0; half < 2; ++half, ++h) {
-            const uint32_t s = h % NSL;
-            if (!tc::mbar_wait(&full[s], (h / NSL) & 1, a.status, abort)) { ok = false; break; }
-            tc::fence_after();
-            uint8_t* buf = smem + s * SLB;
-            if (half == 0) {
-              const uint64_t dg = tc::sdesc_sw128(buf);
-              const uint64_t db = tc::sdesc_sw128(buf + G_BYTES);
-#pragma unroll
-              for (int k = 0; k < BK / 16; ++k) {
-                const uint32_t acc = (kb | k) ? 1u : 0u;
-                tc::mma_bf16(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), idN0, acc);
-                if (N1 > 0)
-                  tc::mma_bf16(tbase + N0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, N0 * ROWB + k * 32), idN1, acc);
-              }
-            } else {
-              const uint64_t d1 = tc::sdesc_sw128(buf), d2 = tc::sdesc_sw128(buf + G_BYTES);
-              const uint64_t d3 = tc::sdesc_sw128(buf + 2 * G_BYTES), de = tc::sdesc_sw128(buf + 3 * G_BYTES);
-#pragma unroll
-              for (int k = 0; k < BK / 16; ++k) {
-                const uint32_t acc = (kb | k) ? 1u : 0u;
-                // A1 x [E1 | E2 | E3s] -> [level 0 | a | b]
-                tc::mma_bf16(tbase + C2B, tc::sdesc_add(d1, k * 32), tc::sdesc_add(de, TT * ROWB + k * 32), id3, acc);
-                // A2 x [E2s | E1] -> its own two groups
-                tc::mma_bf16(tbase + C2B + 3 * TT, tc::sdesc_add(d2, k * 32), tc::sdesc_add(de, k * 32), id2, acc);
-                // A3s x E1 -> its own group
-                tc::mma_bf16(tbase + C2B + 5 * TT, tc::sdesc_add(d3, k * 32), tc::sdesc_add(de, TT * ROWB + k * 32), id1,
-                             acc);
-              }
-            }
-            if (NC > 1) tc::mma_commit_mc(&empty[s], release);
-            else tc::mma_commit(&empty[s]);
-          }
-        }
-        if (ok) tc::mma_commit(acc_full);
-      }
-    }
-  } else {
-    // ------------------------------------------------------------ epilogue (EPW warps)
-    const int ew = warp - 2;
-    const int q = warp % 4;                            // TMEM lane quarter this warp may access
-    constexpr int JPW = TT / (EPW / 4);                // traits per epilogue warp
-    const int jbeg = (ew / 4) * JPW;
-    const uint32_t lane_base = tbase + ((uint32_t)(q * 32) << 16);
-    const float inv_dof = 1.f / a.dof;
-    uint32_t tcount = 0;
-    unsigned long long nsing = 0;
-    for (int u = cid; u < nsuper; u += ncl, ++tcount) {
-      // this tile's SNPs [snp0, snp0+128) (valid in [snp_lo, snp_end)), output origin and stride,
-      // first trait (jbase) within its request, constants and output arrays
-      int64_t snp0, snp_lo, snp_end, oi0, ldo;
-      int ntrait, jbase, full_b;
-      const float* cst_tile;
-      float *obeta, *ose;
-      double* ob64;
-      unsigned long long* sing_ctr;
-      if (SERVE) {
-        const int4 w = a.units[u];
-        const ServeDesc rd = a.reqs[w.z];
-        snp0 = w.x; snp_lo = rd.i0; snp_end = rd.i1; oi0 = rd.i0; ldo = rd.ldo; ntrait = rd.ntrait; jbase = w.w * TT;
-        full_b = rd.full_b; cst_tile = a.cst + (size_t)w.y * TT * CSTR;
-        obeta = rd.beta; ose = rd.se; ob64 = rd.b64; sing_ctr = rd.singular;
-      } else {
-        int us, ut;
-        super_coords<CS, CT>(u, a, us, ut);
-        const int st = us * CS + sr, tt = ut * CT + tr;
-        snp0 = a.row0 + (int64_t)st * BM; snp_lo = a.snp_lo; snp_end = a.row0 + a.nsnp; oi0 = a.i0; ldo = a.ldo; ntrait = a.ntrait;
-        jbase = tt * TT; full_b = a.full_b; cst_tile = a.cst + (size_t)jbase * CSTR;
-        obeta = a.out_beta; ose = a.out_se; ob64 = a.out_b64; sing_ctr = nullptr;
-      }
-      // stage this tile's per-trait constants (double buffer: the barrier of the previous
-      // tile guarantees every epilogue warp has finished reading this buffer)
-      float* cs = cst_smem + (tcount & 1) * TT * CSTR;
-      for (int e = ew * 32 + lane; e < TT * CSTR; e += EPW * 32)
-        cs[e] = jbase + e / CSTR < ntrait ? cst_tile[e] : 0.f;
-      tc::named_sync(1, EPW * 32);
-      const bool ok = tc::mbar_wait(acc_full, tcount & 1, a.status, abort);
-      tc::fence_after();
-      const int64_t snp = snp0 + q * 32 + lane;
-      const bool valid_i = ok && snp >= snp_lo && snp < snp_end;
-      const float sA = valid_i ? a.sA[snp] : 0.f;
-      float ac[Q1] = {};
-      if (valid_i && full_b) {
-#pragma unroll
-        for (int c = 0; c < PM1; ++c) ac[c] = a.acoef[snp * PM1 + c];
-      }
-      unsigned long long tsing = 0;
-      // All TMEM reads of this warp's JPW traits come first, reduced at once to the few
-      // per-pair values the solve needs; the accumulators are released before any of the
-      // per-pair arithmetic and output stores, so the next tile's MMAs wait only for the reads.
-      static_assert(JPW % 4 == 0, "epilogue reads traits in groups of 4");
-      float num_r[JPW], zz_r[JPW], s_r[JPW], z_r[JPW][Q1];
-      const float F = 1.f / 256.f;
-#pragma unroll
-      for (int g = 0; g < JPW / 4; ++g) {
-        const int j0 = jbeg + 4 * g;
-        {
-          // C1, w: slices 1 and 2 (groups 0 and 1 + q) and the groups of slices 3 and 4 -> num
-          uint32_t hw[4], lw[4], w3[4], w4[4];
-          tc::tmem_ld4(lane_base + 0 * TT + j0, hw);
-          tc::tmem_ld4(lane_base + (1 + PM1) * TT + j0, lw);
-          tc::tmem_ld4(lane_base + (2 + 2 * PM1) * TT + j0, w3);
-          tc::tmem_ld4(lane_base + (3 + 2 * PM1) * TT + j0, w4);
-          tc::tmem_ld_wait();
-          tc::reg_fence(hw); tc::reg_fence(lw); tc::reg_fence(w3); tc::reg_fence(w4);
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            num_r[4 * g + v] = cs[(j0 + v) * CSTR] *
-                               fmaf(F, fmaf(F, fmaf(F, __uint_as_float(w4[v]), __uint_as_float(w3[v])),
-                                            __uint_as_float(lw[v])), __uint_as_float(hw[v]));
-            zz_r[4 * g + v] = 0.f;
-          }
-        }
-        // C1, v_c: slices 1 and 2 (groups 1 + c and 2 + q + c) -> z_c, three covariates per wait
-#pragma unroll
-        for (int c0 = 0; c0 < PM1; c0 += 3) {
-          constexpr int CB = 3;
-          uint32_t hz[CB][4], lz[CB][4];
-#pragma unroll
-          for (int c = 0; c < CB; ++c)
-            if (c0 + c < PM1) {
-              tc::tmem_ld4(lane_base + (1 + c0 + c) * TT + j0, hz[c]);
-              tc::tmem_ld4(lane_base + (2 + PM1 + c0 + c) * TT + j0, lz[c]);
-            }
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int c = 0; c < CB; ++c)
-            if (c0 + c < PM1) { tc::reg_fence(hz[c]); tc::reg_fence(lz[c]); }
-#pragma unroll
-          for (int v = 0; v < 4; ++v)
-#pragma unroll
-            for (int c = 0; c < CB; ++c)
-              if (c0 + c < PM1) {
-                const float z = cs[(j0 + v) * CSTR + 1 + c0 + c] * fmaf(F, __uint_as_float(lz[c][v]), __uint_as_float(hz[c][v]));
-                z_r[4 * g + v][c0 + c] = z;
-                zz_r[4 * g + v] = fmaf(z, z, zz_r[4 * g + v]);
-              }
-        }
-        {
-          // C2: level 0 and the five level-1 groups -> s
-          uint32_t d0[4], da[4], db[4], ea[4], eb[4], ec[4];
-          tc::tmem_ld4(lane_base + C2B + 0 * TT + j0, d0);
-          tc::tmem_ld4(lane_base + C2B + 1 * TT + j0, da);
-          tc::tmem_ld4(lane_base + C2B + 2 * TT + j0, db);
-          tc::tmem_ld4(lane_base + C2B + 3 * TT + j0, ea);
-          tc::tmem_ld4(lane_base + C2B + 4 * TT + j0, eb);
-          tc::tmem_ld4(lane_base + C2B + 5 * TT + j0, ec);
-          tc::tmem_ld_wait();
-          tc::reg_fence(d0); tc::reg_fence(da); tc::reg_fence(db);
-          tc::reg_fence(ea); tc::reg_fence(eb); tc::reg_fence(ec);
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const float lvl1 = (__uint_as_float(da[v]) + __uint_as_float(db[v])) +
-                               (__uint_as_float(ea[v]) + __uint_as_float(eb[v])) + __uint_as_float(ec[v]);
-            s_r[4 * g + v] = (sA * cs[(j0 + v) * CSTR + cst_escale(Q)]) * fmaf(F, lvl1, __uint_as_float(d0[v]));
-          }
-        }
-      }
-      // every TMEM read of this warp for this tile is complete: release the accumulators
-      tc::fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        // relaxed: the TMEM loads are complete (tcgen05.wait::ld); nothing else is ordered
-        if (PAIR) tc::mbar_arrive_cluster_relaxed(tc::mapa(acc_empty, 0));
-        else tc::mbar_arrive(acc_empty);
-      }
-      if (valid_i) {
-#pragma unroll
-        for (int r = 0; r < JPW; ++r) {
-          const int jl = jbeg + r;
-          const int jj = jbase + jl;            // trait index within the block (request)
-          if (jj >= ntrait) break;
-          const float* cj = cs + jl * CSTR;
-          const float num = num_r[r], zz = zz_r[r], s = s_r[r];
-          const float delta = s - zz;
-          float beta, se;
-          const bool sing = !(delta > 1e-6f * s) || !(sA > 0.f);
-          if (sing) {
-            beta = se = __int_as_float(0x7fc00000);
-            ++tsing;
-          } else {
-            const float inv = __frcp_rn(delta);
-            beta = num * inv;
-            const float rss = fmaxf(fmaf(-num, beta, cj[cst_rr(Q)]), 0.f);
-            se = __fsqrt_rn(rss * inv * inv_dof);
-          }
-          const int64_t o = (int64_t)jj * ldo + (snp - oi0);
-          if (full_b) {
-            double* ob = ob64 + o * (PM1 + 1);
-#pragma unroll
-            for (int c = 0; c < PM1; ++c) {
-              // beta_L = g - L^-T z beta - a_i beta
-              float t = cj[cst_g(Q) + c];
-#pragma unroll
-              for (int d = 0; d < PM1; ++d) t = fmaf(-cj[cst_lit(Q) + c * PM1 + d] * z_r[r][d], beta, t);
-              t = fmaf(-ac[c], beta, t);
-              ob[c] = sing ? (double)beta : (double)t;
-            }
-            ob[PM1] = (double)beta;
-          } else {
-            // streaming stores: the grid is never re-read here, so it should not push the
-            // genotype and trait tiles out of L2
-            __stcs(obeta + o, beta);
-            __stcs(ose + o, se);
-          }
-        }
-      }
-      if (SERVE && sing_ctr) {
-        unsigned long long v = tsing;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0 && v) atomicAdd(sing_ctr, v);
-      }
-      nsing += tsing;
-    }
-    // warp-aggregated count of singular pairs
-    for (int o = 16; o > 0; o >>= 1) nsing += __shfl_xor_sync(0xffffffffu, nsing, o);
-    if (lane == 0 && nsing) atomicAdd(a.singular, nsing);
-  }
-  tc::fence_before();
-  __syncthreads();
-  if (NC > 1) tc::cluster_sync();
-  if (warp == 1) {
-    if (PAIR) tc::tmem_dealloc_pair(tbase, TMEM_COLS);
-    else tc::tmem_dealloc(tbase, TMEM_COLS);
-  }
-}
 
 struct Shape {
   int cs, ct, epw, pair;
@@ -570,59 +22,6 @@ Shape shape_from_env(int q) {
   return sh;
 }
 
-template <int CS, int CT, int EPW, bool SERVE, bool PAIR, int Q>
-int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const CUtensorMap& ma,
-                 const CUtensorMap& m1, const CUtensorMap& m2) {
-  constexpr int NC = CS * CT;
-  auto kern = fused_kernel<CS, CT, EPW, SERVE, PAIR, Q>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(PAIR, Q));
-    attr = true;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = NC;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(64 + 32 * EPW);
-  cfg.dynamicSmemBytes = smem_bytes(PAIR, Q);
-  cfg.stream = c->stream;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  int nsm = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-  int nclusters = nsm / NC;
-  cfg.gridDim = dim3(nclusters * NC);
-  int maxc = 0;
-  if (cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg) == cudaSuccess && maxc > 0) nclusters = maxc;
-  cudaGetLastError();
-  const int nsuper = SERVE ? a.nunits : ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
-  nclusters = std::min(nclusters, nsuper);
-  if (a.max_ctas > 0) nclusters = std::max(1, std::min(nclusters, a.max_ctas / NC));
-  cfg.gridDim = dim3(nclusters * NC);
-  ProfScope ps(c, SERVE ? "fused_serve" : "fused");
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mg, ma, m1, m2, a);
-  c->launches++;
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return ctx_fail(c, GWAS_ERR_CUDA, std::string("fused kernel launch: ") + cudaGetErrorString(e));
-  }
-  return GWAS_OK;
-}
-
-// Tensor maps of the one-CTA-per-tile shapes: boxes of 128 genotype rows, 192 rows of
-// x'^2 planes, the C1 trait rows in one or two boxes of at most 256 rows, and the C2 trait rows.
-bool make_big_maps(int q, CUtensorMap* mg, CUtensorMap* ma, CUtensorMap* m1, CUtensorMap* m2, const FusedArgs& a,
-                   const __nv_bfloat16* G, const __nv_bfloat16* A2, const __nv_bfloat16* B1, const __nv_bfloat16* B2,
-                   int ttiles) {
-  const int r1 = c1_rows(q), r2 = c2_rows(q), b1box = r1 <= 256 ? r1 : r1 / 2;
-  return make_bf16_map(mg, G, a.mpad, a.Kpad, BM, BK) && make_bf16_map(ma, A2, 3ull * a.mpad, a.Kpad, 3 * BM / 2, BK) &&
-         make_bf16_map(m1, B1, (uint64_t)ttiles * r1, a.Kpad, b1box, BK) &&
-         make_bf16_map(m2, B2, (uint64_t)ttiles * r2, a.Kpad, r2, BK);
-}
-
 }  // namespace
 
 int fused_trait_tile_multiple() { return 4; }
@@ -633,7 +32,8 @@ int launch_fused(gwas_ctx* c, int q, const FusedArgs& args, const __nv_bfloat16*
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2) {
   FusedArgs a = args;
   if (a.n_stiles == 0 || a.n_ttiles == 0) return GWAS_OK;
-  if (q < 0 || q > 7) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: p-1 outside [0, 7]");
+  if (q < 0 || q > MIXED_MAX_Q) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: p-1 outside [0, 19]");
+  if (q > 7) return launch_fused_wide(c, q, a, G, A2, B1, B2, false, (a.n_ttiles + 3) / 4 * 4);
   const Shape sh = shape_from_env(q);
   const int ttiles_pad = (a.n_ttiles + 3) / 4 * 4;   // trait operands are allocated for a multiple of 4 tiles
   CUtensorMap mg, ma, m1, m2;
@@ -668,7 +68,8 @@ int launch_fused(gwas_ctx* c, int q, const FusedArgs& args, const __nv_bfloat16*
 int launch_fused_serve(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                        const __nv_bfloat16* B1, const __nv_bfloat16* B2, int b_tiles) {
   if (a.nunits == 0) return GWAS_OK;
-  if (q < 0 || q > 7) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: p-1 outside [0, 7]");
+  if (q < 0 || q > MIXED_MAX_Q) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: p-1 outside [0, 19]");
+  if (q > 7) return launch_fused_wide(c, q, a, G, A2, B1, B2, true, b_tiles);
   CUtensorMap mg, ma, m1, m2;
   if (!make_big_maps(q, &mg, &ma, &m1, &m2, a, G, A2, B1, B2, b_tiles))
     return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");

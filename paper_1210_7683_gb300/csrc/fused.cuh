@@ -6,17 +6,22 @@
 
 struct gwas_ctx;
 
-// Geometry of the mixed path for q = p - 1 covariates (0 <= q <= 7).
+// Geometry of the mixed path for q = p - 1 covariates (0 <= q <= 19, i.e. 1 <= p <= 20).
 //   A trait tile holds mixed_tt(q) traits.  Its C1 operand has c1_groups(q) groups of
 //   mixed_tt(q) rows: [w1 | v_1..v_q] (slice 1), [w2 | v_1..v_q] (slice 2), w3, w4.  Its
 //   C2 operand has 4 groups [E2s | E1 | E2 | E3s].  The accumulators of a tile take
-//   (c1_groups(q) + 6) * mixed_tt(q) <= 512 TMEM columns.
-__host__ __device__ constexpr int mixed_tt(int q) { return q <= 3 ? 32 : 16; }
+//   c1_groups(q) * mixed_tt(q) + c2_cols(q) <= 512 TMEM columns, and the C1 half-stage (a
+//   genotype tile and the C1 operand, 128-byte rows) fits a 64 KB ring slot.
+__host__ __device__ constexpr int mixed_tt(int q) { return q <= 3 ? 32 : q <= 10 ? 16 : 8; }
 __host__ __device__ constexpr int c1_groups(int q) { return 4 + 2 * q; }
 __host__ __device__ constexpr int c1_rows(int q) { return c1_groups(q) * mixed_tt(q); }
 __host__ __device__ constexpr int c2_rows(int q) { return 4 * mixed_tt(q); }
+// TMEM columns of the C2 accumulators: six groups; with 8-trait tiles the MMAs (M = 128 needs
+// N % 16 == 0) are widened to eight groups, two of which hold unused products.
+__host__ __device__ constexpr int c2_cols(int q) { return mixed_tt(q) == 8 ? 8 * mixed_tt(q) : 6 * mixed_tt(q); }
 // C2 rows allocated per trait tile (the CTA-pair layout, q = 3 only, needs 6 groups)
 __host__ __device__ constexpr int c2_alloc(int q) { return 6 * mixed_tt(q); }
+constexpr int MIXED_MAX_Q = 19;
 
 // Runs the statement in the variadic arguments with the compile-time constant Q = q (0..7,
 // larger values run as 7).
@@ -31,6 +36,29 @@ __host__ __device__ constexpr int c2_alloc(int q) { return 6 * mixed_tt(q); }
     case 6: { constexpr int Q = 6; __VA_ARGS__; } break;     \
     default: { constexpr int Q = 7; __VA_ARGS__; } break;    \
   }
+// The same over 8..19 (smaller values run as 8).
+#define Q_DISPATCH_WIDE(q, ...)                              \
+  switch (q) {                                               \
+    case 9: { constexpr int Q = 9; __VA_ARGS__; } break;     \
+    case 10: { constexpr int Q = 10; __VA_ARGS__; } break;   \
+    case 11: { constexpr int Q = 11; __VA_ARGS__; } break;   \
+    case 12: { constexpr int Q = 12; __VA_ARGS__; } break;   \
+    case 13: { constexpr int Q = 13; __VA_ARGS__; } break;   \
+    case 14: { constexpr int Q = 14; __VA_ARGS__; } break;   \
+    case 15: { constexpr int Q = 15; __VA_ARGS__; } break;   \
+    case 16: { constexpr int Q = 16; __VA_ARGS__; } break;   \
+    case 17: { constexpr int Q = 17; __VA_ARGS__; } break;   \
+    case 18: { constexpr int Q = 18; __VA_ARGS__; } break;   \
+    case 19: { constexpr int Q = 19; __VA_ARGS__; } break;   \
+    default: { constexpr int Q = 8; __VA_ARGS__; } break;    \
+  }
+// Q = q for 0 <= q <= 19.
+#define Q_DISPATCH_ALL(q, ...)                               \
+  if ((q) <= 7) {                                            \
+    Q_DISPATCH(q, __VA_ARGS__)                               \
+  } else {                                                   \
+    Q_DISPATCH_WIDE(q, __VA_ARGS__)                          \
+  }
 
 // Per-trait FP32 constants of the epilogue, cst_stride(q) floats per trait:
 //   [0] scale of w, [1..q] scales of v'_1..q, [q+1] scale of e, [q+2] r^T M^-1 r,
@@ -41,8 +69,13 @@ __host__ __device__ constexpr int cst_escale(int q) { return q + 1; }
 __host__ __device__ constexpr int cst_rr(int q) { return q + 2; }
 __host__ __device__ constexpr int cst_g(int q) { return q + 3; }
 __host__ __device__ constexpr int cst_lit(int q) { return 2 * q + 3; }
-static_assert(cst_stride(3) == 20 && (c1_groups(3) + 6) * mixed_tt(3) == 512, "p = 4 geometry");
-static_assert((c1_groups(7) + 6) * mixed_tt(7) <= 512, "TMEM columns");
+static_assert(cst_stride(3) == 20 && c1_rows(3) + c2_cols(3) == 512, "p = 4 geometry");
+__host__ __device__ constexpr bool tmem_fits_all_q() {
+  for (int q = 0; q <= MIXED_MAX_Q; ++q)
+    if (c1_rows(q) + c2_cols(q) > 512 || c1_rows(q) % 16 || c2_cols(q) % 16) return false;
+  return true;
+}
+static_assert(tmem_fits_all_q(), "TMEM columns");
 
 // Row of plane p (0..2) of SNP i in the x'_c^2 slice array: the three planes of each
 // 128-SNP tile are stored next to one another ([tile][plane][128 rows][Kpad]), so that
@@ -96,8 +129,8 @@ int fused_trait_tile_multiple();
 // 1 when the selected kernel shape is the CTA-pair one, whose trait operands use the pair layout.
 int fused_pair_layout(int q);
 
-// q = p - 1 selects the kernel's geometry; shapes other than the default one-CTA shape
-// are built for q = 3 only.
+// q = p - 1 (0..19) selects the kernel's geometry; shapes other than the default one-CTA
+// shape are built for q = 3 only.
 int launch_fused(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2);
 // Single-trait kernel (gemv.cu): the same solve for a.ntrait == 1, streaming the SNPs'
@@ -109,3 +142,7 @@ int launch_gemv1(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G,
 // b_tiles = trait-tile slots of the B1/B2 arena.
 int launch_fused_serve(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                        const __nv_bfloat16* B1, const __nv_bfloat16* B2, int b_tiles);
+// The one-CTA kernel for 8 <= q <= 19 (fused_wide.cu), for either of the two launches above;
+// b_tiles = trait tiles allocated in B1/B2.
+int launch_fused_wide(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
+                      const __nv_bfloat16* B1, const __nv_bfloat16* B2, bool serve, int b_tiles);

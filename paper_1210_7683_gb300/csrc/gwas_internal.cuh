@@ -10,7 +10,7 @@
 
 #include "../../include/gwas.h"
 
-#define GWAS_MAX_PM1 7
+#define GWAS_MAX_PM1 19
 
 // Raw device buffer owned by a context; freed in gwas_destroy.
 struct DevBuf {

@@ -174,76 +174,78 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
                                                          float* __restrict__ cst, const int* __restrict__ slot,
                                                          int pair) {
   constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = mixed_tt(Q);
+  constexpr int NTRI = PM1 * (PM1 + 1) / 2;
   const int j = blockIdx.x;
   const double h = h2[j];
   const double* y = Yt + (size_t)j * ldy;
-  __shared__ double red[8][PM1 * PM1 + PM1 + 1];
+  __shared__ double red[8], sh_ent[NTRI + Q1];         // lower triangle of S_TL, then b_T
+  __shared__ double sh_L[Q1 * Q1], sh_Li[Q1 * Q1];      // L (lower) and L^-1 (lower), row-major
   __shared__ double sh_g[Q1], sh_Lit[Q1 * Q1], sh_se;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
-  double part[PM1 * PM1 + PM1 + 1];
-  for (int q = 0; q < PM1 * PM1 + PM1 + 1; ++q) part[q] = 0;
+  // e_j, held in row 0 of this trait's Wt until w_j replaces it below, and its maximum
+  double* e_row = Wt + (size_t)j * (PM1 + 1) * Kpad;
+  double emax = 0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const double e = 1.0 / (h * lam[k] + (1.0 - h));
-    double xl[Q1];
-    for (int a = 0; a < PM1; ++a) xl[a] = XLt[(size_t)a * n + k];
-    for (int a = 0; a < PM1; ++a) {
-      for (int b = 0; b < PM1; ++b) part[a * PM1 + b] += e * xl[a] * xl[b];
-      part[PM1 * PM1 + a] += e * xl[a] * y[k];
-    }
-    part[PM1 * PM1 + PM1] = fmax(part[PM1 * PM1 + PM1], e);
+    e_row[k] = e;
+    emax = fmax(emax, e);
   }
-  for (int q = 0; q < PM1 * PM1 + PM1 + 1; ++q) {
-    double v = part[q];
-    for (int o = 16; o > 0; o >>= 1) {
-      const double w = __shfl_xor_sync(0xffffffffu, v, o);
-      v = (q == PM1 * PM1 + PM1) ? fmax(v, w) : v + w;
+  for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  if (lane == 0) red[warp] = emax;
+  __syncthreads();  // e_row (global) and red are visible to the whole block
+  // S_TL = X'_L^T diag(e) X'_L (lower triangle) and b_T = X'_L^T (e . y'): a warp per entry
+  for (int q = warp; q < NTRI + PM1; q += nw) {
+    const double *u, *v;
+    if (q < NTRI) {
+      int a = 0;
+      while ((a + 1) * (a + 2) / 2 <= q) ++a;
+      u = XLt + (size_t)a * n;
+      v = XLt + (size_t)(q - a * (a + 1) / 2) * n;
+    } else {
+      u = XLt + (size_t)(q - NTRI) * n;
+      v = y;
     }
-    if (lane == 0) red[warp][q] = v;
+    double acc = 0;
+    for (int k = lane; k < n; k += 32) acc = fma(e_row[k] * u[k], v[k], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sh_ent[q] = acc;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double S[Q1][Q1], bT[Q1], emax = 0;
-    for (int a = 0; a < PM1; ++a) {
+    double em = 0;
+    for (int w = 0; w < nw; ++w) em = fmax(em, red[w]);
+    // L L^T = S_TL
+    for (int a = 0; a < PM1; ++a)
       for (int b = 0; b < PM1; ++b) {
         double v = 0;
-        for (int w = 0; w < nw; ++w) v += red[w][a * PM1 + b];
-        S[a][b] = v;
+        if (b <= a) {
+          v = sh_ent[a * (a + 1) / 2 + b];
+          for (int k = 0; k < b; ++k) v -= sh_L[a * Q1 + k] * sh_L[b * Q1 + k];
+          v = (a == b) ? sqrt(fmax(v, 1e-300)) : v / sh_L[b * Q1 + b];
+        }
+        sh_L[a * Q1 + b] = v;
       }
-      double v = 0;
-      for (int w = 0; w < nw; ++w) v += red[w][PM1 * PM1 + a];
-      bT[a] = v;
-    }
-    for (int w = 0; w < nw; ++w) emax = fmax(emax, red[w][PM1 * PM1 + PM1]);
-    double L[Q1][Q1] = {};
-    for (int a = 0; a < PM1; ++a)
-      for (int b = 0; b <= a; ++b) {
-        double v = S[a][b];
-        for (int k = 0; k < b; ++k) v -= L[a][k] * L[b][k];
-        L[a][b] = (a == b) ? sqrt(fmax(v, 1e-300)) : v / L[b][b];
-      }
-    // Linv = L^-1 (lower)
-    double Li[Q1][Q1] = {};
+    // L^-1 (lower)
     for (int c = 0; c < PM1; ++c)
       for (int a = 0; a < PM1; ++a) {
         double v = (a == c) ? 1.0 : 0.0;
-        for (int k = 0; k < a; ++k) v -= L[a][k] * Li[k][c];
-        Li[a][c] = v / L[a][a];
+        for (int k = 0; k < a; ++k) v -= sh_L[a * Q1 + k] * sh_Li[k * Q1 + c];
+        sh_Li[a * Q1 + c] = v / sh_L[a * Q1 + a];
       }
-    // g = L^-T L^-1 b_T
-    double zt[Q1];
-    for (int a = 0; a < PM1; ++a) {
+    // g = L^-T L^-1 b_T; L^-1 b_T replaces b_T in place, last row first (row a reads rows <= a)
+    for (int a = PM1 - 1; a >= 0; --a) {
       double v = 0;
-      for (int k = 0; k <= a; ++k) v += Li[a][k] * bT[k];
-      zt[a] = v;
+      for (int k = 0; k <= a; ++k) v += sh_Li[a * Q1 + k] * sh_ent[NTRI + k];
+      sh_ent[NTRI + a] = v;
     }
     for (int a = 0; a < PM1; ++a) {
       double v = 0;
-      for (int k = a; k < PM1; ++k) v += Li[k][a] * zt[k];
+      for (int k = a; k < PM1; ++k) v += sh_Li[k * Q1 + a] * sh_ent[NTRI + k];
       sh_g[a] = v;
     }
     for (int a = 0; a < PM1; ++a)
-      for (int c = 0; c < PM1; ++c) sh_Lit[a * PM1 + c] = Li[c][a];  // (L^-T)[a][c]
-    sh_se = emax / 256.0;
+      for (int c = 0; c < PM1; ++c) sh_Lit[a * PM1 + c] = sh_Li[c * Q1 + a];  // (L^-T)[a][c]
+    sh_se = em / 256.0;
   }
   __syncthreads();
   const double se = sh_se, inv_se = 1.0 / se;
@@ -299,11 +301,11 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
   }
   for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
   __syncthreads();
-  if (lane == 0) red[warp][0] = rr;
+  if (lane == 0) red[warp] = rr;
   __syncthreads();
   if (threadIdx.x == 0) {
     double v = 0;
-    for (int w = 0; w < nw; ++w) v += red[w][0];
+    for (int w = 0; w < nw; ++w) v += red[w];
     float* cj = cst + ((size_t)tile * TT + jj) * cst_stride(Q);
     cj[cst_escale(Q)] = (float)se;
     cj[cst_rr(Q)] = (float)v;
@@ -422,7 +424,7 @@ static void mixed_destroy_setup(gwas_ctx* c) {
 // One-time preparation of the B operands of the three rotations.
 static int mixed_setup(gwas_ctx* c) {
   if (c->mixed && c->mixed->Brot) return GWAS_OK;
-  if (c->pm1 < 0 || c->pm1 > 7) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "mixed path needs 0 <= p-1 <= 7");
+  if (c->pm1 < 0 || c->pm1 > MIXED_MAX_Q) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "mixed path needs 0 <= p-1 <= 19");
   if (!c->mixed) c->mixed = new MixedState;
   MixedState* s = c->mixed;
   const int n = c->n, PM1 = c->pm1;
@@ -449,7 +451,7 @@ static int mixed_setup(gwas_ctx* c) {
   if (PM1 > 0)
     cudaMemcpyAsync(s->XtXinv, c->h_XtXinv.data(), sizeof(double) * PM1 * PM1, cudaMemcpyHostToDevice, c->stream);
   { ProfScope ps(c, "setup_rotation_operands");
-  Q_DISPATCH(PM1, rot_b_kernel<Q><<<n + PM1, 256, 0, c->stream>>>(c->Z, c->XL, s->XtXinv, n, rot));
+  Q_DISPATCH_ALL(PM1, rot_b_kernel<Q><<<n + PM1, 256, 0, c->stream>>>(c->Z, c->XL, s->XtXinv, n, rot));
   c->launches++;
   dim3 tb(32, 8), tg((n + 31) / 32, (n + 31) / 32);
   transpose_kernel<<<tg, tb, 0, c->stream>>>(c->Z, n, zr);
@@ -613,7 +615,7 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h
   if ((rc = launch_xgemm(c, 4, 4, 3, g, Ysl, s->Bzt)) == GWAS_OK) {
     // per-trait algebra and the C2 operand
     ProfScope ps(c, "prep_traits");
-    Q_DISPATCH(q, prep_mixed_kernel<Q><<<tb, 256, 0, c->stream>>>(Yt, Kpad, h2, c->lam, c->XLt, n, Kpad, Wt, B2, cst,
+    Q_DISPATCH_ALL(q, prep_mixed_kernel<Q><<<tb, 256, 0, c->stream>>>(Yt, Kpad, h2, c->lam, c->XLt, n, Kpad, Wt, B2, cst,
                                                                   slot, pair));
     c->launches++;
     // back-rotation [w | v] = Z [e.r' | (e.X'_L) L^-T]
@@ -630,7 +632,7 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h
   }
   if (rc == GWAS_OK) {
     ProfScope ps(c, "pack_trait_columns");
-    Q_DISPATCH(q, pack_c1_kernel<Q><<<tb, 256, 0, c->stream>>>(Wt, c->XL, s->XtXinv, n, Kpad, B1, cst, slot, pair));
+    Q_DISPATCH_ALL(q, pack_c1_kernel<Q><<<tb, 256, 0, c->stream>>>(Wt, c->XL, s->XtXinv, n, Kpad, B1, cst, slot, pair));
     c->launches++;
   }
   return rc;

@@ -52,8 +52,9 @@ def test_argument_errors_without_gpu(libpath):
     assert rc == 1  # GWAS_ERR_ARG
     lib.gwas_last_error.restype = ctypes.c_char_p
     assert b"n = 0" in lib.gwas_last_error(None)
-    rc = lib.gwas_setup(ctypes.byref(ctx), 100, 9, None, None, 1, None, None)
-    assert rc == 8  # GWAS_ERR_UNSUPPORTED
+    rc = lib.gwas_setup(ctypes.byref(ctx), 100, 20, None, None, 1, None, None)
+    assert rc == 8  # GWAS_ERR_UNSUPPORTED: p = 21 is above the paper's range 2 <= p <= 20
+    assert b"[0, 19]" in lib.gwas_last_error(None)
     rc = lib.gwas_solve(None, None, 0, 0, None)
     assert rc == 1
     # the streaming entry points reject a missing context before any device work

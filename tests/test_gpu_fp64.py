@@ -64,7 +64,8 @@ def test_tiny_last_se(gw, tiny):
     assert se_err(s, se) <= 2 ** -23
 
 
-@pytest.mark.parametrize("n,m,t,pm1", [(300, 777, 13, 2), (130, 65, 17, 0), (97, 200, 5, 7), (64, 1, 1, 3), (5, 3, 2, 3)])
+@pytest.mark.parametrize("n,m,t,pm1", [(300, 777, 13, 2), (130, 65, 17, 0), (97, 200, 5, 7), (64, 1, 1, 3), (5, 3, 2, 3),
+                                       (200, 77, 11, 8), (150, 100, 9, 12), (200, 65, 17, 19), (21, 40, 3, 19)])
 def test_ragged_shapes(gw, n, m, t, pm1):
     P = make_problem(n, m, t, pm1=pm1, seed=n + m)
     out, rc, _ = run(gw, P, gw.GWAS_OUT_FULL_B)

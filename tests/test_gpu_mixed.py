@@ -115,8 +115,11 @@ def test_sampled_pairs_at_full_mixed_workload(gw):
 
 # Any number of covariates: q = p - 1 from 0 to 7.  Tiles hold 32 traits for q <= 3 and 16
 # above; the trait and SNP counts leave ragged last tiles.
+# p - 1 up to 19 (Section 3: 2 <= p <= 20): trait tiles of 32 (p - 1 <= 3), 16 (<= 10) and 8
 @pytest.mark.parametrize("pm1,n,m,t", [(0, 200, 300, 40), (1, 256, 257, 33), (2, 300, 200, 17), (4, 256, 300, 20),
-                                       (5, 130, 129, 45), (6, 200, 256, 19), (7, 97, 300, 35)])
+                                       (5, 130, 129, 45), (6, 200, 256, 19), (7, 97, 300, 35), (8, 200, 300, 37),
+                                       (10, 160, 257, 33), (11, 200, 300, 21), (13, 130, 129, 17), (16, 256, 200, 9),
+                                       (19, 200, 300, 25)])
 def test_general_p_last_se(gw, pm1, n, m, t):
     P = make_problem(n, m, t, pm1=pm1, seed=101 * pm1 + n)
     out, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE)
@@ -125,7 +128,7 @@ def test_general_p_last_se(gw, pm1, n, m, t):
     check_last(out, b, se)
 
 
-@pytest.mark.parametrize("pm1", [0, 2, 5, 7])
+@pytest.mark.parametrize("pm1", [0, 2, 5, 7, 10, 11, 19])
 def test_general_p_full_b(gw, pm1):
     P = make_problem(160, 290, 37, pm1=pm1, seed=7 + pm1)
     out, rc, _ = solve(gw, P, gw.GWAS_OUT_FULL_B)
@@ -136,7 +139,8 @@ def test_general_p_full_b(gw, pm1):
 
 
 # One trait: the single-trait (GEMV-shaped, HBM-bound) kernel instead of the fused one.
-@pytest.mark.parametrize("pm1", [0, 3, 7])
+# (p - 1 > 7 has no single-trait kernel: the fused kernel solves the one-trait tile)
+@pytest.mark.parametrize("pm1", [0, 3, 7, 12])
 def test_single_trait(gw, pm1):
     P = make_problem(300, 1500, 1, pm1=pm1, seed=83 + pm1)
     b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)

@@ -55,7 +55,8 @@ def out_of_core(g, P, precision, output, slab, block, xr=None):
     return out, seen
 
 
-@pytest.mark.parametrize("precision_name,pm1", [("GWAS_MIXED", 3), ("GWAS_MIXED", 5), ("GWAS_FP64", 2)])
+@pytest.mark.parametrize("precision_name,pm1", [("GWAS_MIXED", 3), ("GWAS_MIXED", 5), ("GWAS_MIXED", 11),
+                                                 ("GWAS_FP64", 2), ("GWAS_FP64", 15)])
 @pytest.mark.parametrize("output_name", ["GWAS_OUT_LAST_SE", "GWAS_OUT_FULL_B"])
 def test_ooc_equals_in_core(gw, precision_name, pm1, output_name):
     precision, output = getattr(gw, precision_name), getattr(gw, output_name)

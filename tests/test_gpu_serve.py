@@ -98,10 +98,10 @@ def test_poll_and_singular_request(gw):
         gw.gwas_destroy(ctx)
 
 
-@pytest.mark.parametrize("pm1", [0, 5])
+@pytest.mark.parametrize("pm1", [0, 5, 9, 14])
 def test_serving_general_p(gw, pm1):
-    """Serving with q = p - 1 other than 3 (tiles of 16 traits for q = 5): a mix of
-    requests equals gwas_solve of each request and the oracle."""
+    """Serving with q = p - 1 other than 3 (tiles of 16 traits for q = 5 and 9, of 8 for
+    q = 14): a mix of requests equals gwas_solve of each request and the oracle."""
     P = make_problem(160, 1200, 2, pm1=pm1, seed=43 + pm1)
     reqs = requests(P, 6, 11 + pm1)
     ctx = new_ctx(gw, P)

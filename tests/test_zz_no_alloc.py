@@ -40,7 +40,8 @@ def rotated_inputs(P, dev):
 def test_noalloc_matches_gwas_solve_twice(gw):
     torch = pytest.importorskip("torch")
     dev = torch.device("cuda:0")
-    problems = [make_problem(256, 500, 24, seed=31), make_problem(200, 333, 17, seed=32)]
+    problems = [make_problem(256, 500, 24, seed=31), make_problem(200, 333, 17, seed=32),
+                make_problem(120, 70, 9, pm1=19, seed=34)]  # p = 20, the top of the paper's range
     for P in problems:  # two calls in a row, the second on other data and sizes
         ref = regular(gw, P, gw.GWAS_OUT_FULL_B)
         lam, XLt, Xt, Yt, h2 = rotated_inputs(P, dev)
