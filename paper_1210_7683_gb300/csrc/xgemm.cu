@@ -9,7 +9,8 @@
 // product whose partial sums stay below 2^24 (2*bits + log2(K) <= 24), so it is
 // exact in FP32 whatever the accumulation order; the higher levels are 2^-bits
 // smaller and their FP32 rounding is negligible.  The epilogue combines the
-// levels and the scales in FP64.
+// levels and the scales in FP64.  K is contracted in chunks of at most 1024, one launch
+// each, so that bits = 7 at any n (4 slices: 28 bits); later chunks add to the output.
 //
 // Used for the rotations by Z of Algorithm 5 (X'_R := Z^T X_R with exact int8
 // genotypes as A, and Y' := Z^T Y) and for the back-rotation Z W' of the
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(192, 1) xgemm_kernel(const __grid_constant__ C
   volatile int* abort = (volatile int*)(tslot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;
-  const int nk = g.Kpad / BK;
+  const int kb0 = g.kb0, nk = g.kb1 - g.kb0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::STAGES; ++s) {
       tc::mbar_init(&full[s], 1);
@@ -77,10 +78,12 @@ __global__ void __launch_bounds__(192, 1) xgemm_kernel(const __grid_constant__ C
       uint8_t* st = smem + s * Cfg::STAGE;
       tc::mbar_expect_tx(&full[s], Cfg::STAGE);
 #pragma unroll
-      for (int a = 0; a < SA; ++a) tc::tma_load_2d(st + a * Cfg::A_BYTES, &mapA, &full[s], kb * BK, a * g.rowsA_pad + r0);
+      for (int a = 0; a < SA; ++a)
+        tc::tma_load_2d(st + a * Cfg::A_BYTES, &mapA, &full[s], (kb0 + kb) * BK, a * g.rowsA_pad + r0);
 #pragma unroll
       for (int b = 0; b < SB; ++b)
-        tc::tma_load_2d(st + SA * Cfg::A_BYTES + b * Cfg::B_BYTES, &mapB, &full[s], kb * BK, b * g.rowsB_pad + c0);
+        tc::tma_load_2d(st + SA * Cfg::A_BYTES + b * Cfg::B_BYTES, &mapB, &full[s], (kb0 + kb) * BK,
+                        b * g.rowsB_pad + c0);
     }
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t idesc = tc::idesc_bf16(BM, BN);
@@ -131,7 +134,8 @@ __global__ void __launch_bounds__(192, 1) xgemm_kernel(const __grid_constant__ C
           double acc = (double)__uint_as_float(v[L][j]);
 #pragma unroll
           for (int l = L - 1; l >= 0; --l) acc = fma(acc, g.level_scale, (double)__uint_as_float(v[l][j]));
-          g.out64[(size_t)r * g.ldo + c] = acc * sa * g.scaleB[c];
+          double* o = g.out64 + (size_t)r * g.ldo + c;
+          *o = g.accumulate ? *o + acc * sa * g.scaleB[c] : acc * sa * g.scaleB[c];
         }
       } else {
         // FP32 result: each level sum is an exact integer below 2^24, so combining the
@@ -144,7 +148,8 @@ __global__ void __launch_bounds__(192, 1) xgemm_kernel(const __grid_constant__ C
           float acc = __uint_as_float(v[L][j]);
 #pragma unroll
           for (int l = L - 1; l >= 0; --l) acc = fmaf(acc, ls, __uint_as_float(v[l][j]));
-          g.out32[(size_t)r * g.ldo + c] = acc * (saf * (float)g.scaleB[c]);
+          float* o = g.out32 + (size_t)r * g.ldo + c;
+          *o = g.accumulate ? *o + acc * (saf * (float)g.scaleB[c]) : acc * (saf * (float)g.scaleB[c]);
         }
       }
     }
@@ -259,11 +264,19 @@ static int run_xgemm(gwas_ctx* c, const XgemmArgs& g, const __nv_bfloat16* A, co
   return GWAS_OK;
 }
 
-int launch_xgemm(gwas_ctx* c, int SA, int SB, int L, const XgemmArgs& g, const __nv_bfloat16* A,
+int launch_xgemm(gwas_ctx* c, int SA, int SB, int L, const XgemmArgs& args, const __nv_bfloat16* A,
                  const __nv_bfloat16* B) {
-  if (g.rowsA_pad % BM || g.rowsB_pad % 64 || g.Kpad % BK)
+  if (args.rowsA_pad % BM || args.rowsB_pad % 64 || args.Kpad % BK)
     return ctx_fail(c, GWAS_ERR_ARG, "xgemm: padded sizes are not tile multiples");
-  if (SA == 4 && SB == 4 && L == 3) return run_xgemm<4, 4, 3>(c, g, A, B);
-  if (SA == 1 && SB == 4 && L == 3) return run_xgemm<1, 4, 3>(c, g, A, B);
-  return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "xgemm: slice configuration not instantiated");
+  if (!((SA == 4 && SB == 4 && L == 3) || (SA == 1 && SB == 4 && L == 3)))
+    return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "xgemm: slice configuration not instantiated");
+  for (int k0 = 0; k0 < args.Kpad; k0 += XGEMM_KCHUNK) {
+    XgemmArgs g = args;
+    g.kb0 = k0 / BK;
+    g.kb1 = std::min(args.Kpad, k0 + XGEMM_KCHUNK) / BK;
+    g.accumulate = k0 > 0;
+    const int rc = SA == 4 ? run_xgemm<4, 4, 3>(c, g, A, B) : run_xgemm<1, 4, 3>(c, g, A, B);
+    if (rc != GWAS_OK) return rc;
+  }
+  return GWAS_OK;
 }

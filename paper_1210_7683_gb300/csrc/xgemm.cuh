@@ -18,13 +18,20 @@ struct XgemmArgs {
   int64_t ldo;               // output row stride (elements)
   unsigned long long* status;  // status[0] <- 1 when a bounded wait expires
   const char* name;          // timer name in profiling mode
+  // set by launch_xgemm: the K blocks [kb0, kb1) of one launch, and whether it adds to the output
+  int kb0, kb1, accumulate;
 };
 
-// Bits per slice for which the level-0 product of two slices is exact in FP32
-// over a K extent of Kpad: 2 * bits + log2(Kpad) <= 24.
+// K is contracted in chunks of at most XGEMM_KCHUNK; each chunk's level sums are exact
+// in FP32 and the chunks are added in the output's precision.
+constexpr int XGEMM_KCHUNK = 1024;
+
+// Bits per slice for which the level-0 product of two slices is exact in FP32 over one
+// K chunk: 2 * bits + log2(min(Kpad, XGEMM_KCHUNK)) <= 24 (7 bits for Kpad > 512).
 inline int xgemm_bits(int Kpad) {
+  const int K = Kpad < XGEMM_KCHUNK ? Kpad : XGEMM_KCHUNK;
   int lg = 0;
-  while ((1 << lg) < Kpad) ++lg;
+  while ((1 << lg) < K) ++lg;
   int b = (24 - lg) / 2;
   return b > 8 ? 8 : b;
 }

@@ -173,3 +173,17 @@ def test_single_trait_singular_snp(gw):
     ok[40] = False
     b, se = EigOracle(P.phi, P.XL).solve(P.XR[ok], P.Y, P.h2)
     check_last(out[:, :, ok], b, se)
+
+
+def test_largest_n_of_the_paper(gw):
+    # n = 10^4, the top of the paper's range (Section 3): the slice scales and the exactness
+    # bound of the level-0 sums (512 n < 2^24 for C1) at their largest; FP64 path alongside
+    P = make_problem(10_000, 260, 12, seed=2024)
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    out, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE)
+    assert rc == gw.GWAS_OK
+    check_last(out, b, se)
+    full, rc, _ = solve(gw, P, gw.GWAS_OUT_FULL_B)
+    assert full_b_err(full.transpose(1, 0, 2), b, se) <= TOL
+    full64, rc, _ = solve(gw, P, gw.GWAS_OUT_FULL_B, precision=gw.GWAS_FP64)
+    assert full_b_err(full64.transpose(1, 0, 2), b, se) <= 1e-10
