@@ -137,9 +137,11 @@ GWAS_API int gwas_load_snps(gwas_ctx* ctx, int64_t m, const int8_t* XR);
  * RSS the squared norm of the whitened residual (the paper defines none).
  * Returns GWAS_ERR_SINGULAR_PAIRS (a warning) when some pair's Schur
  * complement is <= 1e-10 times its diagonal entry; those outputs are NaN.
- * A host `out` receives the results trait block by trait block (opts.trait_block),
- * each block's copy overlapping the next block's computation when `out` is
- * page-locked.
+ * A host `out` receives the results trait block by trait block, each block's
+ * copy overlapping the next block's computation when `out` is page-locked.
+ * The blocks start at 1/8 of opts.trait_block traits (about 8 GB of results when
+ * trait_block is 0) and grow by 1.4x per block up to it, so that the first copy
+ * starts early; a device `out` is computed in blocks of opts.trait_block.
  */
 GWAS_API int gwas_solve(gwas_ctx* ctx, const double* Y, int64_t i0, int64_t i1, void* out);
 

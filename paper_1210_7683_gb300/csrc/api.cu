@@ -460,7 +460,23 @@ int ensure_copy_stream(gwas_ctx* c) {
 int run_blocks(gwas_ctx* c, const double* dY, int64_t i0, int64_t i1, int tb, const OutSink& sink) {
   const int n = c->n, t = c->t, p = c->p;
   const int64_t M = i1 - i0;
-  const int nblocks = (t + tb - 1) / tb;
+  // Trait blocks [bj0[b], bj0[b] + bnb[b]).  Into a host array the downloads bound the solve (the
+  // device -> host link is slower than the compute per trait), so the first block is small and
+  // each next block grows by 1.4x up to tb: the link starts early and stays busy, each block's
+  // compute hiding under the previous block's download.  Otherwise uniform blocks of tb.
+  std::vector<int> bj0, bnb;
+  {
+    const int unit = c->precision == GWAS_MIXED ? mixed_tt(c->pm1) : 16;
+    int nb = (sink.kind == 1 && t > tb) ? std::min(tb, std::max(unit, (tb / 8) / unit * unit)) : tb;
+    for (int j0 = 0; j0 < t;) {
+      const int w = std::min(std::min(nb, tb), t - j0);  // never above tb: the workspaces hold tb traits
+      bj0.push_back(j0);
+      bnb.push_back(w);
+      j0 += w;
+      nb = std::min(tb, std::max(nb + unit, (int)(nb * 1.4) / unit * unit));
+    }
+  }
+  const int nblocks = (int)bj0.size();
   const bool lastse = c->output == GWAS_OUT_LAST_SE;
   const size_t pair_bytes = lastse ? 2 * sizeof(float) : sizeof(double) * p;
   int rc = GWAS_OK;
@@ -496,7 +512,7 @@ int run_blocks(gwas_ctx* c, const double* dY, int64_t i0, int64_t i1, int tb, co
   }
   // block b's device output pointers (beta or b, and se)
   auto block_out = [&](int b, int nb, void** ob, void** os) {
-    const int j0 = b * tb;
+    const int j0 = bj0[b];
     *os = nullptr;
     if (sink.kind == 0) {
       if (!lastse) {
@@ -511,7 +527,7 @@ int run_blocks(gwas_ctx* c, const double* dY, int64_t i0, int64_t i1, int tb, co
     }
   };
   auto compute = [&](int b) -> int {
-    const int j0 = b * tb, nb = std::min(tb, t - j0);
+    const int j0 = bj0[b], nb = bnb[b];
     void *ob, *os;
     block_out(b, nb, &ob, &os);
     if (c->precision == GWAS_FP64) {
@@ -529,7 +545,7 @@ int run_blocks(gwas_ctx* c, const double* dY, int64_t i0, int64_t i1, int tb, co
     return mixed_solve_block(c, ws, dY + (size_t)j0 * n, j0, nb, i0, i1, M, lastse ? (void*)pair : ob);
   };
   auto copy_out = [&](int b) -> int {
-    const int j0 = b * tb, nb = std::min(tb, t - j0);
+    const int j0 = bj0[b], nb = bnb[b];
     const int k = b & 1;
     int r = GWAS_OK;
     // ev_compute[k] was recorded right after block b's kernels, so the download overlaps block b+1
@@ -619,7 +635,15 @@ extern "C" int gwas_solve(gwas_ctx* c, const double* Y, int64_t i0, int64_t i1, 
   OutSink sink;
   sink.kind = odev ? 0 : 1;
   sink.out = out;
-  const int tb = (c->trait_block > 0 && c->trait_block < c->t) ? c->trait_block : c->t;
+  int tb = (c->trait_block > 0 && c->trait_block < c->t) ? c->trait_block : c->t;
+  if (!odev && c->trait_block <= 0 && i1 > i0) {
+    // host output, no block size given: blocks of about 8 GB of results, so that the downloads
+    // are pipelined behind the compute and the two staging buffers stay small
+    const int64_t pair_bytes = c->output == GWAS_OUT_LAST_SE ? 8 : 8 * (int64_t)c->p;
+    const int unit = c->precision == GWAS_MIXED ? mixed_tt(c->pm1) : 16;
+    const int64_t per = (8ll << 30) / (pair_bytes * (i1 - i0));
+    tb = (int)std::min<int64_t>(c->t, std::max<int64_t>(unit, per / unit * unit));
+  }
   return solve_impl(c, Y, i0, i1, tb, sink);
 }
 

@@ -187,3 +187,27 @@ def test_largest_n_of_the_paper(gw):
     assert full_b_err(full.transpose(1, 0, 2), b, se) <= TOL
     full64, rc, _ = solve(gw, P, gw.GWAS_OUT_FULL_B, precision=gw.GWAS_FP64)
     assert full_b_err(full64.transpose(1, 0, 2), b, se) <= 1e-10
+
+
+def test_host_output_in_growing_blocks(gw):
+    # a host output is solved in trait blocks growing from tb/8 (here 32, 64, 64, 40 traits);
+    # every pair's result is the same as with one device-side block
+    import torch
+    P = make_problem(256, 700, 200, seed=2025)
+    o = gw.gwas_default_opts(precision=gw.GWAS_MIXED, output=gw.GWAS_OUT_LAST_SE, trait_block=64)
+    ctx = gw.gwas_setup(P.n, P.pm1, P.phi, P.XL, P.t, P.h2, o)
+    try:
+        gw.gwas_load_snps(ctx, P.m, P.XR, P.n)
+        dev = torch.full((2, P.t, P.m), float("nan"), dtype=torch.float32, device="cuda:0")
+        gw.gwas_solve(ctx, P.Y, 0, P.m, dev)
+        pinned = torch.full((2, P.t, P.m), float("nan"), dtype=torch.float32).pin_memory()
+        gw.gwas_solve(ctx, P.Y, 0, P.m, pinned)
+        pageable = np.full((2, P.t, P.m), np.nan, dtype=np.float32)
+        gw.gwas_solve(ctx, P.Y, 0, P.m, pageable)
+    finally:
+        gw.gwas_destroy(ctx)
+    ref = dev.cpu().numpy()
+    np.testing.assert_array_equal(pinned.numpy(), ref)
+    np.testing.assert_array_equal(pageable, ref)
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    check_last(ref, b, se)
