@@ -32,6 +32,15 @@ def small():
     return make_problem(96, 40, 6, pm1=3, seed=7)
 
 
+@pytest.fixture(scope="module")
+def wide():
+    # p = 20, the top of the paper's range (Section 3)
+    return make_problem(96, 24, 4, pm1=19, seed=8)
+
+
+both_p = pytest.mark.parametrize("case", ["small", "wide"])
+
+
 # ---------------------------------------------------------------- rational
 def _frac_solve(A, B):
     """Gauss-Jordan elimination over the rationals: A^-1 B."""
@@ -89,8 +98,9 @@ def test_rational_definition():
 
 
 # ---------------------------------------------------------------- two routes
-def test_eig_matches_direct(small):
-    P = small
+@both_p
+def test_eig_matches_direct(case, request):
+    P = request.getfixturevalue(case)
     bd, sd = direct_gls(P.phi, P.XL, P.XR, P.Y, P.h2)
     be, se = eig_gls(P.phi, P.XL, P.XR, P.Y, P.h2)
     assert _rel(be, bd) < 1e-10
@@ -117,9 +127,10 @@ def _ols(XL, xr, y):
     return b, np.sqrt(s2 * (Rinv[p - 1] @ Rinv[p - 1]))
 
 
+@both_p
 @pytest.mark.parametrize("route", ["direct", "eig"])
-def test_ols_at_h2_zero(small, route):
-    P = small
+def test_ols_at_h2_zero(case, route, request):
+    P = request.getfixturevalue(case)
     h2 = np.zeros(P.t)
     f = direct_gls if route == "direct" else eig_gls
     b, se = f(P.phi, P.XL, P.XR, P.Y, h2)
@@ -141,8 +152,9 @@ def test_ols_at_identity_kinship(small):
 
 
 # ---------------------------------------------------------------- planted coefficients
-def test_planted_coefficients(small):
-    P = small
+@both_p
+def test_planted_coefficients(case, request):
+    P = request.getfixturevalue(case)
     rng = np.random.default_rng(11)
     i = 5
     beta = rng.standard_normal(P.p)
@@ -155,8 +167,9 @@ def test_planted_coefficients(small):
 
 
 # ---------------------------------------------------------------- optimality certificate
-def test_normal_equation_residual(small):
-    P = small
+@both_p
+def test_normal_equation_residual(case, request):
+    P = request.getfixturevalue(case)
     b, _ = eig_gls(P.phi, P.XL, P.XR, P.Y, P.h2)
     for j in range(P.t):
         M = P.h2[j] * P.phi + (1 - P.h2[j]) * np.eye(P.n)
