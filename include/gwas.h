@@ -138,7 +138,10 @@ GWAS_API int gwas_load_snps(gwas_ctx* ctx, int64_t m, const int8_t* XR);
  * Returns GWAS_ERR_SINGULAR_PAIRS (a warning) when some pair's Schur
  * complement is <= 1e-10 times its diagonal entry; those outputs are NaN.
  * A host `out` receives the results trait block by trait block, each block's
- * copy overlapping the next block's computation when `out` is page-locked.
+ * copy overlapping the next block's computation when `out` is page-locked
+ * (the copies reach the link's full rate from memory on huge pages, e.g.
+ * cudaHostAlloc or madvise(MADV_HUGEPAGE) + cudaHostRegister; registered memory
+ * on small base pages measured about half of it).
  * The blocks start at 1/8 of opts.trait_block traits (about 8 GB of results when
  * trait_block is 0) and grow by 1.4x per block up to it, so that the first copy
  * starts early; a device `out` is computed in blocks of opts.trait_block.

@@ -1,6 +1,7 @@
 // Fused contraction + Schur solve kernel (fused.cu).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cstdint>
 
@@ -134,8 +135,11 @@ int fused_pair_layout(int q);
 int launch_fused(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2);
 // Single-trait kernel (gemv.cu): the same solve for a.ntrait == 1, streaming the SNPs'
-// operands once through a TMA ring (HBM-bound); for the one-CTA operand layout.
+// operands once through a TMA ring (HBM-bound); for the one-CTA operand layout, 0 <= q <= 19.
 bool gemv1_supported(int q, int Kpad);
+// 8 <= q <= 19 (gemv_wide.cu), with the tensor maps launch_gemv1 builds.
+int launch_gemv1_wide(gwas_ctx* c, int q, const FusedArgs& a, const CUtensorMap& mg, const CUtensorMap& ma,
+                      const CUtensorMap& m1, const CUtensorMap& m2);
 int launch_gemv1(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2);
 // Serving mode: processes a.units (a.cst indexed by trait-tile slot) with per-request outputs.

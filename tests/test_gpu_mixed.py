@@ -139,8 +139,7 @@ def test_general_p_full_b(gw, pm1):
 
 
 # One trait: the single-trait (GEMV-shaped, HBM-bound) kernel instead of the fused one.
-# (p - 1 > 7 has no single-trait kernel: the fused kernel solves the one-trait tile)
-@pytest.mark.parametrize("pm1", [0, 3, 7, 12])
+@pytest.mark.parametrize("pm1", [0, 3, 7, 12, 19])
 def test_single_trait(gw, pm1):
     P = make_problem(300, 1500, 1, pm1=pm1, seed=83 + pm1)
     b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
