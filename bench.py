@@ -63,6 +63,15 @@ def fused_traffic(workload):
     return FUSED_TRAFFIC["read"] + FUSED_TRAFFIC["write"]
 
 
+def algorithmic_flops(n, p, pairs, form="gemm"):
+    """Flops of the GLS grid.  "paper": (5 + 2(p-1)) n per (SNP, trait) pair, the count of
+    the paper's tile cost (Section 4, Eq. (tb)): b_B, S_BL and S_BR = sum_k e_k x_k^2 with the
+    squares formed per pair.  "gemm": 2(p+1) n per pair, the same contractions in GEMM form
+    with the squares precomputed per SNP (num, p-1 values of z and s)."""
+    per_pair = (5 + 2 * (p - 1)) * n if form == "paper" else 2 * (p + 1) * n
+    return float(per_pair) * pairs
+
+
 def pinned_host_array(shape, dtype, torch):
     """A page-locked host array of exactly this size: anonymous memory advised to use huge
     pages, registered with the driver.  (torch's page-locked allocator rounds sizes up to a
@@ -379,7 +388,7 @@ def main():
     # ---------------------------------------------------------------- roofline of the fused kernel
     pk, pk_src = peaks()
     fused_ms = ktimes["fused"][0] / ktimes["fused"][1]
-    useful = 2.0 * (PM1 + 2) * n * pairs                     # 2 (p+1) n flops per pair
+    useful = algorithmic_flops(n, PM1 + 1, pairs)            # 2 (p+1) n flops per pair
     kpad = (n + 63) // 64 * 64
     tiles = ((m + 127) // 128) * ((t + 31) // 32)
     issued = 2.0 * 128 * 512 * kpad * tiles                  # MMA columns per tile per K: 512
