@@ -30,7 +30,14 @@ struct MixedState {
   float *sA = nullptr, *acoef = nullptr;
   float* Xc = nullptr;     // FP32 scratch of the rotation, kept while slabs are reloaded
   int64_t xc_rows = 0;
+  double* rk = nullptr;    // [n] ||P_c z_k||^2: the share of eigenvector k outside span(X_L)
 };
+
+// Eigen-directions k with ||P_c z_k||^2 at or below this carry no energy of any centred SNP
+// (x'_c,k = (P_c z_k)^T x): their weights e_k are left out of the C2 operand and of its
+// scale.  Typical case: a standardised kinship has the intercept as an eigenvector with a
+// tiny eigenvalue, whose weight 1/(h^2 lambda + 1 - h^2) dominates as h^2 -> 1.
+constexpr double RK_NULL = 1e-16;
 
 namespace {
 
@@ -41,7 +48,8 @@ inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 // (P_c Z)^T x = Z^T P_c x); row n + a holds the map x -> a_i[a] = ((X_L^T X_L)^-1 X_L^T x)[a].
 template <int Q>
 __global__ void rot_b_kernel(const double* __restrict__ Zc, const double* __restrict__ XL,
-                             const double* __restrict__ XtXinv, int n, double* __restrict__ out) {
+                             const double* __restrict__ XtXinv, int n, double* __restrict__ out,
+                             double* __restrict__ rk) {
   constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1;
   const int k = blockIdx.x;
   __shared__ double red[Q1][8];
@@ -69,10 +77,22 @@ __global__ void rot_b_kernel(const double* __restrict__ Zc, const double* __rest
       coef[threadIdx.x] = cf;
     }
     __syncthreads();
+    double r2 = 0;
     for (int l = threadIdx.x; l < n; l += blockDim.x) {
       double v = z[l];
       for (int a = 0; a < PM1; ++a) v -= XL[(size_t)a * n + l] * coef[a];
       out[(size_t)k * n + l] = v;
+      r2 += v * v;
+    }
+    // ||P_c z_k||^2
+    __shared__ double rr[8];
+    for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    if (lane == 0) rr[warp] = r2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = 0;
+      for (int w = 0; w < (int)blockDim.x / 32; ++w) v += rr[w];
+      rk[k] = v;
     }
   } else {
     const int a = k - n;
@@ -172,7 +192,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
                                                          const double* __restrict__ XLt, int n, int Kpad,
                                                          double* __restrict__ Wt, __nv_bfloat16* __restrict__ B2,
                                                          float* __restrict__ cst, const int* __restrict__ slot,
-                                                         int pair) {
+                                                         int pair, const double* __restrict__ rk) {
   constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = mixed_tt(Q);
   constexpr int NTRI = PM1 * (PM1 + 1) / 2;
   const int j = blockIdx.x;
@@ -188,7 +208,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const double e = 1.0 / (h * lam[k] + (1.0 - h));
     e_row[k] = e;
-    emax = fmax(emax, e);
+    if (rk[k] > RK_NULL) emax = fmax(emax, e);  // the C2 scale: directions SNPs can reach
   }
   for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
   if (lane == 0) red[warp] = emax;
@@ -280,7 +300,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
         for (int a = 0; a < PM1; ++a) t += xl[a] * sh_Lit[a * PM1 + c];
         v[c] = e * t;
       }
-      const double t = e * inv_se;
+      const double t = rk[k] > RK_NULL ? e * inv_se : 0.0;
       const double d0 = rint(t);
       const double r1 = (t - d0) * 256.0;
       const double d1 = rint(r1);
@@ -419,6 +439,8 @@ static void mixed_destroy_setup(gwas_ctx* c) {
   ctx_free(c, s->Brot); ctx_free(c, s->Bzt); ctx_free(c, s->Bz);
   ctx_free(c, s->sBrot); ctx_free(c, s->sBzt); ctx_free(c, s->sBz);
   ctx_free(c, s->XtXinv);
+  ctx_free(c, s->rk);
+  s->rk = nullptr;
 }
 
 // One-time preparation of the B operands of the three rotations.
@@ -442,7 +464,8 @@ static int mixed_setup(gwas_ctx* c) {
       (rc = ctx_alloc(c, 2ull * 4 * plane_rows_z * s->Kpad, (void**)&s->Bz)) ||
       (rc = ctx_alloc(c, sizeof(double) * plane_rows_rot, (void**)&s->sBrot)) ||
       (rc = ctx_alloc(c, sizeof(double) * plane_rows_z, (void**)&s->sBzt)) ||
-      (rc = ctx_alloc(c, sizeof(double) * plane_rows_z, (void**)&s->sBz))) {
+      (rc = ctx_alloc(c, sizeof(double) * plane_rows_z, (void**)&s->sBz)) ||
+      (rc = ctx_alloc(c, sizeof(double) * n, (void**)&s->rk))) {
     ctx_free(c, rot);
     ctx_free(c, zr);
     mixed_destroy_setup(c);
@@ -451,7 +474,7 @@ static int mixed_setup(gwas_ctx* c) {
   if (PM1 > 0)
     cudaMemcpyAsync(s->XtXinv, c->h_XtXinv.data(), sizeof(double) * PM1 * PM1, cudaMemcpyHostToDevice, c->stream);
   { ProfScope ps(c, "setup_rotation_operands");
-  Q_DISPATCH_ALL(PM1, rot_b_kernel<Q><<<n + PM1, 256, 0, c->stream>>>(c->Z, c->XL, s->XtXinv, n, rot));
+  Q_DISPATCH_ALL(PM1, rot_b_kernel<Q><<<n + PM1, 256, 0, c->stream>>>(c->Z, c->XL, s->XtXinv, n, rot, s->rk));
   c->launches++;
   dim3 tb(32, 8), tg((n + 31) / 32, (n + 31) / 32);
   transpose_kernel<<<tg, tb, 0, c->stream>>>(c->Z, n, zr);
@@ -616,7 +639,7 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h
     // per-trait algebra and the C2 operand
     ProfScope ps(c, "prep_traits");
     Q_DISPATCH_ALL(q, prep_mixed_kernel<Q><<<tb, 256, 0, c->stream>>>(Yt, Kpad, h2, c->lam, c->XLt, n, Kpad, Wt, B2, cst,
-                                                                  slot, pair));
+                                                                  slot, pair, s->rk));
     c->launches++;
     // back-rotation [w | v] = Z [e.r' | (e.X'_L) L^-T]
     launch_slice_rows(c, Wt, Kpad, tb * p, n, rowsW, Kpad, 4, s->bits, Wsl, sW);

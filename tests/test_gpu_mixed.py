@@ -210,3 +210,20 @@ def test_host_output_in_growing_blocks(gw):
     np.testing.assert_array_equal(pageable, ref)
     b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
     check_last(ref, b, se)
+
+
+def test_extreme_heritabilities(gw):
+    # h^2 over the whole range of the model, both ends included: M_j = I (ordinary least
+    # squares) at 0 and M_j = Phi at 1; near 1 the weights e_j = 1/(h^2 lambda + 1 - h^2)
+    # spread over three orders of magnitude
+    P = make_problem(300, 400, 8, seed=2026)
+    P.h2[:] = [0.0, 1e-3, 0.5, 0.9, 0.95, 0.99, 0.999, 1.0]
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    out, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE)
+    assert rc == gw.GWAS_OK
+    beta, s = out[0].T.astype(np.float64), out[1].T.astype(np.float64)
+    errs = [last_coef_err(beta[:, j:j + 1], s[:, j:j + 1], b[:, j:j + 1], se[:, j:j + 1]) for j in range(P.t)]
+    serrs = [se_err(s[:, j:j + 1], se[:, j:j + 1]) for j in range(P.t)]
+    assert max(errs) <= TOL and max(serrs) <= TOL, (errs, serrs)
+    full64, rc, _ = solve(gw, P, gw.GWAS_OUT_FULL_B, precision=gw.GWAS_FP64)
+    assert full_b_err(full64.transpose(1, 0, 2), b, se) <= 1e-10
