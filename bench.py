@@ -370,8 +370,11 @@ def main():
     launches = 0
     ktimes = {}
     ev0.record(stream)
+    step_ev = []
     for _ in range(args.steps):
         rc, kt, nl = step(g, opts, n, m, t, inp_d, out)
+        step_ev.append(torch.cuda.Event(enable_timing=True))
+        step_ev[-1].record(stream)
         launches += nl
         for k, (ms, cnt) in kt.items():
             a = ktimes.setdefault(k, [0.0, 0])
@@ -383,6 +386,8 @@ def main():
     last_sample = out[:, :128, :8192].cpu().numpy()
     from paper_1210_7683_gb300.sharding import max_over_ranks, weak_scaling_rate
     ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+    marks = [ev0] + step_ev
+    per_step = [marks[i].elapsed_time(marks[i + 1]) for i in range(len(step_ev))]
     value = weak_scaling_rate(pairs, world, ms_step)
 
     # ---------------------------------------------------------------- roofline of the fused kernel
@@ -404,6 +409,23 @@ def main():
     solve_ms = sum(v[0] for k, v in ktimes.items() if k in (
         "xgemm_rotate_traits", "prep_traits", "xgemm_back_rotate", "pack_trait_columns", "fused")) / args.steps
     breakdown = {k: round(v[0] / args.steps, 3) for k, v in ktimes.items()}
+    # the genotype rotation X'_R = (P_c Z)^T X_R (Algorithm 5's preloop gemm) as an exact sliced
+    # GEMM: one bf16 plane of genotypes against 4 slices of the rotation, 4 slice products
+    rot = None
+    if "xgemm_rotate_snps" in ktimes:
+        rot_ms = ktimes["xgemm_rotate_snps"][0] / ktimes["xgemm_rotate_snps"][1]
+        mpad, ldx = (m + 127) // 128 * 128, (n + PM1 + 63) // 64 * 64
+        issued_r = 2.0 * mpad * ldx * kpad * 4
+        useful_r = 2.0 * n * n * m
+        bytes_r = 2.0 * mpad * kpad + 4 * 2.0 * ldx * kpad + 4.0 * m * ldx   # G in, slices in, FP32 out
+        rot = {"kernel": "xgemm_kernel (genotype rotation)", "launch_ms": rot_ms,
+               "issued_tflops": issued_r / (rot_ms / 1e3) / 1e12,
+               "issued_frac": issued_r / (rot_ms / 1e3) / 1e12 / peak,
+               "useful_tflops": useful_r / (rot_ms / 1e3) / 1e12,
+               "dram_gbs": bytes_r / (rot_ms / 1e3) / 1e9,
+               "dram_frac": bytes_r / (rot_ms / 1e3) / 1e9 / pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]),
+               "note": "issued: 4 bf16 slice products of 2 mpad ldx Kpad flops; useful: 2 n^2 m; bytes: genotype "
+                       "plane + rotation slices + FP32 output (algorithmic, not measured)"}
 
     result = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -411,7 +433,8 @@ def main():
               "config": {"workload": f"GLS grid n={n} p=4 m={m} t={t}, mixed precision, beta+SE fp32 out",
                          "n": n, "p": 4, "m": m, "t": t, "parallelism": f"snp-shard x{world}",
                          "l2": "inputs larger than L2 (1 GB genotypes, 8 GB resident operand slices per step)"},
-              "roofline": roofline, "gpu_launches": launches, "clocks": clk,
+              "step_ms": {"median": statistics.median(per_step), "min": min(per_step), "max": max(per_step)},
+              "roofline": roofline, "rotation_roofline": rot, "gpu_launches": launches, "clocks": clk,
               "kernel_ms_per_step": breakdown,
               "solve_only": {"value": pairs / (solve_ms / 1e3), "unit": "pairs/s",
                              "note": "device time of gwas_solve kernels (Y rotation, per-trait prep, fused)"}}
