@@ -86,6 +86,8 @@ typedef struct gwas_opts {
   int profile;        /* nonzero: time every kernel launch with CUDA events (see gwas_kernel_time) */
   size_t hbm_budget;  /* bytes the context may allocate on the device; 0 = no limit */
   void* stream;       /* cudaStream_t the context runs on; NULL = the context creates one */
+  const char* tune_cache; /* JSON file of autotuned launch shapes (gwas_autotune); NULL = none.
+                             gwas_setup applies the entry for its (n, p, mode, t) if present */
 } gwas_opts;
 
 /* Fill *opts with the defaults: GWAS_MIXED, GWAS_OUT_LAST_SE, trait_block 0,
@@ -231,6 +233,29 @@ GWAS_API int64_t gwas_singular_count(const gwas_ctx* ctx);
 
 /* Number of kernels this context launched since it was created. */
 GWAS_API int64_t gwas_kernel_launches(const gwas_ctx* ctx);
+
+/*
+ * gwas_autotune -- choose the mixed path's fused-kernel launch shape for this context by
+ * timing the candidates on a sample of the grid (the loop tiles of the paper are tuned
+ * empirically on the target machine, Section 5).
+ *
+ *   Y         traits as for gwas_solve; the first t_sample of them are used
+ *   t_sample  traits of the sample (<= t; <= 0: min(t, 1024))
+ *   m_sample  SNPs of the sample, from SNP 0 (<= m; <= 0: min(m, 2^17))
+ *   best_ms   out (may be NULL): device time of one solve of the sample with the chosen shape
+ *
+ * Candidates: the one-CTA shape for every p; for p = 4 also the CTA pair and the 1x2, 2x1
+ * and 2x2 multicast clusters; each with 8, 16 or 32 SNP tiles per traversal group.  The
+ * fastest is kept unless the default shape is within 2 % of it.  The context uses the choice
+ * from then on, and it is written to opts.tune_cache when that was given.  Results do not
+ * depend on the shape beyond rounding.  Mixed precision only (GWAS_ERR_UNSUPPORTED
+ * otherwise); GWAS_ERR_STATE before gwas_load_snps or while the serving loop runs.
+ */
+GWAS_API int gwas_autotune(gwas_ctx* ctx, const double* Y, int t_sample, int64_t m_sample, double* best_ms);
+
+/* The context's launch shape: shape[0..4] = cluster CTAs along SNPs, along traits,
+ * epilogue warps, CTA-pair mode (0/1), SNP tiles per traversal group. */
+GWAS_API int gwas_tune_shape(const gwas_ctx* ctx, int* shape);
 
 /* Accumulated device time (ms, from CUDA events recorded on the context's stream
  * around each launch) and launch count of one kernel family since the last

@@ -45,7 +45,8 @@ class GwasError(RuntimeError):
 
 class gwas_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("output", C.c_int), ("trait_block", C.c_int), ("device", C.c_int),
-                ("profile", C.c_int), ("hbm_budget", C.c_size_t), ("stream", C.c_void_p)]
+                ("profile", C.c_int), ("hbm_budget", C.c_size_t), ("stream", C.c_void_p),
+                ("tune_cache", C.c_char_p)]
 
 
 # void (*)(void* user, int j0, int nb, const void* host_block)
@@ -66,6 +67,10 @@ def _load():
     lib.gwas_load_snps.restype = ci
     lib.gwas_solve.argtypes = [vp, vp, i64, i64, vp]
     lib.gwas_solve.restype = ci
+    lib.gwas_autotune.argtypes = [vp, vp, ci, i64, C.POINTER(C.c_double)]
+    lib.gwas_autotune.restype = ci
+    lib.gwas_tune_shape.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.gwas_tune_shape.restype = ci
     lib.gwas_set_h2.argtypes = [vp, ci, vp]
     lib.gwas_set_h2.restype = ci
     lib.gwas_singular_count.argtypes = [vp]
@@ -151,8 +156,26 @@ def gwas_default_opts(**kw) -> gwas_opts:
     o = gwas_opts()
     lib.gwas_default_opts(C.byref(o))
     for k, v in kw.items():
+        if k == "tune_cache" and isinstance(v, str):
+            v = v.encode()
         setattr(o, k, v)
     return o
+
+
+def gwas_autotune(ctx, Y, t_sample=0, m_sample=0) -> float:
+    """Choose the fused-kernel launch shape by timing candidates on a sample (see
+    include/gwas.h); returns the sample's solve time in ms with the chosen shape."""
+    best = C.c_double()
+    _check(lib.gwas_autotune(ctx, _addr(Y, np.float64, None, "Y"), int(t_sample), int(m_sample), C.byref(best)), ctx)
+    return best.value
+
+
+def gwas_tune_shape(ctx) -> dict:
+    """The context's launch shape: cluster CTAs along SNPs and traits, epilogue warps,
+    CTA-pair mode, SNP tiles per traversal group."""
+    v = (C.c_int * 5)()
+    _check(lib.gwas_tune_shape(ctx, v), ctx)
+    return dict(zip(("cs", "ct", "epw", "pair", "group"), list(v)))
 
 
 def gwas_setup(n, pm1, phi, XL, t, h2, opts: gwas_opts | None = None):

@@ -17,19 +17,6 @@ static thread_local std::string g_setup_err;
 
 namespace {
 
-// Restores the caller's current device when a call returns.
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
 // One cuSOLVER handle per device for the whole process, created on first use: creating a
 // handle and its first eigensolver call cost several milliseconds that every gwas_setup
 // would otherwise pay.  The mutex serialises contexts of different host threads that run
@@ -254,6 +241,10 @@ extern "C" int gwas_setup(gwas_ctx** out, int n, int pm1, const double* phi, con
   c->n = n; c->pm1 = pm1; c->p = pm1 + 1; c->t = t; c->device = o.device;
   c->precision = o.precision; c->output = o.output; c->trait_block = o.trait_block; c->budget = o.hbm_budget;
   c->profile = o.profile != 0;
+  if (o.tune_cache) {
+    c->tune_cache = o.tune_cache;
+    tune_apply_cache(c);
+  }
   int rc = GWAS_OK;
   auto fail = [&](int code) { g_setup_err = c->err; destroy_impl(c); return code; };
   if (o.stream) {
@@ -768,7 +759,7 @@ extern "C" int gwas_solve_ooc(gwas_ctx* c, int64_t m, const int8_t* XR, int64_t 
   // ---- the per-trait operands of every trait block, prepared once
   const int TT = mixed_tt(q), tm = fused_trait_tile_multiple();
   const int tpb = ((tb + TT - 1) / TT + tm - 1) / tm * tm;  // trait tiles allocated per block
-  const int pair = mixed ? fused_pair_layout(q) : 0;
+  const int pair = mixed ? fused_pair_layout(c, q) : 0;
   int64_t kp = 0;
   if (mixed) {
     if ((rc = mixed_ws_alloc(c, tb, &ws))) return fail(rc);

@@ -9,12 +9,13 @@ struct Shape {
   int cs, ct, epw, pair;
 };
 
-// Kernel shape "CSxCTxEPW[xPAIR]" from GWAS_FUSED_SHAPE (q = 3 only; every other q runs the
-// default one-CTA shape).
-Shape shape_from_env(int q) {
+// The context's kernel shape (autotuned or default).  Shapes other than 1x1x16 exist for q = 3
+// only; every other q runs 1x1x16.  GWAS_FUSED_SHAPE="CSxCTxEPW[xPAIR]" overrides it (q = 3).
+Shape shape_of(const gwas_ctx* c, int q) {
   Shape sh{1, 1, 16, 0};
-  const char* e = getenv("GWAS_FUSED_SHAPE");
-  if (e && q == 3) {
+  if (q != 3) return sh;
+  if (c) sh = {c->tune.cs, c->tune.ct, c->tune.epw, c->tune.pair};
+  if (const char* e = getenv("GWAS_FUSED_SHAPE")) {
     int cs = 0, ct = 0, epw = 0, pr = 0;
     const int k = sscanf(e, "%dx%dx%dx%d", &cs, &ct, &epw, &pr);
     if (k >= 3) sh = {cs, ct, epw, k == 4 ? pr : 0};
@@ -26,7 +27,14 @@ Shape shape_from_env(int q) {
 
 int fused_trait_tile_multiple() { return 4; }
 
-int fused_pair_layout(int q) { return shape_from_env(q).pair; }
+int fused_pair_layout(const gwas_ctx* c, int q) { return shape_of(c, q).pair; }
+
+bool fused_shape_supported(int q, int cs, int ct, int epw, int pair) {
+  if (cs == 1 && ct == 1 && epw == 16 && !pair) return true;
+  if (q != 3 || epw != 16) return false;
+  if (pair) return cs == 2 && ct == 1;
+  return (cs == 1 && ct == 2) || (cs == 2 && ct == 1) || (cs == 2 && ct == 2);
+}
 
 int launch_fused(gwas_ctx* c, int q, const FusedArgs& args, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2) {
@@ -34,7 +42,7 @@ int launch_fused(gwas_ctx* c, int q, const FusedArgs& args, const __nv_bfloat16*
   if (a.n_stiles == 0 || a.n_ttiles == 0) return GWAS_OK;
   if (q < 0 || q > MIXED_MAX_Q) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: p-1 outside [0, 19]");
   if (q > 7) return launch_fused_wide(c, q, a, G, A2, B1, B2, false, (a.n_ttiles + 3) / 4 * 4);
-  const Shape sh = shape_from_env(q);
+  const Shape sh = shape_of(c, q);
   const int ttiles_pad = (a.n_ttiles + 3) / 4 * 4;   // trait operands are allocated for a multiple of 4 tiles
   CUtensorMap mg, ma, m1, m2;
   bool maps_ok;

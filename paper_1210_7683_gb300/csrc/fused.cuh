@@ -127,8 +127,10 @@ struct FusedArgs {
 // Trait operands (B1, B2) must be allocated (and zeroed) for a multiple of this many trait tiles,
 // with c1_rows(q) B1 rows and c2_alloc(q) B2 rows per trait tile.
 int fused_trait_tile_multiple();
-// 1 when the selected kernel shape is the CTA-pair one, whose trait operands use the pair layout.
-int fused_pair_layout(int q);
+// 1 when the context's kernel shape is the CTA-pair one, whose trait operands use the pair layout.
+int fused_pair_layout(const gwas_ctx* c, int q);
+// Whether a launch shape (CS x CT cluster, EPW epilogue warps, CTA pair) is built for q.
+bool fused_shape_supported(int q, int cs, int ct, int epw, int pair);
 
 // q = p - 1 (0..19) selects the kernel's geometry; shapes other than the default one-CTA
 // shape are built for q = 3 only.

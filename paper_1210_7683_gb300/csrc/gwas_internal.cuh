@@ -61,6 +61,13 @@ struct gwas_ctx {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_compute[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
 
+  // fused-kernel launch shape of the mixed path (from the autotuner or its cache; defaults otherwise):
+  // CS x CT CTA clusters, EPW epilogue warps, CTA-pair mode, SNP tiles per traversal group
+  struct FusedTune {
+    int cs = 1, ct = 1, epw = 16, pair = 0, group = 16;
+  } tune;
+  std::string tune_cache;  // JSON cache of autotuned shapes ("" = none)
+
   // profiling: per-kernel device time from CUDA events on `stream`
   bool profile = false;
   std::vector<ProfPending> pending;
@@ -79,6 +86,22 @@ struct ProfScope {
 void prof_flush(gwas_ctx* c);
 
 // ---------------------------------------------------------------- helpers (api.cu)
+// Restores the caller's current device when a call returns.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Applies the launch shape that c->tune_cache holds for this context's (n, p, mode, t), if any.
+void tune_apply_cache(gwas_ctx* c);
+
 int ctx_fail(gwas_ctx* c, int code, const std::string& msg);
 int ctx_alloc(gwas_ctx* c, size_t bytes, void** out);          // budget-checked cudaMalloc
 void ctx_free(gwas_ctx* c, void* p);

@@ -671,7 +671,7 @@ int mixed_prep_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb) 
                        fused_trait_tile_multiple();
   cudaMemsetAsync(w->B1, 0, 2ull * nt_alloc * c1_rows(q) * Kpad, c->stream);
   cudaMemsetAsync(w->B2, 0, 2ull * nt_alloc * c2_alloc(q) * Kpad, c->stream);
-  return mixed_prep_traits(c, w, dY, c->h2 + j0, tb, w->B1, w->B2, w->cst, nullptr, fused_pair_layout(q));
+  return mixed_prep_traits(c, w, dY, c->h2 + j0, tb, w->B1, w->B2, w->cst, nullptr, fused_pair_layout(c, q));
 }
 
 int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B2, const float* cst, int tb, int64_t i0,
@@ -690,7 +690,7 @@ int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B
     a.nsnp = i1 - a.row0;
     a.n_stiles = (int)((a.nsnp + 127) / 128);
     a.n_ttiles = nt_tiles;
-    a.group = 16;
+    a.group = std::max(1, c->tune.group);
     if (const char* e = getenv("GWAS_FUSED_GROUP")) a.group = std::max(1, atoi(e));
     a.ntrait = tb;
     a.Kpad = Kpad;
@@ -712,7 +712,7 @@ int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B
     a.status = c->d_status;
     a.singular = c->d_status + 1;
     // one trait: the contractions are matrix-vector products, bound by HBM (gemv.cu)
-    if (tb == 1 && gemv1_supported(q, Kpad) && !fused_pair_layout(q)) rc = launch_gemv1(c, q, a, s->G, s->A2, B1, B2);
+    if (tb == 1 && gemv1_supported(q, Kpad) && !fused_pair_layout(c, q)) rc = launch_gemv1(c, q, a, s->G, s->A2, B1, B2);
     else rc = launch_fused(c, q, a, s->G, s->A2, B1, B2);
   }
   return rc;
