@@ -45,14 +45,17 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # null traffic.
 FUSED_TRAFFIC = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "tc.cuh", "mixed.cu"],
                  "sha256": "662d2ef1286cc467085643a20660e2a6876c372ba2a74729ef4b2390d095e06a",
-                 "workload": (1000, 3, 1_000_000, 10_000), "read": 166.72e9, "write": 80.01e9}
+                 "workload": (1000, 3, 1_000_000, 10_000), "read": 166.72e9, "write": 80.01e9,
+                 "shape": {"cs": 1, "ct": 1, "epw": 16, "pair": 0, "group": 16}}
 
 
-def fused_traffic(workload):
+def fused_traffic(workload, shape=None):
     """DRAM bytes per fused_kernel launch from the committed capture, or None when the workload
-    differs from the captured one or the kernel's sources changed since."""
+    or the launch shape differs from the captured one, or the kernel's sources changed since."""
     import hashlib
     if tuple(workload) != FUSED_TRAFFIC["workload"]:
+        return None
+    if shape is not None and shape != FUSED_TRAFFIC["shape"]:
         return None
     h = hashlib.sha256()
     for f in FUSED_TRAFFIC["sources"]:
@@ -413,7 +416,7 @@ def main():
     issued = 2.0 * 128 * 512 * kpad * tiles                  # MMA columns per tile per K: 512
     peak = pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
     achieved = useful / (fused_ms / 1e3) / 1e12
-    traffic = fused_traffic((n, PM1, m, t))
+    traffic = fused_traffic((n, PM1, m, t), tune["shape"])
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "fused_kernel",
                 "peak_source": f"{pk_src} bf16 sustained (kernel runs ~{fused_ms:.0f} ms inside a long step)",

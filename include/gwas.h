@@ -224,6 +224,10 @@ GWAS_API int gwas_poll(gwas_ctx* ctx, uint64_t req_id, int* done);
 GWAS_API int gwas_wait(gwas_ctx* ctx, uint64_t req_id, double timeout_s);
 /* Host steady-clock times (seconds) of a request's submission, admission and completion. */
 GWAS_API int gwas_request_times(gwas_ctx* ctx, uint64_t req_id, double* t_submit, double* t_admit, double* t_done);
+/* Rounds the serving loop has run since it started, and how many of them were replays of
+ * the captured CUDA graph of a round (the work-list upload and the persistent kernel launch;
+ * the first round launches directly and is then captured). */
+GWAS_API int gwas_serve_stats(const gwas_ctx* ctx, int64_t* rounds, int64_t* graph_rounds);
 
 /* Replace the t heritabilities given at setup (same t). */
 GWAS_API int gwas_set_h2(gwas_ctx* ctx, int t, const double* h2);

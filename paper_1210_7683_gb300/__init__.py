@@ -71,6 +71,8 @@ def _load():
     lib.gwas_autotune.restype = ci
     lib.gwas_tune_shape.argtypes = [vp, C.POINTER(C.c_int)]
     lib.gwas_tune_shape.restype = ci
+    lib.gwas_serve_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+    lib.gwas_serve_stats.restype = ci
     lib.gwas_set_h2.argtypes = [vp, ci, vp]
     lib.gwas_set_h2.restype = ci
     lib.gwas_singular_count.argtypes = [vp]
@@ -168,6 +170,13 @@ def gwas_autotune(ctx, Y, t_sample=0, m_sample=0) -> float:
     best = C.c_double()
     _check(lib.gwas_autotune(ctx, _addr(Y, np.float64, None, "Y"), int(t_sample), int(m_sample), C.byref(best)), ctx)
     return best.value
+
+
+def gwas_serve_stats(ctx):
+    """(rounds, rounds replayed from the captured CUDA graph) of the serving loop."""
+    r, gr = C.c_int64(), C.c_int64()
+    _check(lib.gwas_serve_stats(ctx, C.byref(r), C.byref(gr)), ctx)
+    return r.value, gr.value
 
 
 def gwas_tune_shape(ctx) -> dict:

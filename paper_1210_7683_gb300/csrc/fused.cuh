@@ -120,7 +120,8 @@ struct FusedArgs {
   int max_ctas;       // 0 = one CTA per SM
   // serving mode: work units {first SNP row of the tile, trait-tile slot, request, request-local trait tile}
   const int4* units;
-  int nunits;
+  int nunits;             // units (an upper bound when nunits_dev is set)
+  const int* nunits_dev;  // NULL, or the units of the launch in device memory (captured graphs)
   const ServeDesc* reqs;
 };
 

@@ -154,7 +154,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   for (int k = 0; k < CT; ++k) maskA |= (uint16_t)(1u << (sr + CS * k));
 #pragma unroll
   for (int k = 0; k < CS; ++k) maskB |= (uint16_t)(1u << (CS * tr + k));
-  const int nsuper = SERVE ? a.nunits : ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
+  // serving: the round's work units (from device memory when the launch is a captured graph's)
+  const int nsuper = SERVE ? (a.nunits_dev ? min(*a.nunits_dev, a.nunits) : a.nunits)
+                           : ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
   const int nkb = a.Kpad / BK;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSL; ++s) {

@@ -83,9 +83,58 @@ struct ServeState {
   int failed = GWAS_OK;
   std::string fail_msg;
   int64_t rounds = 0;
+  // the round's upload of its work list and its persistent kernel launch, captured once as a
+  // CUDA graph (the launch reads the unit count from d_nunits) and replayed every round after
+  int* d_nunits = nullptr;
+  int* h_nunits = nullptr;    // pinned
+  cudaGraphExec_t round_graph = nullptr;
+  bool graph_failed = false;
+  int64_t graph_rounds = 0;
 };
 
 namespace {
+
+// The fused kernel's arguments for a serving round, but for the unit count.
+FusedArgs round_args(gwas_ctx* c, ServeState* S) {
+  FusedArgs a{};
+  a.Kpad = (int)((c->n + 63) / 64 * 64);
+  a.mpad = mixed_mpad(c);
+  a.dof = (float)(c->n - c->p);
+  a.sA = mixed_sA(c);
+  a.acoef = mixed_acoef(c);
+  a.cst = S->cst;
+  a.status = c->d_status;
+  a.singular = c->d_status + 1;
+  a.units = S->d_units;
+  a.reqs = S->d_desc;
+  return a;
+}
+
+// Captures a round as a CUDA graph: the upload of the work list and its count from the pinned
+// buffers, and the persistent kernel over at most round_units units.  Every pointer it holds
+// lives as long as the serving state.  On failure the rounds keep launching directly.
+void capture_round(gwas_ctx* c, ServeState* S) {
+  FusedArgs a = round_args(c, S);
+  a.nunits = S->round_units;
+  a.nunits_dev = S->d_nunits;
+  const bool prof = c->profile;
+  const int64_t launches = c->launches;
+  c->profile = false;  // no timing events inside the graph
+  cudaGraph_t g = nullptr;
+  int rc = GWAS_ERR_CUDA;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+    cudaMemcpyAsync(S->d_units, S->h_units, sizeof(int4) * S->round_units, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(S->d_nunits, S->h_nunits, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    rc = launch_fused_serve(c, c->pm1, a, mixed_G(c), mixed_A2(c), S->B1, S->B2, S->slots);
+    if (cudaStreamEndCapture(c->stream, &g) != cudaSuccess) rc = GWAS_ERR_CUDA;
+  }
+  c->profile = prof;
+  c->launches = launches;
+  if (rc == GWAS_OK && g && cudaGraphInstantiate(&S->round_graph, g, 0) != cudaSuccess) S->round_graph = nullptr;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  if (!S->round_graph) S->graph_failed = true;
+}
 
 // Unit u of a request in its traversal order: groups of GROUP SNP tiles x all trait tiles.
 void unit_coords(const Request& r, int64_t u, int& st, int& tt) {
@@ -237,20 +286,21 @@ void serve_loop(gwas_ctx* c) {
       }
     }
     if (nu > 0) {
-      cudaMemcpyAsync(S->d_units, S->h_units, sizeof(int4) * nu, cudaMemcpyHostToDevice, c->stream);
-      FusedArgs a{};
-      a.Kpad = (int)((n + 63) / 64 * 64);
-      a.mpad = mixed_mpad(c);
-      a.dof = (float)(n - c->p);
-      a.sA = mixed_sA(c);
-      a.acoef = mixed_acoef(c);
-      a.cst = S->cst;
-      a.status = c->d_status;
-      a.singular = c->d_status + 1;
-      a.units = S->d_units;
-      a.nunits = nu;
-      a.reqs = S->d_desc;
-      rc = launch_fused_serve(c, c->pm1, a, mixed_G(c), mixed_A2(c), S->B1, S->B2, S->slots);
+      *S->h_nunits = (int)nu;
+      if (S->round_graph) {
+        // the captured upload (the whole work-list buffer and the count) and persistent launch
+        if (cudaGraphLaunch(S->round_graph, c->stream) != cudaSuccess) {
+          cudaGetLastError();
+          rc = GWAS_ERR_CUDA;
+        }
+        ++S->graph_rounds;
+        c->launches++;
+      } else {
+        cudaMemcpyAsync(S->d_units, S->h_units, sizeof(int4) * nu, cudaMemcpyHostToDevice, c->stream);
+        FusedArgs a = round_args(c, S);
+        a.nunits = (int)nu;
+        rc = launch_fused_serve(c, c->pm1, a, mixed_G(c), mixed_A2(c), S->B1, S->B2, S->slots);
+      }
       cudaError_t e = cudaStreamSynchronize(c->stream);
       unsigned long long st0 = 0;
       if (rc == GWAS_OK && e == cudaSuccess) {
@@ -268,6 +318,8 @@ void serve_loop(gwas_ctx* c) {
       }
       ++S->rounds;
       prof_flush(c);
+      // after one direct round (which also set the kernel's attributes), capture the round
+      if (!S->round_graph && !S->graph_failed) capture_round(c, S);
     }
     // 4. completions
     {
@@ -322,8 +374,10 @@ int serve_init(gwas_ctx* c) {
   auto fail = [&](int code) {
     ctx_free(c, S->B1); ctx_free(c, S->B2); ctx_free(c, S->cst); ctx_free(c, S->d_desc); ctx_free(c, S->d_sing);
     ctx_free(c, S->d_units); ctx_free(c, S->d_Y); ctx_free(c, S->d_h2); ctx_free(c, S->d_slot);
+    ctx_free(c, S->d_nunits);
     if (S->ws) mixed_ws_free(c, S->ws);
     if (S->h_units) cudaFreeHost(S->h_units);
+    if (S->h_nunits) cudaFreeHost(S->h_nunits);
     if (S->h_Y) cudaFreeHost(S->h_Y);
     if (S->h_h2) cudaFreeHost(S->h_h2);
     if (S->h_slot) cudaFreeHost(S->h_slot);
@@ -336,6 +390,7 @@ int serve_init(gwas_ctx* c) {
       (rc = ctx_alloc(c, sizeof(ServeDesc) * S->max_reqs, (void**)&S->d_desc)) ||
       (rc = ctx_alloc(c, sizeof(unsigned long long) * S->max_reqs, (void**)&S->d_sing)) ||
       (rc = ctx_alloc(c, sizeof(int4) * S->round_units, (void**)&S->d_units)) ||
+      (rc = ctx_alloc(c, sizeof(int), (void**)&S->d_nunits)) ||
       (rc = ctx_alloc(c, sizeof(double) * S->max_prep * n, (void**)&S->d_Y)) ||
       (rc = ctx_alloc(c, sizeof(double) * S->max_prep, (void**)&S->d_h2)) ||
       (rc = ctx_alloc(c, sizeof(int) * S->max_prep / TT, (void**)&S->d_slot)) ||
@@ -344,7 +399,8 @@ int serve_init(gwas_ctx* c) {
   if (cudaHostAlloc((void**)&S->h_units, sizeof(int4) * S->round_units, cudaHostAllocDefault) != cudaSuccess ||
       cudaHostAlloc((void**)&S->h_Y, sizeof(double) * S->max_prep * n, cudaHostAllocDefault) != cudaSuccess ||
       cudaHostAlloc((void**)&S->h_h2, sizeof(double) * S->max_prep, cudaHostAllocDefault) != cudaSuccess ||
-      cudaHostAlloc((void**)&S->h_slot, sizeof(int) * S->max_prep / TT, cudaHostAllocDefault) != cudaSuccess) {
+      cudaHostAlloc((void**)&S->h_slot, sizeof(int) * S->max_prep / TT, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc((void**)&S->h_nunits, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx_fail(c, GWAS_ERR_OOM, "pinned host staging for serving"));
   }
@@ -373,8 +429,11 @@ void serve_shutdown(gwas_ctx* c) {
   cudaStreamSynchronize(c->stream);
   ctx_free(c, S->B1); ctx_free(c, S->B2); ctx_free(c, S->cst); ctx_free(c, S->d_desc); ctx_free(c, S->d_sing);
   ctx_free(c, S->d_units); ctx_free(c, S->d_Y); ctx_free(c, S->d_h2); ctx_free(c, S->d_slot);
+  ctx_free(c, S->d_nunits);
+  if (S->round_graph) cudaGraphExecDestroy(S->round_graph);
   if (S->ws) mixed_ws_free(c, S->ws);
   cudaFreeHost(S->h_units);
+  cudaFreeHost(S->h_nunits);
   cudaFreeHost(S->h_Y);
   cudaFreeHost(S->h_h2);
   cudaFreeHost(S->h_slot);
@@ -492,5 +551,13 @@ extern "C" int gwas_request_times(gwas_ctx* c, uint64_t id, double* t_submit, do
   if (t_submit) *t_submit = it->second.t_submit;
   if (t_admit) *t_admit = it->second.t_admit;
   if (t_done) *t_done = it->second.t_done;
+  return GWAS_OK;
+}
+
+extern "C" int gwas_serve_stats(const gwas_ctx* c, int64_t* rounds, int64_t* graph_rounds) {
+  if (!c) return GWAS_ERR_ARG;
+  const ServeState* S = c->serve;
+  if (rounds) *rounds = S ? S->rounds : 0;
+  if (graph_rounds) *graph_rounds = S ? S->graph_rounds : 0;
   return GWAS_OK;
 }

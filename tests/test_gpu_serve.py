@@ -1,5 +1,6 @@
 """Serving with continuous batching: every request's result is the same alone and in a
-mix (bitwise: the arithmetic of a pair does not depend on its round), the same as a
+mix (bitwise: the arithmetic of a pair does not depend on its round, nor on whether the
+round was launched directly or replayed from its captured CUDA graph), the same as a
 separate gwas_solve of the request, and within the parity bar of the oracle."""
 import numpy as np
 import pytest
@@ -57,8 +58,11 @@ def test_alone_equals_mix_equals_solve(gw):
             assert gw.gwas_wait(ctx, rid, 120.0) == gw.GWAS_OK
         mix = [o.cpu().numpy() for o in outs]
         ts = [gw.gwas_request_times(ctx, rid) for rid in ids]
+        rounds, graph_rounds = gw.gwas_serve_stats(ctx)
     finally:
         gw.gwas_destroy(ctx)
+    # the first round launches directly and is captured; the others replay the CUDA graph
+    assert rounds >= len(reqs) + 1 and graph_rounds == rounds - 1
     for a, b in zip(alone, mix):
         np.testing.assert_array_equal(a, b)
     assert all(t0 <= t1 <= t2 for t0, t1, t2 in ts)
