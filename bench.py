@@ -44,8 +44,8 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # the kernel's sources hash to the value the captures were taken on: a changed kernel reports
 # null traffic.
 FUSED_TRAFFIC = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "tc.cuh", "mixed.cu"],
-                 "sha256": "662d2ef1286cc467085643a20660e2a6876c372ba2a74729ef4b2390d095e06a",
-                 "workload": (1000, 3, 1_000_000, 10_000), "read": 166.72e9, "write": 80.01e9,
+                 "sha256": "09974a1ef8ef3577483200da915a89520f4fa06fb717dd3bb5ac110f2b9e8931",
+                 "workload": (1000, 3, 1_000_000, 10_000), "read": 149.31e9, "write": 80.01e9,
                  "shape": {"cs": 1, "ct": 1, "epw": 16, "pair": 0, "group": 16}}
 
 
@@ -430,12 +430,14 @@ def main():
     # GEMM: one bf16 plane of genotypes against 4 slices of the rotation, 4 slice products
     rot = None
     if "xgemm_rotate_snps" in ktimes:
-        rot_ms = ktimes["xgemm_rotate_snps"][0] / ktimes["xgemm_rotate_snps"][1]
+        # all launches of one step (the rotation runs in blocks of SNP rows)
+        rot_ms = ktimes["xgemm_rotate_snps"][0] / args.steps
         mpad, ldx = (m + 127) // 128 * 128, (n + PM1 + 63) // 64 * 64
         issued_r = 2.0 * mpad * ldx * kpad * 4
         useful_r = 2.0 * n * n * m
         bytes_r = 2.0 * mpad * kpad + 4 * 2.0 * ldx * kpad + 4.0 * m * ldx   # G in, slices in, FP32 out
-        rot = {"kernel": "xgemm_kernel (genotype rotation)", "launch_ms": rot_ms,
+        rot = {"kernel": "xgemm_kernel (genotype rotation)", "ms_per_step": rot_ms,
+               "launches_per_step": ktimes["xgemm_rotate_snps"][1] // args.steps,
                "issued_tflops": issued_r / (rot_ms / 1e3) / 1e12,
                "issued_frac": issued_r / (rot_ms / 1e3) / 1e12 / peak,
                "useful_tflops": useful_r / (rot_ms / 1e3) / 1e12,
