@@ -378,14 +378,17 @@ def main():
     opts = g.gwas_default_opts(precision=g.GWAS_MIXED, output=g.GWAS_OUT_LAST_SE, device=local, profile=1,
                                stream=stream.cuda_stream, tune_cache=tune_path)
 
+    torch.cuda.nvtx.range_push("warmup")
     for _ in range(args.warmup):
         step(g, opts, n, m, t, inp_d, out)
+    torch.cuda.nvtx.range_pop()
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches = 0
     ktimes = {}
+    torch.cuda.nvtx.range_push("timed")  # ncu --nvtx --nvtx-include "timed/" selects these launches
     ev0.record(stream)
     step_ev = []
     for _ in range(args.steps):
@@ -398,6 +401,7 @@ def main():
             a[0] += ms
             a[1] += cnt
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier()
     clk = clocks.stop()
     last_sample = out[:, :128, :8192].cpu().numpy()
