@@ -113,9 +113,8 @@ def test_sampled_pairs_at_full_mixed_workload(gw):
     check_last(got, b, se)
 
 
-# Any number of covariates: q = p - 1 from 0 to 7.  Tiles hold 32 traits for q <= 3 and 16
-# above; the trait and SNP counts leave ragged last tiles.
-# p - 1 up to 19 (Section 3: 2 <= p <= 20): trait tiles of 32 (p - 1 <= 3), 16 (<= 10) and 8
+# p - 1 up to 19 (Section 3: 2 <= p <= 20): trait tiles of 32 (p - 1 <= 3), 16 (<= 10) and 8;
+# the trait and SNP counts leave ragged last tiles.
 @pytest.mark.parametrize("pm1,n,m,t", [(0, 200, 300, 40), (1, 256, 257, 33), (2, 300, 200, 17), (4, 256, 300, 20),
                                        (5, 130, 129, 45), (6, 200, 256, 19), (7, 97, 300, 35), (8, 200, 300, 37),
                                        (10, 160, 257, 33), (11, 200, 300, 21), (13, 130, 129, 17), (16, 256, 200, 9),
