@@ -115,15 +115,35 @@ __global__ void transpose_kernel(const double* __restrict__ in, int n, double* _
     if (ox < n && oy0 + dy < n) out[(size_t)(oy0 + dy) * n + ox] = t[threadIdx.x][dy];
 }
 
-// int8 genotypes [m][n] -> bf16 [mpad][Kpad] (zero padded)
+// int8 genotypes [m][n] -> bf16 [mpad][Kpad] (zero padded).  One thread per 8 consecutive
+// values of a row: an 8-byte load when the row's bytes allow it, one 16-byte store.
 __global__ void geno_bf16_kernel(const int8_t* __restrict__ X, int64_t m, int n, int64_t mpad, int Kpad,
                                  __nv_bfloat16* __restrict__ G) {
-  const int64_t total = mpad * (int64_t)Kpad;
+  const int per_row = Kpad / 8;
+  const int64_t total = mpad * (int64_t)per_row;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / Kpad;
-    const int k = (int)(e % Kpad);
-    const float v = (i < m && k < n) ? (float)X[i * n + k] : 0.f;
-    G[e] = __float2bfloat16(v);
+    const int64_t i = e / per_row;
+    const int k0 = (int)(e - i * per_row) * 8;
+    float v[8];
+    const int64_t src = i * (int64_t)n + k0;
+    if (i < m && k0 + 8 <= n && (src & 7) == 0) {
+      const uint2 w = *reinterpret_cast<const uint2*>(X + src);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        v[j] = (float)(int8_t)((w.x >> (8 * j)) & 0xffu);
+        v[4 + j] = (float)(int8_t)((w.y >> (8 * j)) & 0xffu);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = (i < m && k0 + j < n) ? (float)X[src + j] : 0.f;
+    }
+    uint32_t u[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      u[j] = *reinterpret_cast<const uint32_t*>(&b);
+    }
+    *reinterpret_cast<uint4*>(G + i * Kpad + k0) = make_uint4(u[0], u[1], u[2], u[3]);
   }
 }
 
@@ -511,7 +531,7 @@ int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m, bool reuse) {
     }
   }
   { ProfScope ps(c, "genotypes_bf16");
-  geno_bf16_kernel<<<4 * 152, 256, 0, c->stream>>>(dXR, m, n, s->mpad, s->Kpad, s->G);
+  geno_bf16_kernel<<<16 * 152, 256, 0, c->stream>>>(dXR, m, n, s->mpad, s->Kpad, s->G);
   c->launches++; }
   // rotate in chunks of SNPs to bound the FP32 scratch
   const int64_t chunk = std::min<int64_t>(s->mpad, 1 << 18);

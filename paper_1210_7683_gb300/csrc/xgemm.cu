@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(192, 1) xgemm_kernel(const __grid_constant__ C
   uint32_t* tslot = (uint32_t*)(done + 1);
   volatile int* abort = (volatile int*)(tslot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;
+  // column tiles along x: the CTAs of one row tile are scheduled together and share its A tile in L2
+  const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
   const int kb0 = g.kb0, nk = g.kb1 - g.kb0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -257,7 +258,8 @@ static int run_xgemm(gwas_ctx* c, const XgemmArgs& g, const __nv_bfloat16* A, co
   }
   // a last partial column tile reads past its plane (the next plane, or TMA zero fill
   // after the last one); those columns are >= g.cols and never stored
-  dim3 grid(g.rowsA_pad / BM, (g.rowsB_pad + Cfg::BN - 1) / Cfg::BN);
+  dim3 grid((g.rowsB_pad + Cfg::BN - 1) / Cfg::BN, g.rowsA_pad / BM);
+  if (grid.y > 65535) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "xgemm: more than 65535 row tiles");
   ProfScope ps(c, g.name ? g.name : "xgemm");
   xgemm_kernel<SA, SB, L><<<grid, 192, Cfg::SMEM, c->stream>>>(ma, mb, g);
   c->launches++;
