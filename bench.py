@@ -43,8 +43,8 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # single-pass ncu captures of dram__bytes_read.sum + dram__bytes_write.sum.  Valid only while
 # the kernel's sources hash to the value the captures were taken on: a changed kernel reports
 # null traffic.
-FUSED_TRAFFIC = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "tc.cuh", "mixed.cu"],
-                 "sha256": "09974a1ef8ef3577483200da915a89520f4fa06fb717dd3bb5ac110f2b9e8931",
+FUSED_TRAFFIC = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "tc.cuh"],
+                 "sha256": "5cf249f9ab0e04290d1422070a5375c559a91ba08fcdfb77470db9e890d1d940",
                  "workload": (1000, 3, 1_000_000, 10_000), "read": 149.31e9, "write": 80.01e9,
                  "shape": {"cs": 1, "ct": 1, "epw": 16, "pair": 0, "group": 16}}
 
