@@ -352,7 +352,7 @@ extern "C" int gwas_setup(gwas_ctx** out, int n, int pm1, const double* phi, con
     if ((rc = ctx_alloc(c, sizeof(double) * pm1 * n, (void**)&c->XL))) return fail(rc);
     if ((rc = ctx_alloc(c, sizeof(double) * pm1 * n, (void**)&c->XLt))) return fail(rc);
     cudaMemcpyAsync(c->XL, c->h_XL.data(), sizeof(double) * pm1 * n, cudaMemcpyHostToDevice, c->stream);
-    launch_rotate_fp64_f64(c, c->XL, pm1, n, c->XLt);
+    launch_rotate_fp64_rows(c, c->XL, pm1, n, c->XLt);
   }
   if (!ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "setup", &rc)) return fail(rc);
   if (!ctx_cuda_ok(c, cudaGetLastError(), "setup kernels", &rc)) return fail(rc);

@@ -59,6 +59,24 @@ __global__ void __launch_bounds__(256) rotate_fp64_kernel(const TA* __restrict__
   }
 }
 
+// The same product for a few rows (the covariates X_L, at setup): one warp per output C[r][col], a dot
+// product of row r of A with eigenvector col (contiguous in Zc).  The 64-row tiles of the
+// kernel above would spend 64/rows times the FP64 work of this product.
+template <typename TA>
+__global__ void __launch_bounds__(256) rotate_rows_kernel(const TA* __restrict__ A, int64_t rows, int64_t lda,
+                                                          const double* __restrict__ Zc, int n, double* __restrict__ C) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (w >= rows * n) return;
+  const int64_t r = w / n;
+  const int col = (int)(w % n);
+  const double* z = Zc + (size_t)col * n;
+  double acc = 0.0;
+  for (int k = lane; k < n; k += 32) acc = fma((double)A[r * lda + k], z[k], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) C[r * n + col] = acc;
+}
+
 template <typename TA>
 void rotate(gwas_ctx* c, const TA* A, int64_t rows, int64_t lda, double* C) {
   if (rows <= 0) return;
@@ -282,6 +300,13 @@ void launch_rotate_fp64_i8(gwas_ctx* c, const int8_t* A, int64_t rows, int64_t l
 }
 void launch_rotate_fp64_f64(gwas_ctx* c, const double* A, int64_t rows, int64_t lda, double* C) {
   rotate<double>(c, A, rows, lda, C);
+}
+void launch_rotate_fp64_rows(gwas_ctx* c, const double* A, int64_t rows, int64_t lda, double* C) {
+  if (rows <= 0) return;
+  const int64_t warps = rows * (int64_t)c->n;
+  ProfScope ps(c, "rotate_fp64");
+  rotate_rows_kernel<double><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, c->stream>>>(A, rows, lda, c->Z, c->n, C);
+  c->launches++;
 }
 
 void launch_prep_fp64(gwas_ctx* c, const double* Yt, int tb, const double* h2, double* R, double* consts) {

@@ -115,6 +115,8 @@ int ptr_kind(gwas_ctx* c, const void* p, bool* is_device);
 void launch_rotate_fp64_i8(gwas_ctx* c, const int8_t* A, int64_t rows, int64_t lda, double* C);
 void launch_rotate_fp64_f64(gwas_ctx* c, const double* A, int64_t rows, int64_t lda, double* C);
 // Per-trait FP64 prep: R[j] = [e∘y~ | e∘x~_L | e] ([t][p+1][n]); consts[j] = {S_TL, b_T, yy}.
+// X'_L = Z^T X_L for the few covariate rows (one warp per output).
+void launch_rotate_fp64_rows(gwas_ctx* c, const double* A, int64_t rows, int64_t lda, double* C);
 void launch_prep_fp64(gwas_ctx* c, const double* Yt, int tb, const double* h2, double* R, double* consts);
 // Fused FP64 contraction + per-pair solve for SNPs [i0,i1) x traits [j0, j0+tb).
 void launch_fused_fp64(gwas_ctx* c, int64_t i0, int64_t i1, int j0, int tb, int64_t ldo, const double* R,
