@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
     double w = 0, v[Q1] = {};
     float q0 = 0, q1 = 0, q2 = 0;
     if (k < n) {
-      const double e = 1.0 / (h * lam[k] + (1.0 - h));
+      const double e = e_row[k];  // from the first pass (this thread's k); w replaces it below
       double xl[Q1];
       for (int a = 0; a < PM1; ++a) xl[a] = XLt[(size_t)a * n + k];
       double r = y[k];
