@@ -65,3 +65,11 @@ def test_argument_errors_without_gpu(libpath):
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     assert lib.gwas_solve_stream(None, None, 0, 0, 1, None, None, None, None) == 1
 
+    # the autotuner and the introspection calls too
+    lib.gwas_autotune.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p]
+    assert lib.gwas_autotune(None, None, 0, 0, None) == 1
+    shape = (ctypes.c_int * 5)()
+    lib.gwas_tune_shape.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.gwas_tune_shape(None, shape) == 1
+    lib.gwas_serve_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.gwas_serve_stats(None, None, None) == 1

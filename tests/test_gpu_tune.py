@@ -73,3 +73,25 @@ def test_unbuilt_shape_in_the_cache_is_ignored(gw, tmp_path):
     assert shape == DEFAULT
     b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
     check(out, b, se)
+
+
+def test_autotune_states(gw):
+    P = make_problem(128, 200, 8, seed=3033)
+    o = gw.gwas_default_opts(precision=gw.GWAS_FP64, output=gw.GWAS_OUT_LAST_SE)
+    ctx = gw.gwas_setup(P.n, P.pm1, P.phi, P.XL, P.t, P.h2, o)
+    try:
+        gw.gwas_load_snps(ctx, P.m, P.XR, P.n)
+        with pytest.raises(gw.GwasError) as e:   # the FP64 path has no launch shape
+            gw.gwas_autotune(ctx, P.Y)
+        assert e.value.code == gw.GWAS_ERR_UNSUPPORTED
+    finally:
+        gw.gwas_destroy(ctx)
+    o = gw.gwas_default_opts(precision=gw.GWAS_MIXED, output=gw.GWAS_OUT_LAST_SE)
+    ctx = gw.gwas_setup(P.n, P.pm1, P.phi, P.XL, P.t, P.h2, o)
+    try:
+        with pytest.raises(gw.GwasError) as e:   # nothing to time before the genotypes are loaded
+            gw.gwas_autotune(ctx, P.Y)
+        assert e.value.code == gw.GWAS_ERR_STATE
+        assert gw.gwas_tune_shape(ctx) == DEFAULT
+    finally:
+        gw.gwas_destroy(ctx)
