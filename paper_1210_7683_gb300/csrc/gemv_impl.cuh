@@ -11,7 +11,8 @@
 //
 // One persistent CTA per SM: a TMA producer warp and 4 consumer warps, 256 SNPs (two 128-SNP
 // tiles) per unit, two SNPs per thread (row r of each tile), so that each read of the trait's
-// slices from shared memory serves two SNPs.  A stage holds 32 values of k: eight 8 KB boxes
+// slices from shared memory serves two SNPs (one SNP per thread on 8 warps for p - 1 >= 8).  A
+// stage holds 32 values of k: eight 8 KB boxes
 // (genotypes and the three planes, two tiles; 64-byte swizzle, so that the row-per-thread
 // reads are free of bank conflicts) and the trait's 32-wide slices (two strided boxes that
 // pick trait 0's row of every group).  A ring of three stages keeps ~200 KB per SM in flight.
@@ -27,15 +28,26 @@ namespace {
 
 constexpr int GK = 32;                   // values of k per stage
 constexpr int GNS = 3;                   // ring stages
-constexpr int GCONS = 4;                 // consumer warps
-constexpr int GTHR = GCONS * 32;         // consumer threads
-constexpr int GUNIT = 2 * GTHR;          // SNPs per unit: two tiles, two SNPs per thread
+constexpr int GUNIT = 256;               // SNPs per unit: two 128-row tiles
+// Consumers: 4 warps with two SNPs per thread (row r of both tiles), so that every broadcast
+// read of the trait's row serves two SNPs; for p - 1 >= 8 (up to 48 accumulators per SNP) 8 warps
+// with one SNP per thread, which measured 2-6 % faster there (the shared-memory wavefronts of
+// the broadcast reads bound the kernel at large p).
+template <int Q>
+struct GemvPar {
+  static constexpr int NT = Q >= 8 ? 1 : 2;  // SNPs (tiles) per consumer thread
+  static constexpr int THR = GUNIT / NT;     // consumer threads
+  static constexpr int CONS = THR / 32;      // consumer warps
+};
 constexpr int GBOX = 128 * GK * 2;       // one box: 128 rows x 32 bf16 = 8 KB
 constexpr int GDATA = 8 * GBOX;          // G + three planes, two tiles
 
 template <int Q>
 struct GemvGeo {
-  static constexpr int G1 = c1_groups(Q), NR = G1 + 4, NRP = (NR + 3) / 4 * 4;
+  // NRP: the FP32 row stride, = 2 (mod 4): the per-stage conversion writes consecutive k at
+  // this stride, which then meets 16 banks (a multiple of 4 met 2 banks: 16-way conflicts);
+  // the rows stay 8-byte aligned for the main loop's float2 broadcast reads
+  static constexpr int G1 = c1_groups(Q), NR = G1 + 4, NRP = NR % 4 == 2 ? NR : NR + 2;
   static constexpr int TRAW = (NR * GK * 2 + 1023) / 1024 * 1024;  // bf16 trait rows of a stage
   static constexpr int STAGE = GDATA + TRAW;
   static constexpr int TF32 = GK * NRP * 4;                         // the same rows, FP32, [k][row]
@@ -52,7 +64,7 @@ __device__ __forceinline__ void bf16x8(const uint4& v, float* f) {
 }
 
 template <int Q>
-__global__ void __launch_bounds__(32 + GTHR, 1)
+__global__ void __launch_bounds__(32 + GemvPar<Q>::THR, 1)
     gemv1_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapA,
                  const __grid_constant__ CUtensorMap mapT1, const __grid_constant__ CUtensorMap mapT2, FusedArgs a) {
   using Geo = GemvGeo<Q>;
@@ -68,7 +80,7 @@ __global__ void __launch_bounds__(32 + GTHR, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < GNS; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], GCONS);
+      tc::mbar_init(&empty[s], GemvPar<Q>::CONS);
     }
     *abort = 0;
     tc::fence_mbar_init();
@@ -114,17 +126,19 @@ __global__ void __launch_bounds__(32 + GTHR, 1)
     }
     return;
   }
-  // -------------------------------------------------------------- consumers: two SNPs per thread
-  const int ct = threadIdx.x - 32, r = ct;  // row r of both tiles
+  // -------------------------------------------------------------- consumers: NT SNPs per thread
+  constexpr int NT = GemvPar<Q>::NT, GTHR = GemvPar<Q>::THR;
+  const int ct = threadIdx.x - 32, r = ct % 128;  // row r of tiles t0 .. t0 + NT - 1
+  const int t0 = NT == 2 ? 0 : ct / 128;
   const float inv_dof = 1.f / a.dof, F = 1.f / 256.f;
   const int full_b = a.full_b;
   unsigned long long nsing = 0;
   uint32_t h = 0;
   bool ok = true;
   for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-    float acc[2][G1], c2[2][6];
+    float acc[NT][G1], c2[NT][6];
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NT; ++t) {
 #pragma unroll
       for (int i = 0; i < G1; ++i) acc[t][i] = 0.f;
 #pragma unroll
@@ -143,23 +157,29 @@ __global__ void __launch_bounds__(32 + GTHR, 1)
 #pragma unroll
       for (int c = 0; c < GK / 8; ++c) {
         const uint32_t off = (uint32_t)r * (GK * 2) + ((c ^ sw) << 4);
-        float xg[2][8], xa1[2][8], xa2[2][8], xa3[2][8];
+        float xg[NT][8], xa1[NT][8], xa2[NT][8], xa3[NT][8];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          bf16x8(*(const uint4*)(buf + t * GBOX + off), xg[t]);
-          bf16x8(*(const uint4*)(buf + (2 + t) * GBOX + off), xa1[t]);
-          bf16x8(*(const uint4*)(buf + (4 + t) * GBOX + off), xa2[t]);
-          bf16x8(*(const uint4*)(buf + (6 + t) * GBOX + off), xa3[t]);
+        for (int t = 0; t < NT; ++t) {
+          const int tb = t0 + t;
+          bf16x8(*(const uint4*)(buf + tb * GBOX + off), xg[t]);
+          bf16x8(*(const uint4*)(buf + (2 + tb) * GBOX + off), xa1[t]);
+          bf16x8(*(const uint4*)(buf + (4 + tb) * GBOX + off), xa2[t]);
+          bf16x8(*(const uint4*)(buf + (6 + tb) * GBOX + off), xa3[t]);
         }
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const float* tr = tfs + (8 * c + e) * NRP;
-          float tv[NR];
+          // the trait's row of this k: NRP floats, 8-byte aligned (NRP is even)
+          const float2* tr = reinterpret_cast<const float2*>(tfs + (8 * c + e) * NRP);
+          float tv[NRP];
 #pragma unroll
-          for (int i = 0; i < NR; ++i) tv[i] = tr[i];
+          for (int i = 0; i < NRP / 2; ++i) {
+            const float2 v2 = tr[i];
+            tv[2 * i] = v2.x;
+            tv[2 * i + 1] = v2.y;
+          }
           const float e2s = tv[G1], e1 = tv[G1 + 1], e2 = tv[G1 + 2], e3s = tv[G1 + 3];
 #pragma unroll
-          for (int t = 0; t < 2; ++t) {
+          for (int t = 0; t < NT; ++t) {
 #pragma unroll
             for (int i = 0; i < G1; ++i) acc[t][i] = fmaf(xg[t][e], tv[i], acc[t][i]);
             c2[t][0] = fmaf(xa1[t][e], e1, c2[t][0]);   // A1 x E1   (level 0)
@@ -176,8 +196,8 @@ __global__ void __launch_bounds__(32 + GTHR, 1)
       if (lane == 0) tc::mbar_arrive(&empty[s]);
     }
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int64_t snp = a.row0 + u * GUNIT + 128 * t + r;
+    for (int t = 0; t < NT; ++t) {
+      const int64_t snp = a.row0 + u * GUNIT + 128 * (t0 + t) + r;
       const bool valid = ok && snp >= a.snp_lo && snp < snp_end;
       if (!valid) continue;
       const float* acc_t = acc[t];
@@ -243,7 +263,7 @@ int launch_gemv1_q(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const
   static_assert(smem <= 227 * 1024, "single-trait kernel shared memory");
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   ProfScope ps(c, "gemv1");
-  kern<<<blocks, 32 + GTHR, smem, c->stream>>>(mg, ma, m1, m2, a);
+  kern<<<blocks, 32 + GemvPar<Q>::THR, smem, c->stream>>>(mg, ma, m1, m2, a);
   c->launches++;
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return ctx_fail(c, GWAS_ERR_CUDA, std::string("single-trait kernel launch: ") + cudaGetErrorString(e));
