@@ -31,6 +31,7 @@ int fused_pair_layout(const gwas_ctx* c, int q) { return shape_of(c, q).pair; }
 
 bool fused_shape_supported(int q, int cs, int ct, int epw, int pair) {
   if (cs == 1 && ct == 1 && epw == 16 && !pair) return true;
+  if (q == 3 && cs == 1 && ct == 1 && epw == 8 && !pair) return true;
   if (q != 3 || epw != 16) return false;
   if (pair) return cs == 2 && ct == 1;
   return (cs == 1 && ct == 2) || (cs == 2 && ct == 1) || (cs == 2 && ct == 2);
@@ -64,6 +65,7 @@ int launch_fused(gwas_ctx* c, int q, const FusedArgs& args, const __nv_bfloat16*
   // optional cluster shapes (q = 3): TMA multicast of shared operands, or the CTA pair
 #define GWAS_SHAPE(CS, CT, EPW) \
   if (sh.cs == CS && sh.ct == CT && sh.epw == EPW && !sh.pair) return launch_shape<CS, CT, EPW, false, false, 3>(c, a, mg, ma, m1, m2);
+  GWAS_SHAPE(1, 1, 8)   // 8 epilogue warps of 16 traits each: fewer warps beside the MMA issuer
   GWAS_SHAPE(1, 2, 16)
   GWAS_SHAPE(2, 1, 16)
   GWAS_SHAPE(2, 2, 16)
