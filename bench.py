@@ -39,13 +39,13 @@ from synth import covariates, genotypes, heritabilities, kinship, phenotypes  # 
 N_IND, PM1, M_SNP, T_TRAIT = 1000, 3, 1_000_000, 10_000
 METRIC = "GLS pairs/s (n=1000, p=4, m=1e6 SNPs, t=1e4 traits; SNP coefficient + SE)"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# DRAM bytes of one fused_kernel launch at n=1000 p=4 m=1e6 t=1e4: the median of three
+# DRAM bytes of one fused_kernel launch at n=1000 p=4 m=1e6 t=1e4: the mean of two
 # single-pass ncu captures of dram__bytes_read.sum + dram__bytes_write.sum.  Valid only while
 # the kernel's sources hash to the value the captures were taken on: a changed kernel reports
 # null traffic.
 FUSED_TRAFFIC = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "tc.cuh"],
-                 "sha256": "5cf249f9ab0e04290d1422070a5375c559a91ba08fcdfb77470db9e890d1d940",
-                 "workload": (1000, 3, 1_000_000, 10_000), "read": 149.31e9, "write": 80.01e9,
+                 "sha256": "18bc6a27b7fdd3dbeeee6ee6b014789f7e3d650dda6469e8fc6a825771e7803a",
+                 "workload": (1000, 3, 1_000_000, 10_000), "read": 150.05e9, "write": 80.01e9,
                  "shape": {"cs": 1, "ct": 1, "epw": 16, "pair": 0, "group": 16}}
 
 
