@@ -259,7 +259,13 @@ GWAS_API int64_t gwas_kernel_launches(const gwas_ctx* ctx);
 GWAS_API int gwas_autotune(gwas_ctx* ctx, const double* Y, int t_sample, int64_t m_sample, double* best_ms);
 
 /* The context's launch shape: shape[0..4] = cluster CTAs along SNPs, along traits,
- * epilogue warps, CTA-pair mode (0/1), SNP tiles per traversal group. */
+ * epilogue warps, CTA-pair mode (0/1), SNP tiles per traversal group.
+ *
+ * Developer overrides, read from the environment at each launch (they take precedence over
+ * the tuned shape; for measurements, not for production use):
+ *   GWAS_FUSED_SHAPE="CSxCTxEPW[xPAIR]"  launch shape at p = 4 (e.g. "2x1x16x1", the CTA pair)
+ *   GWAS_FUSED_GROUP=<k>                  SNP tiles per traversal group
+ *   GWAS_SERVE_SLOTS=<k>, GWAS_SERVE_ROUND=<k>  serving arena trait-tile slots and units per round */
 GWAS_API int gwas_tune_shape(const gwas_ctx* ctx, int* shape);
 
 /* Accumulated device time (ms, from CUDA events recorded on the context's stream
