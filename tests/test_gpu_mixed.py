@@ -226,3 +226,22 @@ def test_extreme_heritabilities(gw):
     assert max(errs) <= TOL and max(serrs) <= TOL, (errs, serrs)
     full64, rc, _ = solve(gw, P, gw.GWAS_OUT_FULL_B, precision=gw.GWAS_FP64)
     assert full_b_err(full64.transpose(1, 0, 2), b, se) <= 1e-10
+
+
+@pytest.mark.parametrize("n,m,t,pm1", [(8, 1, 1, 3), (30, 1, 40, 3), (64, 129, 1, 0), (64, 300, 33, 19), (1000, 1, 1, 3),
+                                       (70, 5, 2, 1)])
+def test_degenerate_shapes(gw, n, m, t, pm1):
+    # one SNP, one trait, few degrees of freedom (4 at n = 8, 44 at p = 20), n below one K block
+    # of 64 and not a multiple of it; both output modes against the oracle.  (With n - p of 1 or
+    # 2, RSS = rr - num beta can be a tiny difference for some pairs and the FP32 epilogue's SE
+    # loses its relative accuracy there; the FP64 path covers that regime, far below the paper's
+    # n >= 10^3.)
+    P = make_problem(n, m, t, pm1=pm1, seed=5000 + n + m + t)
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    out, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE)
+    assert rc == gw.GWAS_OK
+    check_last(out, b, se)
+    full, rc, _ = solve(gw, P, gw.GWAS_OUT_FULL_B)
+    assert full_b_err(full.transpose(1, 0, 2), b, se) <= TOL
+    empty, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE, 0, 0)
+    assert rc == gw.GWAS_OK and empty.size == 0
