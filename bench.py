@@ -98,6 +98,48 @@ def pinned_host_array(shape, dtype, torch):
         return None, False
 
 
+def hugepage_fraction(addr, nbytes):
+    """Share of [addr, addr + nbytes) backed by transparent huge pages, from /proc/self/smaps
+    (None where that file is not readable)."""
+    try:
+        lines = open("/proc/self/smaps").read().splitlines()
+    except OSError:
+        return None
+    huge = 0
+    inside = False
+    for ln in lines:
+        head = ln.split()[0] if ln else ""
+        if "-" in head and not head.endswith(":"):
+            lo, hi = (int(x, 16) for x in head.split("-"))
+            inside = lo < addr + nbytes and hi > addr
+        elif inside and head == "AnonHugePages:":
+            huge += int(ln.split()[1]) * 1024
+    return huge / nbytes if nbytes else None
+
+
+def host_link_probe(torch, dev, host, nbytes=4 << 30, reps=3):
+    """Device -> host copy rate (GB/s, best of `reps`) into the first `nbytes` of a page-locked
+    host buffer, timed with CUDA events on a side stream: the link rate the e2e step sees."""
+    if isinstance(host, np.ndarray):
+        host = torch.from_numpy(host.reshape(-1).view(np.uint8))
+    else:
+        host = host.reshape(-1).view(torch.uint8)
+    nbytes = min(nbytes, host.numel())
+    src = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    best = 0.0
+    with torch.cuda.stream(s):
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            host[:nbytes].copy_(src, non_blocking=True)
+            e1.record(s)
+            e1.synchronize()
+            best = max(best, nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del src
+    return best
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -114,7 +156,8 @@ def parse():
     ap.add_argument("--no-t1", action="store_true", help="skip the single-trait measurement")
     ap.add_argument("--serving-requests", type=int, default=400,
                     help="requests of the serving run (the full serving workload has 2000; 0 skips it)")
-    ap.add_argument("--serving-load", type=float, default=0.8, help="offered load as a fraction of saturation")
+    ap.add_argument("--serving-load", default="0.8,0.5,0.95",
+                    help="offered loads as fractions of saturation, comma-separated; the first is the headline")
     return ap.parse_args()
 
 
@@ -227,13 +270,13 @@ def cpu_baseline(n, inp, m_s=8192, t_s=128):
             "seconds": t_solve + t_eig}, (b, se, m_s, t_s)
 
 
-def serving_run(g, torch, dev, local, count, load, seed_offset=0):
+def serving_run(g, torch, dev, local, count, loads, seed_offset=0):
     """Serving workload: n=2000, m=1e6 resident SNPs, Poisson stream of requests with
     t_k ~ log-uniform[1, 2000] traits and SNP ranges of log-uniform length in [1e4, 1e6].
 
     First all requests are submitted at once (saturation throughput); then the same
-    stream is replayed with Poisson arrivals at `load` x that throughput, and the
-    latency (submit -> done) percentiles are measured on the host clock.
+    stream is replayed with Poisson arrivals at each of `loads` x that throughput, and the
+    latency (arrival -> done) percentiles are measured on the host clock.
     """
     from synth import BASE_SEED, serving_requests
     n, m = 2000, 1_000_000
@@ -286,16 +329,22 @@ def serving_run(g, torch, dev, local, count, load, seed_offset=0):
         span, _, total_pairs = run(np.zeros(len(reqs)))          # saturation: all at once
         sat = total_pairs / span
         mean_pairs = total_pairs / len(reqs)
-        rate = load * sat / mean_pairs                            # requests per second
-        gaps = np.random.default_rng(BASE_SEED + 9).exponential(1.0 / rate, len(reqs))
-        span2, lat, pairs2 = run(np.cumsum(gaps))
+        sweep = []
+        for load in loads:
+            rate = load * sat / mean_pairs                        # requests per second
+            gaps = np.random.default_rng(BASE_SEED + 9).exponential(1.0 / rate, len(reqs))
+            span2, lat, pairs2 = run(np.cumsum(gaps))
+            sweep.append({"offered_load": load, "pairs_per_s": pairs2 / span2,
+                          "p50_latency_s": float(np.percentile(lat, 50)),
+                          "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean())})
     finally:
         g.gwas_destroy(ctx)
+    head = sweep[0]
     return {"workload": f"n={n} p=4 m={m} resident, {len(reqs)} requests, t_k log-uniform[1,2000], "
-                        f"SNP ranges log-uniform[1e4,1e6], Poisson arrivals at {load:.2f} of saturation",
-            "saturated_pairs_per_s": sat, "pairs_per_s": pairs2 / span2, "offered_load": load,
-            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "mean_latency_s": float(lat.mean()), "requests": len(reqs), "pairs": int(total_pairs)}
+                        f"SNP ranges log-uniform[1e4,1e6], Poisson arrivals at {head['offered_load']:.2f} "
+                        f"of saturation (other loads under load_sweep)",
+            "saturated_pairs_per_s": sat, **head, "requests": len(reqs), "pairs": int(total_pairs),
+            "load_sweep": sweep}
 
 
 def run_reference(args, rank, world):
@@ -436,7 +485,7 @@ def main():
     if "xgemm_rotate_snps" in ktimes:
         # all launches of one step (the rotation runs in blocks of SNP rows)
         rot_ms = ktimes["xgemm_rotate_snps"][0] / args.steps
-        mpad, ldx = (m + 127) // 128 * 128, (n + PM1 + 63) // 64 * 64
+        mpad, ldx, kpad = (m + 127) // 128 * 128, (n + PM1 + 63) // 64 * 64, (n + 63) // 64 * 64
         issued_r = 2.0 * mpad * ldx * kpad * 4
         useful_r = 2.0 * n * n * m
         bytes_r = 2.0 * mpad * kpad + 4 * 2.0 * ldx * kpad + 4.0 * m * ldx   # G in, slices in, FP32 out
@@ -539,8 +588,13 @@ def main():
                 step(g, opts_h, n, m, t, pin, hout)
             barrier()
             e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
+            link = {"d2h_gbs": host_link_probe(torch, dev, hout),
+                    "hugepage_frac": hugepage_fraction(hout.ctypes.data, d2h) if registered else None,
+                    "note": "raw device -> host copy rate into this result buffer (4 GB, best of 3) and the "
+                            "share of the buffer on transparent huge pages; the grid's download bounds "
+                            "the step at d2h_bytes / d2h_gbs"}
             result["e2e"] = {"value": world * pairs / (e_ms / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
-                             "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": e_steps,
+                             "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": e_steps, "host_link": link,
                              "note": out_note + "; inputs from pinned host memory; wall clock around the C calls"}
             if registered:
                 torch.cuda.cudart().cudaHostUnregister(hout.ctypes.data)
@@ -584,7 +638,8 @@ def main():
     if args.serving_requests > 0 and rank == 0:
         del inp_d, out
         torch.cuda.empty_cache()
-        result["serving"] = serving_run(g, torch, dev, local, args.serving_requests, args.serving_load)
+        result["serving"] = serving_run(g, torch, dev, local, args.serving_requests,
+                                        [float(x) for x in args.serving_load.split(",")])
         out = None
 
     # ---------------------------------------------------------------- CPU oracle and sampled error
