@@ -117,27 +117,55 @@ def hugepage_fraction(addr, nbytes):
     return huge / nbytes if nbytes else None
 
 
-def host_link_probe(torch, dev, host, nbytes=4 << 30, reps=3):
-    """Device -> host copy rate (GB/s, best of `reps`) into the first `nbytes` of a page-locked
-    host buffer, timed with CUDA events on a side stream: the link rate the e2e step sees."""
+def numa_pages(addr, nbytes):
+    """Pages of [addr, addr + nbytes) per NUMA node ({"N0": pages, ...}), from /proc/self/numa_maps
+    (None where that file is not readable)."""
+    try:
+        lines = open("/proc/self/numa_maps").read().splitlines()
+    except OSError:
+        return None
+    out = {}
+    for ln in lines:
+        f = ln.split()
+        if not f:
+            continue
+        start = int(f[0], 16)
+        if not addr <= start < addr + nbytes:
+            continue
+        for kv in f[1:]:
+            if kv.startswith("N") and "=" in kv:
+                k, v = kv.split("=")
+                out[k] = out.get(k, 0) + int(v)
+    return out
+
+
+def host_link_probe(torch, dev, host, nbytes=2 << 30, reps=2):
+    """Device -> host copy rates (GB/s, best of `reps`) into `nbytes` at the start, 1/3, 2/3 and
+    end of a page-locked host buffer, timed with CUDA events on a side stream: the link rate
+    the e2e step sees in each part of its result buffer."""
     if isinstance(host, np.ndarray):
         host = torch.from_numpy(host.reshape(-1).view(np.uint8))
     else:
         host = host.reshape(-1).view(torch.uint8)
-    nbytes = min(nbytes, host.numel())
+    total = host.numel()
+    nbytes = min(nbytes, total)
     src = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     s = torch.cuda.Stream(device=dev)
-    best = 0.0
+    rates = []
     with torch.cuda.stream(s):
-        for _ in range(reps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            host[:nbytes].copy_(src, non_blocking=True)
-            e1.record(s)
-            e1.synchronize()
-            best = max(best, nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        for frac in (0.0, 1 / 3, 2 / 3, 1.0):
+            off = min(int(frac * total) // 4096 * 4096, total - nbytes)
+            best = 0.0
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                host[off:off + nbytes].copy_(src, non_blocking=True)
+                e1.record(s)
+                e1.synchronize()
+                best = max(best, nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9)
+            rates.append(round(best, 1))
     del src
-    return best
+    return rates
 
 
 def parse():
@@ -590,9 +618,11 @@ def main():
             e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
             link = {"d2h_gbs": host_link_probe(torch, dev, hout),
                     "hugepage_frac": hugepage_fraction(hout.ctypes.data, d2h) if registered else None,
-                    "note": "raw device -> host copy rate into this result buffer (4 GB, best of 3) and the "
-                            "share of the buffer on transparent huge pages; the grid's download bounds "
-                            "the step at d2h_bytes / d2h_gbs"}
+                    "numa_pages": numa_pages(hout.ctypes.data, d2h) if registered else None,
+                    "note": "raw device -> host copy rates into 2 GB at the start, 1/3, 2/3 and end of this "
+                            "result buffer (best of 2), the share of the buffer on transparent huge pages "
+                            "and its pages per NUMA node; the grid's download bounds the step at "
+                            "d2h_bytes / d2h_gbs"}
             result["e2e"] = {"value": world * pairs / (e_ms / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                              "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": e_steps, "host_link": link,
                              "note": out_note + "; inputs from pinned host memory; wall clock around the C calls"}
