@@ -258,12 +258,20 @@ def make_inputs(n, m, t, seed_offset=0):
             "Y": phenotypes(n, t)}
 
 
-def step(g, opts, n, m, t, inp, out):
-    """One pass of the whole path; returns the context's per-kernel timings and launch count."""
+def step(g, opts, n, m, t, inp, out, phases=None):
+    """One pass of the whole path; returns the context's per-kernel timings and launch count.
+    `phases`, a dict of lists, collects the host wall time (ms) of each call (each returns
+    after its work has completed)."""
+    t0 = time.perf_counter()
     ctx = g.gwas_setup(n, PM1, inp["phi"], inp["XL"], t, inp["h2"], opts)
+    t1 = time.perf_counter()
     try:
         g.gwas_load_snps(ctx, m, inp["XR"], n)
+        t2 = time.perf_counter()
         rc = g.gwas_solve(ctx, inp["Y"], 0, m, out)
+        if phases is not None:
+            for k, v in (("setup", t1 - t0), ("load_snps", t2 - t1), ("solve", time.perf_counter() - t2)):
+                phases.setdefault(k, []).append(round(v * 1e3, 1))
         names = ["eigendecomposition", "setup_rotation_operands", "slice_rows", "genotypes_bf16", "xgemm_rotate_snps",
                  "slice_snp_squares", "xgemm_rotate_traits", "prep_traits", "xgemm_back_rotate",
                  "pack_trait_columns", "fused", "rotate_fp64", "prep_fp64", "fused_fp64"]
@@ -611,9 +619,10 @@ def main():
             step(g, opts_h, n, m, t, pin, hout)
             barrier()
             e_steps = max(1, min(args.steps, 3))
+            phases = {}
             t0 = time.perf_counter()
             for _ in range(e_steps):
-                step(g, opts_h, n, m, t, pin, hout)
+                step(g, opts_h, n, m, t, pin, hout, phases)
             barrier()
             e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
             link = {"d2h_gbs": host_link_probe(torch, dev, hout),
@@ -625,6 +634,7 @@ def main():
                             "d2h_bytes / d2h_gbs"}
             result["e2e"] = {"value": world * pairs / (e_ms / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                              "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": e_steps, "host_link": link,
+                             "phase_ms": phases,
                              "note": out_note + "; inputs from pinned host memory; wall clock around the C calls"}
             if registered:
                 torch.cuda.cudart().cudaHostUnregister(hout.ctypes.data)
