@@ -139,12 +139,16 @@ GWAS_API int gwas_load_snps(gwas_ctx* ctx, int64_t m, const int8_t* XR);
  * RSS the squared norm of the whitened residual (the paper defines none).
  * Returns GWAS_ERR_SINGULAR_PAIRS (a warning) when some pair's Schur
  * complement is <= 1e-10 times its diagonal entry; those outputs are NaN.
- * A host `out` receives the results trait block by trait block, each block's
- * copy overlapping the next block's computation when `out` is page-locked
- * (the copies reach the link's full rate from memory on huge pages, e.g.
- * cudaHostAlloc or madvise(MADV_HUGEPAGE) + cudaHostRegister; registered memory
- * on small base pages measured about half of it).
- * The blocks start at 1/8 of opts.trait_block traits (about 8 GB of results when
+ * Where the device reads the CPU's page tables (Grace-class systems) and `out` is
+ * page-locked host memory mapped for the device (cudaHostAlloc, or cudaHostRegister),
+ * the kernels store the results into `out` directly, in blocks of opts.trait_block, with
+ * no device staging and no copies.  (GWAS_HOST_OUTPUT=staged in the environment selects
+ * the staged copies below instead.)  Any other host `out` receives the results trait
+ * block by trait block through two device staging buffers, each block's copy overlapping
+ * the next block's computation when `out` is page-locked (the copies reach the link's
+ * full rate from memory on huge pages, e.g. cudaHostAlloc or madvise(MADV_HUGEPAGE) +
+ * cudaHostRegister; registered memory on small base pages measured about half of it).
+ * The staged blocks start at 1/8 of opts.trait_block traits (about 8 GB of results when
  * trait_block is 0) and grow by 1.4x per block up to it, so that the first copy
  * starts early; a device `out` is computed in blocks of opts.trait_block.
  */
@@ -265,7 +269,9 @@ GWAS_API int gwas_autotune(gwas_ctx* ctx, const double* Y, int t_sample, int64_t
  * the tuned shape; for measurements, not for production use):
  *   GWAS_FUSED_SHAPE="CSxCTxEPW[xPAIR]"  launch shape at p = 4 (e.g. "2x1x16x1", the CTA pair)
  *   GWAS_FUSED_GROUP=<k>                  SNP tiles per traversal group
- *   GWAS_SERVE_SLOTS=<k>, GWAS_SERVE_ROUND=<k>  serving arena trait-tile slots and units per round */
+ *   GWAS_SERVE_SLOTS=<k>, GWAS_SERVE_ROUND=<k>  serving arena trait-tile slots and units per round
+ *   GWAS_HOST_OUTPUT=staged               gwas_solve copies page-locked host outputs through device
+ *                                         staging instead of storing them from the kernels */
 GWAS_API int gwas_tune_shape(const gwas_ctx* ctx, int* shape);
 
 /* Accumulated device time (ms, from CUDA events recorded on the context's stream

@@ -5,7 +5,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -97,6 +99,35 @@ int ptr_kind(gwas_ctx* c, const void* p, bool* is_device) {
     *is_device = true;
   }
   return GWAS_OK;
+}
+
+// Whether the kernels can store a host output [p, p + bytes) directly: the device reads the
+// CPU's page tables (Grace-class systems, where every address of the process is reachable
+// from the device), both ends of the range are page-locked host memory mapped for the device,
+// and the device addresses of the ends are as far apart as the host ones.  Page-locked memory
+// is resident, so the stores never wait for a page fault.  GWAS_HOST_OUTPUT=staged in the
+// environment keeps the staged copies.
+static bool direct_host_output(gwas_ctx* c, void* p, size_t bytes, void** dptr) {
+  if (bytes == 0) return false;
+  if (const char* e = getenv("GWAS_HOST_OUTPUT"))
+    if (!strcmp(e, "staged")) return false;
+  int ats = 0;
+  if (cudaDeviceGetAttribute(&ats, cudaDevAttrPageableMemoryAccessUsesHostPageTables, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (!ats) return false;
+  cudaPointerAttributes a0, a1;
+  const char* last = (const char*)p + bytes - 1;
+  if (cudaPointerGetAttributes(&a0, p) != cudaSuccess || cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+    return false;
+  if ((const char*)a1.devicePointer - (const char*)a0.devicePointer != (ptrdiff_t)(bytes - 1)) return false;
+  *dptr = a0.devicePointer;
+  return true;
 }
 
 int ctx_upload(gwas_ctx* c, const void* src, size_t bytes, void* dst) {
@@ -626,6 +657,17 @@ extern "C" int gwas_solve(gwas_ctx* c, const double* Y, int64_t i0, int64_t i1, 
   OutSink sink;
   sink.kind = odev ? 0 : 1;
   sink.out = out;
+  if (!odev) {
+    // a page-locked host output that the device can address is written by the kernels
+    // themselves, without device staging or copies
+    const size_t pair_bytes = c->output == GWAS_OUT_LAST_SE ? 8 : 8 * (size_t)c->p;
+    void* dptr = nullptr;
+    if (direct_host_output(c, out, pair_bytes * (size_t)c->t * (size_t)(i1 - i0), &dptr)) {
+      sink.kind = 0;
+      sink.out = dptr;
+      odev = true;
+    }
+  }
   int tb = (c->trait_block > 0 && c->trait_block < c->t) ? c->trait_block : c->t;
   if (!odev && c->trait_block <= 0 && i1 > i0) {
     // host output, no block size given: blocks of about 8 GB of results, so that the downloads

@@ -211,6 +211,40 @@ def test_host_output_in_growing_blocks(gw):
     check_last(ref, b, se)
 
 
+@pytest.mark.parametrize("precision,output", [("mixed", "last"), ("mixed", "full"), ("fp64", "last")])
+def test_page_locked_output_direct_and_staged(gw, monkeypatch, precision, output):
+    # a page-locked host output is stored by the kernels themselves where the device reads the
+    # CPU's page tables, else (and with GWAS_HOST_OUTPUT=staged) copied through device staging;
+    # both give the device output bit for bit
+    import torch
+    P = make_problem(200, 650, 70, pm1=4, seed=2027)
+    prec = gw.GWAS_MIXED if precision == "mixed" else gw.GWAS_FP64
+    out_kind = gw.GWAS_OUT_LAST_SE if output == "last" else gw.GWAS_OUT_FULL_B
+    shape, dt = ((2, P.t, P.m), torch.float32) if output == "last" else ((P.t, P.m, P.p), torch.float64)
+    o = gw.gwas_default_opts(precision=prec, output=out_kind, trait_block=32)
+    ctx = gw.gwas_setup(P.n, P.pm1, P.phi, P.XL, P.t, P.h2, o)
+    try:
+        gw.gwas_load_snps(ctx, P.m, P.XR, P.n)
+        dev = torch.full(shape, float("nan"), dtype=dt, device="cuda:0")
+        gw.gwas_solve(ctx, P.Y, 0, P.m, dev)
+        direct = torch.full(shape, float("nan"), dtype=dt).pin_memory()
+        gw.gwas_solve(ctx, P.Y, 0, P.m, direct)
+        monkeypatch.setenv("GWAS_HOST_OUTPUT", "staged")
+        staged = torch.full(shape, float("nan"), dtype=dt).pin_memory()
+        gw.gwas_solve(ctx, P.Y, 0, P.m, staged)
+        monkeypatch.delenv("GWAS_HOST_OUTPUT")
+        # a sub-range of SNPs into a page-locked array sized for it
+        part = torch.full((2, P.t, 300) if output == "last" else (P.t, 300, P.p), float("nan"), dtype=dt).pin_memory()
+        gw.gwas_solve(ctx, P.Y, 100, 400, part)
+    finally:
+        gw.gwas_destroy(ctx)
+    ref = dev.cpu().numpy()
+    np.testing.assert_array_equal(direct.numpy(), ref)
+    np.testing.assert_array_equal(staged.numpy(), ref)
+    np.testing.assert_array_equal(part.numpy(), ref[:, :, 100:400] if output == "last" else ref[:, 100:400])
+    assert np.isfinite(ref).all()
+
+
 def test_extreme_heritabilities(gw):
     # h^2 over the whole range of the model, both ends included: M_j = I (ordinary least
     # squares) at 0 and M_j = Phi at 1; near 1 the weights e_j = 1/(h^2 lambda + 1 - h^2)
