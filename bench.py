@@ -615,7 +615,7 @@ def main():
             h2d = sum(v.numel() * v.element_size() for v in pin.values())
             d2h = hout.nbytes if isinstance(hout, np.ndarray) else hout.numel() * hout.element_size()
             opts_h = g.gwas_default_opts(precision=g.GWAS_MIXED, output=g.GWAS_OUT_LAST_SE, device=local,
-                                         stream=stream.cuda_stream, trait_block=1250, tune_cache=tune_path)
+                                         stream=stream.cuda_stream, trait_block=0, tune_cache=tune_path)
             step(g, opts_h, n, m, t, pin, hout)
             barrier()
             e_steps = max(1, min(args.steps, 3))
