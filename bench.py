@@ -45,17 +45,24 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # null traffic.
 FUSED_TRAFFIC = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "tc.cuh"],
                  "sha256": "18bc6a27b7fdd3dbeeee6ee6b014789f7e3d650dda6469e8fc6a825771e7803a",
-                 "workload": (1000, 3, 1_000_000, 10_000), "read": 150.05e9, "write": 80.01e9,
-                 "shape": {"cs": 1, "ct": 1, "epw": 16, "pair": 0, "group": 16}}
+                 "workload": (1000, 3, 1_000_000, 10_000),
+                 # one single-pass ncu capture per launch shape the autotuner has chosen on this GPU
+                 "captures": [
+                     {"shape": {"cs": 1, "ct": 1, "epw": 16, "pair": 0, "group": 16}, "read": 150.05e9, "write": 80.01e9},
+                     {"shape": {"cs": 1, "ct": 1, "epw": 8, "pair": 0, "group": 8}, "read": 253.98e9, "write": 80.01e9},
+                 ]}
 
 
 def fused_traffic(workload, shape=None):
-    """DRAM bytes per fused_kernel launch from the committed capture, or None when the workload
-    or the launch shape differs from the captured one, or the kernel's sources changed since."""
+    """DRAM bytes per fused_kernel launch from the committed capture of this launch shape (the
+    first, default shape when none is given), or None when the workload differs from the
+    captured one, no capture has this shape, or the kernel's sources changed since."""
     import hashlib
     if tuple(workload) != FUSED_TRAFFIC["workload"]:
         return None
-    if shape is not None and shape != FUSED_TRAFFIC["shape"]:
+    caps = FUSED_TRAFFIC["captures"]
+    cap = caps[0] if shape is None else next((c for c in caps if c["shape"] == shape), None)
+    if cap is None:
         return None
     h = hashlib.sha256()
     for f in FUSED_TRAFFIC["sources"]:
@@ -63,7 +70,7 @@ def fused_traffic(workload, shape=None):
             h.update(fh.read())
     if h.hexdigest() != FUSED_TRAFFIC["sha256"]:
         return None
-    return FUSED_TRAFFIC["read"] + FUSED_TRAFFIC["write"]
+    return cap["read"] + cap["write"]
 
 
 def algorithmic_flops(n, p, pairs, form="gemm"):

@@ -21,12 +21,15 @@ def _current_sha():
 def test_traffic_record_tied_to_sources_workload_and_shape(monkeypatch):
     rec = dict(bench.FUSED_TRAFFIC, sha256=_current_sha())
     monkeypatch.setattr(bench, "FUSED_TRAFFIC", rec)
-    w, shape = rec["workload"], dict(rec["shape"])
-    assert bench.fused_traffic(w, shape) == rec["read"] + rec["write"]
-    assert bench.fused_traffic(w) == rec["read"] + rec["write"]           # shape unknown: not checked
+    w = rec["workload"]
+    for cap in rec["captures"]:
+        assert bench.fused_traffic(w, dict(cap["shape"])) == cap["read"] + cap["write"]
+    first = rec["captures"][0]
+    shape = dict(first["shape"])
+    assert bench.fused_traffic(w) == first["read"] + first["write"]       # shape unknown: the default
     assert bench.fused_traffic((w[0], w[1], w[2] // 2, w[3]), shape) is None
-    assert bench.fused_traffic(w, dict(shape, group=8)) is None
-    assert bench.fused_traffic(w, dict(shape, epw=8)) is None
+    assert bench.fused_traffic(w, dict(shape, group=32)) is None           # no capture of this shape
+    assert bench.fused_traffic(w, dict(shape, cs=2, pair=1)) is None
     monkeypatch.setattr(bench, "FUSED_TRAFFIC", dict(rec, sha256="0" * 64))  # sources changed since
     assert bench.fused_traffic(w, shape) is None
 
