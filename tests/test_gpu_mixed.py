@@ -86,6 +86,33 @@ def test_mixed_matches_fp64_gpu(gw):
     check_last(mixed, b, fse[1].T.astype(np.float64))
 
 
+def test_mixed_matches_fp64_gpu_on_workload_slice(gw):
+    """Every pair of SNPs [0, 16384) x all 10,000 traits of the n=1000, p=4 workload: the mixed
+    path against the FP64 GPU path (itself pinned to the oracle at 1e-10), compared on the device."""
+    torch = pytest.importorskip("torch")
+    n, M, t = 1000, 16384, 10_000
+    dev = torch.device("cuda:0")
+    phi, XL, h2 = kinship(n), covariates(n), heritabilities(t)
+    XR = torch.from_numpy(genotypes(n, 1_000_000, i0=0, i1=M)).to(dev)
+    Y = torch.from_numpy(phenotypes(n, t)).to(dev)
+    outs = {}
+    for prec in (gw.GWAS_MIXED, gw.GWAS_FP64):
+        o = gw.gwas_default_opts(precision=prec, output=gw.GWAS_OUT_LAST_SE)
+        ctx = gw.gwas_setup(n, 3, phi, XL, t, h2, o)
+        try:
+            gw.gwas_load_snps(ctx, M, XR, n)
+            out = torch.full((2, t, M), float("nan"), dtype=torch.float32, device=dev)
+            assert gw.gwas_solve(ctx, Y, 0, M, out) == gw.GWAS_OK
+            outs[prec] = out.double()
+        finally:
+            gw.gwas_destroy(ctx)
+    (bm, sm), (b64, s64) = outs[gw.GWAS_MIXED], outs[gw.GWAS_FP64]
+    assert bool(torch.isfinite(bm).all()) and bool(torch.isfinite(sm).all())
+    err_b = ((bm - b64).abs() / torch.maximum(b64.abs(), s64)).max().item()
+    err_se = ((sm - s64).abs() / s64).max().item()
+    assert err_b <= TOL and err_se <= TOL, (err_b, err_se)
+
+
 def test_sampled_pairs_at_full_mixed_workload(gw):
     """n=1000, p=4, m=1,000,000, t=10,000 on the device; the oracle checks sampled pairs."""
     torch = pytest.importorskip("torch")
