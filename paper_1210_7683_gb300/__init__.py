@@ -148,6 +148,34 @@ def _addr(x, dtype, shape=None, name="array"):
     raise TypeError(f"{name}: expected a numpy array or a torch tensor")
 
 
+# context address -> (n, p, t, output mode): the sizes the binding checks arrays against.  The
+# C calls take bare pointers and trust the caller for sizes; from Python the array sizes are
+# known, so an array too small for what a call reads or writes is refused before the call.
+_CTX = {}
+
+
+def _key(ctx):
+    return getattr(ctx, "value", ctx)
+
+
+def _nbytes(x):
+    if isinstance(x, np.ndarray):
+        return x.nbytes
+    if hasattr(x, "data_ptr"):
+        return x.numel() * x.element_size()
+    return None
+
+
+def _need(x, nbytes, name):
+    have = _nbytes(x)
+    if have is not None and have < nbytes:
+        raise ValueError(f"{name}: {have} bytes, the call needs {nbytes}")
+
+
+def _out_pair_bytes(p, output):
+    return 8 if output == GWAS_OUT_LAST_SE else 8 * p
+
+
 def _check(rc: int, ctx=None, allow=()):
     if rc != GWAS_OK and rc not in allow:
         raise GwasError(rc, lib.gwas_last_error(ctx).decode())
@@ -194,12 +222,16 @@ def gwas_setup(n, pm1, phi, XL, t, h2, opts: gwas_opts | None = None):
                         _addr(XL, np.float64, (pm1, n), "XL") if pm1 > 0 else None, t,
                         _addr(h2, np.float64, (t,), "h2"), C.byref(opts) if opts is not None else None)
     _check(rc, None)
+    _CTX[_key(ctx)] = (int(n), int(pm1) + 1, int(t), opts.output if opts is not None else GWAS_OUT_LAST_SE)
     return ctx
 
 
 def gwas_load_snps(ctx, m, XR, n=None):
     """XR: (m, n) int8, SNP-major."""
     shape = None if n is None else (m, n)
+    info = _CTX.get(_key(ctx))
+    if info is not None:
+        _need(XR, int(m) * info[0], "XR")
     return _check(lib.gwas_load_snps(ctx, m, _addr(XR, np.int8, shape, "XR")), ctx)
 
 
@@ -208,6 +240,11 @@ def gwas_solve(ctx, Y, i0, i1, out):
 
     Returns GWAS_OK or GWAS_ERR_SINGULAR_PAIRS (a warning); raises on errors.
     """
+    info = _CTX.get(_key(ctx))
+    if info is not None:
+        n, p, t, output = info
+        _need(Y, 8 * t * n, "Y")
+        _need(out, _out_pair_bytes(p, output) * t * max(int(i1) - int(i0), 0), "out")
     yv = _addr(Y, np.float64, None, "Y")
     dt = np.float64 if getattr(out, "dtype", None) in (np.float64, getattr(_torch(), "float64", None)) else np.float32
     return _check(lib.gwas_solve(ctx, yv, int(i0), int(i1), _addr(out, dt, None, "out")), ctx,
@@ -244,6 +281,11 @@ def gwas_solve_ooc(ctx, m, XR, slab, Y, block_traits, buf0, buf1, fn, n=None):
 def gwas_submit(ctx, Y, tk, h2k, i0, i1, out) -> int:
     """Queue a serving request (see include/gwas.h); returns its id."""
     rid = C.c_uint64()
+    info = _CTX.get(_key(ctx))
+    if info is not None:
+        n, p, _, output = info
+        _need(Y, 8 * int(tk) * n, "Y")
+        _need(out, _out_pair_bytes(p, output) * int(tk) * max(int(i1) - int(i0), 0), "out")
     dt = np.float64 if getattr(out, "dtype", None) in (np.float64, getattr(_torch(), "float64", None)) else np.float32
     _check(lib.gwas_submit(ctx, _addr(Y, np.float64, None, "Y"), int(tk), _addr(h2k, np.float64, (tk,), "h2k"),
                            int(i0), int(i1), _addr(out, dt, None, "out"), C.byref(rid)), ctx)
@@ -320,6 +362,7 @@ def gwas_last_error(ctx=None) -> str:
 
 
 def gwas_destroy(ctx) -> None:
+    _CTX.pop(_key(ctx), None)
     lib.gwas_destroy(ctx)
 
 

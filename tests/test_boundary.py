@@ -73,3 +73,31 @@ def test_argument_errors_without_gpu(libpath):
     assert lib.gwas_tune_shape(None, shape) == 1
     lib.gwas_serve_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     assert lib.gwas_serve_stats(None, None, None) == 1
+
+
+def test_binding_refuses_arrays_too_small_for_the_call(monkeypatch):
+    # the binding records each context's n, p, t and output mode at setup and refuses an array
+    # smaller than what a call reads or writes, before the C call (which trusts pointers)
+    import numpy as np
+    import paper_1210_7683_gb300 as g
+    fake = 0x5EED
+    n, p, t = 100, 4, 7
+    monkeypatch.setitem(g._CTX, fake, (n, p, t, g.GWAS_OUT_LAST_SE))
+    Y = np.zeros((t, n))
+    cases = [
+        lambda: g.gwas_solve(fake, Y, 0, 10, np.zeros((2, t, 9), np.float32)),      # one SNP short
+        lambda: g.gwas_solve(fake, Y[:6], 0, 10, np.zeros((2, t, 10), np.float32)),  # one trait short
+        lambda: g.gwas_solve(fake, Y, 5, 20, np.zeros((2, t, 10), np.float32)),     # range wider than out
+        lambda: g.gwas_load_snps(fake, 50, np.zeros((49, n), np.int8)),
+        lambda: g.gwas_submit(fake, np.zeros((3, n)), 4, np.zeros(4), 0, 8, np.zeros((2, 4, 8), np.float32)),
+        lambda: g.gwas_submit(fake, np.zeros((4, n)), 4, np.zeros(4), 0, 8, np.zeros((2, 4, 7), np.float32)),
+    ]
+    for call in cases:
+        with pytest.raises(ValueError):
+            call()
+    # full coefficient vectors: p doubles per pair, so a float32 array of the LAST_SE size is short
+    monkeypatch.setitem(g._CTX, fake, (n, p, t, g.GWAS_OUT_FULL_B))
+    with pytest.raises(ValueError):
+        g.gwas_solve(fake, Y, 0, 10, np.zeros((2, t, 10), np.float32))
+    with pytest.raises(ValueError):
+        g.gwas_solve(fake, Y, 0, 10, np.zeros((t, 10, p - 1)))
