@@ -253,8 +253,7 @@ GWAS_API int64_t gwas_kernel_launches(const gwas_ctx* ctx);
  *   best_ms   out (may be NULL): device time of one solve of the sample with the chosen shape
  *
  * Candidates: the one-CTA shape for every p; for p = 4 also the one-CTA shape with 8
- * epilogue warps, the CTA pair and the 1x2, 2x1 and 2x2 multicast clusters; each with 8, 16
- * or 32 SNP tiles per traversal group.  The
+ * epilogue warps and the CTA pair; each with 8, 16 or 32 SNP tiles per traversal group.  The
  * fastest is kept unless the default shape is within 2 % of it.  The context uses the choice
  * from then on, and it is written to opts.tune_cache when that was given.  Results do not
  * depend on the shape beyond rounding.  Mixed precision only (GWAS_ERR_UNSUPPORTED
@@ -267,7 +266,8 @@ GWAS_API int gwas_autotune(gwas_ctx* ctx, const double* Y, int t_sample, int64_t
  *
  * Developer overrides, read from the environment at each launch (they take precedence over
  * the tuned shape; for measurements, not for production use):
- *   GWAS_FUSED_SHAPE="CSxCTxEPW[xPAIR]"  launch shape at p = 4 (e.g. "2x1x16x1", the CTA pair)
+ *   GWAS_FUSED_SHAPE="CSxCTxEPW[xPAIR]"  launch shape at p = 4: "1x1x16" (default), "1x1x8" or
+ *                                         "2x1x16x1" (the CTA pair); other values are ignored
  *   GWAS_FUSED_GROUP=<k>                  SNP tiles per traversal group
  *   GWAS_SERVE_SLOTS=<k>, GWAS_SERVE_ROUND=<k>  serving arena trait-tile slots and units per round
  *   GWAS_HOST_OUTPUT=staged               gwas_solve copies page-locked host outputs through device

@@ -1,6 +1,6 @@
 // Launches of the fused contraction + Schur solve kernel (fused_impl.cuh) for 0 <= p - 1 <= 7,
-// with the optional cluster and CTA-pair shapes of p = 4; 8 <= p - 1 <= 19 is instantiated
-// in fused_wide.cu.
+// with the optional 8-epilogue-warp and CTA-pair shapes of p = 4; 8 <= p - 1 <= 19 is
+// instantiated in fused_wide.cu.
 #include "fused_impl.cuh"
 
 namespace {
@@ -10,7 +10,8 @@ struct Shape {
 };
 
 // The context's kernel shape (autotuned or default).  Shapes other than 1x1x16 exist for q = 3
-// only; every other q runs 1x1x16.  GWAS_FUSED_SHAPE="CSxCTxEPW[xPAIR]" overrides it (q = 3).
+// only (1x1x8 and the CTA pair 2x1x16x1); every other q runs 1x1x16.
+// GWAS_FUSED_SHAPE="CSxCTxEPW[xPAIR]" overrides it (q = 3) when it names one of those shapes.
 Shape shape_of(const gwas_ctx* c, int q) {
   Shape sh{1, 1, 16, 0};
   if (q != 3) return sh;
@@ -18,7 +19,7 @@ Shape shape_of(const gwas_ctx* c, int q) {
   if (const char* e = getenv("GWAS_FUSED_SHAPE")) {
     int cs = 0, ct = 0, epw = 0, pr = 0;
     const int k = sscanf(e, "%dx%dx%dx%d", &cs, &ct, &epw, &pr);
-    if (k >= 3) sh = {cs, ct, epw, k == 4 ? pr : 0};
+    if (k >= 3 && fused_shape_supported(q, cs, ct, epw, k == 4 ? pr : 0)) sh = {cs, ct, epw, k == 4 ? pr : 0};
   }
   return sh;
 }
@@ -31,10 +32,9 @@ int fused_pair_layout(const gwas_ctx* c, int q) { return shape_of(c, q).pair; }
 
 bool fused_shape_supported(int q, int cs, int ct, int epw, int pair) {
   if (cs == 1 && ct == 1 && epw == 16 && !pair) return true;
-  if (q == 3 && cs == 1 && ct == 1 && epw == 8 && !pair) return true;
-  if (q != 3 || epw != 16) return false;
-  if (pair) return cs == 2 && ct == 1;
-  return (cs == 1 && ct == 2) || (cs == 2 && ct == 1) || (cs == 2 && ct == 2);
+  if (q != 3) return false;
+  if (cs == 1 && ct == 1 && epw == 8 && !pair) return true;
+  return cs == 2 && ct == 1 && epw == 16 && pair == 1;
 }
 
 int launch_fused(gwas_ctx* c, int q, const FusedArgs& args, const __nv_bfloat16* G, const __nv_bfloat16* A2,
@@ -51,28 +51,14 @@ int launch_fused(gwas_ctx* c, int q, const FusedArgs& args, const __nv_bfloat16*
     maps_ok = make_bf16_map(&mg, G, a.mpad, a.Kpad, BM, BK) && make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM, BK) &&
               make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * c1_rows(3), a.Kpad, PC1_ROWS, BK) &&
               make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * c2_alloc(3), a.Kpad, PC2_ROWS, BK);
-  else if (sh.cs == 1 && sh.ct == 1)
-    maps_ok = make_big_maps(q, &mg, &ma, &m1, &m2, a, G, A2, B1, B2, ttiles_pad);
   else
-    maps_ok = make_bf16_map(&mg, G, a.mpad, a.Kpad, BM / sh.ct, BK) &&
-              make_bf16_map(&ma, A2, 3ull * a.mpad, a.Kpad, BM / sh.ct, BK) &&
-              make_bf16_map(&m1, B1, (uint64_t)ttiles_pad * c1_rows(3), a.Kpad, BBOX, BK) &&
-              make_bf16_map(&m2, B2, (uint64_t)ttiles_pad * c2_rows(3), a.Kpad, BBOX, BK);
+    maps_ok = make_big_maps(q, &mg, &ma, &m1, &m2, a, G, A2, B1, B2, ttiles_pad);
   if (!maps_ok) return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
-  if (sh.cs == 1 && sh.ct == 1 && sh.epw == 16 && !sh.pair) {
-    Q_DISPATCH(q, return launch_shape<1, 1, 16, false, false, Q>(c, a, mg, ma, m1, m2));
-  }
-  // optional cluster shapes (q = 3): TMA multicast of shared operands, or the CTA pair
-#define GWAS_SHAPE(CS, CT, EPW) \
-  if (sh.cs == CS && sh.ct == CT && sh.epw == EPW && !sh.pair) return launch_shape<CS, CT, EPW, false, false, 3>(c, a, mg, ma, m1, m2);
-  GWAS_SHAPE(1, 1, 8)   // 8 epilogue warps of 16 traits each: fewer warps beside the MMA issuer
-  GWAS_SHAPE(1, 2, 16)
-  GWAS_SHAPE(2, 1, 16)
-  GWAS_SHAPE(2, 2, 16)
-  if (sh.cs == 2 && sh.ct == 1 && sh.epw == 16 && sh.pair)
-    return launch_shape<2, 1, 16, false, true, 3>(c, a, mg, ma, m1, m2);
-#undef GWAS_SHAPE
-  return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: cluster shape not instantiated");
+  if (sh.pair) return launch_shape<16, false, true, 3>(c, a, mg, ma, m1, m2);
+  // 8 epilogue warps of 16 traits each (q = 3): fewer warps beside the MMA issuer
+  if (sh.epw == 8) return launch_shape<8, false, false, 3>(c, a, mg, ma, m1, m2);
+  Q_DISPATCH(q, return launch_shape<16, false, false, Q>(c, a, mg, ma, m1, m2));
+  return GWAS_OK;
 }
 
 int launch_fused_serve(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
@@ -83,6 +69,6 @@ int launch_fused_serve(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat
   CUtensorMap mg, ma, m1, m2;
   if (!make_big_maps(q, &mg, &ma, &m1, &m2, a, G, A2, B1, B2, b_tiles))
     return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
-  Q_DISPATCH(q, return launch_shape<1, 1, 16, true, false, Q>(c, a, mg, ma, m1, m2));
+  Q_DISPATCH(q, return launch_shape<16, true, false, Q>(c, a, mg, ma, m1, m2));
   return GWAS_OK;
 }

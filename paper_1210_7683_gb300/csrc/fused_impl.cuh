@@ -18,11 +18,10 @@
 // lower levels go to separate accumulators, and the levels are recombined in the
 // epilogue.
 //
-// Work is split into tiles of 128 SNPs x TT traits (TT = 32 for p = 4).  A thread-block
-// cluster of CS x CT CTAs works on CS SNP tiles x CT trait tiles at once: the CTAs on
-// the same SNP tile share its genotype operands through TMA multicast (each loads 1/CT
-// of the rows for all of them), those on the same trait tile share the trait operands
-// (1/CS each), and every CTA releases a ring slot to all CTAs that write into it.
+// Work is split into tiles of 128 SNPs x TT traits (TT = 32 for p = 4), one CTA per tile,
+// or (the optional CTA-pair shape, p = 4) a pair of CTAs on two SNP tiles and one trait
+// tile issuing M = 256 MMAs (cta_group::2), each CTA loading its own SNP rows and half of
+// the trait rows.
 // TMEM columns of each CTA for p = 4:
 //   [0,128)   C1 level 0  (slice 1 of w, v1, v2, v3; 32 traits each)
 //   [128,256) C1 level 1  (slice 2)
@@ -51,7 +50,6 @@ namespace {
 constexpr int BM = 128, BK = 64;
 constexpr int ROWB = BK * 2;                         // bytes per operand row of a stage
 constexpr int G_BYTES = BM * ROWB;                   // 16 KB: one A tile
-constexpr int BBOX = 32;                             // rows per TMA box of the trait operands (cluster shapes)
 constexpr int SLOT = 64 * 1024;                      // one-CTA shapes: a ring slot holds either half-stage
 constexpr int SLOTS = 3;
 // half-stages of the one-CTA shapes: G + the C1 trait rows; the three x'^2 planes + the C2 trait rows
@@ -84,9 +82,9 @@ __host__ __device__ constexpr bool JPW_OK(int tt, int epw) { return epw % 4 == 0
 // the epilogue warps of a tile width: 16, or 8 for 8-trait tiles
 __host__ __device__ constexpr int epw_for(int q) { return mixed_tt(q) == 8 ? 8 : 16; }
 
-template <int CS, int CT>
+template <int CS>
 __device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us, int& ut) {
-  const int nss = (a.n_stiles + CS - 1) / CS, nst = (a.n_ttiles + CT - 1) / CT;
+  const int nss = (a.n_stiles + CS - 1) / CS, nst = a.n_ttiles;
   const int per_group = a.group * nst;
   const int g = u / per_group;
   const int w = u % per_group;
@@ -100,14 +98,12 @@ __device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us,
 // (cta_group::2); each holds its own 128 SNP rows and half of every MMA's trait rows (the
 // pair layout of the C2 operand, c2_alloc rows per tile), the leader (rank 0) issues the
 // MMAs, and both CTAs' loads complete on the leader's barriers.
-template <int CS, int CT, int EPW, bool SERVE, bool PAIR, int Q>
+template <int EPW, bool SERVE, bool PAIR, int Q>
 __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     fused_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapA2,
                  const __grid_constant__ CUtensorMap mapB1, const __grid_constant__ CUtensorMap mapB2, FusedArgs a) {
-  constexpr int NC = CS * CT;
-  constexpr int AROWS = BM / CT;                    // genotype rows this CTA loads per plane
-  static_assert(!PAIR || (CS == 2 && CT == 1 && !SERVE), "pair mode is a 2 x 1 cluster");
-  static_assert(NC == 1 || Q == 3, "cluster and pair shapes are built for q = 3");
+  constexpr int CS = PAIR ? 2 : 1;                  // SNP tiles per cluster (the CTA pair: 2)
+  static_assert(!PAIR || (!SERVE && Q == 3), "the pair shape is built for q = 3 outside serving");
   constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = mixed_tt(Q), CSTR = cst_stride(Q);
   constexpr int B1_ROWS = c1_rows(Q), B2_ROWS = c2_rows(Q), B2_ROWS_PAIR = c2_alloc(Q);
   constexpr int C2B = c1_groups(Q) * TT;            // first TMEM column of the C2 accumulators
@@ -121,15 +117,10 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   // TMA boxes of the C1 trait rows in the one-CTA shapes (at most 256 rows per box)
   constexpr int B1_NBOX = B1_ROWS <= 256 ? 1 : 2, B1_BOX = B1_ROWS / B1_NBOX;
   static_assert(N1 >= 0 && N1 <= 256 && N0 % 16 == 0 && N1 % 16 == 0 && B1_BOX % 8 == 0, "C1 geometry");
-  // multicast cluster shapes: each CTA loads 1/CS of the trait rows in 32-row boxes
-  constexpr int B1_BOXES = B1_ROWS / BBOX / CS, B2_BOXES = B2_ROWS / BBOX / CS;
-  static_assert(NC == 1 || (B1_ROWS % (BBOX * CS) == 0 && B2_ROWS % (BBOX * CS) == 0 && BM % (8 * CT) == 0),
-                "cluster shape");
   // One CTA per tile: every half-stage is three TMA boxes of 128 to 192 rows (the genotype
-  // tile and the C1 trait rows in two halves; the three x'^2 planes, stored next to one
-  // another, in two halves and the C2 trait rows).  The TMA unit pays a fixed cost per box
-  // of the order of 50 cycles, so the 32-row boxes of the cluster shapes cap the load rate.
-  constexpr bool BIG = CS == 1 && CT == 1 && !PAIR;
+  // tile and the C1 trait rows in one or two boxes; the three x'^2 planes, stored next to
+  // one another, in two halves and the C2 trait rows).  The TMA unit pays a fixed cost per
+  // box of the order of 50 cycles, so large boxes keep the load rate up.
   constexpr int NSL = PAIR ? PSLOTS : SLOTS, SLB = PAIR ? PSLOT : SLOT;  // ring slots and their size
   constexpr int NI = PAIR ? 3 : 2;                                        // ring items per K block
   extern __shared__ uint8_t smem_raw[];
@@ -143,25 +134,20 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   volatile int* abort = (volatile int*)(tslot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   uint32_t crank = 0, cid = blockIdx.x, ncl = gridDim.x;
-  if (NC > 1) {
+  if (PAIR) {
     crank = tc::cluster_ctarank();
     cid = tc::cluster_id_x();
     ncl = tc::cluster_count_x();
   }
-  const int sr = crank % CS, tr = crank / CS;
-  uint16_t maskA = 0, maskB = 0;   // CTAs sharing this CTA's genotype / trait operands
-#pragma unroll
-  for (int k = 0; k < CT; ++k) maskA |= (uint16_t)(1u << (sr + CS * k));
-#pragma unroll
-  for (int k = 0; k < CS; ++k) maskB |= (uint16_t)(1u << (CS * tr + k));
+  const int sr = (int)crank;       // this CTA's SNP tile within the cluster
   // serving: the round's work units (from device memory when the launch is a captured graph's)
   const int nsuper = SERVE ? (a.nunits_dev ? min(*a.nunits_dev, a.nunits) : a.nunits)
-                           : ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
+                           : ((a.n_stiles + CS - 1) / CS) * a.n_ttiles;
   const int nkb = a.Kpad / BK;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSL; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], PAIR ? 1 : CS + CT - 1);
+      tc::mbar_init(&empty[s], 1);
     }
     tc::mbar_init(acc_full, 1);
     tc::mbar_init(acc_empty, PAIR ? 2 * EPW : EPW);
@@ -174,7 +160,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   }
   tc::fence_before();
   __syncthreads();
-  if (NC > 1) tc::cluster_sync();
+  if (PAIR) tc::cluster_sync();
   tc::fence_after();
   const uint32_t tbase = *tslot;
   const bool leader = !PAIR || crank == 0;
@@ -192,20 +178,20 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         int row, tt;
         if (SERVE) {
           const int4 w = a.units[u];
-          row = w.x + tr * AROWS;
+          row = w.x;
           tt = w.y;
         } else {
           int us, ut;
-          super_coords<CS, CT>(u, a, us, ut);
-          row = (int)a.row0 + (us * CS + sr) * BM + tr * AROWS;
-          tt = ut * CT + tr;
-          if (BIG && u + (int)ncl < nsuper) {
+          super_coords<CS>(u, a, us, ut);
+          row = (int)a.row0 + (us * CS + sr) * BM;
+          tt = ut;
+          if (!PAIR && u + (int)ncl < nsuper) {
             // When the next unit starts a new trait tile, its first two K blocks of trait
             // operands are prefetched into L2: the 16 CTAs of a traversal group start that tile
             // together and would otherwise all wait on its first DRAM reads.  Measured at
             // p = 4, n = 1000: 285.6 -> 281.7 ms; prefetching 3, 4, 8 or 16 blocks was slower.
             int us2, ut2;
-            super_coords<CS, CT>(u + ncl, a, us2, ut2);
+            super_coords<CS>(u + ncl, a, us2, ut2);
             if (ut2 != ut) {
               constexpr int PREFETCH_KB = 2;
               const int kbe = PREFETCH_KB < nkb ? PREFETCH_KB : nkb;
@@ -239,48 +225,18 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               }
               continue;
             }
-            if (BIG) {
-              if (half == 0) {
-                tc::mbar_expect_tx(&full[s], H1_BYTES);
-                tc::tma_load_2d(buf, &mapG, &full[s], x, row);
-#pragma unroll
-                for (int b = 0; b < B1_NBOX; ++b)
-                  tc::tma_load_2d(buf + G_BYTES + b * B1_BOX * ROWB, &mapB1, &full[s], x, tt * B1_ROWS + b * B1_BOX);
-              } else {
-                const int y = (int)a2_row(0, row);
-                tc::mbar_expect_tx(&full[s], H2_BYTES);
-                tc::tma_load_2d(buf, &mapA2, &full[s], x, y);
-                tc::tma_load_2d(buf + 3 * BM / 2 * ROWB, &mapA2, &full[s], x, y + 3 * BM / 2);
-                tc::tma_load_2d(buf + 3 * G_BYTES, &mapB2, &full[s], x, tt * B2_ROWS);
-              }
-              continue;
-            }
             if (half == 0) {
               tc::mbar_expect_tx(&full[s], H1_BYTES);
-              if (CT > 1) tc::tma_load_2d_mc(buf + tr * AROWS * ROWB, &mapG, &full[s], x, row, maskA);
-              else tc::tma_load_2d(buf, &mapG, &full[s], x, row);
+              tc::tma_load_2d(buf, &mapG, &full[s], x, row);
 #pragma unroll
-              for (int q = 0; q < B1_BOXES; ++q) {
-                const int r = (sr * B1_BOXES + q) * BBOX;
-                uint8_t* dst = buf + G_BYTES + r * ROWB;
-                if (CS > 1) tc::tma_load_2d_mc(dst, &mapB1, &full[s], x, tt * B1_ROWS + r, maskB);
-                else tc::tma_load_2d(dst, &mapB1, &full[s], x, tt * B1_ROWS + r);
-              }
+              for (int b = 0; b < B1_NBOX; ++b)
+                tc::tma_load_2d(buf + G_BYTES + b * B1_BOX * ROWB, &mapB1, &full[s], x, tt * B1_ROWS + b * B1_BOX);
             } else {
+              const int y = (int)a2_row(0, row);
               tc::mbar_expect_tx(&full[s], H2_BYTES);
-#pragma unroll
-              for (int p = 0; p < 3; ++p) {
-                uint8_t* dst = buf + p * G_BYTES + tr * AROWS * ROWB;
-                if (CT > 1) tc::tma_load_2d_mc(dst, &mapA2, &full[s], x, (int)a2_row(p, row), maskA);
-                else tc::tma_load_2d(dst, &mapA2, &full[s], x, (int)a2_row(p, row));
-              }
-#pragma unroll
-              for (int q = 0; q < B2_BOXES; ++q) {
-                const int r = (sr * B2_BOXES + q) * BBOX;
-                uint8_t* dst = buf + 3 * G_BYTES + r * ROWB;
-                if (CS > 1) tc::tma_load_2d_mc(dst, &mapB2, &full[s], x, tt * B2_ROWS + r, maskB);
-                else tc::tma_load_2d(dst, &mapB2, &full[s], x, tt * B2_ROWS + r);
-              }
+              tc::tma_load_2d(buf, &mapA2, &full[s], x, y);
+              tc::tma_load_2d(buf + 3 * BM / 2 * ROWB, &mapA2, &full[s], x, y + 3 * BM / 2);
+              tc::tma_load_2d(buf + 3 * G_BYTES, &mapB2, &full[s], x, tt * B2_ROWS);
             }
           }
         }
@@ -353,7 +309,6 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       constexpr uint32_t idN0 = tc::idesc_bf16(BM, N0), idN1 = tc::idesc_bf16(BM, N1 > 0 ? N1 : 16);
       constexpr uint32_t id3 = tc::idesc_bf16(BM, 3 * TT + C2_OFF), id2 = tc::idesc_bf16(BM, 2 * TT);
       constexpr uint32_t id1 = tc::idesc_bf16(BM, TT + C2_OFF);
-      const uint16_t release = maskA | maskB;
       uint32_t h = 0, tcount = 0;
       bool ok = true;
       for (int u = cid; u < nsuper && ok; u += ncl, ++tcount) {
@@ -392,8 +347,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                              tc::sdesc_add(de, TT * ROWB + k * 32), id1, acc);
               }
             }
-            if (NC > 1) tc::mma_commit_mc(&empty[s], release);
-            else tc::mma_commit(&empty[s]);
+            tc::mma_commit(&empty[s]);
           }
         }
         if (ok) tc::mma_commit(acc_full);
@@ -426,8 +380,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         obeta = rd.beta; ose = rd.se; ob64 = rd.b64; sing_ctr = rd.singular;
       } else {
         int us, ut;
-        super_coords<CS, CT>(u, a, us, ut);
-        const int st = us * CS + sr, tt = ut * CT + tr;
+        super_coords<CS>(u, a, us, ut);
+        const int st = us * CS + sr, tt = ut;
         snp0 = a.row0 + (int64_t)st * BM; snp_lo = a.snp_lo; snp_end = a.row0 + a.nsnp; oi0 = a.i0; ldo = a.ldo; ntrait = a.ntrait;
         jbase = tt * TT; full_b = a.full_b; cst_tile = a.cst + (size_t)jbase * CSTR;
         obeta = a.out_beta; ose = a.out_se; ob64 = a.out_b64; sing_ctr = nullptr;
@@ -582,18 +536,18 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   }
   tc::fence_before();
   __syncthreads();
-  if (NC > 1) tc::cluster_sync();
+  if (PAIR) tc::cluster_sync();
   if (warp == 1) {
     if (PAIR) tc::tmem_dealloc_pair(tbase, TMEM_COLS);
     else tc::tmem_dealloc(tbase, TMEM_COLS);
   }
 }
 
-template <int CS, int CT, int EPW, bool SERVE, bool PAIR, int Q>
+template <int EPW, bool SERVE, bool PAIR, int Q>
 int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const CUtensorMap& ma,
                  const CUtensorMap& m1, const CUtensorMap& m2) {
-  constexpr int NC = CS * CT;
-  auto kern = fused_kernel<CS, CT, EPW, SERVE, PAIR, Q>;
+  constexpr int NC = PAIR ? 2 : 1;
+  auto kern = fused_kernel<EPW, SERVE, PAIR, Q>;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(PAIR, Q));
@@ -617,7 +571,7 @@ int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const C
   int maxc = 0;
   if (cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg) == cudaSuccess && maxc > 0) nclusters = maxc;
   cudaGetLastError();
-  const int nsuper = SERVE ? a.nunits : ((a.n_stiles + CS - 1) / CS) * ((a.n_ttiles + CT - 1) / CT);
+  const int nsuper = SERVE ? a.nunits : ((a.n_stiles + NC - 1) / NC) * a.n_ttiles;
   nclusters = std::min(nclusters, nsuper);
   if (a.max_ctas > 0) nclusters = std::max(1, std::min(nclusters, a.max_ctas / NC));
   cfg.gridDim = dim3(nclusters * NC);

@@ -12,9 +12,9 @@ int launch_fused_wide(gwas_ctx* c, int q, const FusedArgs& args, const __nv_bflo
   if (!make_big_maps(q, &mg, &ma, &m1, &m2, a, G, A2, B1, B2, b_tiles))
     return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
   if (serve) {
-    Q_DISPATCH_WIDE(q, return launch_shape<1, 1, epw_for(Q), true, false, Q>(c, a, mg, ma, m1, m2));
+    Q_DISPATCH_WIDE(q, return launch_shape<epw_for(Q), true, false, Q>(c, a, mg, ma, m1, m2));
   } else {
-    Q_DISPATCH_WIDE(q, return launch_shape<1, 1, epw_for(Q), false, false, Q>(c, a, mg, ma, m1, m2));
+    Q_DISPATCH_WIDE(q, return launch_shape<epw_for(Q), false, false, Q>(c, a, mg, ma, m1, m2));
   }
   return GWAS_OK;
 }

@@ -2,9 +2,8 @@
 // study, Section 5: the loop tiles are tuned empirically on the target machine).
 //
 // Candidates: the one-CTA shape (1 x 1 cluster, 16 epilogue warps) for every p; for p = 4 also
-// the one-CTA shape with 8 epilogue warps, the CTA pair (cta_group::2) and the multicast
-// clusters 1x2, 2x1, 2x2; each with 8, 16 or 32
-// SNP tiles per traversal group.  Every candidate solves the same sample of the grid (the first
+// the one-CTA shape with 8 epilogue warps and the CTA pair (cta_group::2); each with 8, 16 or
+// 32 SNP tiles per traversal group.  Every candidate solves the same sample of the grid (the first
 // SNPs and traits of the problem, device output) once untimed and twice timed with CUDA events;
 // the fastest wins, but the default shape is kept when it is within 2 % of it (a plateau, not a
 // noisy optimum).  The choice is stored in the context and, when opts.tune_cache names a file,
@@ -139,7 +138,7 @@ extern "C" int gwas_autotune(gwas_ctx* c, const double* Y, int t_sample, int64_t
   int rc = ctx_alloc(c, sizeof(float) * 2 * (size_t)ts * (size_t)ms, (void**)&out);
   if (rc) return rc;
   std::vector<gwas_ctx::FusedTune> cand;
-  const int shapes[6][4] = {{1, 1, 16, 0}, {1, 1, 8, 0}, {2, 1, 16, 1}, {1, 2, 16, 0}, {2, 1, 16, 0}, {2, 2, 16, 0}};
+  const int shapes[3][4] = {{1, 1, 16, 0}, {1, 1, 8, 0}, {2, 1, 16, 1}};
   for (const auto& sh : shapes)
     if (fused_shape_supported(c->pm1, sh[0], sh[1], sh[2], sh[3]))
       for (int g : {16, 8, 32}) cand.push_back({sh[0], sh[1], sh[2], sh[3], g});

@@ -1,7 +1,7 @@
 """Autotuner of the fused kernel's launch shape and its JSON cache: a tuned context and a
 context that reads the cache use the same shape and give the same results, a cached shape
 other than the default is applied (the CTA pair), and an entry naming a shape that is not
-built is ignored."""
+built (another p, or a multi-CTA cluster other than the pair) is ignored."""
 import json
 
 import numpy as np
@@ -72,6 +72,24 @@ def test_unbuilt_shape_in_the_cache_is_ignored(gw, tmp_path):
     out, shape, _ = solve(gw, P, opts)
     assert shape == DEFAULT
     b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    check(out, b, se)
+
+
+def test_cluster_shapes_without_a_kernel_are_ignored(gw, tmp_path, monkeypatch):
+    """Only the one-CTA shapes and the CTA pair are built: a cached or forced 1x2, 2x1 or 2x2
+    cluster shape (no such kernel exists) leaves the default shape in place."""
+    P = make_problem(192, 700, 36, seed=3034)
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    for cs, ct in ((1, 2), (2, 1), (2, 2)):
+        cache = tmp_path / f"tune_{cs}{ct}.json"
+        cache.write_text(json.dumps({"n=192,p=4,mode=mixed,t=2^5": {"cs": cs, "ct": ct, "epw": 16, "pair": 0,
+                                                                     "group": 8}}))
+        opts = gw.gwas_default_opts(precision=gw.GWAS_MIXED, output=gw.GWAS_OUT_LAST_SE, tune_cache=str(cache))
+        out, shape, _ = solve(gw, P, opts)
+        assert shape == DEFAULT
+        check(out, b, se)
+    monkeypatch.setenv("GWAS_FUSED_SHAPE", "2x2x16")
+    out, _, _ = solve(gw, P, gw.gwas_default_opts(precision=gw.GWAS_MIXED, output=gw.GWAS_OUT_LAST_SE))
     check(out, b, se)
 
 
