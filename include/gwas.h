@@ -294,23 +294,29 @@ GWAS_API void gwas_reset_timers(gwas_ctx* ctx);
  * scratch is a fixed 8 MiB device array inside the library, which every GPU
  * that loads the library keeps until the process exits.
  *
- * Inputs are the already-rotated quantities of Algorithm 5, all device pointers
- * on the current device:
+ * Inputs are already rotated by the eigenvectors Z of Phi = Z diag(lam) Z^T.
+ * Every array must be device memory of the current device (or managed memory);
+ * anything else (a host pointer, pinned or not, or another device's memory) is
+ * refused with GWAS_ERR_ARG before any device work:
  *   lam  n eigenvalues of Phi          XLt  [pm1][n] rows Z^T x_L,l
  *   Xt   [m][n] rows Z^T x_i (FP64)    Yt   [t][n] rows Z^T y_j
- *   h2   t heritabilities
+ *   h2   t heritabilities, each in [0, 1]
  * out: GWAS_OUT_FULL_B double[t][m][p]; GWAS_OUT_LAST_SE float beta[t][m], then
  * float se[t][m].  stream: cudaStream_t (NULL = legacy default stream); the call
  * returns after the stream has finished.  *singular (may be NULL) receives the
  * number of singular pairs.
  *
  * The scratch must hold t (p+1) n + t (pm1^2 + pm1 + 1) doubles plus 256 bytes:
- * larger requests return GWAS_ERR_UNSUPPORTED before any device work.  The first
- * call on a device looks up the array's device address (once per device, with
- * that device current); make that first call before any stream capture.  Every
- * call shares the one array and it keeps the last call's contents: calls that
- * overlap on the GPU race on it.  Returns GWAS_OK, GWAS_ERR_SINGULAR_PAIRS (a
- * warning), GWAS_ERR_ARG or GWAS_ERR_CUDA; gwas_last_error is not set.
+ * larger requests return GWAS_ERR_UNSUPPORTED before any device work.  The
+ * array's device address is looked up on every call with the current device, so
+ * a context torn down and created again (cudaDeviceReset) is handled.  The
+ * heritabilities are checked on the device before any result is written: h2
+ * outside [0, 1] returns GWAS_ERR_ARG, and a D_j = h2 lam + 1 - h2 with an entry
+ * <= 1e-12 of its largest returns GWAS_ERR_NOT_SPD (the check gwas_setup makes).
+ * Every call shares the one array and it keeps the last call's contents: calls
+ * that overlap on the GPU race on it.  Returns GWAS_OK, GWAS_ERR_SINGULAR_PAIRS
+ * (a warning), GWAS_ERR_ARG, GWAS_ERR_NOT_SPD, GWAS_ERR_UNSUPPORTED or
+ * GWAS_ERR_CUDA; gwas_last_error is not set.
  */
 GWAS_API int gwas_solve_fp64_noalloc(int n, int pm1, const double* lam, const double* XLt, const double* Xt,
                                      int64_t m, const double* Yt, const double* h2, int t, int output, void* out,

@@ -338,6 +338,13 @@ def gwas_solve_fp64_noalloc(n, pm1, lam, XLt, Xt, m, Yt, h2, t, output, out, str
     Returns (status, singular_pairs); raises GwasError on failures other than
     the singular-pairs warning.
     """
+    for name, a in (("lam", lam), ("XLt", XLt), ("Xt", Xt), ("Yt", Yt), ("h2", h2), ("out", out)):
+        if a is None and name == "XLt" and pm1 == 0:
+            continue
+        if not (hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)):
+            raise TypeError(f"{name}: gwas_solve_fp64_noalloc takes CUDA tensors only (device memory)")
+    p = int(pm1) + 1
+    _need(out, (8 * p if output == GWAS_OUT_FULL_B else 8) * int(t) * int(m), "out")
     sing = C.c_int64(0)
     dt = np.float64 if output == GWAS_OUT_FULL_B else np.float32
     rc = lib.gwas_solve_fp64_noalloc(n, pm1, _addr(lam, np.float64, (n,), "lam"),
