@@ -14,9 +14,15 @@ plain FP64 GPU path on a SNP sample of the same workload, the roofline of the
 fused contraction kernel, the CPU oracle on a bounded sample (cpu_baseline),
 and the error of sampled pairs against that oracle.
 
+Further legs, each on its workload's stated size: the FP64 path against the mixed path with
+the full coefficient vector returned (n = 1000, m = 1e5, t = 1000), the paper-scale shape
+(t = 1e5 in blocks of 5000 traits streamed to page-locked host buffers), the single-trait
+kernel, out-of-core genotype streaming and serving (2000 requests, Poisson arrivals).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun (N > 1) every rank solves its own SNP set (weak scaling, no
-collective on the data path); rank 0 prints the JSON line.
+Under torchrun (N > 1) the ranks share one problem of N * m SNPs: each generates, loads
+and solves only its own contiguous shard (weak scaling, no collective on the data path),
+sampled results are gathered to rank 0 to be checked, and rank 0 prints the JSON line.
 """
 from __future__ import annotations
 
@@ -82,7 +88,7 @@ def algorithmic_flops(n, p, pairs, form="gemm"):
     return float(per_pair) * pairs
 
 
-def pinned_host_array(shape, dtype, torch):
+def pinned_host_array(shape, dtype, torch, fallback=True):
     """A page-locked host array of exactly this size: anonymous memory advised to use huge
     pages, registered with the driver.  (torch's page-locked allocator rounds sizes up to a
     power of two, which pins 128 GB for the 80 GB result grid; registered memory on the
@@ -99,6 +105,8 @@ def pinned_host_array(shape, dtype, torch):
             return a, True
     except Exception:
         pass
+    if not fallback:
+        return None, False
     try:
         return torch.empty(shape, dtype=torch.float32).pin_memory(), False
     except RuntimeError:
@@ -189,8 +197,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-ooc", action="store_true", help="skip the out-of-core measurement")
     ap.add_argument("--no-t1", action="store_true", help="skip the single-trait measurement")
-    ap.add_argument("--serving-requests", type=int, default=400,
-                    help="requests of the serving run (the full serving workload has 2000; 0 skips it)")
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="requests of the serving run (the serving workload's 2000; 0 skips it)")
+    ap.add_argument("--no-c2", action="store_true", help="skip the FP64-vs-mixed full-b measurement")
+    ap.add_argument("--no-c5", action="store_true", help="skip the paper-scale streamed measurement")
     ap.add_argument("--serving-load", default="0.8,0.5,0.95",
                     help="offered loads as fractions of saturation, comma-separated; the first is the headline")
     return ap.parse_args()
@@ -258,11 +268,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_inputs(n, m, t, seed_offset=0):
-    from synth import BASE_SEED
-    seed = BASE_SEED + seed_offset
-    return {"phi": kinship(n), "XL": covariates(n, PM1), "h2": heritabilities(t), "XR": genotypes(n, m, seed),
-            "Y": phenotypes(n, t)}
+def make_inputs(n, m, t, rank=0, world=1):
+    """Inputs of `rank`: the shared Phi, X_L, h^2 and Y, and the rank's shard of the genotypes of
+    one problem of m * world SNPs.  Returns (inputs, (m_total, i0, i1))."""
+    from paper_1210_7683_gb300.sharding import weak_shard
+    m_total, i0, i1 = weak_shard(m, rank, world)
+    return ({"phi": kinship(n), "XL": covariates(n, PM1), "h2": heritabilities(t),
+             "XR": genotypes(n, m_total, i0=i0, i1=i1), "Y": phenotypes(n, t)}, (m_total, i0, i1))
 
 
 def step(g, opts, n, m, t, inp, out, phases=None):
@@ -344,7 +356,7 @@ def serving_run(g, torch, dev, local, count, loads, seed_offset=0):
             # arrives while the cap is reached waits on the client, and its latency counts
             # from its arrival, not from its submission
             t0 = time.perf_counter()
-            pending, lat, pairs = {}, [], 0
+            pending, lat, sizes, pairs = {}, [], [], 0
             k = 0
             while k < len(reqs) or pending:
                 now = time.perf_counter() - t0
@@ -364,22 +376,28 @@ def serving_run(g, torch, dev, local, count, loads, seed_offset=0):
                         ts, _, td = g.gwas_request_times(ctx, rid)
                         _, np_, late = pending.pop(rid)
                         lat.append(td - ts + late)
+                        sizes.append(np_)
                         pairs += np_
                 nxt = arrivals[k] - (time.perf_counter() - t0) if k < len(reqs) else 0.0
                 time.sleep(min(max(nxt, 0.0), 0.0005))
-            return time.perf_counter() - t0, np.array(lat), pairs
+            return time.perf_counter() - t0, np.array(lat), np.array(sizes, dtype=np.float64), pairs
 
-        span, _, total_pairs = run(np.zeros(len(reqs)))          # saturation: all at once
+        span, _, _, total_pairs = run(np.zeros(len(reqs)))       # saturation: all at once
         sat = total_pairs / span
         mean_pairs = total_pairs / len(reqs)
         sweep = []
         for load in loads:
             rate = load * sat / mean_pairs                        # requests per second
             gaps = np.random.default_rng(BASE_SEED + 9).exponential(1.0 / rate, len(reqs))
-            span2, lat, pairs2 = run(np.cumsum(gaps))
+            span2, lat, size, pairs2 = run(np.cumsum(gaps))
+            # slowdown: latency over the request's own service time at the saturated rate
+            slow = lat / (size / sat)
             sweep.append({"offered_load": load, "pairs_per_s": pairs2 / span2,
                           "p50_latency_s": float(np.percentile(lat, 50)),
-                          "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean())})
+                          "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
+                          "p99_over_p50": float(np.percentile(lat, 99) / np.percentile(lat, 50)),
+                          "p50_slowdown": float(np.percentile(slow, 50)), "p99_slowdown": float(np.percentile(slow, 99)),
+                          "p99_service_s": float(np.percentile(size, 99) / sat)})
     finally:
         g.gwas_destroy(ctx)
     head = sweep[0]
@@ -388,6 +406,127 @@ def serving_run(g, torch, dev, local, count, loads, seed_offset=0):
                         f"of saturation (other loads under load_sweep)",
             "saturated_pairs_per_s": sat, **head, "requests": len(reqs), "pairs": int(total_pairs),
             "load_sweep": sweep}
+
+
+def c2_run(g, torch, dev, local, stream):
+    """FP64 against mixed precision with the full coefficient vector returned: n = 1000, p = 4,
+    m = 1e5 SNPs, t = 1000 traits, double b[t][m][p] (3.2 GB) into device memory.  Each path's
+    gwas_solve is timed whole (wall clock; the call returns with its results complete), with
+    gwas_setup and gwas_load_snps reported beside it; the error of the mixed b against the FP64
+    b is taken over the whole grid, relative to max(|b|_inf, SE) per pair."""
+    n, m2, t2 = 1000, 100_000, 1000
+    host = {"phi": kinship(n), "XL": covariates(n, PM1), "h2": heritabilities(t2), "XR": genotypes(n, m2),
+            "Y": phenotypes(n, t2)}
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in host.items()}
+    res, outs = {}, {}
+    for name, prec in (("fp64", g.GWAS_FP64), ("mixed", g.GWAS_MIXED)):
+        o = g.gwas_default_opts(precision=prec, output=g.GWAS_OUT_FULL_B, device=local, stream=stream.cuda_stream)
+        out = torch.empty((t2, m2, PM1 + 1), dtype=torch.float64, device=dev)
+        runs = []
+        for rep in range(3):  # the first is a warm-up
+            t0 = time.perf_counter()
+            ctx = g.gwas_setup(n, PM1, d["phi"], d["XL"], t2, d["h2"], o)
+            try:
+                t1 = time.perf_counter()
+                g.gwas_load_snps(ctx, m2, d["XR"], n)
+                t2_ = time.perf_counter()
+                g.gwas_solve(ctx, d["Y"], 0, m2, out)
+                t3 = time.perf_counter()
+            finally:
+                g.gwas_destroy(ctx)
+            if rep:
+                runs.append({"setup": (t1 - t0) * 1e3, "load_snps": (t2_ - t1) * 1e3, "solve": (t3 - t2_) * 1e3})
+        solve_ms = statistics.median(r["solve"] for r in runs)
+        step_ms = statistics.median(r["setup"] + r["load_snps"] + r["solve"] for r in runs)
+        res[name] = {"value": m2 * t2 / (solve_ms / 1e3), "unit": "pairs/s", "solve_ms": solve_ms,
+                     "step_ms": step_ms, "step_value": m2 * t2 / (step_ms / 1e3),
+                     "phase_ms": {k: round(statistics.median(r[k] for r in runs), 2) for k in runs[0]}}
+        outs[name] = out
+    # the FP64 standard errors for the error metric
+    se = torch.empty((2, t2, m2), dtype=torch.float32, device=dev)
+    o = g.gwas_default_opts(precision=g.GWAS_FP64, output=g.GWAS_OUT_LAST_SE, device=local, stream=stream.cuda_stream)
+    ctx = g.gwas_setup(n, PM1, d["phi"], d["XL"], t2, d["h2"], o)
+    try:
+        g.gwas_load_snps(ctx, m2, d["XR"], n)
+        g.gwas_solve(ctx, d["Y"], 0, m2, se)
+    finally:
+        g.gwas_destroy(ctx)
+    b64, bmx = outs["fp64"], outs["mixed"]
+    num = (bmx - b64).abs().amax(dim=-1)
+    den = torch.maximum(b64.abs().amax(dim=-1), se[1].double())
+    rel = num / den
+    torch.cuda.synchronize()
+    return {"workload": f"n={n} p=4 m={m2} t={t2}, full b (double[t][m][p], {8 * (PM1 + 1) * m2 * t2 / 1e9:.1f} GB) "
+                        f"into device memory, each path's whole gwas_solve",
+            "fp64": res["fp64"], "mixed": res["mixed"], "mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
+            "err_mixed_vs_fp64": {"max": float(rel.max()), "median": float(rel.median()),
+                                  "definition": "||b_mixed - b_fp64||_inf / max(||b_fp64||_inf, SE_fp64) per pair, "
+                                                "over all pairs"}}
+
+
+def c5_run(g, torch, dev, local, stream, tune_path, XR_dev, phi, XL):
+    """The paper-scale shape (the out-of-core example of Section 4): n = 1000, p = 4, m = 1e6
+    SNPs resident, t = 1e5 traits in blocks of 5000, the SNP coefficient and its SE of every
+    block streamed to one of two page-locked host buffers (40 GB each) by gwas_solve_stream
+    while the next block computes.  Reports pairs/s of the whole gwas_solve_stream, the floor
+    the device -> host link sets (800 GB / measured link rate) and the share of it achieved."""
+    n, m, t5, blk = 1000, 1_000_000, 100_000, 5000
+    Y5, h5 = phenotypes(n, t5), heritabilities(t5)
+    Yd = torch.from_numpy(Y5).to(dev)
+    bufs = []
+    for _ in range(2):
+        b, reg = pinned_host_array((2, blk, m), np.float32, torch, fallback=False)
+        if b is None:
+            for x in bufs:
+                torch.cuda.cudart().cudaHostUnregister(x.ctypes.data)
+            return {"skipped": "could not allocate two 40 GB page-locked host buffers"}
+        bufs.append(b)
+    samples = {}
+
+    def on_block(j0, nb, ptr):
+        buf = bufs[0] if ptr == bufs[0].ctypes.data else bufs[1]
+        flat = buf.reshape(-1)
+        beta = flat[:nb * m].reshape(nb, m)
+        se = flat[nb * m:2 * nb * m].reshape(nb, m)
+        samples[j0] = (beta[:4, :64].copy(), se[:4, :64].copy())
+
+    o = g.gwas_default_opts(precision=g.GWAS_MIXED, output=g.GWAS_OUT_LAST_SE, device=local,
+                            stream=stream.cuda_stream, tune_cache=tune_path)
+    t0 = time.perf_counter()
+    ctx = g.gwas_setup(n, PM1, phi, XL, t5, torch.from_numpy(h5).to(dev), o)
+    try:
+        t1 = time.perf_counter()
+        g.gwas_load_snps(ctx, m, XR_dev, n)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        g.gwas_solve_stream(ctx, Yd, 0, m, blk, bufs[0], bufs[1], on_block)
+        t3 = time.perf_counter()
+    finally:
+        g.gwas_destroy(ctx)
+    link = host_link_probe(torch, dev, bufs[0])
+    for b in bufs:
+        torch.cuda.cudart().cudaHostUnregister(b.ctypes.data)
+    del bufs
+    # sampled pairs of every block against the oracle: SNPs [0, 64) x the block's first 4 traits
+    from oracle import EigOracle
+    js = np.array(sorted(j0 + k for j0 in samples for k in range(4)))
+    bo, so = EigOracle(phi.cpu().numpy(), XL.cpu().numpy()).solve(XR_dev[:64].cpu().numpy(), Y5[js], h5[js])
+    got_b = np.concatenate([samples[j0][0] for j0 in sorted(samples)]).T.astype(np.float64)
+    got_s = np.concatenate([samples[j0][1] for j0 in sorted(samples)]).T.astype(np.float64)
+    bl = bo[..., -1]
+    err = float(np.max(np.abs(got_b - bl) / np.maximum(np.abs(bl), so)))
+    solve_ms = (t3 - t2) * 1e3
+    d2h = 8.0 * m * t5
+    floor_ms = d2h / (statistics.mean(link) * 1e9) * 1e3
+    return {"workload": f"n={n} p=4 m={m} t={t5}, blocks of {blk} traits, beta+SE fp32 of each block streamed to "
+                        f"two page-locked host buffers of {2 * 4 * blk * m / 1e9:.0f} GB",
+            "value": m * t5 / (solve_ms / 1e3), "unit": "pairs/s", "solve_stream_ms": solve_ms,
+            "setup_ms": (t1 - t0) * 1e3, "load_snps_ms": (t2 - t1) * 1e3,
+            "blocks": len(samples), "d2h_bytes": d2h, "link_d2h_gbs": link,
+            "link_floor_ms": floor_ms, "link_floor_frac": floor_ms / solve_ms,
+            "err": {"max": err, "se_max": float(np.max(np.abs(got_s - so) / so)), "pairs": int(bl.size),
+                    "sample": "SNPs [0,64) x the first 4 traits of every block, against the oracle"},
+            "paper_context": "the paper reports about 12 h for this shape on 40 Xeon cores (FP64, from disk)"}
 
 
 def run_reference(args, rank, world):
@@ -449,7 +588,7 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    inp_h = make_inputs(n, m, t, seed_offset=rank)
+    inp_h, (m_total, s_i0, s_i1) = make_inputs(n, m, t, rank, world)
     inp_d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in inp_h.items()}
     out = torch.empty((2, t, m), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -497,7 +636,8 @@ def main():
     barrier()
     clk = clocks.stop()
     last_sample = out[:, :128, :8192].cpu().numpy()
-    from paper_1210_7683_gb300.sharding import max_over_ranks, weak_scaling_rate
+    shard_sample = out[:, :64, :64].cpu().numpy()   # gathered from every rank under torchrun
+    from paper_1210_7683_gb300.sharding import gather_blocks, max_over_ranks, weak_scaling_rate
     ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
     marks = [ev0] + step_ev
     per_step = [marks[i].elapsed_time(marks[i + 1]) for i in range(len(step_ev))]
@@ -547,6 +687,8 @@ def main():
               "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
               "config": {"workload": f"GLS grid n={n} p=4 m={m} t={t}, mixed precision, beta+SE fp32 out",
                          "n": n, "p": 4, "m": m, "t": t, "parallelism": f"snp-shard x{world}",
+                         "problem": f"one grid of {m_total} SNPs x {t} traits; this rank's shard [{s_i0},{s_i1})"
+                                    if world > 1 else "one grid",
                          "l2": "inputs larger than L2 (1 GB genotypes, 8 GB resident operand slices per step)"},
               "step_ms": {"median": statistics.median(per_step), "min": min(per_step), "max": max(per_step)},
               "roofline": roofline, "rotation_roofline": rot, "autotune": tune, "gpu_launches": launches, "clocks": clk,
@@ -625,13 +767,18 @@ def main():
                                          stream=stream.cuda_stream, trait_block=0, tune_cache=tune_path)
             step(g, opts_h, n, m, t, pin, hout)
             barrier()
-            e_steps = max(1, min(args.steps, 3))
+            # at least 5 timed steps, each bracketed by barriers; per step the slowest rank's wall
+            # time, and the median of those
+            e_steps = max(5, min(args.steps, 10))
             phases = {}
-            t0 = time.perf_counter()
+            e_times = []
             for _ in range(e_steps):
+                barrier()
+                t0 = time.perf_counter()
                 step(g, opts_h, n, m, t, pin, hout, phases)
-            barrier()
-            e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
+                barrier()
+                e_times.append(max_over_ranks((time.perf_counter() - t0) * 1e3))
+            e_ms = statistics.median(e_times)
             link = {"d2h_gbs": host_link_probe(torch, dev, hout),
                     "hugepage_frac": hugepage_fraction(hout.ctypes.data, d2h) if registered else None,
                     "numa_pages": numa_pages(hout.ctypes.data, d2h) if registered else None,
@@ -641,8 +788,11 @@ def main():
                             "d2h_bytes / d2h_gbs"}
             result["e2e"] = {"value": world * pairs / (e_ms / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                              "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": e_steps, "host_link": link,
+                             "step_ms": {"median": e_ms, "min": min(e_times), "max": max(e_times),
+                                         "all": [round(x, 1) for x in e_times]},
                              "phase_ms": phases,
-                             "note": out_note + "; inputs from pinned host memory; wall clock around the C calls"}
+                             "note": out_note + "; inputs from pinned host memory; wall clock around the C calls; "
+                                                "value from the median step"}
             if registered:
                 torch.cuda.cudart().cudaHostUnregister(hout.ctypes.data)
             del hout
@@ -681,13 +831,23 @@ def main():
                                      "piece downloaded to pinned host buffers; wall clock"}
             del bufs
 
+    del out
+    torch.cuda.empty_cache()
+    # ---------------------------------------------------------------- FP64 vs mixed, full b (n=1000, m=1e5, t=1000)
+    if not args.no_c2 and rank == 0:
+        result["fp64_vs_mixed_full_b"] = c2_run(g, torch, dev, local, stream)
+        torch.cuda.empty_cache()
+    # ---------------------------------------------------------------- paper scale: t=1e5 streamed to host
+    if not args.no_c5 and not args.no_e2e and rank == 0 and m == M_SNP and n == N_IND:
+        result["paper_scale"] = c5_run(g, torch, dev, local, stream, tune_path, inp_d["XR"], inp_d["phi"], inp_d["XL"])
+        torch.cuda.empty_cache()
+
     # ---------------------------------------------------------------- serving (continuous batching)
     if args.serving_requests > 0 and rank == 0:
-        del inp_d, out
+        del inp_d
         torch.cuda.empty_cache()
         result["serving"] = serving_run(g, torch, dev, local, args.serving_requests,
                                         [float(x) for x in args.serving_load.split(",")])
-        out = None
 
     # ---------------------------------------------------------------- CPU oracle and sampled error
     if not args.no_cpu and rank == 0:
@@ -702,6 +862,20 @@ def main():
                          "definition": "|beta - beta*| / max(|beta*|, SE*) over the cpu_baseline sample",
                          "pairs": int(err.size)}
     if world > 1:
+        # the first 64 SNPs x 64 traits of every rank's shard, gathered on rank 0 and checked
+        # against the oracle at those SNPs of the one problem
+        blocks = gather_blocks(shard_sample, s_i0)
+        if rank == 0 and not args.no_cpu:
+            from oracle import EigOracle
+            o = EigOracle(inp_h["phi"], inp_h["XL"])
+            worst = 0.0
+            for b0, b1, blk in blocks:
+                xr = genotypes(n, m_total, i0=b0, i1=b1)
+                bo, so = o.solve(xr, inp_h["Y"][:64], inp_h["h2"][:64])
+                bl = bo[..., -1].T
+                worst = max(worst, float(np.max(np.abs(blk[0] - bl) / np.maximum(np.abs(bl), so.T))))
+            result["shard_err"] = {"max": worst, "ranks": len(blocks),
+                                   "sample": "SNPs [i0, i0+64) of every rank's shard x traits [0, 64)"}
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(result), flush=True)

@@ -6,9 +6,12 @@
 //      operand arena, whose size is the admission budget in HBM;
 //   2. prepares the per-trait operands of the newly admitted requests (rotation of
 //      their traits, per-trait algebra, back-rotation, slicing) into their arena slots;
-//   3. builds a list of work units (one SNP tile x one trait tile of one request),
-//      giving every active request an equal share of the round, and runs the
-//      persistent fused kernel over the list;
+//   3. builds a list of work units (one SNP tile x one trait tile of one request) and
+//      runs the persistent fused kernel over the list.  The round is shared by remaining
+//      size: every active request first gets a floor of round_units / (4 x active) units
+//      (so that no request starves), then the rest of the round goes to the requests
+//      with the fewest remaining units first, so a small request finishes in the round
+//      after its arrival however large the requests beside it are;
 //   4. marks the requests whose last unit ran as done and frees their slots.
 // Requests that arrive while a round runs join the next one, so work of different
 // requests overlaps on the device.  The arithmetic of a pair does not depend on which
@@ -261,29 +264,37 @@ void serve_loop(gwas_ctx* c) {
       fail_all(c, S, rc, c->err);
       return;
     }
-    // 3. round: equal shares for the active requests, the remainder to the oldest
+    // 3. round: a floor share for every active request, then the rest by fewest remaining units
     int nu = 0;
     std::vector<std::pair<uint64_t, int64_t>> took;
     {
       std::lock_guard<std::mutex> lk(S->mu);
       const int nact = (int)S->active.size();
       if (nact == 0) continue;
-      const int64_t quota = std::max<int64_t>(1, S->round_units / nact);
+      const int64_t floor_share = std::max<int64_t>(1, S->round_units / (4 * (int64_t)nact));
+      // admission order within equal remaining work (stable sort)
+      std::vector<uint64_t> order(S->active);
+      std::stable_sort(order.begin(), order.end(), [&](uint64_t a, uint64_t b) {
+        const Request &ra = S->reqs[a], &rb = S->reqs[b];
+        return ra.units - ra.next_unit < rb.units - rb.next_unit;
+      });
+      std::map<uint64_t, int64_t> taken;
       for (int pass = 0; pass < 2 && nu < S->round_units; ++pass) {
-        for (uint64_t id : S->active) {
+        for (uint64_t id : order) {
           Request& r = S->reqs[id];
-          const int64_t want = pass == 0 ? quota : S->round_units - nu;
+          const int64_t want = pass == 0 ? floor_share : S->round_units - nu;
           const int64_t take = std::min<int64_t>({want, r.units - r.next_unit, (int64_t)S->round_units - nu});
           for (int64_t u = 0; u < take; ++u) {
             int st, tt;
             unit_coords(r, r.next_unit + u, st, tt);
             S->h_units[nu++] = make_int4((int)((r.i0 & ~(int64_t)127) + (int64_t)st * 128), r.slots[tt], r.desc, tt);
           }
-          if (take > 0) took.push_back({id, take});
+          if (take > 0) taken[id] += take;
           r.next_unit += take;
           if (nu >= S->round_units) break;
         }
       }
+      for (const auto& kv : taken) took.push_back(kv);
     }
     if (nu > 0) {
       *S->h_nunits = (int)nu;
@@ -361,7 +372,7 @@ int serve_init(gwas_ctx* c) {
   const int64_t Kpad = (n + 63) / 64 * 64;
   S->slots = 512;
   S->max_prep = 2048;
-  S->round_units = 152 * 96;
+  S->round_units = 152 * 48;
   S->max_reqs = 4096;
   if (const char* e = getenv("GWAS_SERVE_SLOTS")) S->slots = std::max(8, atoi(e));
   if (const char* e = getenv("GWAS_SERVE_ROUND")) S->round_units = std::max(152, atoi(e));
