@@ -293,7 +293,8 @@ def step(g, opts, n, m, t, inp, out, phases=None):
                 phases.setdefault(k, []).append(round(v * 1e3, 1))
         names = ["eigendecomposition", "setup_rotation_operands", "slice_rows", "genotypes_bf16", "xgemm_rotate_snps",
                  "slice_snp_squares", "xgemm_rotate_traits", "prep_traits", "xgemm_back_rotate",
-                 "pack_trait_columns", "fused", "rotate_fp64", "prep_fp64", "fused_fp64"]
+                 "pack_trait_columns", "cheb_nodes", "cheb_coefficients", "fused", "rotate_fp64", "prep_fp64",
+                 "fused_fp64"]
         times = {k: g.gwas_kernel_time(ctx, k) for k in names}
         return rc, {k: v for k, v in times.items() if v[1]}, g.gwas_kernel_launches(ctx)
     finally:
@@ -604,6 +605,7 @@ def main():
         tune_ms = g.gwas_autotune(ctx, inp_d["Y"], min(t, 1024), min(m, 1 << 17))
         tune = {"shape": g.gwas_tune_shape(ctx), "sample": f"SNPs [0,{min(m, 1 << 17)}) x traits [0,{min(t, 1024)})",
                 "sample_ms": tune_ms}
+        sbr = g.gwas_sbr_info(ctx)
     finally:
         g.gwas_destroy(ctx)
     opts = g.gwas_default_opts(precision=g.GWAS_MIXED, output=g.GWAS_OUT_LAST_SE, device=local, profile=1,
@@ -649,7 +651,10 @@ def main():
     useful = algorithmic_flops(n, PM1 + 1, pairs)            # 2 (p+1) n flops per pair
     kpad = (n + 63) // 64 * 64
     tiles = ((m + 127) // 128) * ((t + 31) // 32)
-    issued = 2.0 * 128 * 512 * kpad * tiles                  # MMA columns per tile per K: 512
+    # MMA columns per tile per K: 320 for the C1 block (num and z: 4 + 2(p-1) slice groups of 32
+    # traits), plus 192 for the S_BR contraction when it is not interpolated
+    mma_cols = 320 if sbr["terms"] > 0 else 512
+    issued = 2.0 * 128 * mma_cols * kpad * tiles
     peak = pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
     achieved = useful / (fused_ms / 1e3) / 1e12
     traffic = fused_traffic((n, PM1, m, t), tune["shape"])
@@ -658,9 +663,15 @@ def main():
                 "peak_source": f"{pk_src} bf16 sustained (kernel runs ~{fused_ms:.0f} ms inside a long step)",
                 "issued_tflops": issued / (fused_ms / 1e3) / 1e12,
                 "issued_frac": issued / (fused_ms / 1e3) / 1e12 / peak,
-                "algorithmic_flops_per_launch": useful, "launch_ms": fused_ms}
+                "issued_note": "issued = MMA columns x 128 rows x 2 Kpad per tile (an analytic count of the "
+                               "tcgen05.mma work, not the ncu tensor-pipe counter)",
+                "algorithmic_flops_per_launch": useful, "launch_ms": fused_ms,
+                "s_br": dict(sbr, note="terms > 0: S_BR from its Chebyshev series in h^2 over the traits' "
+                                       "heritabilities (relative error <= bound), contracted exactly at the "
+                                       "terms' node heritabilities once per step (cheb_nodes)")}
     solve_ms = sum(v[0] for k, v in ktimes.items() if k in (
-        "xgemm_rotate_traits", "prep_traits", "xgemm_back_rotate", "pack_trait_columns", "fused")) / args.steps
+        "xgemm_rotate_traits", "prep_traits", "xgemm_back_rotate", "pack_trait_columns", "cheb_nodes",
+        "cheb_coefficients", "fused")) / args.steps
     breakdown = {k: round(v[0] / args.steps, 3) for k, v in ktimes.items()}
     # the genotype rotation X'_R = (P_c Z)^T X_R (Algorithm 5's preloop gemm) as an exact sliced
     # GEMM: one bf16 plane of genotypes against 4 slices of the rotation, 4 slice products

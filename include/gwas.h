@@ -65,6 +65,11 @@ extern "C" {
 #define GWAS_FP64  0  /* every step in FP64 (the paper's arithmetic, Section 6) */
 #define GWAS_MIXED 1  /* bf16 tensor-core contractions on exact fixed-point slices with
                          FP32 accumulation; FP64 eigendecomposition and per-trait algebra.
+                         S_BR (the contraction of the squared rotated SNPs with D_j^-1) is
+                         taken from its Chebyshev series in h^2 over the context's
+                         heritabilities when the series' error bound is <= 1e-10 with at
+                         most 24 terms (see gwas_sbr_info); otherwise it is contracted for
+                         every pair like the other two blocks.
                          Any 0 <= p-1 <= 19 (the paper's 2 <= p <= 20, Section 3);
                          traits are processed in tiles of 32 for p-1 <= 3, 16 for
                          p-1 <= 10 and 8 above (the accumulators of a tile take
@@ -271,7 +276,9 @@ GWAS_API int gwas_autotune(gwas_ctx* ctx, const double* Y, int t_sample, int64_t
  *   GWAS_FUSED_GROUP=<k>                  SNP tiles per traversal group
  *   GWAS_SERVE_SLOTS=<k>, GWAS_SERVE_ROUND=<k>  serving arena trait-tile slots and units per round
  *   GWAS_HOST_OUTPUT=staged               gwas_solve copies page-locked host outputs through device
- *                                         staging instead of storing them from the kernels */
+ *                                         staging instead of storing them from the kernels
+ *   GWAS_S_BR=exact                       the mixed path contracts S_BR for every pair (read when a
+ *                                         context plans it: its first solve, or after gwas_set_h2) */
 GWAS_API int gwas_tune_shape(const gwas_ctx* ctx, int* shape);
 
 /* Accumulated device time (ms, from CUDA events recorded on the context's stream
@@ -280,9 +287,42 @@ GWAS_API int gwas_tune_shape(const gwas_ctx* ctx, int* shape);
  * Families: "eigendecomposition", "rotate_fp64", "prep_fp64", "fused_fp64",
  * "setup_rotation_operands", "slice_rows", "genotypes_bf16", "xgemm_rotate_snps",
  * "slice_snp_squares", "xgemm_rotate_traits", "prep_traits", "xgemm_back_rotate",
- * "pack_trait_columns", "fused". */
+ * "pack_trait_columns", "cheb_nodes" (S_BR at the node heritabilities), "cheb_coefficients",
+ * "fused". */
 GWAS_API int gwas_kernel_time(const gwas_ctx* ctx, const char* kernel, double* ms, int64_t* launches);
 GWAS_API void gwas_reset_timers(gwas_ctx* ctx);
+
+/*
+ * gwas_sbr_info -- how the mixed path of this context obtains S_BR = sum_k e_jk x'^2_ik, the
+ * pair's diagonal entry of Algorithm 5 (the contraction (X'_R o X'_R)^T D_j^-1).
+ *
+ * For a SNP, S_BR is a positive combination of the functions h -> 1/(1 - h + h lambda_k) of the
+ * heritability.  Its interpolant at the Chebyshev points of [lo, hi], the range of the
+ * context's heritabilities, has relative error at most omega(h)/omega(h*_k) per term (omega the
+ * node polynomial, h*_k = 1/(1 - lambda_k) the term's pole), taken over the eigen-directions
+ * that SNPs centred against X_L reach.  When that bound is <= 1e-10 for some number of terms
+ * R <= 24, the library contracts S_BR exactly at the R node heritabilities once per loaded
+ * genotype set, converts the node values to Chebyshev coefficients (FP64) and the fused kernel
+ * evaluates the series per pair; its K loop then streams only the other two blocks' operands.
+ * Otherwise (e.g. an eigenvalue near 0 reached by the SNPs with heritabilities near 1), and
+ * under GWAS_S_BR=exact, S_BR is contracted for every pair.  Serving requests (their own
+ * heritabilities) and single-trait blocks always contract it.
+ *
+ *   terms  out: R, or 0 when S_BR is contracted per pair (and for GWAS_FP64 contexts)
+ *   lo, hi out: the interpolation interval;  bound  out: the relative error bound
+ * The plan is made (if not yet) for the current heritabilities; call after gwas_load_snps or a
+ * gwas_solve for a mixed context.
+ */
+GWAS_API int gwas_sbr_info(gwas_ctx* ctx, int* terms, double* lo, double* hi, double* bound);
+
+/*
+ * gwas_cheb_plan -- the planning rule of gwas_sbr_info on its own (host only, no device work):
+ * the least R in [4, 24] whose bound (above) is <= tol for the eigenvalues lam[k] with
+ * reach[k] != 0 on [lo, hi] (0 <= lo < hi <= 1), or *R = 0 when none is; *bound (may be NULL)
+ * receives the bound of the last R tried.  GWAS_ERR_ARG on invalid arguments.
+ */
+GWAS_API int gwas_cheb_plan(int n, const double* lam, const unsigned char* reach, double lo, double hi, double tol,
+                            int* R, double* bound);
 
 /*
  * gwas_solve_fp64_noalloc -- the FP64 per-trait preparation and the fused FP64

@@ -100,6 +100,12 @@ def _load():
     lib.gwas_request_times.argtypes = [vp, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                        C.POINTER(C.c_double)]
     lib.gwas_request_times.restype = ci
+    lib.gwas_sbr_info.argtypes = [vp, C.POINTER(ci), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]
+    lib.gwas_sbr_info.restype = ci
+    lib.gwas_cheb_plan.argtypes = [ci, vp, vp, C.c_double, C.c_double, C.c_double, C.POINTER(ci),
+                                   C.POINTER(C.c_double)]
+    lib.gwas_cheb_plan.restype = ci
     lib.gwas_check_bounded_wait.argtypes = [ci, C.c_double, C.POINTER(C.c_double)]
     lib.gwas_check_bounded_wait.restype = ci
     lib.gwas_destroy.argtypes = [vp]
@@ -355,6 +361,28 @@ def gwas_solve_fp64_noalloc(n, pm1, lam, XLt, Xt, m, Yt, h2, t, output, out, str
     if rc not in (GWAS_OK, GWAS_ERR_SINGULAR_PAIRS):
         raise GwasError(rc, "gwas_solve_fp64_noalloc failed")
     return rc, sing.value
+
+
+def gwas_sbr_info(ctx) -> dict:
+    """How the mixed path obtains S_BR (see include/gwas.h): terms R (0: contracted per pair),
+    the interpolation interval and the relative error bound."""
+    r, lo, hi, b = C.c_int(), C.c_double(), C.c_double(), C.c_double()
+    _check(lib.gwas_sbr_info(ctx, C.byref(r), C.byref(lo), C.byref(hi), C.byref(b)), ctx)
+    return {"terms": r.value, "lo": lo.value, "hi": hi.value, "bound": b.value}
+
+
+def gwas_cheb_plan(lam, reach, lo, hi, tol=1e-10):
+    """(R, bound) of the S_BR interpolation plan for eigenvalues lam (float64) and the mask reach."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    reach = np.ascontiguousarray(reach, dtype=np.uint8)
+    if reach.shape != lam.shape:
+        raise ValueError("lam and reach differ in length")
+    r, b = C.c_int(), C.c_double()
+    rc = lib.gwas_cheb_plan(lam.size, lam.ctypes.data, reach.ctypes.data, float(lo), float(hi), float(tol),
+                            C.byref(r), C.byref(b))
+    if rc != GWAS_OK:
+        raise GwasError(rc, "gwas_cheb_plan: invalid arguments")
+    return r.value, b.value
 
 
 def gwas_check_bounded_wait(device=0, limit_s=0.05):

@@ -215,8 +215,7 @@ static void destroy_impl(gwas_ctx* c) {
   }
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   mixed_free(c);
-  delete c->mixed;
-  c->mixed = nullptr;
+  mixed_destroy(c);
   for (auto& b : c->bufs) cudaFree(b.ptr);
   c->bufs.clear();
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -404,6 +403,7 @@ extern "C" int gwas_set_h2(gwas_ctx* c, int t, const double* h2) {
   else std::memcpy(v.data(), h2, sizeof(double) * t);
   if ((rc = check_h2(c, v))) return rc;
   c->h_h2 = v;
+  ++c->h2_gen;  // plans that depend on the heritabilities (the interpolated S_BR) are redone
   cudaMemcpyAsync(c->h2, v.data(), sizeof(double) * t, cudaMemcpyHostToDevice, c->stream);
   if (!ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "set_h2", &rc)) return rc;
   return GWAS_OK;
@@ -801,7 +801,7 @@ extern "C" int gwas_solve_ooc(gwas_ctx* c, int64_t m, const int8_t* XR, int64_t 
   // ---- the per-trait operands of every trait block, prepared once
   const int TT = mixed_tt(q), tm = fused_trait_tile_multiple();
   const int tpb = ((tb + TT - 1) / TT + tm - 1) / tm * tm;  // trait tiles allocated per block
-  const int pair = mixed ? fused_pair_layout(c, q) : 0;
+  const int pair = mixed ? mixed_pair_layout(c) : 0;
   int64_t kp = 0;
   if (mixed) {
     if ((rc = mixed_ws_alloc(c, tb, &ws))) return fail(rc);
@@ -872,7 +872,7 @@ extern "C" int gwas_solve_ooc(gwas_ctx* c, int64_t m, const int8_t* XR, int64_t 
     void* pieces[2] = {stage[k], (float*)stage[k] + (size_t)nb * rows};
     void* out = lastse ? (void*)pieces : stage[k];
     if (mixed)
-      r = mixed_fused_ops(c, b1_of(b), b2_of(b), cst_of(b), nb, 0, rows, rows, out);
+      r = mixed_fused_ops(c, b1_of(b), b2_of(b), cst_of(b), nb, 0, rows, rows, out, j0);
     else
       launch_fused_fp64(c, 0, rows, j0, nb, rows, R + (size_t)j0 * (p + 1) * n, cst + (size_t)j0 * consts_stride(q), out);
     // recorded here, not at delivery, so that the piece's download overlaps the next unit

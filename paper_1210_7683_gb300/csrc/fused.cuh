@@ -23,6 +23,8 @@ __host__ __device__ constexpr int c2_cols(int q) { return mixed_tt(q) == 8 ? 8 *
 // C2 rows allocated per trait tile (the CTA-pair layout, q = 3 only, needs 6 groups)
 __host__ __device__ constexpr int c2_alloc(int q) { return 6 * mixed_tt(q); }
 constexpr int MIXED_MAX_Q = 19;
+// S_BR by Chebyshev interpolation in h^2: at most this many terms (node heritabilities).
+constexpr int CHEB_MAX_R = 24;
 
 // Runs the statement in the variadic arguments with the compile-time constant Q = q (0..7,
 // larger values run as 7).
@@ -110,7 +112,9 @@ struct FusedArgs {
   const float* sA;    // [m] scale of the x'_c^2 slices of each SNP (0 marks a singular SNP)
   const float* acoef; // [m][q] centring coefficients a_i (full output only)
   const float* cst;   // [trait tiles * mixed_tt(q)][cst_stride(q)]
-  int full_b;         // 1: double b[ntrait][ldo][q + 1]; 0: float beta/se [ntrait][ldo]
+  int full_b;         // 1: double b[ntrait][ldo][q + 1]; 0: float beta/se [ntrait][ldo];
+                      // 2: the level-0 and level-1 sums of S_BR into out_beta / out_se [ntrait][ldo]
+                      //    (node heritabilities of the Chebyshev interpolation; exact kernel only)
   int64_t ldo;        // output stride between traits (SNPs)
   float* out_beta;
   float* out_se;
@@ -123,6 +127,13 @@ struct FusedArgs {
   int nunits;             // units (an upper bound when nunits_dev is set)
   const int* nunits_dev;  // NULL, or the units of the launch in device memory (captured graphs)
   const ServeDesc* reqs;
+  // S_BR by Chebyshev interpolation in h^2 (NULL cheb_coef: S_BR is contracted in the kernel):
+  // s_ij = sum_{k < cheb_R} c_ik T_k(x_j), c_ik = cheb_coef[k * cheb_ld + i] (row CHEB_MAX_R
+  // holds the low part of c_i0), T_k(x_j) = cheb_T[j * CHEB_MAX_R + k] for the block's trait j
+  const float* cheb_coef;
+  const float* cheb_T;
+  int cheb_R;
+  int64_t cheb_ld;
 };
 
 // Trait operands (B1, B2) must be allocated (and zeroed) for a multiple of this many trait tiles,
@@ -137,6 +148,12 @@ bool fused_shape_supported(int q, int cs, int ct, int epw, int pair);
 // shape are built for q = 3 only.
 int launch_fused(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* A2,
                  const __nv_bfloat16* B1, const __nv_bfloat16* B2);
+// The kernel with S_BR evaluated from its Chebyshev series in h^2 (a.cheb_coef set):
+// 0 <= q <= 7 in fused_cheb.cu, 8 <= q <= 19 in fused_cheb_wide.cu; b_tiles as above.
+int launch_fused_cheb(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* B1,
+                      int b_tiles);
+int launch_fused_cheb_wide(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* B1,
+                           int b_tiles);
 // Single-trait kernel (gemv.cu): the same solve for a.ntrait == 1, streaming the SNPs'
 // operands once through a TMA ring (HBM-bound); for the one-CTA operand layout, 0 <= q <= 19.
 bool gemv1_supported(int q, int Kpad);

@@ -64,12 +64,24 @@ constexpr int PI0_BYTES = G_BYTES + PC1_ROWS * ROWB;   // G + this CTA's C1 trai
 constexpr int PI1_BYTES = PC2_ROWS * ROWB + G_BYTES;   // this CTA's C2 trait rows + A1
 constexpr int PI2_BYTES = 2 * G_BYTES;                 // A2 + A3s
 __host__ __device__ constexpr int cst_bytes(int q) { return mixed_tt(q) * cst_stride(q) * 4; }  // one tile's constants
-__host__ __device__ constexpr int ring_bytes(bool pair) { return pair ? PSLOTS * PSLOT : SLOTS * SLOT; }
-__host__ __device__ constexpr int smem_bytes(bool pair, int q) { return ring_bytes(pair) + 2 * cst_bytes(q) + 1024 + 512; }
+// With S_BR interpolated (INTERP) a K block is one item, the C1 half-stage, in slots of its own size.
+__host__ __device__ constexpr int slot_bytes(bool interp, int q) { return interp ? (h1_bytes(q) + 1023) / 1024 * 1024 : SLOT; }
+__host__ __device__ constexpr int ring_bytes(bool pair, bool interp, int q) {
+  return pair ? PSLOTS * PSLOT : SLOTS * slot_bytes(interp, q);
+}
+// INTERP: the tile's Chebyshev coefficients [CHEB_MAX_R + 1][128 SNPs] and T_k(x_j) [CHEB_MAX_R][TT]
+__host__ __device__ constexpr int cheb_stage_bytes(bool interp, int q) {
+  return interp ? ((CHEB_MAX_R + 1) * 128 + CHEB_MAX_R * mixed_tt(q)) * 4 : 0;
+}
+__host__ __device__ constexpr int smem_bytes(bool pair, int q, bool interp = false) {
+  return ring_bytes(pair, interp, q) + 2 * cst_bytes(q) + cheb_stage_bytes(interp, q) + 1024 + 512;
+}
 constexpr int TMEM_COLS = 512;
 constexpr bool fits_all_q() {
   for (int q = 0; q <= MIXED_MAX_Q; ++q)
-    if (h1_bytes(q) > SLOT || h2_bytes(q) > SLOT || smem_bytes(false, q) > 227 * 1024) return false;
+    if (h1_bytes(q) > SLOT || h2_bytes(q) > SLOT || smem_bytes(false, q) > 227 * 1024 ||
+        smem_bytes(false, q, true) > 227 * 1024)
+      return false;
   return true;
 }
 static_assert(fits_all_q(), "half-stage does not fit a slot");
@@ -98,12 +110,16 @@ __device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us,
 // (cta_group::2); each holds its own 128 SNP rows and half of every MMA's trait rows (the
 // pair layout of the C2 operand, c2_alloc rows per tile), the leader (rank 0) issues the
 // MMAs, and both CTAs' loads complete on the leader's barriers.
-template <int EPW, bool SERVE, bool PAIR, int Q>
+// INTERP: S_BR is not contracted here but evaluated per pair from its Chebyshev series in
+// h^2 (FusedArgs::cheb_*): the K loop streams only the C1 operands (genotypes and the trait
+// columns [w | v']), one item per K block.
+template <int EPW, bool SERVE, bool PAIR, int Q, bool INTERP = false>
 __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     fused_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapA2,
                  const __grid_constant__ CUtensorMap mapB1, const __grid_constant__ CUtensorMap mapB2, FusedArgs a) {
   constexpr int CS = PAIR ? 2 : 1;                  // SNP tiles per cluster (the CTA pair: 2)
   static_assert(!PAIR || (!SERVE && Q == 3), "the pair shape is built for q = 3 outside serving");
+  static_assert(!INTERP || (!SERVE && !PAIR), "the interpolated S_BR is built for the one-CTA solve kernel");
   constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = mixed_tt(Q), CSTR = cst_stride(Q);
   constexpr int B1_ROWS = c1_rows(Q), B2_ROWS = c2_rows(Q), B2_ROWS_PAIR = c2_alloc(Q);
   constexpr int C2B = c1_groups(Q) * TT;            // first TMEM column of the C2 accumulators
@@ -121,12 +137,15 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   // tile and the C1 trait rows in one or two boxes; the three x'^2 planes, stored next to
   // one another, in two halves and the C2 trait rows).  The TMA unit pays a fixed cost per
   // box of the order of 50 cycles, so large boxes keep the load rate up.
-  constexpr int NSL = PAIR ? PSLOTS : SLOTS, SLB = PAIR ? PSLOT : SLOT;  // ring slots and their size
-  constexpr int NI = PAIR ? 3 : 2;                                        // ring items per K block
+  constexpr int NSL = PAIR ? PSLOTS : SLOTS, SLB = PAIR ? PSLOT : slot_bytes(INTERP, Q);  // ring slots, size
+  constexpr int NI = PAIR ? 3 : INTERP ? 1 : 2;                           // ring items per K block
+  constexpr int RING = ring_bytes(PAIR, INTERP, Q);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* cst_smem = (float*)(smem + ring_bytes(PAIR));  // [2][TT][CSTR], double-buffered by tile
-  uint64_t* full = (uint64_t*)(smem + ring_bytes(PAIR) + 2 * cst_bytes(Q));
+  float* cst_smem = (float*)(smem + RING);  // [2][TT][CSTR], double-buffered by tile
+  float* cheb_c = cst_smem + 2 * TT * CSTR;                // INTERP: [CHEB_MAX_R + 1][128]
+  float* cheb_t = cheb_c + (CHEB_MAX_R + 1) * 128;          // INTERP: [CHEB_MAX_R][TT]
+  uint64_t* full = (uint64_t*)(smem + RING + 2 * cst_bytes(Q) + cheb_stage_bytes(INTERP, Q));
   uint64_t* empty = full + NSL;
   uint64_t* acc_full = empty + NSL;
   uint64_t* acc_empty = acc_full + 1;
@@ -197,7 +216,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               const int kbe = PREFETCH_KB < nkb ? PREFETCH_KB : nkb;
               for (int kb = 0; kb < kbe; ++kb) {
                 for (int b = 0; b < B1_NBOX; ++b) tc::tma_prefetch_2d(&mapB1, kb * BK, ut2 * B1_ROWS + b * B1_BOX);
-                tc::tma_prefetch_2d(&mapB2, kb * BK, ut2 * B2_ROWS);
+                if (!INTERP) tc::tma_prefetch_2d(&mapB2, kb * BK, ut2 * B2_ROWS);
               }
             }
           }
@@ -315,7 +334,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         if (tcount > 0 && !tc::mbar_wait(acc_empty, (tcount - 1) & 1, a.status, abort)) { ok = false; break; }
         tc::fence_after();
         for (int kb = 0; kb < nkb && ok; ++kb) {
-          for (int half = 0; half < 2; ++half, ++h) {
+          for (int half = 0; half < NI; ++half, ++h) {
             const uint32_t s = h % NSL;
             if (!tc::mbar_wait(&full[s], (h / NSL) & 1, a.status, abort)) { ok = false; break; }
             tc::fence_after();
@@ -391,6 +410,20 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       float* cs = cst_smem + (tcount & 1) * TT * CSTR;
       for (int e = ew * 32 + lane; e < TT * CSTR; e += EPW * 32)
         cs[e] = jbase + e / CSTR < ntrait ? cst_tile[e] : 0.f;
+      if (INTERP) {
+        // the tile's Chebyshev coefficients (rows 0..R-1: c_k; row R: low part of c_0) and its
+        // traits' T_k(x_j); one buffer: every warp passed barrier 2 of the previous tile, which
+        // follows its last read of these
+        const int R = a.cheb_R;
+        for (int e = ew * 32 + lane; e < (R + 1) * 128; e += EPW * 32) {
+          const int k = e >> 7, kk = k < R ? k : CHEB_MAX_R;
+          cheb_c[e] = a.cheb_coef[(int64_t)kk * a.cheb_ld + snp0 + (e & 127)];
+        }
+        for (int e = ew * 32 + lane; e < R * TT; e += EPW * 32) {
+          const int k = e / TT, jl = e % TT;
+          cheb_t[e] = jbase + jl < ntrait ? a.cheb_T[(size_t)(jbase + jl) * CHEB_MAX_R + k] : 0.f;
+        }
+      }
       tc::named_sync(1, EPW * 32);
       const bool ok = tc::mbar_wait(acc_full, tcount & 1, a.status, abort);
       tc::fence_after();
@@ -398,7 +431,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       const bool valid_i = ok && snp >= snp_lo && snp < snp_end;
       const float sA = valid_i ? a.sA[snp] : 0.f;
       float ac[Q1] = {};
-      if (valid_i && full_b) {
+      if (valid_i && full_b == 1) {
 #pragma unroll
         for (int c = 0; c < PM1; ++c) ac[c] = a.acoef[snp * PM1 + c];
       }
@@ -454,7 +487,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                 zz_r[4 * g + v] = fmaf(z, z, zz_r[4 * g + v]);
               }
         }
-        {
+        if (!INTERP) {
           // C2: level 0 and the five level-1 groups -> s
           uint32_t d0[4], da[4], db[4], ea[4], eb[4], ec[4];
           tc::tmem_ld4(lane_base + C2B + C2_OFF + 0 * TT + j0, d0);
@@ -471,6 +504,15 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             const float lvl1 = (__uint_as_float(da[v]) + __uint_as_float(db[v])) +
                                (__uint_as_float(ea[v]) + __uint_as_float(eb[v])) + __uint_as_float(ec[v]);
             s_r[4 * g + v] = (sA * cs[(j0 + v) * CSTR + cst_escale(Q)]) * fmaf(F, lvl1, __uint_as_float(d0[v]));
+            if (!SERVE && full_b == 2) {
+              // node heritabilities of the interpolated S_BR: the two sums, combined in FP64 later
+              const int jj = jbase + j0 + v;
+              if (valid_i && jj < ntrait) {
+                const int64_t o = (int64_t)jj * ldo + (snp - oi0);
+                obeta[o] = __uint_as_float(d0[v]);
+                ose[o] = lvl1;
+              }
+            }
           }
         }
       }
@@ -482,7 +524,28 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         if (PAIR) tc::mbar_arrive_cluster_relaxed(tc::mapa(acc_empty, 0));
         else tc::mbar_arrive(acc_empty);
       }
-      if (valid_i) {
+      if (INTERP) {
+        // S_BR = sum_k c_k T_k(x_j): the tail (k >= 2, terms decreasing like a geometric series)
+        // in FP32 from the smallest term up, then c_0 (two floats) + c_1 T_1 (with the product's
+        // rounding error) added last, so that s carries about one rounding of its own size
+        const int R = a.cheb_R, i = q * 32 + lane;
+#pragma unroll
+        for (int r = 0; r < JPW; ++r) s_r[r] = 0.f;
+        for (int k = R - 1; k >= 2; --k) {
+          const float ck = cheb_c[k * 128 + i];
+#pragma unroll
+          for (int r = 0; r < JPW; ++r) s_r[r] = fmaf(ck, cheb_t[k * TT + jbeg + r], s_r[r]);
+        }
+        const float c0 = cheb_c[i], c1 = cheb_c[128 + i], c0lo = cheb_c[R * 128 + i];
+#pragma unroll
+        for (int r = 0; r < JPW; ++r) {
+          const float t1 = cheb_t[TT + jbeg + r];
+          const float pp = c1 * t1, pe = fmaf(c1, t1, -pp);
+          s_r[r] = c0 + (pp + ((s_r[r] + pe) + c0lo));
+        }
+        tc::named_sync(2, EPW * 32);
+      }
+      if (valid_i && full_b != 2) {
 #pragma unroll
         for (int r = 0; r < JPW; ++r) {
           const int jl = jbeg + r;
@@ -503,7 +566,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             se = __fsqrt_rn(rss * inv * inv_dof);
           }
           const int64_t o = (int64_t)jj * ldo + (snp - oi0);
-          if (full_b) {
+          if (full_b == 1) {
             double* ob = ob64 + o * (PM1 + 1);
 #pragma unroll
             for (int c = 0; c < PM1; ++c) {
@@ -543,14 +606,15 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   }
 }
 
-template <int EPW, bool SERVE, bool PAIR, int Q>
+template <int EPW, bool SERVE, bool PAIR, int Q, bool INTERP = false>
 int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const CUtensorMap& ma,
                  const CUtensorMap& m1, const CUtensorMap& m2) {
   constexpr int NC = PAIR ? 2 : 1;
-  auto kern = fused_kernel<EPW, SERVE, PAIR, Q>;
+  constexpr int SMEM = smem_bytes(PAIR, Q, INTERP);
+  auto kern = fused_kernel<EPW, SERVE, PAIR, Q, INTERP>;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(PAIR, Q));
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     attr = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -560,7 +624,7 @@ int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const C
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.blockDim = dim3(64 + 32 * EPW);
-  cfg.dynamicSmemBytes = smem_bytes(PAIR, Q);
+  cfg.dynamicSmemBytes = SMEM;
   cfg.stream = c->stream;
   cfg.attrs = at;
   cfg.numAttrs = 1;
@@ -575,7 +639,7 @@ int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const C
   nclusters = std::min(nclusters, nsuper);
   if (a.max_ctas > 0) nclusters = std::max(1, std::min(nclusters, a.max_ctas / NC));
   cfg.gridDim = dim3(nclusters * NC);
-  ProfScope ps(c, SERVE ? "fused_serve" : "fused");
+  ProfScope ps(c, SERVE ? "fused_serve" : a.full_b == 2 ? "cheb_nodes" : "fused");
   cudaError_t e = cudaLaunchKernelEx(&cfg, kern, mg, ma, m1, m2, a);
   c->launches++;
   if (e != cudaSuccess) {

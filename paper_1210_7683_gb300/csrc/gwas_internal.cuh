@@ -56,6 +56,7 @@ struct gwas_ctx {
   unsigned long long* d_status = nullptr;
   int64_t singular = 0;
   int64_t launches = 0;
+  int64_t h2_gen = 0;  // incremented whenever the heritabilities change (gwas_set_h2)
 
   // output streaming: side stream and events of the double-buffered device-to-host copies
   cudaStream_t copy_stream = nullptr;
@@ -139,14 +140,25 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* ws, const double* dY, const double* 
 // Enqueues (no synchronisation) the per-trait operands of traits [j0, j0+tb) into the workspace.
 int mixed_prep_block(gwas_ctx* c, MixedWs* ws, const double* dY, int j0, int tb);
 // Enqueues the fused kernel for the workspace's tb traits x SNPs [i0, i1) into dout.
-int mixed_fused_block(gwas_ctx* c, MixedWs* ws, int tb, int64_t i0, int64_t i1, int64_t ldo, void* dout);
+int mixed_fused_block(gwas_ctx* c, MixedWs* ws, int tb, int64_t i0, int64_t i1, int64_t ldo, void* dout, int j0);
 // The same for trait operands prepared elsewhere (mixed_prep_traits into B1, B2, cst).
+// j0: the first trait of the block among the context's traits (its S_BR may then be interpolated
+// in h^2), or -1 for traits with heritabilities of their own.
 int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B2, const float* cst, int tb, int64_t i0,
-                    int64_t i1, int64_t ldo, void* dout);
+                    int64_t i1, int64_t ldo, void* dout, int j0);
 // Enqueues (no synchronisation) the solve of traits [j0, j0+tb) x SNPs [i0, i1) into dout.
 int mixed_solve_block(gwas_ctx* c, MixedWs* ws, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
                       void* dout);
 void mixed_free(gwas_ctx* c);
+void mixed_destroy(gwas_ctx* c);  // frees the mixed-path state itself (after mixed_free)
+// S_BR by Chebyshev interpolation in h^2 over the context's heritabilities (mixed.cu): plans it
+// for the current heritabilities (once per gwas_set_h2) and returns 1 when the kernel may use it,
+// -1 when S_BR is contracted exactly.
+int mixed_cheb_plan(gwas_ctx* c);
+// State of the plan (1 usable, -1 exact, 0 not planned) with its terms, interval and error bound.
+int mixed_cheb_info(gwas_ctx* c, int* R, double* lo, double* hi, double* bound);
+// Whether the trait operands use the CTA-pair layout (never while S_BR is interpolated).
+int mixed_pair_layout(gwas_ctx* c);
 // resident mixed-path data (for the serving kernel launches)
 int64_t mixed_mpad(gwas_ctx* c);
 int mixed_kpad(gwas_ctx* c);  // padded n of the mixed path's operands (after mixed setup)

@@ -31,6 +31,23 @@ struct MixedState {
   float* Xc = nullptr;     // FP32 scratch of the rotation, kept while slabs are reloaded
   int64_t xc_rows = 0;
   double* rk = nullptr;    // [n] ||P_c z_k||^2: the share of eigenvector k outside span(X_L)
+  int64_t load_gen = 0;    // incremented by every genotype load (or slab)
+  // S_BR by Chebyshev interpolation in h^2 (see the section at the end of this file)
+  struct Cheb {
+    int state = 0;               // 1: usable for h2_gen; -1: the exact contraction; 0: not planned
+    int64_t h2_gen = -1;         // the context's heritability generation the plan was made for
+    int R = 0;
+    double lo = 0, hi = 1, bound = 0;
+    MixedWs* ws = nullptr;       // operands of the R node heritabilities
+    double* nodes = nullptr;     // [R]
+    double* yzero = nullptr;     // [R][n] zero traits for the node operands
+    double* tab = nullptr;       // [R][R] DCT weights
+    float* T = nullptr;          // [t][CHEB_MAX_R] T_k(x_j) of the context's traits
+    float* raw = nullptr;        // [2][R][ld] level-0 and level-1 node sums
+    float* coef = nullptr;       // [CHEB_MAX_R + 1][ld] coefficients (last row: low part of c_0)
+    int64_t ld = 0;              // columns of raw and coef
+    int64_t coef_gen = -1;       // load generation the coefficients belong to
+  } cheb;
 };
 
 // Eigen-directions k with ||P_c z_k||^2 at or below this carry no energy of any centred SNP
@@ -38,6 +55,8 @@ struct MixedState {
 // scale.  Typical case: a standardised kinship has the intercept as an eigenvector with a
 // tiny eigenvalue, whose weight 1/(h^2 lambda + 1 - h^2) dominates as h^2 -> 1.
 constexpr double RK_NULL = 1e-16;
+
+static int cheb_coefficients(gwas_ctx* c);
 
 namespace {
 
@@ -440,6 +459,13 @@ const float* mixed_acoef(gwas_ctx* c) { return c->mixed ? c->mixed->acoef : null
 const __nv_bfloat16* mixed_G(gwas_ctx* c) { return c->mixed ? c->mixed->G : nullptr; }
 const __nv_bfloat16* mixed_A2(gwas_ctx* c) { return c->mixed ? c->mixed->A2 : nullptr; }
 
+void mixed_destroy(gwas_ctx* c) {
+  if (!c->mixed) return;
+  if (c->mixed->cheb.ws) mixed_ws_free(c, c->mixed->cheb.ws);
+  delete c->mixed;
+  c->mixed = nullptr;
+}
+
 void mixed_free(gwas_ctx* c) {
   MixedState* s = c->mixed;
   if (!s) return;
@@ -530,6 +556,7 @@ int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m, bool reuse) {
       return rc;
     }
   }
+  ++s->load_gen;
   { ProfScope ps(c, "genotypes_bf16");
   geno_bf16_kernel<<<16 * 152, 256, 0, c->stream>>>(dXR, m, n, s->mpad, s->Kpad, s->G);
   c->launches++; }
@@ -691,11 +718,11 @@ int mixed_prep_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb) 
                        fused_trait_tile_multiple();
   cudaMemsetAsync(w->B1, 0, 2ull * nt_alloc * c1_rows(q) * Kpad, c->stream);
   cudaMemsetAsync(w->B2, 0, 2ull * nt_alloc * c2_alloc(q) * Kpad, c->stream);
-  return mixed_prep_traits(c, w, dY, c->h2 + j0, tb, w->B1, w->B2, w->cst, nullptr, fused_pair_layout(c, q));
+  return mixed_prep_traits(c, w, dY, c->h2 + j0, tb, w->B1, w->B2, w->cst, nullptr, mixed_pair_layout(c));
 }
 
 int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B2, const float* cst, int tb, int64_t i0,
-                    int64_t i1, int64_t ldo, void* out) {
+                    int64_t i1, int64_t ldo, void* out, int j0) {
   MixedState* s = c->mixed;
   if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
   const int n = c->n, q = c->pm1, p = q + 1, Kpad = s->Kpad, TT = mixed_tt(q);
@@ -731,19 +758,297 @@ int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B
     }
     a.status = c->d_status;
     a.singular = c->d_status + 1;
+    const bool gemv = tb == 1 && gemv1_supported(q, Kpad) && !mixed_pair_layout(c);
+    // S_BR from its Chebyshev series in h^2 when the plan allows it (traits of the context)
+    if (!gemv && j0 >= 0 && mixed_cheb_plan(c) == 1) {
+      if ((rc = cheb_coefficients(c))) return rc;
+      a.cheb_coef = s->cheb.coef;
+      a.cheb_T = s->cheb.T + (size_t)j0 * CHEB_MAX_R;
+      a.cheb_R = s->cheb.R;
+      a.cheb_ld = s->cheb.ld;
+    }
     // one trait: the contractions are matrix-vector products, bound by HBM (gemv.cu)
-    if (tb == 1 && gemv1_supported(q, Kpad) && !fused_pair_layout(c, q)) rc = launch_gemv1(c, q, a, s->G, s->A2, B1, B2);
+    if (gemv) rc = launch_gemv1(c, q, a, s->G, s->A2, B1, B2);
     else rc = launch_fused(c, q, a, s->G, s->A2, B1, B2);
   }
   return rc;
 }
 
-int mixed_fused_block(gwas_ctx* c, MixedWs* w, int tb, int64_t i0, int64_t i1, int64_t ldo, void* out) {
-  return mixed_fused_ops(c, w->B1, w->B2, w->cst, tb, i0, i1, ldo, out);
+int mixed_fused_block(gwas_ctx* c, MixedWs* w, int tb, int64_t i0, int64_t i1, int64_t ldo, void* out, int j0) {
+  return mixed_fused_ops(c, w->B1, w->B2, w->cst, tb, i0, i1, ldo, out, j0);
 }
 
 int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
                       void* out) {
   int rc = mixed_prep_block(c, w, dY, j0, tb);
-  return rc ? rc : mixed_fused_block(c, w, tb, i0, i1, ldo, out);
+  return rc ? rc : mixed_fused_block(c, w, tb, i0, i1, ldo, out, j0);
+}
+
+// ---------------------------------------------------------------- S_BR by Chebyshev interpolation in h^2
+//
+// For SNP i, S_BR as a function of the heritability, s_i(h) = sum_k e_k(h) x'^2_ck with
+// e_k(h) = 1 / (1 - h + h lambda_k), is a positive combination of the functions e_k.  On an
+// interval [lo, hi] holding the context's heritabilities it is replaced by its interpolant at the
+// R Chebyshev points of [lo, hi] (a polynomial of degree R - 1 in h):
+//   - the node values s_i(h_r) are the exact contraction (X'_R o X'_R)^T D^-1 of the fused kernel
+//     (Algorithm 5's S_BR) for R node heritabilities, taken from its level-0 and level-1 sums;
+//   - their Chebyshev coefficients c_ik follow by a discrete cosine transform (FP64);
+//   - the fused kernel then evaluates s_ij = sum_k c_ik T_k(x_j), x_j the image of h_j in [-1, 1],
+//     instead of contracting the squares of the rotated SNPs with D_j^-1 for every trait.
+// The interpolant of 1/(a + b h) with its pole at h* has relative error omega(h) / omega(h*) at h,
+// omega the node polynomial, so that, the terms being positive, s_i has relative error at most
+// max_k max_h |omega(h)| / |omega(h*_k)| over the eigen-directions that centred SNPs reach.  R is
+// the least number of nodes with that bound <= kChebTol; when no R <= CHEB_MAX_R meets it (a pole
+// close to the interval: an eigenvalue near 0 reached by the SNPs and heritabilities near 1), or
+// GWAS_S_BR=exact is set, the fused kernel contracts S_BR itself.
+
+namespace {
+
+constexpr double kChebTol = 1e-10;
+
+// T_k(x_j) for the context's traits, k < R (zero beyond)
+__global__ void cheb_t_kernel(const double* __restrict__ h2, int t, double lo, double hi, int R, float* __restrict__ T) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= t) return;
+  const double x = fmin(1.0, fmax(-1.0, (2.0 * h2[j] - (lo + hi)) / (hi - lo)));
+  double tm = 1.0, tk = x;
+  for (int k = 0; k < CHEB_MAX_R; ++k) {
+    double v = 0.0;
+    if (k == 0) v = 1.0;
+    else if (k == 1) v = x;
+    else {
+      const double tn = 2.0 * x * tk - tm;
+      tm = tk;
+      tk = tn;
+      v = tn;
+    }
+    T[(size_t)j * CHEB_MAX_R + k] = k < R ? (float)v : 0.f;
+  }
+}
+
+// Coefficients of SNP i from its node sums: s_i(h_r) = sA_i escale_r (level 0 + level 1 / 256),
+// c_k = sum_r tab[k][r] s_i(h_r) in FP64; c_0 is kept as two floats.
+__global__ void __launch_bounds__(256) cheb_coef_kernel(const float* __restrict__ raw, int R, int64_t ld, int64_t m,
+                                                        const float* __restrict__ sA, const float* __restrict__ cst,
+                                                        int cstr, int eoff, const double* __restrict__ tab,
+                                                        float* __restrict__ coef) {
+  __shared__ double stab[CHEB_MAX_R * CHEB_MAX_R];
+  __shared__ double sesc[CHEB_MAX_R];
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) stab[e] = tab[e];
+  for (int e = threadIdx.x; e < R; e += blockDim.x) sesc[e] = (double)cst[(size_t)e * cstr + eoff];
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ld) return;
+  double sv[CHEB_MAX_R];
+  const double a = i < m ? (double)sA[i] : 0.0;
+#pragma unroll
+  for (int r = 0; r < CHEB_MAX_R; ++r)
+    sv[r] = r < R ? a * sesc[r] * ((double)raw[(size_t)r * ld + i] + (double)raw[(size_t)(R + r) * ld + i] * (1.0 / 256.0))
+                  : 0.0;
+  for (int k = 0; k < R; ++k) {
+    double ck = 0.0;
+#pragma unroll
+    for (int r = 0; r < CHEB_MAX_R; ++r)
+      if (r < R) ck = fma(stab[k * R + r], sv[r], ck);
+    const float hi = (float)ck;
+    coef[(size_t)k * ld + i] = hi;
+    if (k == 0) coef[(size_t)CHEB_MAX_R * ld + i] = (float)(ck - (double)hi);
+  }
+}
+
+// The Chebyshev points of [lo, hi], largest first (x_r = cos(pi r / (R - 1))).
+void cheb_nodes(int R, double lo, double hi, double* h) {
+  for (int r = 0; r < R; ++r) h[r] = 0.5 * (lo + hi) + 0.5 * (hi - lo) * std::cos(M_PI * r / (R - 1));
+}
+
+}  // namespace
+
+// Relative error bound of the degree-(R-1) interpolant of every e_k on [lo, hi] (see above);
+// reach[k] != 0 marks the eigen-directions that enter S_BR.
+static double cheb_bound(int n, const double* lam, const unsigned char* reach, double lo, double hi, int R) {
+  std::vector<double> h(R);
+  cheb_nodes(R, lo, hi, h.data());
+  // log max |omega| over a fine grid of [lo, hi], with a margin for the grid
+  double lmax = -1e300;
+  const int G = 4096;
+  for (int g = 0; g <= G; ++g) {
+    const double x = lo + (hi - lo) * g / G;
+    double l = 0;
+    for (int r = 0; r < R; ++r) l += std::log(std::fabs(x - h[r]) + 1e-300);
+    lmax = std::max(lmax, l);
+  }
+  lmax += std::log(2.0);
+  double worst = 0;
+  for (int k = 0; k < n; ++k) {
+    if (!reach[k] || lam[k] == 1.0) continue;
+    const double hs = 1.0 / (1.0 - lam[k]);   // the pole of 1 / (1 - h + h lambda_k)
+    if (hs >= lo && hs <= hi) return INFINITY;
+    double l = 0;
+    for (int r = 0; r < R; ++r) l += std::log(std::fabs(hs - h[r]));
+    worst = std::max(worst, std::exp(lmax - l));
+  }
+  return worst;
+}
+
+extern "C" int gwas_cheb_plan(int n, const double* lam, const unsigned char* reach, double lo, double hi, double tol,
+                              int* R, double* bound) {
+  if (n < 1 || !lam || !reach || !R || !(lo >= 0.0) || !(hi <= 1.0) || !(hi > lo) || !(tol > 0.0)) return GWAS_ERR_ARG;
+  *R = 0;
+  double b = INFINITY;
+  for (int r = 4; r <= CHEB_MAX_R; ++r) {
+    b = cheb_bound(n, lam, reach, lo, hi, r);
+    if (b <= tol) {
+      *R = r;
+      break;
+    }
+  }
+  if (bound) *bound = b;
+  return GWAS_OK;
+}
+
+int mixed_cheb_plan(gwas_ctx* c) {
+  MixedState* s = c->mixed;
+  if (!s || !s->rk || c->h_h2.empty()) return -1;
+  auto& ch = s->cheb;
+  if (ch.state != 0 && ch.h2_gen == c->h2_gen) return ch.state;
+  ch.h2_gen = c->h2_gen;
+  ch.state = -1;
+  ch.coef_gen = -1;
+  if (const char* e = getenv("GWAS_S_BR"))
+    if (!strcmp(e, "exact")) return -1;
+  const int n = c->n, t = (int)c->h_h2.size();  // every trait of the context (c->t may be a sample's)
+  double lo = *std::min_element(c->h_h2.begin(), c->h_h2.end());
+  double hi = *std::max_element(c->h_h2.begin(), c->h_h2.end());
+  if (hi - lo < 1e-3) {  // a narrow interval: widen it, inside [0, 1]
+    const double mid = std::min(1.0 - 5e-4, std::max(5e-4, 0.5 * (lo + hi)));
+    lo = mid - 5e-4;
+    hi = mid + 5e-4;
+  }
+  std::vector<double> rk(n);
+  if (cudaMemcpy(rk.data(), s->rk, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  std::vector<unsigned char> reach(n);
+  for (int k = 0; k < n; ++k) reach[k] = rk[k] > RK_NULL;
+  int R = 0;
+  double bound = 0;
+  gwas_cheb_plan(n, c->h_lam.data(), reach.data(), lo, hi, kChebTol, &R, &bound);
+  if (R == 0) return -1;
+  // node operands (zero traits at the node heritabilities), DCT weights and T_k(x_j)
+  if (!ch.ws) {
+    if (mixed_ws_alloc(c, CHEB_MAX_R, &ch.ws) || ctx_alloc(c, sizeof(double) * CHEB_MAX_R, (void**)&ch.nodes) ||
+        ctx_alloc(c, sizeof(double) * CHEB_MAX_R * n, (void**)&ch.yzero) ||
+        ctx_alloc(c, sizeof(double) * CHEB_MAX_R * CHEB_MAX_R, (void**)&ch.tab) ||
+        ctx_alloc(c, sizeof(float) * (size_t)t * CHEB_MAX_R, (void**)&ch.T)) {
+      c->err.clear();
+      return -1;
+    }
+    cudaMemsetAsync(ch.yzero, 0, sizeof(double) * CHEB_MAX_R * n, c->stream);
+  }
+  std::vector<double> h(R), tab((size_t)R * R);
+  cheb_nodes(R, lo, hi, h.data());
+  for (int k = 0; k < R; ++k)
+    for (int r = 0; r < R; ++r) {
+      const double w = (r == 0 || r == R - 1) ? 0.5 : 1.0, ck = (k == 0 || k == R - 1) ? 0.5 : 1.0;
+      tab[(size_t)k * R + r] = 2.0 / (R - 1) * w * ck * std::cos(M_PI * k * r / (R - 1));
+    }
+  cudaMemcpyAsync(ch.nodes, h.data(), sizeof(double) * R, cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(ch.tab, tab.data(), sizeof(double) * R * R, cudaMemcpyHostToDevice, c->stream);
+  const int q = c->pm1, Kpad = s->Kpad;
+  const int nt_tiles = (CHEB_MAX_R + mixed_tt(q) - 1) / mixed_tt(q);
+  const int nt_pad = (nt_tiles + fused_trait_tile_multiple() - 1) / fused_trait_tile_multiple() * fused_trait_tile_multiple();
+  cudaMemsetAsync(ch.ws->B1, 0, 2ull * nt_pad * c1_rows(q) * Kpad, c->stream);
+  cudaMemsetAsync(ch.ws->B2, 0, 2ull * nt_pad * c2_alloc(q) * Kpad, c->stream);
+  if (mixed_prep_traits(c, ch.ws, ch.yzero, ch.nodes, R, ch.ws->B1, ch.ws->B2, ch.ws->cst, nullptr, 0)) {
+    c->err.clear();
+    return -1;
+  }
+  cheb_t_kernel<<<(t + 255) / 256, 256, 0, c->stream>>>(c->h2, t, lo, hi, R, ch.T);
+  c->launches++;
+  ch.R = R;
+  ch.lo = lo;
+  ch.hi = hi;
+  ch.bound = bound;
+  ch.state = 1;
+  return 1;
+}
+
+int mixed_pair_layout(gwas_ctx* c) { return mixed_cheb_plan(c) == 1 ? 0 : fused_pair_layout(c, c->pm1); }
+
+int mixed_cheb_info(gwas_ctx* c, int* R, double* lo, double* hi, double* bound) {
+  const int st = c->mixed ? c->mixed->cheb.state : 0;
+  if (st == 1) {
+    *R = c->mixed->cheb.R;
+    *lo = c->mixed->cheb.lo;
+    *hi = c->mixed->cheb.hi;
+    *bound = c->mixed->cheb.bound;
+  } else {
+    *R = 0;
+    *lo = *hi = *bound = 0;
+  }
+  return st;
+}
+
+// The coefficients of the loaded SNPs (once per load): the exact kernel at the node heritabilities,
+// then the transform.
+static int cheb_coefficients(gwas_ctx* c) {
+  MixedState* s = c->mixed;
+  auto& ch = s->cheb;
+  if (ch.coef_gen == s->load_gen) return GWAS_OK;
+  const int q = c->pm1, R = ch.R;
+  int rc;
+  if (ch.ld < s->mpad) {
+    ctx_free(c, ch.raw);
+    ctx_free(c, ch.coef);
+    ch.raw = ch.coef = nullptr;
+    ch.ld = 0;
+    if ((rc = ctx_alloc(c, sizeof(float) * 2 * CHEB_MAX_R * s->mpad, (void**)&ch.raw)) ||
+        (rc = ctx_alloc(c, sizeof(float) * (CHEB_MAX_R + 1) * s->mpad, (void**)&ch.coef)))
+      return rc;
+    ch.ld = s->mpad;
+  }
+  FusedArgs a{};
+  a.row0 = 0;
+  a.snp_lo = 0;
+  a.i0 = 0;
+  a.nsnp = s->m;
+  a.n_stiles = (int)((s->m + 127) / 128);
+  a.n_ttiles = (R + mixed_tt(q) - 1) / mixed_tt(q);
+  a.group = 16;
+  a.ntrait = R;
+  a.Kpad = s->Kpad;
+  a.mpad = s->mpad;
+  a.dof = (float)(c->n - c->p);
+  a.sA = s->sA;
+  a.acoef = s->acoef;
+  a.cst = ch.ws->cst;
+  a.full_b = 2;
+  a.ldo = ch.ld;
+  a.out_beta = ch.raw;
+  a.out_se = ch.raw + (size_t)R * ch.ld;
+  a.status = c->d_status;
+  a.singular = c->d_status + 1;
+  if ((rc = launch_fused(c, q, a, s->G, s->A2, ch.ws->B1, ch.ws->B2))) return rc;
+  {
+    ProfScope ps(c, "cheb_coefficients");
+    cheb_coef_kernel<<<(unsigned)((ch.ld + 255) / 256), 256, 0, c->stream>>>(
+        ch.raw, R, ch.ld, s->m, s->sA, ch.ws->cst, cst_stride(q), cst_escale(q), ch.tab, ch.coef);
+    c->launches++;
+  }
+  ch.coef_gen = s->load_gen;
+  return GWAS_OK;
+}
+
+extern "C" int gwas_sbr_info(gwas_ctx* c, int* terms, double* lo, double* hi, double* bound) {
+  if (!c || !terms || !lo || !hi || !bound) return GWAS_ERR_ARG;
+  if (c->precision != GWAS_MIXED || !c->mixed) {
+    *terms = 0;
+    *lo = *hi = *bound = 0;
+    return GWAS_OK;
+  }
+  DeviceGuard guard(c->device);
+  mixed_cheb_plan(c);
+  mixed_cheb_info(c, terms, lo, hi, bound);
+  return GWAS_OK;
 }

@@ -42,3 +42,12 @@ def gw():
     gbuild.build()
     import paper_1210_7683_gb300 as g
     return g
+
+
+@pytest.fixture(scope="session")
+def gw_cpu():
+    """The binding with the library built, for host-only entry points (no GPU needed)."""
+    from paper_1210_7683_gb300 import build as gbuild
+    gbuild.build()
+    import paper_1210_7683_gb300 as g
+    return g

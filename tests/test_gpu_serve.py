@@ -1,7 +1,8 @@
 """Serving with continuous batching: every request's result is the same alone and in a
 mix (bitwise: the arithmetic of a pair does not depend on its round, nor on whether the
 round was launched directly or replayed from its captured CUDA graph), the same as a
-separate gwas_solve of the request, and within the parity bar of the oracle."""
+separate gwas_solve of the request with S_BR contracted per pair as serving does
+(GWAS_S_BR=exact), and within the parity bar of the oracle."""
 import numpy as np
 import pytest
 
@@ -38,7 +39,7 @@ def alloc_out(tk, M, k):
     return t.pin_memory() if k % 2 == 0 else t.cuda()
 
 
-def test_alone_equals_mix_equals_solve(gw):
+def test_alone_equals_mix_equals_solve(gw, monkeypatch):
     P = make_problem(256, 3000, 4, seed=41)
     reqs = requests(P, 14, 7)
     ctx = new_ctx(gw, P)
@@ -67,6 +68,7 @@ def test_alone_equals_mix_equals_solve(gw):
         np.testing.assert_array_equal(a, b)
     assert all(t0 <= t1 <= t2 for t0, t1, t2 in ts)
     # the same request through gwas_solve, and the oracle on a sample of requests
+    monkeypatch.setenv("GWAS_S_BR", "exact")
     for k in (0, 3, 9):
         Y, h2, i0, i1 = reqs[k]
         ctx = new_ctx(gw, P, t=len(h2), h2=h2)
@@ -103,7 +105,7 @@ def test_poll_and_singular_request(gw):
 
 
 @pytest.mark.parametrize("pm1", [0, 5, 9, 14])
-def test_serving_general_p(gw, pm1):
+def test_serving_general_p(gw, pm1, monkeypatch):
     """Serving with q = p - 1 other than 3 (tiles of 16 traits for q = 5 and 9, of 8 for
     q = 14): a mix of requests equals gwas_solve of each request and the oracle."""
     P = make_problem(160, 1200, 2, pm1=pm1, seed=43 + pm1)
@@ -120,6 +122,7 @@ def test_serving_general_p(gw, pm1):
         mix = [o.cpu().numpy() for o in outs]
     finally:
         gw.gwas_destroy(ctx)
+    monkeypatch.setenv("GWAS_S_BR", "exact")
     for k in (0, 2, 5):
         Y, h2, i0, i1 = reqs[k]
         ctx = new_ctx(gw, P, t=len(h2), h2=h2)
