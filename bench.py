@@ -200,6 +200,7 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests of the serving run (the serving workload's 2000; 0 skips it)")
     ap.add_argument("--no-c2", action="store_true", help="skip the FP64-vs-mixed full-b measurement")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default launch shape)")
     ap.add_argument("--no-c5", action="store_true", help="skip the paper-scale streamed measurement")
     ap.add_argument("--serving-load", default="0.8,0.5,0.95",
                     help="offered loads as fractions of saturation, comma-separated; the first is the headline")
@@ -602,7 +603,7 @@ def main():
     ctx = g.gwas_setup(n, PM1, inp_d["phi"], inp_d["XL"], t, inp_d["h2"], o_t)
     try:
         g.gwas_load_snps(ctx, m, inp_d["XR"], n)
-        tune_ms = g.gwas_autotune(ctx, inp_d["Y"], min(t, 1024), min(m, 1 << 17))
+        tune_ms = None if args.no_tune else g.gwas_autotune(ctx, inp_d["Y"], min(t, 1024), min(m, 1 << 17))
         tune = {"shape": g.gwas_tune_shape(ctx), "sample": f"SNPs [0,{min(m, 1 << 17)}) x traits [0,{min(t, 1024)})",
                 "sample_ms": tune_ms}
         sbr = g.gwas_sbr_info(ctx)

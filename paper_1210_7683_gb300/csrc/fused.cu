@@ -42,10 +42,12 @@ int launch_fused(gwas_ctx* c, int q, const FusedArgs& args, const __nv_bfloat16*
   FusedArgs a = args;
   if (a.n_stiles == 0 || a.n_ttiles == 0) return GWAS_OK;
   if (q < 0 || q > MIXED_MAX_Q) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "fused kernel: p-1 outside [0, 19]");
-  // S_BR from its Chebyshev series: the one-CTA shape with the C1 operands only
-  if (a.cheb_coef)
-    return q > 7 ? launch_fused_cheb_wide(c, q, a, G, B1, (a.n_ttiles + 3) / 4 * 4)
-                 : launch_fused_cheb(c, q, a, G, B1, (a.n_ttiles + 3) / 4 * 4);
+  // S_BR from its Chebyshev series: the C1 operands only, in the one-CTA shape or the CTA pair
+  if (a.cheb_coef) {
+    const int bt = (a.n_ttiles + 3) / 4 * 4;
+    if (q == 3 && shape_of(c, q).pair) return launch_fused_cheb_pair(c, a, G, B1, bt);
+    return q > 7 ? launch_fused_cheb_wide(c, q, a, G, B1, bt) : launch_fused_cheb(c, q, a, G, B1, bt);
+  }
   if (q > 7) return launch_fused_wide(c, q, a, G, A2, B1, B2, false, (a.n_ttiles + 3) / 4 * 4);
   // the node sums of the interpolated S_BR use the one-CTA operand layout
   const Shape sh = a.full_b == 2 ? Shape{1, 1, 16, 0} : shape_of(c, q);

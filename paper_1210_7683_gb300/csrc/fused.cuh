@@ -154,6 +154,9 @@ int launch_fused_cheb(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat1
                       int b_tiles);
 int launch_fused_cheb_wide(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* B1,
                            int b_tiles);
+// The CTA-pair shape of the same (q = 3, trait operands in the pair layout).
+int launch_fused_cheb_pair(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* B1,
+                           int b_tiles);
 // Single-trait kernel (gemv.cu): the same solve for a.ntrait == 1, streaming the SNPs'
 // operands once through a TMA ring (HBM-bound); for the one-CTA operand layout, 0 <= q <= 19.
 bool gemv1_supported(int q, int Kpad);

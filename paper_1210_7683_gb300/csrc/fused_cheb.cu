@@ -16,3 +16,14 @@ int launch_fused_cheb(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat1
   Q_DISPATCH(q, return launch_shape<16, false, false, Q, true>(c, a, mg, mg, m1, m1));
   return GWAS_OK;
 }
+
+int launch_fused_cheb_pair(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* B1,
+                           int b_tiles) {
+  if (a.cheb_R < 2 || a.cheb_R > CHEB_MAX_R) return ctx_fail(c, GWAS_ERR_ARG, "Chebyshev terms outside [2, 24]");
+  // each CTA of the pair: its own 128 SNP rows and its 160 of the tile's C1 trait rows (pair layout)
+  CUtensorMap mg, m1;
+  if (!make_bf16_map(&mg, G, a.mpad, a.Kpad, BM, BK) ||
+      !make_bf16_map(&m1, B1, (uint64_t)b_tiles * c1_rows(3), a.Kpad, PC1_ROWS, BK))
+    return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
+  return launch_shape<16, false, true, 3, true>(c, a, mg, mg, m1, m1);
+}

@@ -59,6 +59,7 @@ __host__ __device__ constexpr int h2_bytes(int q) { return 3 * G_BYTES + c2_rows
 // per K block (G + C1 half: 36 KB; C2 half + A1: 28 KB; A2 + A3s: 32 KB) and a ring of six
 // 36 KB slots, i.e. two K blocks in flight.
 constexpr int PSLOT = 36 * 1024, PSLOTS = 6;
+constexpr int PSLOTS_INTERP = 5;  // the pair with S_BR interpolated: item 0 only, five slots in flight
 constexpr int PC1_ROWS = c1_rows(3) / 2, PC2_ROWS = c2_alloc(3) / 2;  // 160 and 96 trait rows per CTA
 constexpr int PI0_BYTES = G_BYTES + PC1_ROWS * ROWB;   // G + this CTA's C1 trait rows
 constexpr int PI1_BYTES = PC2_ROWS * ROWB + G_BYTES;   // this CTA's C2 trait rows + A1
@@ -67,7 +68,7 @@ __host__ __device__ constexpr int cst_bytes(int q) { return mixed_tt(q) * cst_st
 // With S_BR interpolated (INTERP) a K block is one item, the C1 half-stage, in slots of its own size.
 __host__ __device__ constexpr int slot_bytes(bool interp, int q) { return interp ? (h1_bytes(q) + 1023) / 1024 * 1024 : SLOT; }
 __host__ __device__ constexpr int ring_bytes(bool pair, bool interp, int q) {
-  return pair ? PSLOTS * PSLOT : SLOTS * slot_bytes(interp, q);
+  return pair ? (interp ? PSLOTS_INTERP : PSLOTS) * PSLOT : SLOTS * slot_bytes(interp, q);
 }
 // INTERP: the tile's Chebyshev coefficients [CHEB_MAX_R + 1][128 SNPs] and T_k(x_j) [CHEB_MAX_R][TT]
 __host__ __device__ constexpr int cheb_stage_bytes(bool interp, int q) {
@@ -86,7 +87,7 @@ constexpr bool fits_all_q() {
 }
 static_assert(fits_all_q(), "half-stage does not fit a slot");
 static_assert(PI0_BYTES <= PSLOT && PI1_BYTES <= PSLOT && PI2_BYTES <= PSLOT, "pair item does not fit a slot");
-static_assert(smem_bytes(true, 3) <= 227 * 1024, "shared memory");
+static_assert(smem_bytes(true, 3) <= 227 * 1024 && smem_bytes(true, 3, true) <= 227 * 1024, "shared memory");
 
 // epilogue warps EPW for TT traits per tile: four lane quarters, each warp owning TT / (EPW / 4)
 // traits, read from TMEM in groups of 4
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                  const __grid_constant__ CUtensorMap mapB1, const __grid_constant__ CUtensorMap mapB2, FusedArgs a) {
   constexpr int CS = PAIR ? 2 : 1;                  // SNP tiles per cluster (the CTA pair: 2)
   static_assert(!PAIR || (!SERVE && Q == 3), "the pair shape is built for q = 3 outside serving");
-  static_assert(!INTERP || (!SERVE && !PAIR), "the interpolated S_BR is built for the one-CTA solve kernel");
+  static_assert(!INTERP || !SERVE, "the interpolated S_BR is built for the solve kernels");
   constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = mixed_tt(Q), CSTR = cst_stride(Q);
   constexpr int B1_ROWS = c1_rows(Q), B2_ROWS = c2_rows(Q), B2_ROWS_PAIR = c2_alloc(Q);
   constexpr int C2B = c1_groups(Q) * TT;            // first TMEM column of the C2 accumulators
@@ -137,8 +138,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   // tile and the C1 trait rows in one or two boxes; the three x'^2 planes, stored next to
   // one another, in two halves and the C2 trait rows).  The TMA unit pays a fixed cost per
   // box of the order of 50 cycles, so large boxes keep the load rate up.
-  constexpr int NSL = PAIR ? PSLOTS : SLOTS, SLB = PAIR ? PSLOT : slot_bytes(INTERP, Q);  // ring slots, size
-  constexpr int NI = PAIR ? 3 : INTERP ? 1 : 2;                           // ring items per K block
+  constexpr int NSL = PAIR ? (INTERP ? PSLOTS_INTERP : PSLOTS) : SLOTS;   // ring slots
+  constexpr int SLB = PAIR ? PSLOT : slot_bytes(INTERP, Q);               // and their size
+  constexpr int NI = INTERP ? 1 : PAIR ? 3 : 2;                           // ring items per K block
   constexpr int RING = ring_bytes(PAIR, INTERP, Q);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -295,7 +297,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             tc::mma_commit_pair(&empty[s], (uint16_t)3);
             ++h;
           }
-          {
+          if (!INTERP) {
             // items 1 and 2: the C2 trait rows and A1; A2 and A3s
             const uint32_t s1 = h % NSL, s2 = (h + 1) % NSL;
             if (!tc::mbar_wait(&full[s1], (h / NSL) & 1, a.status, abort) ||

@@ -157,7 +157,7 @@ void mixed_destroy(gwas_ctx* c);  // frees the mixed-path state itself (after mi
 int mixed_cheb_plan(gwas_ctx* c);
 // State of the plan (1 usable, -1 exact, 0 not planned) with its terms, interval and error bound.
 int mixed_cheb_info(gwas_ctx* c, int* R, double* lo, double* hi, double* bound);
-// Whether the trait operands use the CTA-pair layout (never while S_BR is interpolated).
+// Whether the trait operands use the CTA-pair layout (the context's launch shape is the pair).
 int mixed_pair_layout(gwas_ctx* c);
 // resident mixed-path data (for the serving kernel launches)
 int64_t mixed_mpad(gwas_ctx* c);

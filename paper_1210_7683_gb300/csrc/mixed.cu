@@ -974,7 +974,7 @@ int mixed_cheb_plan(gwas_ctx* c) {
   return 1;
 }
 
-int mixed_pair_layout(gwas_ctx* c) { return mixed_cheb_plan(c) == 1 ? 0 : fused_pair_layout(c, c->pm1); }
+int mixed_pair_layout(gwas_ctx* c) { return fused_pair_layout(c, c->pm1); }
 
 int mixed_cheb_info(gwas_ctx* c, int* R, double* lo, double* hi, double* bound) {
   const int st = c->mixed ? c->mixed->cheb.state : 0;

@@ -102,3 +102,20 @@ def test_no_covariates_falls_back_to_the_contraction(gw, monkeypatch):
     b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, h2)
     beta, s = got[0].T.astype(np.float64), got[1].T.astype(np.float64)
     assert last_coef_err(beta, s, b, se) <= TOL and se_err(s, se) <= TOL
+
+
+def test_interpolated_sbr_in_the_cta_pair_shape(gw, monkeypatch):
+    """The CTA-pair launch shape (p = 4) with S_BR interpolated: each CTA of the pair streams its
+    own SNP rows and half of the C1 trait rows; an odd number of SNP tiles leaves the second CTA
+    of the last pair without a tile."""
+    monkeypatch.delenv("GWAS_S_BR", raising=False)
+    monkeypatch.setenv("GWAS_FUSED_SHAPE", "2x1x16x1")
+    P = make_problem(333, 5 * 128 + 77, 75, seed=550)
+    got, info = solve(gw, P, gw.GWAS_OUT_LAST_SE, 3, P.m - 2)
+    assert info["terms"] > 0
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR[3:P.m - 2], P.Y, P.h2)
+    beta, s = got[0].T.astype(np.float64), got[1].T.astype(np.float64)
+    assert last_coef_err(beta, s, b, se) <= TOL and se_err(s, se) <= TOL
+    full, _ = solve(gw, P, gw.GWAS_OUT_FULL_B)
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    assert full_b_err(full.transpose(1, 0, 2), b, se) <= TOL
