@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       // per-pair arithmetic and output stores, so the next tile's MMAs wait only for the reads.
       static_assert(JPW % 4 == 0, "epilogue reads traits in groups of 4");
       float num_r[JPW], zz_r[JPW], s_r[JPW], z_r[JPW][Q1];
-      const float F = 1.f / 256.f;
+      const float F = 1.f / 256.f, FV = 1.f / 512.f;  // FV: the v' columns' second slice (9 bits)
 #pragma unroll
       for (int g = 0; g < JPW / 4; ++g) {
         const int j0 = jbeg + 4 * g;
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
             for (int c = 0; c < CB; ++c)
               if (c0 + c < PM1) {
-                const float z = cs[(j0 + v) * CSTR + 1 + c0 + c] * fmaf(F, __uint_as_float(lz[c][v]), __uint_as_float(hz[c][v]));
+                const float z = cs[(j0 + v) * CSTR + 1 + c0 + c] * fmaf(FV, __uint_as_float(lz[c][v]), __uint_as_float(hz[c][v]));
                 z_r[4 * g + v][c0 + c] = z;
                 zz_r[4 * g + v] = fmaf(z, z, zz_r[4 * g + v]);
               }

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(32 + GemvPar<Q>::THR, 1)
   constexpr int NT = GemvPar<Q>::NT, GTHR = GemvPar<Q>::THR;
   const int ct = threadIdx.x - 32, r = ct % 128;  // row r of tiles t0 .. t0 + NT - 1
   const int t0 = NT == 2 ? 0 : ct / 128;
-  const float inv_dof = 1.f / a.dof, F = 1.f / 256.f;
+  const float inv_dof = 1.f / a.dof, F = 1.f / 256.f, FV = 1.f / 512.f;  // FV: the v' columns' second slice
   const int full_b = a.full_b;
   unsigned long long nsing = 0;
   uint32_t h = 0;
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(32 + GemvPar<Q>::THR, 1)
       float z[Q1], zz = 0.f;
 #pragma unroll
       for (int c = 0; c < PM1; ++c) {
-        z[c] = cj[1 + c] * fmaf(F, acc_t[2 + PM1 + c], acc_t[1 + c]);
+        z[c] = cj[1 + c] * fmaf(FV, acc_t[2 + PM1 + c], acc_t[1 + c]);
         zz = fmaf(z[c], z[c], zz);
       }
       const float lvl1 = (c2t[1] + c2t[2]) + (c2t[3] + c2t[4]) + c2t[5];

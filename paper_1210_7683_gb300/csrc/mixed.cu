@@ -443,7 +443,9 @@ __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__
         if (!pair) row = (s < 2 ? s * (1 + Q) + c : 2 * Q + s) * TT + jj;
         else row = (s == 0 ? 0 : s == 1 ? 5 * TT : s == 2 ? 4 * TT : 9 * TT) + (s < 2 ? c * TT : 0) + jj;
         b1[(size_t)row * Kpad + l] = __float2bfloat16((float)q);
-        t = (t - q) * 256.0;
+        // w: 8-bit slices below the first; v': a 9-bit second slice (|q| <= 256 is exact in bf16
+        // and 2 * 256 * n stays below 2^24), which halves z's truncation error
+        t = (t - q) * (c == 0 ? 256.0 : 512.0);
       }
     }
     __syncthreads();
