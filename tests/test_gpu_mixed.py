@@ -306,3 +306,49 @@ def test_degenerate_shapes(gw, n, m, t, pm1):
     assert full_b_err(full.transpose(1, 0, 2), b, se) <= TOL
     empty, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE, 0, 0)
     assert rc == gw.GWAS_OK and empty.size == 0
+
+
+def _conditioning(P):
+    """kappa[i, j] = rr_j / RSS_ij in FP64: the whitened residual of y_j on X_L over that on
+    [X_L | x_i].  The SE is sqrt(RSS / ((n - p) delta)) with RSS = rr - num^2 / delta, so a relative
+    error eps in num^2 / delta moves the SE by about eps * kappa / 2."""
+    lam, Z = np.linalg.eigh(P.phi)
+    kap = np.empty((P.m, P.t))
+    for j in range(P.t):
+        e = 1.0 / (P.h2[j] * lam + 1.0 - P.h2[j])
+        W = (Z * e) @ Z.T                                  # M_j^-1
+        XL = P.XL.T
+        y = P.Y[j]
+
+        def rss(X):
+            A = X.T @ W @ X
+            bb = np.linalg.solve(A, X.T @ W @ y)
+            r = y - X @ bb
+            return r @ W @ r
+
+        rr = rss(XL)
+        for i in range(P.m):
+            kap[i, j] = rr / rss(np.column_stack([XL, P.XR[i].astype(np.float64)]))
+    return kap
+
+
+@pytest.mark.parametrize("n,pm1", [(5, 3), (21, 19), (6, 3), (22, 19)])
+def test_one_and_two_degrees_of_freedom(gw, n, pm1):
+    """n - p of 1 and 2 on the mixed path: the SNP coefficient stays within the 1e-6 bar; the SE
+    stays within 1e-6 where the residual is not a tiny difference, and elsewhere within a bound
+    proportional to rr / RSS (the conditioning of RSS = rr - num^2 / delta: about 1e-7 relative
+    error in num^2 / delta from the slices, whatever precision the subtraction is done in)."""
+    P = make_problem(n, 150, 30, pm1=pm1, seed=7000 + n + pm1)
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
+    out, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE)
+    bl = b[..., -1]
+    beta, s = out[0].T.astype(np.float64), out[1].T.astype(np.float64)
+    ok = np.isfinite(bl) & np.isfinite(se) & (se > 0)
+    assert ok.mean() > 0.9
+    assert np.all(np.isfinite(beta[ok])) and np.all(s[ok] > 0)
+    assert np.max(np.abs(beta - bl)[ok] / np.maximum(np.abs(bl), se)[ok]) <= TOL
+    kap = _conditioning(P)
+    rel = np.abs(s - se) / se
+    assert np.all(rel[ok] <= TOL + 1e-6 * kap[ok])
+    well = ok & (kap <= 10)
+    assert well.sum() > 0 and np.max(rel[well]) <= TOL
