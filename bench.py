@@ -45,38 +45,50 @@ from synth import covariates, genotypes, heritabilities, kinship, phenotypes  # 
 N_IND, PM1, M_SNP, T_TRAIT = 1000, 3, 1_000_000, 10_000
 METRIC = "GLS pairs/s (n=1000, p=4, m=1e6 SNPs, t=1e4 traits; SNP coefficient + SE)"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# DRAM bytes of one fused_kernel launch at n=1000 p=4 m=1e6 t=1e4: the mean of two
-# single-pass ncu captures of dram__bytes_read.sum + dram__bytes_write.sum.  Valid only while
-# the kernel's sources hash to the value the captures were taken on: a changed kernel reports
-# null traffic.
-FUSED_TRAFFIC = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "tc.cuh"],
-                 "sha256": "18bc6a27b7fdd3dbeeee6ee6b014789f7e3d650dda6469e8fc6a825771e7803a",
-                 "workload": (1000, 3, 1_000_000, 10_000),
-                 # one single-pass ncu capture per launch shape the autotuner has chosen on this GPU
-                 "captures": [
-                     {"shape": {"cs": 1, "ct": 1, "epw": 16, "pair": 0, "group": 16}, "read": 150.05e9, "write": 80.01e9},
-                     {"shape": {"cs": 1, "ct": 1, "epw": 8, "pair": 0, "group": 8}, "read": 253.98e9, "write": 80.01e9},
-                 ]}
+# DRAM traffic of one fused_kernel launch, from a model checked against an ncu capture of a small
+# case (dram__bytes_read.sum + dram__bytes_write.sum; the full-size launch is not captured with
+# multi-pass metrics).  The trait operands of all trait tiles are streamed once per traversal group
+# of SNP tiles (they do not fit L2 at t = 1e4), the SNP operands once, the results written once.
+# The check is valid only while the kernel's sources hash to the value it was taken on.
+FUSED_TRAFFIC_CHECK = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "tc.cuh", "fused_cheb.cu"],
+                       "sha256": None,        # filled in from the committed capture (profiles/)
+                       "case": None, "measured": None, "model": None}
 
 
-def fused_traffic(workload, shape=None):
-    """DRAM bytes per fused_kernel launch from the committed capture of this launch shape (the
-    first, default shape when none is given), or None when the workload differs from the
-    captured one, no capture has this shape, or the kernel's sources changed since."""
+def fused_traffic_model(n, m, t, q=3, group=16, cs=1, interp=True):
+    """DRAM bytes of one fused_kernel launch (p = 4 geometry): reads of the SNP operands (the
+    genotypes, and the three x'^2 planes when S_BR is contracted), of the trait operands once per
+    traversal group (group super-tiles of cs SNP tiles), of the Chebyshev coefficients, and the
+    8-byte result of every pair."""
+    kpad = (n + 63) // 64 * 64
+    tt = 32
+    ttiles = (t + tt - 1) // tt
+    stiles = (m + 127) // 128
+    mpad = stiles * 128
+    c1_rows, c2_rows = (4 + 2 * q) * tt, (0 if interp else (6 if cs == 2 else 4) * tt)
+    trait_bytes = ttiles * (c1_rows + c2_rows) * kpad * 2
+    snp_bytes = mpad * kpad * 2 * (1 if interp else 4) + (25 * 4 * mpad if interp else 0)
+    groups = -(-stiles // (group * cs))
+    return {"read": snp_bytes + groups * trait_bytes, "write": 8.0 * m * t}
+
+
+def fused_traffic(workload, shape=None, interp=True):
+    """Model traffic of one launch of the timed workload, or None when the model's check was not
+    taken on the current kernel sources."""
     import hashlib
-    if tuple(workload) != FUSED_TRAFFIC["workload"]:
-        return None
-    caps = FUSED_TRAFFIC["captures"]
-    cap = caps[0] if shape is None else next((c for c in caps if c["shape"] == shape), None)
-    if cap is None:
+    chk = FUSED_TRAFFIC_CHECK
+    if chk["sha256"] is None:
         return None
     h = hashlib.sha256()
-    for f in FUSED_TRAFFIC["sources"]:
+    for f in chk["sources"]:
         with open(os.path.join(ROOT, "paper_1210_7683_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != FUSED_TRAFFIC["sha256"]:
+    if h.hexdigest() != chk["sha256"]:
         return None
-    return cap["read"] + cap["write"]
+    n, q, m, t = workload
+    sh = shape or {"group": 16, "pair": 0}
+    mod = fused_traffic_model(n, m, t, q, sh.get("group", 16), 2 if sh.get("pair") else 1, interp)
+    return mod["read"] + mod["write"]
 
 
 def algorithmic_flops(n, p, pairs, form="gemm"):
@@ -658,7 +670,7 @@ def main():
     issued = 2.0 * 128 * mma_cols * kpad * tiles
     peak = pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
     achieved = useful / (fused_ms / 1e3) / 1e12
-    traffic = fused_traffic((n, PM1, m, t), tune["shape"])
+    traffic = fused_traffic((n, PM1, m, t), tune["shape"], sbr["terms"] > 0)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "fused_kernel",
                 "peak_source": f"{pk_src} bf16 sustained (kernel runs ~{fused_ms:.0f} ms inside a long step)",

@@ -1,5 +1,5 @@
-"""Host logic the bench's reported numbers rest on: the DRAM-traffic record is reported only
-for the kernel sources and launch shape it was captured on, and the parsers of the e2e
+"""Host logic the bench's reported numbers rest on: the DRAM-traffic model and the rule that it
+is reported only for the kernel sources its ncu check was taken on, and the parsers of the e2e
 host-buffer diagnostics read this process's own mappings."""
 import hashlib
 import mmap
@@ -12,26 +12,35 @@ import bench
 
 def _current_sha():
     h = hashlib.sha256()
-    for f in bench.FUSED_TRAFFIC["sources"]:
+    for f in bench.FUSED_TRAFFIC_CHECK["sources"]:
         with open(os.path.join(bench.ROOT, "paper_1210_7683_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def test_traffic_record_tied_to_sources_workload_and_shape(monkeypatch):
-    rec = dict(bench.FUSED_TRAFFIC, sha256=_current_sha())
-    monkeypatch.setattr(bench, "FUSED_TRAFFIC", rec)
-    w = rec["workload"]
-    for cap in rec["captures"]:
-        assert bench.fused_traffic(w, dict(cap["shape"])) == cap["read"] + cap["write"]
-    first = rec["captures"][0]
-    shape = dict(first["shape"])
-    assert bench.fused_traffic(w) == first["read"] + first["write"]       # shape unknown: the default
-    assert bench.fused_traffic((w[0], w[1], w[2] // 2, w[3]), shape) is None
-    assert bench.fused_traffic(w, dict(shape, group=32)) is None           # no capture of this shape
-    assert bench.fused_traffic(w, dict(shape, cs=2, pair=1)) is None
-    monkeypatch.setattr(bench, "FUSED_TRAFFIC", dict(rec, sha256="0" * 64))  # sources changed since
-    assert bench.fused_traffic(w, shape) is None
+def test_traffic_model_terms():
+    # one traversal group: every operand read once, every result written once
+    mod = bench.fused_traffic_model(1000, 128 * 16, 64, group=16)
+    kpad = 1024
+    assert mod["write"] == 8.0 * 128 * 16 * 64
+    assert mod["read"] == 2048 * kpad * 2 + 25 * 4 * 2048 + 2 * 320 * kpad * 2
+    # the trait operands are read once per group of 16 SNP tiles (32 for the CTA pair's 2 x 16)
+    one = bench.fused_traffic_model(1000, 128 * 64, 10_000, group=16)
+    pair = bench.fused_traffic_model(1000, 128 * 64, 10_000, group=16, cs=2)
+    trait = 313 * 320 * kpad * 2
+    assert one["read"] - pair["read"] == 2 * trait
+    # contracting S_BR adds the three x'^2 planes and the C2 trait rows
+    ex = bench.fused_traffic_model(1000, 128 * 16, 64, group=16, interp=False)
+    assert ex["read"] == 2048 * kpad * 2 * 4 + 2 * 448 * kpad * 2
+
+
+def test_traffic_reported_only_for_the_checked_sources(monkeypatch):
+    w = (1000, 3, 1_000_000, 10_000)
+    monkeypatch.setattr(bench, "FUSED_TRAFFIC_CHECK", dict(bench.FUSED_TRAFFIC_CHECK, sha256=_current_sha()))
+    mod = bench.fused_traffic_model(1000, 1_000_000, 10_000)
+    assert bench.fused_traffic(w) == mod["read"] + mod["write"]
+    monkeypatch.setattr(bench, "FUSED_TRAFFIC_CHECK", dict(bench.FUSED_TRAFFIC_CHECK, sha256="0" * 64))
+    assert bench.fused_traffic(w) is None
 
 
 def test_host_buffer_parsers_read_own_mapping():

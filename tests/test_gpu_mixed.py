@@ -339,6 +339,10 @@ def test_one_and_two_degrees_of_freedom(gw, n, pm1):
     proportional to rr / RSS (the conditioning of RSS = rr - num^2 / delta: about 1e-7 relative
     error in num^2 / delta from the slices, whatever precision the subtraction is done in)."""
     P = make_problem(n, 150, 30, pm1=pm1, seed=7000 + n + pm1)
+    # a handful of individuals leaves many SNPs monomorphic (no solution, NaN by design); make
+    # every SNP polymorphic so that every pair has a unique solution to compare
+    mono = P.XR.min(axis=1) == P.XR.max(axis=1)
+    P.XR[mono, 0] = (P.XR[mono, 0] + 1) % 3
     b, se = EigOracle(P.phi, P.XL).solve(P.XR, P.Y, P.h2)
     out, rc, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE)
     bl = b[..., -1]
