@@ -615,8 +615,11 @@ def main():
     ctx = g.gwas_setup(n, PM1, inp_d["phi"], inp_d["XL"], t, inp_d["h2"], o_t)
     try:
         g.gwas_load_snps(ctx, m, inp_d["XR"], n)
-        tune_ms = None if args.no_tune else g.gwas_autotune(ctx, inp_d["Y"], min(t, 1024), min(m, 1 << 17))
-        tune = {"shape": g.gwas_tune_shape(ctx), "sample": f"SNPs [0,{min(m, 1 << 17)}) x traits [0,{min(t, 1024)})",
+        # the sample keeps every trait, so that its trait operands stream from DRAM as in the full
+        # grid (the traversal group size matters only then), and 2^17 SNPs
+        t_s, m_s = min(t, 10_000), min(m, 1 << 17)
+        tune_ms = None if args.no_tune else g.gwas_autotune(ctx, inp_d["Y"], t_s, m_s)
+        tune = {"shape": g.gwas_tune_shape(ctx), "sample": f"SNPs [0,{m_s}) x traits [0,{t_s})",
                 "sample_ms": tune_ms}
         sbr = g.gwas_sbr_info(ctx)
     finally:
