@@ -59,9 +59,10 @@ __host__ __device__ constexpr int h2_bytes(int q) { return 3 * G_BYTES + c2_rows
 // per K block (G + C1 half: 36 KB; C2 half + A1: 28 KB; A2 + A3s: 32 KB) and a ring of six
 // 36 KB slots, i.e. two K blocks in flight.
 constexpr int PSLOT = 36 * 1024, PSLOTS = 6;
-// The pair with S_BR interpolated: item 0 only, in six slots; its Chebyshev coefficients are read
-// from global memory (L1) instead of being staged, to make room for the sixth slot.
-constexpr int PSLOTS_INTERP = 6;
+// The pair with S_BR interpolated: item 0 only, five slots in flight.  (Six slots, with the
+// Chebyshev coefficients read through L1 instead of staged to make room, measured 140 ms at a
+// traversal group of 8 and 167-175 ms at 16-64, against 136-141 ms for this layout.)
+constexpr int PSLOTS_INTERP = 5;
 constexpr int PC1_ROWS = c1_rows(3) / 2, PC2_ROWS = c2_alloc(3) / 2;  // 160 and 96 trait rows per CTA
 constexpr int PI0_BYTES = G_BYTES + PC1_ROWS * ROWB;   // G + this CTA's C1 trait rows
 constexpr int PI1_BYTES = PC2_ROWS * ROWB + G_BYTES;   // this CTA's C2 trait rows + A1
@@ -72,13 +73,12 @@ __host__ __device__ constexpr int slot_bytes(bool interp, int q) { return interp
 __host__ __device__ constexpr int ring_bytes(bool pair, bool interp, int q) {
   return pair ? (interp ? PSLOTS_INTERP : PSLOTS) * PSLOT : SLOTS * slot_bytes(interp, q);
 }
-// INTERP: the tile's Chebyshev coefficients [CHEB_MAX_R + 1][128 SNPs] (one-CTA shapes) and
-// T_k(x_j) [CHEB_MAX_R][TT]
-__host__ __device__ constexpr int cheb_stage_bytes(bool interp, int q, bool pair = false) {
-  return interp ? ((pair ? 0 : (CHEB_MAX_R + 1) * 128) + CHEB_MAX_R * mixed_tt(q)) * 4 : 0;
+// INTERP: the tile's Chebyshev coefficients [CHEB_MAX_R + 1][128 SNPs] and T_k(x_j) [CHEB_MAX_R][TT]
+__host__ __device__ constexpr int cheb_stage_bytes(bool interp, int q) {
+  return interp ? ((CHEB_MAX_R + 1) * 128 + CHEB_MAX_R * mixed_tt(q)) * 4 : 0;
 }
 __host__ __device__ constexpr int smem_bytes(bool pair, int q, bool interp = false) {
-  return ring_bytes(pair, interp, q) + 2 * cst_bytes(q) + cheb_stage_bytes(interp, q, pair) + 1024 + 512;
+  return ring_bytes(pair, interp, q) + 2 * cst_bytes(q) + cheb_stage_bytes(interp, q) + 1024 + 512;
 }
 constexpr int TMEM_COLS = 512;
 constexpr bool fits_all_q() {
@@ -148,10 +148,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* cst_smem = (float*)(smem + RING);  // [2][TT][CSTR], double-buffered by tile
-  constexpr bool STAGE_C = !PAIR;                           // INTERP: coefficients staged in smem
   float* cheb_c = cst_smem + 2 * TT * CSTR;                // INTERP: [CHEB_MAX_R + 1][128]
-  float* cheb_t = cheb_c + (STAGE_C ? (CHEB_MAX_R + 1) * 128 : 0);  // INTERP: [CHEB_MAX_R][TT]
-  uint64_t* full = (uint64_t*)(smem + RING + 2 * cst_bytes(Q) + cheb_stage_bytes(INTERP, Q, PAIR));
+  float* cheb_t = cheb_c + (CHEB_MAX_R + 1) * 128;          // INTERP: [CHEB_MAX_R][TT]
+  uint64_t* full = (uint64_t*)(smem + RING + 2 * cst_bytes(Q) + cheb_stage_bytes(INTERP, Q));
   uint64_t* empty = full + NSL;
   uint64_t* acc_full = empty + NSL;
   uint64_t* acc_empty = acc_full + 1;
@@ -421,11 +420,11 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         // traits' T_k(x_j); one buffer: every warp passed barrier 2 of the previous tile, which
         // follows its last read of these
         const int R = a.cheb_R;
-        if (STAGE_C)
-          for (int e = ew * 32 + lane; e < (R + 1) * 128; e += EPW * 32) {
-            const int k = e >> 7, kk = k < R ? k : CHEB_MAX_R;
-            cheb_c[e] = a.cheb_coef[(int64_t)kk * a.cheb_ld + snp0 + (e & 127)];
-          }
+#pragma unroll 4
+        for (int e = ew * 32 + lane; e < (R + 1) * 128; e += EPW * 32) {
+          const int k = e >> 7, kk = k < R ? k : CHEB_MAX_R;
+          cheb_c[e] = a.cheb_coef[(int64_t)kk * a.cheb_ld + snp0 + (e & 127)];
+        }
         for (int e = ew * 32 + lane; e < R * TT; e += EPW * 32) {
           const int k = e / TT, jl = e % TT;
           cheb_t[e] = jbase + jl < ntrait ? a.cheb_T[(size_t)(jbase + jl) * CHEB_MAX_R + k] : 0.f;
@@ -536,18 +535,14 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         // in FP32 from the smallest term up, then c_0 (two floats) + c_1 T_1 (with the product's
         // rounding error) added last, so that s carries about one rounding of its own size
         const int R = a.cheb_R, i = q * 32 + lane;
-        // the coefficients of this thread's SNP: staged (one-CTA) or from global memory (pair)
-        const float* cb = STAGE_C ? cheb_c + i : a.cheb_coef + snp0 + i;
-        const int64_t cld = STAGE_C ? 128 : a.cheb_ld;
 #pragma unroll
         for (int r = 0; r < JPW; ++r) s_r[r] = 0.f;
-#pragma unroll 4
         for (int k = R - 1; k >= 2; --k) {
-          const float ck = cb[k * cld];
+          const float ck = cheb_c[k * 128 + i];
 #pragma unroll
           for (int r = 0; r < JPW; ++r) s_r[r] = fmaf(ck, cheb_t[k * TT + jbeg + r], s_r[r]);
         }
-        const float c0 = cb[0], c1 = cb[cld], c0lo = cb[(STAGE_C ? R : CHEB_MAX_R) * cld];
+        const float c0 = cheb_c[i], c1 = cheb_c[128 + i], c0lo = cheb_c[R * 128 + i];
 #pragma unroll
         for (int r = 0; r < JPW; ++r) {
           const float t1 = cheb_t[TT + jbeg + r];
