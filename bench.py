@@ -58,6 +58,19 @@ FUSED_TRAFFIC_CHECK = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "t
                        "model": {"pair_g32": (445.4e6, 1310.7e6), "one_g16": (1676.2e6, 1310.7e6)}}
 
 
+# sm__pipe_tensor_cycles_active (% of peak, active cycles) of the interpolated fused kernel from the
+# full-set ncu captures of the small case n = 1000, m = 131072, t = 1024 (one launch each;
+# profiles/fused_kernel_interp_n1000_m131072_t1024.md), valid for the same sources as the check above.
+TENSOR_PIPE_NCU = {"pair": 62.6, "one_cta": 57.5}
+
+
+def tensor_pipe_counter(shape):
+    """The ncu tensor-pipe counter of the launch shape, or None when the sources changed since."""
+    if fused_traffic((1000, 3, 128, 32)) is None:
+        return None
+    return TENSOR_PIPE_NCU["pair" if (shape or {}).get("pair") else "one_cta"]
+
+
 def fused_traffic_model(n, m, t, q=3, group=16, cs=1, interp=True):
     """DRAM bytes of one fused_kernel launch (p = 4 geometry): reads of the SNP operands (the
     genotypes, and the three x'^2 planes when S_BR is contracted), of the trait operands once per
@@ -684,6 +697,10 @@ def main():
                 "issued_frac": issued / (fused_ms / 1e3) / 1e12 / peak,
                 "issued_note": "issued = MMA columns x 128 rows x 2 Kpad per tile (an analytic count of the "
                                "tcgen05.mma work, not the ncu tensor-pipe counter)",
+                "tensor_pipe_ncu_pct": tensor_pipe_counter(tune["shape"]) if sbr["terms"] > 0 else None,
+                "tensor_pipe_note": "sm__pipe_tensor_cycles_active of this launch shape in a full-set ncu capture "
+                                    "of the small case n=1000 m=131072 t=1024 (profiles/); null if the kernel "
+                                    "sources changed since",
                 "algorithmic_flops_per_launch": useful, "launch_ms": fused_ms,
                 "s_br": dict(sbr, note="terms > 0: S_BR from its Chebyshev series in h^2 over the traits' "
                                        "heritabilities (relative error <= bound), contracted exactly at the "
