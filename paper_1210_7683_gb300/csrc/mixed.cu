@@ -841,12 +841,15 @@ __global__ void __launch_bounds__(256) cheb_coef_kernel(const float* __restrict_
   __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= ld) return;
+  // rows past m (tile padding) get zero coefficients; their node sums were never written
   double sv[CHEB_MAX_R];
-  const double a = i < m ? (double)sA[i] : 0.0;
+  const bool in = i < m;
+  const double a = in ? (double)sA[i] : 0.0;
 #pragma unroll
   for (int r = 0; r < CHEB_MAX_R; ++r)
-    sv[r] = r < R ? a * sesc[r] * ((double)raw[(size_t)r * ld + i] + (double)raw[(size_t)(R + r) * ld + i] * (1.0 / 256.0))
-                  : 0.0;
+    sv[r] = (in && r < R)
+                ? a * sesc[r] * ((double)raw[(size_t)r * ld + i] + (double)raw[(size_t)(R + r) * ld + i] * (1.0 / 256.0))
+                : 0.0;
   for (int k = 0; k < R; ++k) {
     double ck = 0.0;
 #pragma unroll
