@@ -34,6 +34,8 @@
 // Every MMA of a K step writes its own columns, so consecutive small MMAs do not wait
 // on one another's accumulator (a chain of dependent N <= 128 MMAs runs at the MMA
 // latency, not at the tensor-core rate); the epilogue adds the level-1 groups.
+// With S_BR interpolated (INTERP, the default where its bound holds) the C2 columns are
+// not used: only [0, 320) at p = 4, and the K loop streams only the C1 operands.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
