@@ -806,11 +806,11 @@ extern "C" int gwas_solve_ooc(gwas_ctx* c, int64_t m, const int8_t* XR, int64_t 
   if (mixed) {
     if ((rc = mixed_ws_alloc(c, tb, &ws))) return fail(rc);
     kp = mixed_kpad(c);
-    if ((rc = talloc(2ull * nblocks * tpb * c1_rows(q) * kp, (void**)&B1)) ||
+    if ((rc = talloc(2ull * nblocks * c1_alloc_rows(q, tb) * kp, (void**)&B1)) ||
         (rc = talloc(2ull * nblocks * tpb * c2_alloc(q) * kp, (void**)&B2)) ||
         (rc = talloc(sizeof(float) * nblocks * tpb * TT * cst_stride(q), (void**)&cst32)))
       return fail(rc);
-    cudaMemsetAsync(B1, 0, 2ull * nblocks * tpb * c1_rows(q) * kp, c->stream);
+    cudaMemsetAsync(B1, 0, 2ull * nblocks * c1_alloc_rows(q, tb) * kp, c->stream);
     cudaMemsetAsync(B2, 0, 2ull * nblocks * tpb * c2_alloc(q) * kp, c->stream);
   } else if ((rc = talloc(sizeof(double) * tb * n, (void**)&Yt)) ||
              (rc = talloc(sizeof(double) * t * (p + 1) * n, (void**)&R)) ||
@@ -818,13 +818,16 @@ extern "C" int gwas_solve_ooc(gwas_ctx* c, int64_t m, const int8_t* XR, int64_t 
              (rc = ctx_alloc(c, sizeof(double) * slab * n, (void**)&c->Xt))) {
     return fail(rc);
   }
-  auto b1_of = [&](int b) { return B1 + (size_t)b * tpb * c1_rows(q) * kp; };
+  auto b1_of = [&](int b) { return B1 + (size_t)b * c1_alloc_rows(q, tb) * kp; };
   auto b2_of = [&](int b) { return B2 + (size_t)b * tpb * c2_alloc(q) * kp; };
   auto cst_of = [&](int b) { return cst32 + (size_t)b * tpb * TT * cst_stride(q); };
   for (int b = 0; b < nblocks && rc == GWAS_OK; ++b) {
     const int j0 = b * tb, nb = std::min(tb, t - j0);
     if (mixed) {
-      rc = mixed_prep_traits(c, ws, dY + (size_t)j0 * n, c->h2 + j0, nb, b1_of(b), b2_of(b), cst_of(b), nullptr, pair);
+      // the layout of the kernel that runs this block (interpolated S_BR or contracted)
+      const bool ip = mixed_block_interp(c, nb);
+      rc = mixed_prep_traits(c, ws, dY + (size_t)j0 * n, c->h2 + j0, nb, b1_of(b), b2_of(b), cst_of(b), nullptr,
+                             ip ? 0 : pair, ip ? tile_traits(q, true) : 0);
     } else {
       launch_rotate_fp64_f64(c, dY + (size_t)j0 * n, nb, n, Yt);
       launch_prep_fp64(c, Yt, nb, c->h2 + j0, R + (size_t)j0 * (p + 1) * n, cst + (size_t)j0 * consts_stride(q));

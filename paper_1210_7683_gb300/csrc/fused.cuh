@@ -25,6 +25,18 @@ __host__ __device__ constexpr int c2_alloc(int q) { return 6 * mixed_tt(q); }
 constexpr int MIXED_MAX_Q = 19;
 // S_BR by Chebyshev interpolation in h^2: at most this many terms (node heritabilities).
 constexpr int CHEB_MAX_R = 24;
+// Trait-tile width of the kernel with S_BR interpolated: at q = 3 tiles of 24 traits, so that the
+// C1 operand (10 groups, 240 rows) is one MMA of N <= 256 per K step and its accumulators can be
+// double-buffered in TMEM; other q keep mixed_tt(q).  Its C1 operand is always in the one-CTA
+// layout: the CTA pair splits that single MMA's rows in halves.
+__host__ __device__ constexpr int tile_traits(int q, bool interp) { return interp && q == 3 ? 24 : mixed_tt(q); }
+__host__ __device__ constexpr int c1_rows_of(int q, bool interp) { return c1_groups(q) * tile_traits(q, interp); }
+// C1 operand rows to allocate for ntrait traits in either layout (trait tiles padded to a multiple of 4)
+__host__ __device__ constexpr int64_t c1_alloc_rows(int q, int ntrait) {
+  const int64_t a = ((ntrait + mixed_tt(q) - 1) / mixed_tt(q) + 3) / 4 * 4 * (int64_t)c1_rows(q);
+  const int64_t b = ((ntrait + tile_traits(q, true) - 1) / tile_traits(q, true) + 3) / 4 * 4 * (int64_t)c1_rows_of(q, true);
+  return a > b ? a : b;
+}
 
 // Runs the statement in the variadic arguments with the compile-time constant Q = q (0..7,
 // larger values run as 7).

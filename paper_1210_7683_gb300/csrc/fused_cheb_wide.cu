@@ -8,10 +8,10 @@ int launch_fused_cheb_wide(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bf
   if (q < 8 || q > MIXED_MAX_Q) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "interpolated fused kernel: p-1 outside [8, 19]");
   if (a.cheb_R < 2 || a.cheb_R > CHEB_MAX_R) return ctx_fail(c, GWAS_ERR_ARG, "Chebyshev terms outside [2, 24]");
   CUtensorMap mg, m1;
-  const int r1 = c1_rows(q), b1box = r1 <= 256 ? r1 : r1 / 2;
+  const int r1 = c1_rows_of(q, true), b1box = r1 <= 256 ? r1 : r1 / 2;
   if (!make_bf16_map(&mg, G, a.mpad, a.Kpad, BM, BK) ||
       !make_bf16_map(&m1, B1, (uint64_t)b_tiles * r1, a.Kpad, b1box, BK))
     return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
-  Q_DISPATCH_WIDE(q, return launch_shape<epw_for(Q), false, false, Q, true>(c, a, mg, mg, m1, m1));
+  Q_DISPATCH_WIDE(q, return launch_shape<epw_interp(Q), false, false, Q, true>(c, a, mg, mg, m1, m1));
   return GWAS_OK;
 }

@@ -61,19 +61,23 @@ __host__ __device__ constexpr int h2_bytes(int q) { return 3 * G_BYTES + c2_rows
 // per K block (G + C1 half: 36 KB; C2 half + A1: 28 KB; A2 + A3s: 32 KB) and a ring of six
 // 36 KB slots, i.e. two K blocks in flight.
 constexpr int PSLOT = 36 * 1024, PSLOTS = 6;
-// The pair with S_BR interpolated: item 0 only, five slots in flight.  (Six slots, with the
-// Chebyshev coefficients read through L1 instead of staged to make room, measured 140 ms at a
-// traversal group of 8 and 167-175 ms at 16-64, against 136-141 ms for this layout.)
-constexpr int PSLOTS_INTERP = 5;
+// With S_BR interpolated a K block is one item: the genotype tile and the C1 trait rows (one CTA),
+// or the CTA's own genotype rows and its half of the C1 rows (pair).  At q = 3 the 24-trait tiles
+// make that 46 KB (one CTA, 4 slots) or 31 KB (pair, 6 slots).
+__host__ __device__ constexpr int interp_item_bytes(int q, bool pair) {
+  return G_BYTES + (pair ? c1_rows_of(q, true) / 2 : c1_rows_of(q, true)) * ROWB;
+}
+__host__ __device__ constexpr int interp_slots(int q, bool pair) { return pair ? 6 : q == 3 ? 4 : 3; }
 constexpr int PC1_ROWS = c1_rows(3) / 2, PC2_ROWS = c2_alloc(3) / 2;  // 160 and 96 trait rows per CTA
 constexpr int PI0_BYTES = G_BYTES + PC1_ROWS * ROWB;   // G + this CTA's C1 trait rows
 constexpr int PI1_BYTES = PC2_ROWS * ROWB + G_BYTES;   // this CTA's C2 trait rows + A1
 constexpr int PI2_BYTES = 2 * G_BYTES;                 // A2 + A3s
 __host__ __device__ constexpr int cst_bytes(int q) { return mixed_tt(q) * cst_stride(q) * 4; }  // one tile's constants
-// With S_BR interpolated (INTERP) a K block is one item, the C1 half-stage, in slots of its own size.
-__host__ __device__ constexpr int slot_bytes(bool interp, int q) { return interp ? (h1_bytes(q) + 1023) / 1024 * 1024 : SLOT; }
+__host__ __device__ constexpr int slot_bytes(bool interp, int q, bool pair = false) {
+  return interp ? (interp_item_bytes(q, pair) + 1023) / 1024 * 1024 : pair ? PSLOT : SLOT;
+}
 __host__ __device__ constexpr int ring_bytes(bool pair, bool interp, int q) {
-  return pair ? (interp ? PSLOTS_INTERP : PSLOTS) * PSLOT : SLOTS * slot_bytes(interp, q);
+  return (interp ? interp_slots(q, pair) : pair ? PSLOTS : SLOTS) * slot_bytes(interp, q, pair);
 }
 // INTERP: the tile's Chebyshev coefficients [CHEB_MAX_R + 1][128 SNPs] and T_k(x_j) [CHEB_MAX_R][TT]
 __host__ __device__ constexpr int cheb_stage_bytes(bool interp, int q) {
@@ -86,7 +90,7 @@ constexpr int TMEM_COLS = 512;
 constexpr bool fits_all_q() {
   for (int q = 0; q <= MIXED_MAX_Q; ++q)
     if (h1_bytes(q) > SLOT || h2_bytes(q) > SLOT || smem_bytes(false, q) > 227 * 1024 ||
-        smem_bytes(false, q, true) > 227 * 1024)
+        smem_bytes(false, q, true) > 227 * 1024 || c1_rows_of(q, true) > 512)
       return false;
   return true;
 }
@@ -97,6 +101,8 @@ static_assert(smem_bytes(true, 3) <= 227 * 1024 && smem_bytes(true, 3, true) <= 
 // epilogue warps EPW for TT traits per tile: four lane quarters, each warp owning TT / (EPW / 4)
 // traits, read from TMEM in groups of 4
 __host__ __device__ constexpr bool JPW_OK(int tt, int epw) { return epw % 4 == 0 && tt % (epw / 4) == 0 && (tt / (epw / 4)) % 4 == 0; }
+// the epilogue warps of the interpolated kernel: 12 for its 24-trait tiles (8 traits per warp)
+__host__ __device__ constexpr int epw_interp(int q) { return tile_traits(q, true) == 24 ? 12 : mixed_tt(q) == 8 ? 8 : 16; }
 // the epilogue warps of a tile width: 16, or 8 for 8-trait tiles
 __host__ __device__ constexpr int epw_for(int q) { return mixed_tt(q) == 8 ? 8 : 16; }
 
@@ -126,14 +132,17 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   constexpr int CS = PAIR ? 2 : 1;                  // SNP tiles per cluster (the CTA pair: 2)
   static_assert(!PAIR || (!SERVE && Q == 3), "the pair shape is built for q = 3 outside serving");
   static_assert(!INTERP || !SERVE, "the interpolated S_BR is built for the solve kernels");
-  constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = mixed_tt(Q), CSTR = cst_stride(Q);
-  constexpr int B1_ROWS = c1_rows(Q), B2_ROWS = c2_rows(Q), B2_ROWS_PAIR = c2_alloc(Q);
+  constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = tile_traits(Q, INTERP), CSTR = cst_stride(Q);
+  constexpr int B1_ROWS = c1_groups(Q) * TT, B2_ROWS = c2_rows(Q), B2_ROWS_PAIR = c2_alloc(Q);
+  // the pair with S_BR interpolated: one MMA of N = B1_ROWS per K step, each CTA holding half of its rows
+  constexpr int PC1I = B1_ROWS / 2, PI0I = G_BYTES + PC1I * ROWB;
+  static_assert(!(PAIR && INTERP) || B1_ROWS <= 256, "the interpolated pair issues one MMA per K step");
   constexpr int C2B = c1_groups(Q) * TT;            // first TMEM column of the C2 accumulators
   // 8-trait tiles widen two C2 MMAs to N = 16 multiples: A1 also multiplies E2s (one unused
   // group in front), A3s also E2 (one unused group at the end)
   constexpr int C2_OFF = TT == 8 ? TT : 0;
   static_assert(JPW_OK(TT, EPW), "epilogue warps: each must own a multiple of 4 traits");
-  constexpr int H1_BYTES = h1_bytes(Q), H2_BYTES = h2_bytes(Q);
+  constexpr int H1_BYTES = G_BYTES + B1_ROWS * ROWB, H2_BYTES = h2_bytes(Q);
   // C1 MMAs of the one-CTA shapes: the C1 trait rows in chunks of at most 256 (N <= 256)
   constexpr int N0 = B1_ROWS < 256 ? B1_ROWS : 256, N1 = B1_ROWS - N0;
   // TMA boxes of the C1 trait rows in the one-CTA shapes (at most 256 rows per box)
@@ -143,8 +152,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   // tile and the C1 trait rows in one or two boxes; the three x'^2 planes, stored next to
   // one another, in two halves and the C2 trait rows).  The TMA unit pays a fixed cost per
   // box of the order of 50 cycles, so large boxes keep the load rate up.
-  constexpr int NSL = PAIR ? (INTERP ? PSLOTS_INTERP : PSLOTS) : SLOTS;   // ring slots
-  constexpr int SLB = PAIR ? PSLOT : slot_bytes(INTERP, Q);               // and their size
+  constexpr int NSL = INTERP ? interp_slots(Q, PAIR) : PAIR ? PSLOTS : SLOTS;  // ring slots
+  constexpr int SLB = slot_bytes(INTERP, Q, PAIR);                             // and their size
   constexpr int NI = INTERP ? 1 : PAIR ? 3 : 2;                           // ring items per K block
   constexpr int RING = ring_bytes(PAIR, INTERP, Q);
   extern __shared__ uint8_t smem_raw[];
@@ -238,10 +247,12 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             if (PAIR) {
               // own SNP rows and own half of the trait rows, completing on the leader's barrier
               const uint32_t fb = tc::mapa(&full[s], 0);
-              if (leader) tc::mbar_expect_tx(&full[s], 2 * (it == 0 ? PI0_BYTES : it == 1 ? PI1_BYTES : PI2_BYTES));
+              if (leader)
+                tc::mbar_expect_tx(&full[s], 2 * (INTERP ? PI0I : it == 0 ? PI0_BYTES : it == 1 ? PI1_BYTES : PI2_BYTES));
               if (it == 0) {
                 tc::tma_load_2d_pair(buf, &mapG, fb, x, row);
-                tc::tma_load_2d_pair(buf + G_BYTES, &mapB1, fb, x, tt * B1_ROWS + (int)crank * PC1_ROWS);
+                tc::tma_load_2d_pair(buf + G_BYTES, &mapB1, fb, x,
+                                     tt * B1_ROWS + (int)crank * (INTERP ? PC1I : PC1_ROWS));
               } else if (it == 1) {
                 tc::tma_load_2d_pair(buf, &mapB2, fb, x, tt * B2_ROWS_PAIR + (int)crank * PC2_ROWS);
                 tc::tma_load_2d_pair(buf + PC2_ROWS * ROWB, &mapA2, fb, x, (int)a2_row(0, row));
@@ -278,6 +289,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     if (PAIR && lane == 0 && leader) {
       constexpr uint32_t id256 = tc::idesc_bf16(2 * BM, 8 * TT), id64 = tc::idesc_bf16(2 * BM, 2 * TT);
       constexpr uint32_t id96 = tc::idesc_bf16(2 * BM, 3 * TT), id32 = tc::idesc_bf16(2 * BM, TT);
+      constexpr uint32_t idI = tc::idesc_bf16(2 * BM, B1_ROWS <= 256 ? B1_ROWS : 256);
       uint32_t h = 0, tcount = 0;
       bool ok = true;
       for (int u = cid; u < nsuper && ok; u += ncl, ++tcount) {
@@ -294,10 +306,15 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k) {
               const uint32_t acc = (kb | k) ? 1u : 0u;
-              // [Q1 | Q2] -> levels 0 and 1 of [w v1 v2 v3]; [Q3 | Q4] -> slices 3, 4 of w
-              tc::mma_bf16_pair(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), id256, acc);
-              tc::mma_bf16_pair(tbase + 8 * TT, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, 4 * TT * ROWB + k * 32),
-                                id64, acc);
+              if (INTERP) {
+                // one MMA over all C1 columns: each CTA supplies half of them, in the one-CTA order
+                tc::mma_bf16_pair(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), idI, acc);
+              } else {
+                // [Q1 | Q2] -> levels 0 and 1 of [w v1 v2 v3]; [Q3 | Q4] -> slices 3, 4 of w
+                tc::mma_bf16_pair(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), id256, acc);
+                tc::mma_bf16_pair(tbase + 8 * TT, tc::sdesc_add(dg, k * 32),
+                                  tc::sdesc_add(db, 4 * TT * ROWB + k * 32), id64, acc);
+              }
             }
             tc::mma_commit_pair(&empty[s], (uint16_t)3);
             ++h;

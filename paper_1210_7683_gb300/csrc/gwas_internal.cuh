@@ -135,8 +135,9 @@ void mixed_ws_free(gwas_ctx* c, MixedWs* ws);
 // Enqueues the per-trait operands of traits [0, tb) of dY (heritabilities h2, device) into
 // trait tiles slot[j/32] (identity when slot is NULL) of the operand arrays B1, B2, cst, in the
 // one-CTA layout or (pair != 0) the CTA-pair layout of the fused kernel.
+// tt: trait-tile width of the C1 layout (0: mixed_tt; the interpolated kernel's tile_traits(q, true)).
 int mixed_prep_traits(gwas_ctx* c, MixedWs* ws, const double* dY, const double* h2, int tb, __nv_bfloat16* B1,
-                      __nv_bfloat16* B2, float* cst, const int* slot, int pair);
+                      __nv_bfloat16* B2, float* cst, const int* slot, int pair, int tt = 0);
 // Enqueues (no synchronisation) the per-trait operands of traits [j0, j0+tb) into the workspace.
 int mixed_prep_block(gwas_ctx* c, MixedWs* ws, const double* dY, int j0, int tb);
 // Enqueues the fused kernel for the workspace's tb traits x SNPs [i0, i1) into dout.
@@ -159,6 +160,9 @@ int mixed_cheb_plan(gwas_ctx* c);
 int mixed_cheb_info(gwas_ctx* c, int* R, double* lo, double* hi, double* bound);
 // Whether the trait operands use the CTA-pair layout (the context's launch shape is the pair).
 int mixed_pair_layout(gwas_ctx* c);
+// Whether a block of tb of the context's traits runs the kernel with S_BR interpolated (tb > 1 and
+// the plan allows it); its trait operands then use that kernel's layout (tile_traits(q, true)).
+bool mixed_block_interp(gwas_ctx* c, int tb);
 // resident mixed-path data (for the serving kernel launches)
 int64_t mixed_mpad(gwas_ctx* c);
 int mixed_kpad(gwas_ctx* c);  // padded n of the mixed path's operands (after mixed setup)

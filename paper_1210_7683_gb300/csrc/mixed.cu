@@ -379,15 +379,17 @@ template <int Q>
 __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__ W, const double* __restrict__ XL,
                                                       const double* __restrict__ XtXinv, int n, int Kpad,
                                                       __nv_bfloat16* __restrict__ B1, float* __restrict__ cst,
-                                                      const int* __restrict__ slot, int pair) {
-  constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = mixed_tt(Q);
+                                                      const int* __restrict__ slot, int pair, int TT) {
+  constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1;
   const int j = blockIdx.x;
   const int p = PM1 + 1;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
   __shared__ double red[8][PM1 + 1];
   __shared__ double coef[Q1], smax;
+  // TT: the trait-tile width of the layout (mixed_tt(Q), or tile_traits(Q, true) for the kernel
+  // with S_BR interpolated); tiles of the C1 operand are c1_groups(Q) x TT rows
   const int tile = slot ? slot[j / TT] : j / TT, jj = j % TT;
-  __nv_bfloat16* b1 = B1 + (size_t)tile * c1_rows(Q) * Kpad;
+  __nv_bfloat16* b1 = B1 + (size_t)tile * c1_groups(Q) * TT * Kpad;
   for (int c = 0; c < p; ++c) {
     const double* col = W + ((size_t)j * p + c) * Kpad;
     double u[Q1] = {};
@@ -649,7 +651,7 @@ int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** out) {
       (rc = ctx_alloc(c, sizeof(double) * (size_t)tb_max * p * Kpad, (void**)&w->Wt)) ||
       (rc = ctx_alloc(c, 2ull * 4 * rowsW * Kpad, (void**)&w->Wsl)) ||
       (rc = ctx_alloc(c, sizeof(double) * rowsW, (void**)&w->sW)) ||
-      (rc = ctx_alloc(c, 2ull * (size_t)nt_alloc * c1_rows(q) * Kpad, (void**)&w->B1)) ||
+      (rc = ctx_alloc(c, 2ull * (size_t)c1_alloc_rows(q, tb_max) * Kpad, (void**)&w->B1)) ||
       (rc = ctx_alloc(c, 2ull * (size_t)nt_alloc * c2_alloc(q) * Kpad, (void**)&w->B2)) ||
       (rc = ctx_alloc(c, sizeof(float) * (size_t)nt_tiles * TT * cst_stride(q), (void**)&w->cst))) {
     mixed_ws_free(c, w);
@@ -660,7 +662,7 @@ int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** out) {
 }
 
 int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h2, int tb, __nv_bfloat16* B1,
-                      __nv_bfloat16* B2, float* cst, const int* slot, int pair) {
+                      __nv_bfloat16* B2, float* cst, const int* slot, int pair, int tt) {
   MixedState* s = c->mixed;
   if (!s || !s->Brot) return ctx_fail(c, GWAS_ERR_STATE, "mixed path not set up");
   if (tb > w->tb_max) return ctx_fail(c, GWAS_ERR_ARG, "trait block larger than its workspace");
@@ -704,7 +706,9 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h
   }
   if (rc == GWAS_OK) {
     ProfScope ps(c, "pack_trait_columns");
-    Q_DISPATCH_ALL(q, pack_c1_kernel<Q><<<tb, 256, 0, c->stream>>>(Wt, c->XL, s->XtXinv, n, Kpad, B1, cst, slot, pair));
+    const int TTc = tt > 0 ? tt : mixed_tt(q);
+    Q_DISPATCH_ALL(q, pack_c1_kernel<Q><<<tb, 256, 0, c->stream>>>(Wt, c->XL, s->XtXinv, n, Kpad, B1, cst, slot, pair,
+                                                                    TTc));
     c->launches++;
   }
   return rc;
@@ -718,16 +722,23 @@ int mixed_prep_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb) 
   const int nt_tiles = (tb + TT - 1) / TT;
   const int nt_alloc = (nt_tiles + fused_trait_tile_multiple() - 1) / fused_trait_tile_multiple() *
                        fused_trait_tile_multiple();
-  cudaMemsetAsync(w->B1, 0, 2ull * nt_alloc * c1_rows(q) * Kpad, c->stream);
+  cudaMemsetAsync(w->B1, 0, 2ull * c1_alloc_rows(q, tb) * Kpad, c->stream);
   cudaMemsetAsync(w->B2, 0, 2ull * nt_alloc * c2_alloc(q) * Kpad, c->stream);
-  return mixed_prep_traits(c, w, dY, c->h2 + j0, tb, w->B1, w->B2, w->cst, nullptr, mixed_pair_layout(c));
+  // the trait operands in the layout of the kernel that will run: the interpolated kernel's
+  // (its tile width, one-CTA order), or the contracting kernel's (pair order for the CTA pair)
+  const bool ip = mixed_block_interp(c, tb);
+  return mixed_prep_traits(c, w, dY, c->h2 + j0, tb, w->B1, w->B2, w->cst, nullptr, ip ? 0 : mixed_pair_layout(c),
+                           ip ? tile_traits(q, true) : 0);
 }
 
 int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B2, const float* cst, int tb, int64_t i0,
                     int64_t i1, int64_t ldo, void* out, int j0) {
   MixedState* s = c->mixed;
   if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
-  const int n = c->n, q = c->pm1, p = q + 1, Kpad = s->Kpad, TT = mixed_tt(q);
+  const int n = c->n, q = c->pm1, p = q + 1, Kpad = s->Kpad;
+  // S_BR from its Chebyshev series in h^2 when the plan allows it (traits of the context)
+  const bool interp = j0 >= 0 && mixed_block_interp(c, tb);
+  const int TT = tile_traits(q, interp);
   const int nt_tiles = (tb + TT - 1) / TT;
   int rc = GWAS_OK;
   {
@@ -761,8 +772,7 @@ int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B
     a.status = c->d_status;
     a.singular = c->d_status + 1;
     const bool gemv = tb == 1 && gemv1_supported(q, Kpad) && !mixed_pair_layout(c);
-    // S_BR from its Chebyshev series in h^2 when the plan allows it (traits of the context)
-    if (!gemv && j0 >= 0 && mixed_cheb_plan(c) == 1) {
+    if (interp) {
       if ((rc = cheb_coefficients(c))) return rc;
       a.cheb_coef = s->cheb.coef;
       a.cheb_T = s->cheb.T + (size_t)j0 * CHEB_MAX_R;
@@ -963,9 +973,9 @@ int mixed_cheb_plan(gwas_ctx* c) {
   const int q = c->pm1, Kpad = s->Kpad;
   const int nt_tiles = (CHEB_MAX_R + mixed_tt(q) - 1) / mixed_tt(q);
   const int nt_pad = (nt_tiles + fused_trait_tile_multiple() - 1) / fused_trait_tile_multiple() * fused_trait_tile_multiple();
-  cudaMemsetAsync(ch.ws->B1, 0, 2ull * nt_pad * c1_rows(q) * Kpad, c->stream);
+  cudaMemsetAsync(ch.ws->B1, 0, 2ull * c1_alloc_rows(q, CHEB_MAX_R) * Kpad, c->stream);
   cudaMemsetAsync(ch.ws->B2, 0, 2ull * nt_pad * c2_alloc(q) * Kpad, c->stream);
-  if (mixed_prep_traits(c, ch.ws, ch.yzero, ch.nodes, R, ch.ws->B1, ch.ws->B2, ch.ws->cst, nullptr, 0)) {
+  if (mixed_prep_traits(c, ch.ws, ch.yzero, ch.nodes, R, ch.ws->B1, ch.ws->B2, ch.ws->cst, nullptr, 0, 0)) {
     c->err.clear();
     return -1;
   }
@@ -980,6 +990,8 @@ int mixed_cheb_plan(gwas_ctx* c) {
 }
 
 int mixed_pair_layout(gwas_ctx* c) { return fused_pair_layout(c, c->pm1); }
+
+bool mixed_block_interp(gwas_ctx* c, int tb) { return tb > 1 && mixed_cheb_plan(c) == 1; }
 
 int mixed_cheb_info(gwas_ctx* c, int* R, double* lo, double* hi, double* bound) {
   const int st = c->mixed ? c->mixed->cheb.state : 0;
