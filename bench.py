@@ -161,19 +161,29 @@ def hugepage_fraction(addr, nbytes):
 
 
 def numa_pages(addr, nbytes):
-    """Pages of [addr, addr + nbytes) per NUMA node ({"N0": pages, ...}), from /proc/self/numa_maps
-    (None where that file is not readable)."""
+    """Pages per NUMA node ({"N0": pages, ...}) of the mappings that overlap [addr, addr + nbytes),
+    from /proc/self/numa_maps joined with the mapping ranges of /proc/self/maps (a fresh mapping
+    can be merged with its neighbour, so it need not start at addr).  None where those files are
+    not readable."""
     try:
-        lines = open("/proc/self/numa_maps").read().splitlines()
+        numa = open("/proc/self/numa_maps").read().splitlines()
+        maps = open("/proc/self/maps").read().splitlines()
     except OSError:
         return None
+    end_of = {}
+    for ln in maps:
+        head = ln.split()[0] if ln else ""
+        if "-" in head:
+            lo, hi = (int(x, 16) for x in head.split("-"))
+            end_of[lo] = hi
     out = {}
-    for ln in lines:
+    for ln in numa:
         f = ln.split()
         if not f:
             continue
         start = int(f[0], 16)
-        if not addr <= start < addr + nbytes:
+        end = end_of.get(start, start + 1)
+        if not (start < addr + nbytes and end > addr):
             continue
         for kv in f[1:]:
             if kv.startswith("N") and "=" in kv:
