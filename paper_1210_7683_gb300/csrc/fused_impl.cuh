@@ -156,6 +156,10 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   constexpr int SLB = slot_bytes(INTERP, Q, PAIR);                             // and their size
   constexpr int NI = INTERP ? 1 : PAIR ? 3 : 2;                           // ring items per K block
   constexpr int RING = ring_bytes(PAIR, INTERP, Q);
+  // Double-buffered accumulators where a tile's C1 columns fit 256 (with S_BR interpolated: at
+  // p = 4 the 24-trait tiles): tile u accumulates into columns [256 (u & 1), +B1_ROWS), so the
+  // MMAs of the next tile do not wait for the epilogue to read this one.
+  constexpr bool DB = INTERP && B1_ROWS <= 256;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float* cst_smem = (float*)(smem + RING);  // [2][TT][CSTR], double-buffered by tile
@@ -163,9 +167,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   float* cheb_t = cheb_c + (CHEB_MAX_R + 1) * 128;          // INTERP: [CHEB_MAX_R][TT]
   uint64_t* full = (uint64_t*)(smem + RING + 2 * cst_bytes(Q) + cheb_stage_bytes(INTERP, Q));
   uint64_t* empty = full + NSL;
-  uint64_t* acc_full = empty + NSL;
-  uint64_t* acc_empty = acc_full + 1;
-  uint32_t* tslot = (uint32_t*)(acc_empty + 1);
+  uint64_t* acc_full = empty + NSL;          // [2]
+  uint64_t* acc_empty = acc_full + 2;        // [2]
+  uint32_t* tslot = (uint32_t*)(acc_empty + 2);
   volatile int* abort = (volatile int*)(tslot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   uint32_t crank = 0, cid = blockIdx.x, ncl = gridDim.x;
@@ -184,8 +188,10 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(acc_full, 1);
-    tc::mbar_init(acc_empty, PAIR ? 2 * EPW : EPW);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], PAIR ? 2 * EPW : EPW);
+    }
     *abort = 0;
     tc::fence_mbar_init();
   }
@@ -293,7 +299,12 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       uint32_t h = 0, tcount = 0;
       bool ok = true;
       for (int u = cid; u < nsuper && ok; u += ncl, ++tcount) {
-        if (tcount > 0 && !tc::mbar_wait(acc_empty, (tcount - 1) & 1, a.status, abort)) { ok = false; break; }
+        const uint32_t ab = DB ? (tcount & 1) : 0, tacc = tbase + ab * 256;
+        if ((DB ? tcount >= 2 : tcount > 0) &&
+            !tc::mbar_wait(&acc_empty[ab], (DB ? (tcount >> 1) - 1 : tcount - 1) & 1, a.status, abort)) {
+          ok = false;
+          break;
+        }
         tc::fence_after();
         for (int kb = 0; kb < nkb && ok; ++kb) {
           {
@@ -308,7 +319,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               const uint32_t acc = (kb | k) ? 1u : 0u;
               if (INTERP) {
                 // one MMA over all C1 columns: each CTA supplies half of them, in the one-CTA order
-                tc::mma_bf16_pair(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), idI, acc);
+                tc::mma_bf16_pair(tacc, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), idI, acc);
               } else {
                 // [Q1 | Q2] -> levels 0 and 1 of [w v1 v2 v3]; [Q3 | Q4] -> slices 3, 4 of w
                 tc::mma_bf16_pair(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), id256, acc);
@@ -346,7 +357,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             h += 2;
           }
         }
-        if (ok) tc::mma_commit_pair(acc_full, (uint16_t)3);
+        if (ok) tc::mma_commit_pair(&acc_full[ab], (uint16_t)3);
       }
     } else if (!PAIR && lane == 0) {
       constexpr uint32_t idN0 = tc::idesc_bf16(BM, N0), idN1 = tc::idesc_bf16(BM, N1 > 0 ? N1 : 16);
@@ -355,7 +366,12 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       uint32_t h = 0, tcount = 0;
       bool ok = true;
       for (int u = cid; u < nsuper && ok; u += ncl, ++tcount) {
-        if (tcount > 0 && !tc::mbar_wait(acc_empty, (tcount - 1) & 1, a.status, abort)) { ok = false; break; }
+        const uint32_t ab = DB ? (tcount & 1) : 0, tacc = tbase + ab * 256;
+        if ((DB ? tcount >= 2 : tcount > 0) &&
+            !tc::mbar_wait(&acc_empty[ab], (DB ? (tcount >> 1) - 1 : tcount - 1) & 1, a.status, abort)) {
+          ok = false;
+          break;
+        }
         tc::fence_after();
         for (int kb = 0; kb < nkb && ok; ++kb) {
           for (int half = 0; half < NI; ++half, ++h) {
@@ -369,9 +385,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
               for (int k = 0; k < BK / 16; ++k) {
                 const uint32_t acc = (kb | k) ? 1u : 0u;
-                tc::mma_bf16(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), idN0, acc);
+                tc::mma_bf16(tacc, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), idN0, acc);
                 if (N1 > 0)
-                  tc::mma_bf16(tbase + N0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, N0 * ROWB + k * 32), idN1, acc);
+                  tc::mma_bf16(tacc + N0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, N0 * ROWB + k * 32), idN1, acc);
               }
             } else {
               const uint64_t d1 = tc::sdesc_sw128(buf), d2 = tc::sdesc_sw128(buf + G_BYTES);
@@ -393,7 +409,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             tc::mma_commit(&empty[s]);
           }
         }
-        if (ok) tc::mma_commit(acc_full);
+        if (ok) tc::mma_commit(&acc_full[ab]);
       }
     }
   } else {
@@ -450,7 +466,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         }
       }
       tc::named_sync(1, EPW * 32);
-      const bool ok = tc::mbar_wait(acc_full, tcount & 1, a.status, abort);
+      const uint32_t ab = DB ? (tcount & 1) : 0;
+      const bool ok = tc::mbar_wait(&acc_full[ab], (DB ? tcount >> 1 : tcount) & 1, a.status, abort);
+      const uint32_t lb = lane_base + ab * 256;  // this tile's accumulator buffer
       tc::fence_after();
       const int64_t snp = snp0 + q * 32 + lane;
       const bool valid_i = ok && snp >= snp_lo && snp < snp_end;
@@ -473,10 +491,10 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         {
           // C1, w: slices 1 and 2 (groups 0 and 1 + q) and the groups of slices 3 and 4 -> num
           uint32_t hw[4], lw[4], w3[4], w4[4];
-          tc::tmem_ld4(lane_base + 0 * TT + j0, hw);
-          tc::tmem_ld4(lane_base + (1 + PM1) * TT + j0, lw);
-          tc::tmem_ld4(lane_base + (2 + 2 * PM1) * TT + j0, w3);
-          tc::tmem_ld4(lane_base + (3 + 2 * PM1) * TT + j0, w4);
+          tc::tmem_ld4(lb + 0 * TT + j0, hw);
+          tc::tmem_ld4(lb + (1 + PM1) * TT + j0, lw);
+          tc::tmem_ld4(lb + (2 + 2 * PM1) * TT + j0, w3);
+          tc::tmem_ld4(lb + (3 + 2 * PM1) * TT + j0, w4);
           tc::tmem_ld_wait();
           tc::reg_fence(hw); tc::reg_fence(lw); tc::reg_fence(w3); tc::reg_fence(w4);
 #pragma unroll
@@ -495,8 +513,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
           for (int c = 0; c < CB; ++c)
             if (c0 + c < PM1) {
-              tc::tmem_ld4(lane_base + (1 + c0 + c) * TT + j0, hz[c]);
-              tc::tmem_ld4(lane_base + (2 + PM1 + c0 + c) * TT + j0, lz[c]);
+              tc::tmem_ld4(lb + (1 + c0 + c) * TT + j0, hz[c]);
+              tc::tmem_ld4(lb + (2 + PM1 + c0 + c) * TT + j0, lz[c]);
             }
           tc::tmem_ld_wait();
 #pragma unroll
@@ -515,12 +533,12 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         if (!INTERP) {
           // C2: level 0 and the five level-1 groups -> s
           uint32_t d0[4], da[4], db[4], ea[4], eb[4], ec[4];
-          tc::tmem_ld4(lane_base + C2B + C2_OFF + 0 * TT + j0, d0);
-          tc::tmem_ld4(lane_base + C2B + C2_OFF + 1 * TT + j0, da);
-          tc::tmem_ld4(lane_base + C2B + C2_OFF + 2 * TT + j0, db);
-          tc::tmem_ld4(lane_base + C2B + C2_OFF + 3 * TT + j0, ea);
-          tc::tmem_ld4(lane_base + C2B + C2_OFF + 4 * TT + j0, eb);
-          tc::tmem_ld4(lane_base + C2B + C2_OFF + 5 * TT + j0, ec);
+          tc::tmem_ld4(lb + C2B + C2_OFF + 0 * TT + j0, d0);
+          tc::tmem_ld4(lb + C2B + C2_OFF + 1 * TT + j0, da);
+          tc::tmem_ld4(lb + C2B + C2_OFF + 2 * TT + j0, db);
+          tc::tmem_ld4(lb + C2B + C2_OFF + 3 * TT + j0, ea);
+          tc::tmem_ld4(lb + C2B + C2_OFF + 4 * TT + j0, eb);
+          tc::tmem_ld4(lb + C2B + C2_OFF + 5 * TT + j0, ec);
           tc::tmem_ld_wait();
           tc::reg_fence(d0); tc::reg_fence(da); tc::reg_fence(db);
           tc::reg_fence(ea); tc::reg_fence(eb); tc::reg_fence(ec);
@@ -546,8 +564,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       __syncwarp();
       if (lane == 0) {
         // relaxed: the TMEM loads are complete (tcgen05.wait::ld); nothing else is ordered
-        if (PAIR) tc::mbar_arrive_cluster_relaxed(tc::mapa(acc_empty, 0));
-        else tc::mbar_arrive(acc_empty);
+        if (PAIR) tc::mbar_arrive_cluster_relaxed(tc::mapa(&acc_empty[ab], 0));
+        else tc::mbar_arrive(&acc_empty[ab]);
       }
       if (INTERP) {
         // S_BR = sum_k c_k T_k(x_j): the tail (k >= 2, terms decreasing like a geometric series)
