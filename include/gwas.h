@@ -258,7 +258,7 @@ GWAS_API int64_t gwas_kernel_launches(const gwas_ctx* ctx);
  *   best_ms   out (may be NULL): device time of one solve of the sample with the chosen shape
  *
  * Candidates: the one-CTA shape for every p; for p = 4 also the one-CTA shape with 8
- * epilogue warps and the CTA pair; each with 8, 16, 32 or 64 SNP tiles per traversal group.  The
+ * epilogue warps and the CTA pair; each with 4, 8, 16, 32 or 64 SNP tiles per traversal group.  The
  * fastest is kept unless the default shape is within 2 % of it.  The context uses the choice
  * from then on, and it is written to opts.tune_cache when that was given.  Results do not
  * depend on the shape beyond rounding.  Mixed precision only (GWAS_ERR_UNSUPPORTED

@@ -2,8 +2,8 @@
 // study, Section 5: the loop tiles are tuned empirically on the target machine).
 //
 // Candidates: the one-CTA shape (1 x 1 cluster, 16 epilogue warps) for every p; for p = 4 also
-// the one-CTA shape with 8 epilogue warps and the CTA pair (cta_group::2); each with 8, 16, 32
-// or 64 SNP tiles per traversal group.  Every candidate solves the same sample of the grid (the first
+// the one-CTA shape with 8 epilogue warps and the CTA pair (cta_group::2); each with 4, 8, 16,
+// 32 or 64 SNP tiles per traversal group.  Every candidate solves the same sample of the grid (the first
 // SNPs and traits of the problem, device output) once untimed and twice timed with CUDA events;
 // the fastest wins, but the default shape is kept when it is within 2 % of it (a plateau, not a
 // noisy optimum).  The choice is stored in the context and, when opts.tune_cache names a file,
@@ -141,7 +141,7 @@ extern "C" int gwas_autotune(gwas_ctx* c, const double* Y, int t_sample, int64_t
   const int shapes[3][4] = {{1, 1, 16, 0}, {1, 1, 8, 0}, {2, 1, 16, 1}};
   for (const auto& sh : shapes)
     if (fused_shape_supported(c->pm1, sh[0], sh[1], sh[2], sh[3]))
-      for (int g : {16, 8, 32, 64}) cand.push_back({sh[0], sh[1], sh[2], sh[3], g});
+      for (int g : {16, 4, 8, 32, 64}) cand.push_back({sh[0], sh[1], sh[2], sh[3], g});
   const gwas_ctx::FusedTune saved = c->tune;
   const int saved_t = c->t;
   const bool saved_prof = c->profile;

@@ -19,15 +19,16 @@ def _current_sha():
 
 
 def test_traffic_model_terms():
-    # one traversal group: every operand read once, every result written once
+    # one traversal group: every operand read once, every result written once (64 traits: three
+    # tiles of 24 in the interpolated kernel)
     mod = bench.fused_traffic_model(1000, 128 * 16, 64, group=16)
     kpad = 1024
     assert mod["write"] == 8.0 * 128 * 16 * 64
-    assert mod["read"] == 2048 * kpad * 2 + 25 * 4 * 2048 + 2 * 320 * kpad * 2
+    assert mod["read"] == 2048 * kpad * 2 + 25 * 4 * 2048 + 3 * 240 * kpad * 2
     # the trait operands are read once per group of 16 SNP tiles (32 for the CTA pair's 2 x 16)
     one = bench.fused_traffic_model(1000, 128 * 64, 10_000, group=16)
     pair = bench.fused_traffic_model(1000, 128 * 64, 10_000, group=16, cs=2)
-    trait = 313 * 320 * kpad * 2
+    trait = 417 * 240 * kpad * 2
     assert one["read"] - pair["read"] == 2 * trait
     # contracting S_BR adds the three x'^2 planes and the C2 trait rows
     ex = bench.fused_traffic_model(1000, 128 * 16, 64, group=16, interp=False)
