@@ -51,17 +51,17 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # of SNP tiles (they do not fit L2 at t = 1e4), the SNP operands once, the results written once.
 # The check is valid only while the kernel's sources hash to the value it was taken on.
 FUSED_TRAFFIC_CHECK = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "tc.cuh", "fused_cheb.cu"],
-                       "sha256": None,
+                       "sha256": "49793b74e8877d39b09a8de28bc1d20adacf2cdb6f8b61ba305a600a9633c233",
                        # n = 1000, m = 16384, t = 1e4 (profiles/fused_kernel_traffic_n1000_m16384_t1e4.md)
                        "case": (1000, 3, 16384, 10_000),
-                       "measured": {"pair_g32": (450.1e6, 1260.5e6), "one_g16": (1690.8e6, 1278.9e6)},
-                       "model": {"pair_g32": (445.4e6, 1310.7e6), "one_g16": (1676.2e6, 1310.7e6)}}
+                       "measured": {"pair_g8": (1688.7e6, 1275.8e6), "one_g16": (1689.0e6, 1279.8e6)},
+                       "model": {"pair_g8": (1674.9e6, 1310.7e6), "one_g16": (1674.9e6, 1310.7e6)}}
 
 
 # sm__pipe_tensor_cycles_active (% of peak, active cycles) of the interpolated fused kernel from the
 # full-set ncu captures of the small case n = 1000, m = 131072, t = 1024 (one launch each;
 # profiles/fused_kernel_interp_n1000_m131072_t1024.md), valid for the same sources as the check above.
-TENSOR_PIPE_NCU = {"pair": 62.6, "one_cta": 57.5}
+TENSOR_PIPE_NCU = {"pair": 69.7, "one_cta": 62.3}
 
 
 def tensor_pipe_counter(shape):
@@ -642,8 +642,8 @@ def main():
     try:
         g.gwas_load_snps(ctx, m, inp_d["XR"], n)
         # the sample keeps every trait, so that its trait operands stream from DRAM as in the full
-        # grid (the traversal group size matters only then), and 2^17 SNPs
-        t_s, m_s = min(t, 10_000), min(m, 1 << 17)
+        # grid (the traversal group size matters only then), and 2^18 SNPs
+        t_s, m_s = min(t, 10_000), min(m, 1 << 18)
         tune_ms = None if args.no_tune else g.gwas_autotune(ctx, inp_d["Y"], t_s, m_s)
         tune = {"shape": g.gwas_tune_shape(ctx), "sample": f"SNPs [0,{m_s}) x traits [0,{t_s})",
                 "sample_ms": tune_ms}
