@@ -692,10 +692,12 @@ def main():
     fused_ms = ktimes["fused"][0] / ktimes["fused"][1]
     useful = algorithmic_flops(n, PM1 + 1, pairs)            # 2 (p+1) n flops per pair
     kpad = (n + 63) // 64 * 64
-    tiles = ((m + 127) // 128) * ((t + 31) // 32)
-    # MMA columns per tile per K: 320 for the C1 block (num and z: 4 + 2(p-1) slice groups of 32
-    # traits), plus 192 for the S_BR contraction when it is not interpolated
-    mma_cols = 320 if sbr["terms"] > 0 else 512
+    # MMA columns per tile per K: the C1 block (num and z: 4 + 2(p-1) = 10 slice groups of the
+    # tile's traits: 24 with S_BR interpolated, 32 otherwise), plus 192 for the S_BR contraction
+    # when it is not interpolated
+    tt = 24 if sbr["terms"] > 0 else 32
+    tiles = ((m + 127) // 128) * ((t + tt - 1) // tt)
+    mma_cols = 10 * tt if sbr["terms"] > 0 else 512
     issued = 2.0 * 128 * mma_cols * kpad * tiles
     peak = pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
     achieved = useful / (fused_ms / 1e3) / 1e12

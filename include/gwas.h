@@ -24,8 +24,9 @@
  *   cudaPointerGetAttributes and copies host data itself.  The caller keeps
  *   ownership of all its buffers and may release them when the call returns.
  * - The context owns every device allocation it makes (Z, Lambda, the rotated
- *   covariates, the resident rotated genotypes and the work buffers) and frees
- *   them in gwas_destroy.
+ *   covariates, the resident rotated genotypes and the work buffers) and gives
+ *   them back in gwas_destroy to the library's device memory pool, which keeps
+ *   them for the next context (gwas_pool_info, gwas_pool_trim).
  * - Calls on one context are not thread-safe; different contexts are
  *   independent.  All work runs on the context's stream; calls return after
  *   their results are complete (host outputs written, device outputs ready).
@@ -71,7 +72,8 @@ extern "C" {
                          most 24 terms (see gwas_sbr_info); otherwise it is contracted for
                          every pair like the other two blocks.
                          Any 0 <= p-1 <= 19 (the paper's 2 <= p <= 20, Section 3);
-                         traits are processed in tiles of 32 for p-1 <= 3, 16 for
+                         traits are processed in tiles of 32 for p-1 <= 3 (24 at
+                         p-1 = 3 when S_BR comes from its series), 16 for
                          p-1 <= 10 and 8 above (the accumulators of a tile take
                          (4 + 2(p-1)) x tile + 6 x tile TMEM columns of 512, 8 x tile for
                          the C2 part of 8-trait tiles). */
@@ -278,7 +280,9 @@ GWAS_API int gwas_autotune(gwas_ctx* ctx, const double* Y, int t_sample, int64_t
  *   GWAS_HOST_OUTPUT=staged               gwas_solve copies page-locked host outputs through device
  *                                         staging instead of storing them from the kernels
  *   GWAS_S_BR=exact                       the mixed path contracts S_BR for every pair (read when a
- *                                         context plans it: its first solve, or after gwas_set_h2) */
+ *                                         context plans it: its first solve, or after gwas_set_h2)
+ *   GWAS_POOL=0                           device buffers from cudaMalloc/cudaFree instead of the
+ *                                         library's pool (read once per process) */
 GWAS_API int gwas_tune_shape(const gwas_ctx* ctx, int* shape);
 
 /* Accumulated device time (ms, from CUDA events recorded on the context's stream
@@ -375,8 +379,28 @@ GWAS_API int gwas_check_bounded_wait(int device, double limit_s, double* waited_
  * gwas_setup when ctx is NULL).  Owned by the library. */
 GWAS_API const char* gwas_last_error(const gwas_ctx* ctx);
 
-/* Free every device and host resource of the context.  NULL is ignored. */
+/* Free every device and host resource of the context; its device buffers go back to the
+ * library's device memory pool (below).  NULL is ignored. */
 GWAS_API void gwas_destroy(gwas_ctx* ctx);
+
+/*
+ * Device memory pool.  Every context's device buffers come from one stream-ordered pool
+ * per device that the library keeps for the life of the process, and memory a context
+ * gives back stays reserved in it for the next context: a step that sets up, solves and
+ * destroys a context does not map and unmap its buffers again (at n = 1000, m = 10^6 that
+ * is ~10 GB, ~6 ms per step).  A buffer is usable from any stream once the call that made
+ * it returns, and is handed out again only after all work on the device has completed.
+ *
+ * gwas_pool_info: *reserved = bytes the pool holds from the device, *used = bytes in live
+ *   context buffers (either pointer may be NULL); both 0 while the pool is not in use
+ *   (GWAS_POOL=0, or no context has allocated on the device yet).
+ * gwas_pool_trim: gives reserved memory that no live buffer uses back to the device, until
+ *   at most keep_bytes stay reserved (0: everything unused).
+ * Both return GWAS_OK, GWAS_ERR_ARG (no such device, or a negative device) or GWAS_ERR_CUDA;
+ * gwas_last_error is not set.  Thread-safe.
+ */
+GWAS_API int gwas_pool_info(int device, uint64_t* reserved, uint64_t* used);
+GWAS_API int gwas_pool_trim(int device, uint64_t keep_bytes);
 
 #ifdef __cplusplus
 }

@@ -110,6 +110,10 @@ def _load():
     lib.gwas_check_bounded_wait.restype = ci
     lib.gwas_destroy.argtypes = [vp]
     lib.gwas_destroy.restype = None
+    lib.gwas_pool_info.argtypes = [ci, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+    lib.gwas_pool_info.restype = ci
+    lib.gwas_pool_trim.argtypes = [ci, C.c_uint64]
+    lib.gwas_pool_trim.restype = ci
     return lib
 
 
@@ -399,6 +403,22 @@ def gwas_last_error(ctx=None) -> str:
 def gwas_destroy(ctx) -> None:
     _CTX.pop(_key(ctx), None)
     lib.gwas_destroy(ctx)
+
+
+def gwas_pool_info(device=0) -> dict:
+    """Bytes the library's device memory pool holds from the device and bytes in live buffers."""
+    r, u = C.c_uint64(), C.c_uint64()
+    rc = lib.gwas_pool_info(int(device), C.byref(r), C.byref(u))
+    if rc != GWAS_OK:
+        raise GwasError(rc, "gwas_pool_info failed")
+    return {"reserved": r.value, "used": u.value}
+
+
+def gwas_pool_trim(device=0, keep_bytes=0) -> None:
+    """Give the pool's unused device memory back until at most keep_bytes stay reserved."""
+    rc = lib.gwas_pool_trim(int(device), int(keep_bytes))
+    if rc != GWAS_OK:
+        raise GwasError(rc, "gwas_pool_trim failed")
 
 
 def _torch():

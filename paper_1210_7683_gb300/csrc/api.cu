@@ -32,6 +32,103 @@ SolverCache& solver_cache() {
   return *s;
 }
 
+// Device memory of every context comes from one stream-ordered pool per device that keeps what
+// contexts give back (its release threshold is unlimited): a context set up after another reuses
+// that memory instead of mapping it again.  Mapping and unmapping are not free: a step of the
+// n = 1000, m = 10^6, t = 10^4 workload allocates ~10 GB, which cudaMalloc maps in ~1 ms and
+// cudaFree unmaps in ~5 ms.  gwas_pool_trim gives kept memory back.  Allocations and frees run on
+// the pool's own stream and are waited for, so a buffer is usable from every stream on return,
+// and the pool never hands out memory whose free is still pending (internal dependencies off).
+// GWAS_POOL=0 in the environment (read once) uses cudaMalloc/cudaFree instead.
+struct DevicePool {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t stream = nullptr;
+};
+struct PoolCache {
+  std::mutex mu;
+  std::map<int, DevicePool> pools;
+  int enabled = -1;
+};
+PoolCache& pool_cache() {
+  static PoolCache* p = new PoolCache;  // never destroyed: pools outlive every context
+  return *p;
+}
+
+// The pool of `dev`, created on first use (`create`); null when pooling is off, the device has
+// no memory pools, or it does not exist yet and `create` is false.
+DevicePool device_pool(int dev, bool create = true) {
+  PoolCache& pc = pool_cache();
+  std::lock_guard<std::mutex> lk(pc.mu);
+  if (pc.enabled < 0) {
+    const char* e = std::getenv("GWAS_POOL");
+    pc.enabled = (e && std::strcmp(e, "0") == 0) ? 0 : 1;
+  }
+  if (!pc.enabled) return {};
+  auto it = pc.pools.find(dev);
+  if (it != pc.pools.end()) return it->second;
+  if (!create) return {};
+  DeviceGuard guard(dev);
+  DevicePool dp;
+  int supported = 0;
+  if (cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev) != cudaSuccess || !supported) {
+    cudaGetLastError();
+    pc.pools[dev] = dp;
+    return dp;
+  }
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  if (cudaMemPoolCreate(&dp.pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    pc.pools[dev] = DevicePool{};
+    return {};
+  }
+  uint64_t keep = ~uint64_t(0);
+  int off = 0;
+  if (cudaMemPoolSetAttribute(dp.pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
+      cudaMemPoolSetAttribute(dp.pool, cudaMemPoolReuseAllowInternalDependencies, &off) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&dp.stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cudaMemPoolDestroy(dp.pool);
+    pc.pools[dev] = DevicePool{};
+    return {};
+  }
+  pc.pools[dev] = dp;
+  return dp;
+}
+
+// Device memory from the pool (or cudaMalloc), aligned to 256 bytes.
+cudaError_t dev_malloc(int dev, void** p, size_t bytes) {
+  DevicePool dp = device_pool(dev);
+  if (!dp.pool) return cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, dp.pool, dp.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(dp.stream);
+  if (e == cudaSuccess && (reinterpret_cast<uintptr_t>(*p) & 255)) {
+    cudaFreeAsync(*p, dp.stream);
+    cudaStreamSynchronize(dp.stream);
+    *p = nullptr;
+    return cudaMalloc(p, bytes);  // not expected: pool blocks are at least 512-byte aligned
+  }
+  if (e != cudaSuccess) *p = nullptr;
+  return e;
+}
+
+// Gives memory back. Like cudaFree it first waits for all work on the device, so no kernel or
+// copy still uses the buffer when the pool may hand it out again.
+void dev_free(int dev, void* p, bool pooled) {
+  if (!p) return;
+  if (!pooled) {
+    cudaFree(p);
+    return;
+  }
+  DevicePool dp = device_pool(dev);
+  DeviceGuard guard(dev);
+  cudaDeviceSynchronize();
+  cudaFreeAsync(p, dp.stream);
+  cudaStreamSynchronize(dp.stream);
+}
+
 std::string fmt(const char* f, ...) {
   char buf[512];
   va_list ap;
@@ -64,12 +161,13 @@ int ctx_alloc(gwas_ctx* c, size_t bytes, void** out) {
     return ctx_fail(c, GWAS_ERR_OOM, fmt("allocation of %zu bytes exceeds the HBM budget (%zu of %zu in use)", b,
                                          c->allocated, c->budget));
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, b);
+  const bool pooled = device_pool(c->device).pool != nullptr;
+  cudaError_t e = dev_malloc(c->device, &p, b);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return ctx_fail(c, GWAS_ERR_OOM, fmt("cudaMalloc(%zu): %s", b, cudaGetErrorString(e)));
+    return ctx_fail(c, GWAS_ERR_OOM, fmt("device allocation of %zu bytes: %s", b, cudaGetErrorString(e)));
   }
-  c->bufs.push_back({p, b});
+  c->bufs.push_back({p, b, pooled});
   c->allocated += b;
   *out = p;
   return GWAS_OK;
@@ -79,7 +177,7 @@ void ctx_free(gwas_ctx* c, void* p) {
   if (!p) return;
   for (size_t i = 0; i < c->bufs.size(); ++i)
     if (c->bufs[i].ptr == p) {
-      cudaFree(p);
+      dev_free(c->device, p, c->bufs[i].pooled);
       c->allocated -= c->bufs[i].bytes;
       c->bufs.erase(c->bufs.begin() + i);
       return;
@@ -216,7 +314,15 @@ static void destroy_impl(gwas_ctx* c) {
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   mixed_free(c);
   mixed_destroy(c);
-  for (auto& b : c->bufs) cudaFree(b.ptr);
+  if (!c->bufs.empty()) cudaDeviceSynchronize();
+  for (auto& b : c->bufs) {
+    if (!b.pooled) {
+      cudaFree(b.ptr);
+      continue;
+    }
+    cudaFreeAsync(b.ptr, device_pool(c->device).stream);
+  }
+  if (!c->bufs.empty() && device_pool(c->device).stream) cudaStreamSynchronize(device_pool(c->device).stream);
   c->bufs.clear();
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   if (have) cudaSetDevice(dev);
@@ -224,6 +330,43 @@ static void destroy_impl(gwas_ctx* c) {
 }
 
 extern "C" void gwas_destroy(gwas_ctx* c) { destroy_impl(c); }
+
+static int pool_device_ok(int device) {
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess) {
+    cudaGetLastError();
+    return GWAS_ERR_CUDA;
+  }
+  return (device < 0 || device >= count) ? GWAS_ERR_ARG : GWAS_OK;
+}
+
+extern "C" int gwas_pool_info(int device, uint64_t* reserved, uint64_t* used) {
+  if (reserved) *reserved = 0;
+  if (used) *used = 0;
+  if (int rc = pool_device_ok(device)) return rc;
+  DevicePool dp = device_pool(device, false);
+  if (!dp.pool) return GWAS_OK;
+  uint64_t r = 0, u = 0;
+  if (cudaMemPoolGetAttribute(dp.pool, cudaMemPoolAttrReservedMemCurrent, &r) != cudaSuccess ||
+      cudaMemPoolGetAttribute(dp.pool, cudaMemPoolAttrUsedMemCurrent, &u) != cudaSuccess) {
+    cudaGetLastError();
+    return GWAS_ERR_CUDA;
+  }
+  if (reserved) *reserved = r;
+  if (used) *used = u;
+  return GWAS_OK;
+}
+
+extern "C" int gwas_pool_trim(int device, uint64_t keep_bytes) {
+  if (int rc = pool_device_ok(device)) return rc;
+  DevicePool dp = device_pool(device, false);
+  if (!dp.pool) return GWAS_OK;
+  if (cudaMemPoolTrimTo(dp.pool, (size_t)keep_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return GWAS_ERR_CUDA;
+  }
+  return GWAS_OK;
+}
 
 extern "C" const char* gwas_last_error(const gwas_ctx* c) { return c ? c->err.c_str() : g_setup_err.c_str(); }
 

@@ -16,6 +16,7 @@
 struct DevBuf {
   void* ptr = nullptr;
   size_t bytes = 0;
+  bool pooled = false;  // from the library's device pool (else cudaMalloc)
 };
 
 struct MixedState;  // mixed-precision resident data (mixed.cu)
@@ -104,7 +105,7 @@ struct DeviceGuard {
 void tune_apply_cache(gwas_ctx* c);
 
 int ctx_fail(gwas_ctx* c, int code, const std::string& msg);
-int ctx_alloc(gwas_ctx* c, size_t bytes, void** out);          // budget-checked cudaMalloc
+int ctx_alloc(gwas_ctx* c, size_t bytes, void** out);          // budget-checked, from the device pool
 void ctx_free(gwas_ctx* c, void* p);
 bool ctx_cuda_ok(gwas_ctx* c, cudaError_t e, const char* what, int* rc);
 // Copy `bytes` from a host or device pointer to a new or given device buffer.
