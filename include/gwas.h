@@ -246,6 +246,15 @@ GWAS_API int gwas_set_h2(gwas_ctx* ctx, int t, const double* h2);
 /* Number of pairs flagged singular by the last gwas_solve. */
 GWAS_API int64_t gwas_singular_count(const gwas_ctx* ctx);
 
+/* How gwas_setup computed Phi = Z Lambda Z^T.  *steps >= 0: the FP32 eigensolver, refined to FP64
+ * accuracy by the iteration of Ogita and Aishima (2018) with FP64-accurate products on the tensor
+ * cores, took *steps refinement steps until max |(Z^T Z - I)_ij| and
+ * max_{i != j} |(Z^T Phi Z)_ij| / max |lambda| were both <= 16 u sqrt(n), u = 2^-53;
+ * *steps = -1: the FP64 eigensolver (cuSOLVER Dsyevd) computed it, because the refinement did not
+ * converge within 8 steps, the FP32 solver failed, or GWAS_EIG=fp64 was set.  Either way Lambda
+ * is ascending and Z column-major.  Returns GWAS_OK or GWAS_ERR_ARG (NULL argument). */
+GWAS_API int gwas_eig_info(const gwas_ctx* ctx, int* steps);
+
 /* Number of kernels this context launched since it was created. */
 GWAS_API int64_t gwas_kernel_launches(const gwas_ctx* ctx);
 
@@ -282,7 +291,9 @@ GWAS_API int gwas_autotune(gwas_ctx* ctx, const double* Y, int t_sample, int64_t
  *   GWAS_S_BR=exact                       the mixed path contracts S_BR for every pair (read when a
  *                                         context plans it: its first solve, or after gwas_set_h2)
  *   GWAS_POOL=0                           device buffers from cudaMalloc/cudaFree instead of the
- *                                         library's pool (read once per process) */
+ *                                         library's pool (read once per process)
+ *   GWAS_EIG=fp64                         gwas_setup computes the eigendecomposition with the FP64
+ *                                         solver (see gwas_eig_info) */
 GWAS_API int gwas_tune_shape(const gwas_ctx* ctx, int* shape);
 
 /* Accumulated device time (ms, from CUDA events recorded on the context's stream
@@ -292,7 +303,8 @@ GWAS_API int gwas_tune_shape(const gwas_ctx* ctx, int* shape);
  * "setup_rotation_operands", "slice_rows", "genotypes_bf16", "xgemm_rotate_snps",
  * "slice_snp_squares", "xgemm_rotate_traits", "prep_traits", "xgemm_back_rotate",
  * "pack_trait_columns", "cheb_nodes" (S_BR at the node heritabilities), "cheb_coefficients",
- * "fused". */
+ * "fused"; and, inside "eigendecomposition", "eig_fp32_solver", "eig_refine_residuals" (R and S of
+ * each refinement step) and "eig_refine_update". */
 GWAS_API int gwas_kernel_time(const gwas_ctx* ctx, const char* kernel, double* ms, int64_t* launches);
 GWAS_API void gwas_reset_timers(gwas_ctx* ctx);
 

@@ -110,6 +110,8 @@ def _load():
     lib.gwas_check_bounded_wait.restype = ci
     lib.gwas_destroy.argtypes = [vp]
     lib.gwas_destroy.restype = None
+    lib.gwas_eig_info.argtypes = [vp, C.POINTER(ci)]
+    lib.gwas_eig_info.restype = ci
     lib.gwas_pool_info.argtypes = [ci, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
     lib.gwas_pool_info.restype = ci
     lib.gwas_pool_trim.argtypes = [ci, C.c_uint64]
@@ -403,6 +405,13 @@ def gwas_last_error(ctx=None) -> str:
 def gwas_destroy(ctx) -> None:
     _CTX.pop(_key(ctx), None)
     lib.gwas_destroy(ctx)
+
+
+def gwas_eig_info(ctx) -> int:
+    """Refinement steps of the context's eigendecomposition (-1: computed by the FP64 solver)."""
+    st = C.c_int()
+    _check(lib.gwas_eig_info(ctx, C.byref(st)), ctx)
+    return st.value
 
 
 def gwas_pool_info(device=0) -> dict:

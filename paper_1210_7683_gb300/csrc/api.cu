@@ -372,6 +372,12 @@ extern "C" const char* gwas_last_error(const gwas_ctx* c) { return c ? c->err.c_
 
 extern "C" int64_t gwas_singular_count(const gwas_ctx* c) { return c ? c->singular : 0; }
 
+extern "C" int gwas_eig_info(const gwas_ctx* c, int* steps) {
+  if (!c || !steps) return GWAS_ERR_ARG;
+  *steps = c->eig_steps;
+  return GWAS_OK;
+}
+
 extern "C" int64_t gwas_kernel_launches(const gwas_ctx* c) { return c ? c->launches : 0; }
 
 static int check_h2(gwas_ctx* c, const std::vector<double>& h2) {
@@ -429,10 +435,14 @@ extern "C" int gwas_setup(gwas_ctx** out, int n, int pm1, const double* phi, con
   if ((rc = ctx_alloc(c, 32, (void**)&c->d_status))) return fail(rc);
   cudaMemsetAsync(c->d_status, 0, 32, c->stream);
 
-  // ---- eigendecomposition Phi = Z Lambda Z^T (Algorithm 5, eigendec), FP64
+  // ---- eigendecomposition Phi = Z Lambda Z^T (Algorithm 5, eigendec), to FP64 accuracy: the
+  // FP32 solver refined on the tensor cores (eig.cu), or the FP64 solver where that does not
+  // converge (or under GWAS_EIG=fp64)
   if ((rc = ctx_alloc(c, sizeof(double) * n * n, (void**)&c->Z))) return fail(rc);
   if ((rc = ctx_alloc(c, sizeof(double) * n, (void**)&c->lam))) return fail(rc);
-  if ((rc = ctx_upload(c, phi, sizeof(double) * n * n, c->Z))) return fail(rc);
+  double* phi_d = nullptr;
+  if ((rc = ctx_alloc(c, sizeof(double) * n * n, (void**)&phi_d))) return fail(rc);
+  if ((rc = ctx_upload(c, phi, sizeof(double) * n * n, phi_d))) return fail(rc);
   SolverCache& sc = solver_cache();
   std::unique_lock<std::mutex> solver_lock(sc.mu);
   cusolverDnHandle_t h = sc.handles.count(c->device) ? sc.handles[c->device] : nullptr;
@@ -441,30 +451,52 @@ extern "C" int gwas_setup(gwas_ctx** out, int n, int pm1, const double* phi, con
     sc.handles[c->device] = h;
   }
   cusolverDnSetStream(h, c->stream);
-  int lwork = 0;
-  if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, c->Z, n, c->lam, &lwork) !=
-      CUSOLVER_STATUS_SUCCESS)
-    return fail(ctx_fail(c, GWAS_ERR_CUDA, "syevd workspace query failed"));
-  double* work = nullptr;
-  int* info = nullptr;
-  if ((rc = ctx_alloc(c, sizeof(double) * std::max(lwork, 1), (void**)&work))) return fail(rc);
-  if ((rc = ctx_alloc(c, sizeof(int), (void**)&info))) return fail(rc);
   ProfScope* eig_scope = new ProfScope(c, "eigendecomposition");
-  if (cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, c->Z, n, c->lam, work, lwork, info) !=
-      CUSOLVER_STATUS_SUCCESS)
-    return fail(ctx_fail(c, GWAS_ERR_CUDA, "syevd failed to launch"));
-  delete eig_scope;
-  int hinfo = 0;
-  c->h_lam.resize(n);
-  if (!ctx_cuda_ok(c, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "info", &rc))
+  const char* eig_env = std::getenv("GWAS_EIG");
+  c->eig_steps = -1;
+  rc = (eig_env && std::strcmp(eig_env, "fp64") == 0) ? EIG_FALL_BACK
+                                                       : eig_refined(c, h, phi_d, n, c->Z, c->lam, &c->eig_steps);
+  if (rc != GWAS_OK && rc != EIG_FALL_BACK) {
+    delete eig_scope;
     return fail(rc);
+  }
+  int hinfo = 0;
+  if (rc == EIG_FALL_BACK) {
+    c->eig_steps = -1;
+    int lwork = 0;
+    if (cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, c->Z, n, c->lam, &lwork) !=
+        CUSOLVER_STATUS_SUCCESS) {
+      delete eig_scope;
+      return fail(ctx_fail(c, GWAS_ERR_CUDA, "syevd workspace query failed"));
+    }
+    double* work = nullptr;
+    int* info = nullptr;
+    if ((rc = ctx_alloc(c, sizeof(double) * std::max(lwork, 1), (void**)&work)) ||
+        (rc = ctx_alloc(c, sizeof(int), (void**)&info))) {
+      delete eig_scope;
+      return fail(rc);
+    }
+    cudaMemcpyAsync(c->Z, phi_d, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->stream);
+    if (cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, c->Z, n, c->lam, work, lwork, info) !=
+        CUSOLVER_STATUS_SUCCESS) {
+      delete eig_scope;
+      return fail(ctx_fail(c, GWAS_ERR_CUDA, "syevd failed to launch"));
+    }
+    if (!ctx_cuda_ok(c, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "info", &rc)) {
+      delete eig_scope;
+      return fail(rc);
+    }
+    ctx_free(c, work);
+    ctx_free(c, info);
+  }
+  delete eig_scope;
+  c->h_lam.resize(n);
   if (!ctx_cuda_ok(c, cudaMemcpyAsync(c->h_lam.data(), c->lam, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream),
                    "lambda", &rc))
     return fail(rc);
   if (!ctx_cuda_ok(c, cudaStreamSynchronize(c->stream), "eigendecomposition", &rc)) return fail(rc);
   solver_lock.unlock();
-  ctx_free(c, work);
-  ctx_free(c, info);
+  ctx_free(c, phi_d);
   if (hinfo != 0) return fail(ctx_fail(c, GWAS_ERR_NOT_SPD, fmt("eigensolver did not converge (info %d)", hinfo)));
   for (double v : c->h_lam)
     if (!std::isfinite(v)) return fail(ctx_fail(c, GWAS_ERR_ARG, "Phi has non-finite entries"));

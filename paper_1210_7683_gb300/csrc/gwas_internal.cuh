@@ -57,6 +57,7 @@ struct gwas_ctx {
   unsigned long long* d_status = nullptr;
   int64_t singular = 0;
   int64_t launches = 0;
+  int eig_steps = -1;  // refinement steps of the eigendecomposition; -1: the FP64 solver computed it
   int64_t h2_gen = 0;  // incremented whenever the heritabilities change (gwas_set_h2)
 
   // output streaming: side stream and events of the double-buffered device-to-host copies
@@ -103,6 +104,13 @@ struct DeviceGuard {
 
 // Applies the launch shape that c->tune_cache holds for this context's (n, p, mode, t), if any.
 void tune_apply_cache(gwas_ctx* c);
+
+// Phi = Z Lambda Z^T by the FP32 solver refined to FP64 accuracy (eig.cu): Z column-major, lam
+// ascending, *steps = refinement steps taken.  Returns GWAS_OK, EIG_FALL_BACK when the FP64 solver
+// must compute it instead (the FP32 solver failed, non-finite values, or no convergence), or an
+// error code.  `solver` is the cusolverDnHandle_t, bound to c->stream.
+constexpr int EIG_FALL_BACK = -1;
+int eig_refined(gwas_ctx* c, void* solver, const double* phi, int n, double* Z, double* lam, int* steps);
 
 int ctx_fail(gwas_ctx* c, int code, const std::string& msg);
 int ctx_alloc(gwas_ctx* c, size_t bytes, void** out);          // budget-checked, from the device pool

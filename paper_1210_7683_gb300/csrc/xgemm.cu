@@ -14,10 +14,12 @@
 //
 // Used for the rotations by Z of Algorithm 5 (X'_R := Z^T X_R with exact int8
 // genotypes as A, and Y' := Z^T Y) and for the back-rotation Z W' of the
-// per-trait operands.
+// per-trait operands, with 4 slices of 7 bits; and with 8 slices and K chunks of
+// 256 for the FP64-accurate products of the eigendecomposition's refinement (eig.cu).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <memory>
 
 #include "gwas_internal.cuh"
 #include "tc.cuh"
@@ -119,6 +121,11 @@ __global__ void __launch_bounds__(192, 1) xgemm_kernel(const __grid_constant__ C
     tc::fence_after();
     const int r = r0 + q * 32 + lane;
     const double sa = (ok && r < g.rows) ? (g.scaleA ? g.scaleA[r] : 1.0) : 0.0;
+    // level_scale = 2^-bits: the value of levels 0..3 is hi * 2^(-bits min(L, 3)), that of levels
+    // 4..L is lo * 2^(-bits L)
+    const int bits = -ilogb(g.level_scale);
+    const double hi_scale = ldexp(1.0, -bits * (L < 3 ? L : 3));
+    const double lo_scale = ldexp(1.0, -bits * (L > 3 ? L - 3 : 0));
     for (int cc = 0; cc < BN; cc += 8) {
       uint32_t v[L + 1][8];
 #pragma unroll
@@ -128,15 +135,31 @@ __global__ void __launch_bounds__(192, 1) xgemm_kernel(const __grid_constant__ C
       for (int l = 0; l <= L; ++l) tc::reg_fence(v[l]);
       if (!ok || r >= g.rows) continue;
       if (g.out64) {
+        // Every level sum is an integer held exactly by its FP32 accumulator (|sum| < 2^26), so
+        // the levels are converted to 32-bit integers and combined exactly in 64-bit integers,
+        // levels 0..3 and 4..7 apart (bits <= 8 keeps each group below 2^53), then converted to
+        // FP64 once per group: FP64, and conversions to or from 64-bit types, run at a small
+        // fraction of the 32-bit rates on this GPU.
+        constexpr int H = L < 3 ? L : 3;
+        const long long base = 1LL << bits;
+        const double sah = sa * hi_scale;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int c = c0 + cc + j;
           if (c >= g.cols) break;
-          double acc = (double)__uint_as_float(v[L][j]);
+          long long hi = 0;
 #pragma unroll
-          for (int l = L - 1; l >= 0; --l) acc = fma(acc, g.level_scale, (double)__uint_as_float(v[l][j]));
+          for (int l = 0; l <= H; ++l) hi = hi * base + __float2int_rn(__uint_as_float(v[l][j]));
+          double acc = (double)hi;
+          if constexpr (L > 3) {
+            long long lo = 0;
+#pragma unroll
+            for (int l = 4; l <= L; ++l) lo = lo * base + __float2int_rn(__uint_as_float(v[l][j]));
+            acc = fma((double)lo, lo_scale, acc);
+          }
           double* o = g.out64 + (size_t)r * g.ldo + c;
-          *o = g.accumulate ? *o + acc * sa * g.scaleB[c] : acc * sa * g.scaleB[c];
+          const double val = acc * (sah * g.scaleB[c]);
+          *o = g.accumulate ? *o + val : val;
         }
       } else {
         // FP32 result: each level sum is an exact integer below 2^24, so combining the
@@ -164,26 +187,63 @@ __global__ void __launch_bounds__(192, 1) xgemm_kernel(const __grid_constant__ C
 // Slices of each row of a FP64 matrix (row r at src + r*lds, K valid entries) into
 // S bf16 planes [S][rows_pad][Kpad]: x = scale * sum_a q_a 2^(-bits a), scale =
 // max|x| / 2^bits, q_0 in [-2^bits, 2^bits], later |q_a| <= 2^(bits-1).
+//
+// The digits come from one 64-bit fixed-point integer per element,
+// X = round(x / scale * 2^(bits (S-1))), |X| <= 2^(bits S): q_0 = round(X / 2^(bits (S-1))), and
+// each later digit is the rounded quotient of the remainder by the next power 2^(bits (S-1-a)),
+// so every remainder is at most half that power.  Two FP64 operations per element (the scaling
+// and the conversion) instead of three per digit; the digits and the dropped tail are those of
+// rounding digit by digit.  bits * S > 62 (not used by this library) takes the FP64 loop.
+// Row maxima compare the bit patterns of |x| as integers (order-preserving for non-negative
+// doubles).  A non-finite entry gives NaN slices.
 __global__ void slice_rows_kernel(const double* __restrict__ src, int64_t lds, int rows, int K, int rows_pad, int Kpad,
                                   int S, int bits, __nv_bfloat16* __restrict__ planes, double* __restrict__ scale) {
   const int warps = blockDim.x / 32;
   const int r = blockIdx.x * warps + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (r >= rows_pad) return;
-  const double two = ldexp(1.0, bits);
-  double mx = 0;
+  const double* row = src + (size_t)r * lds;
+  unsigned long long mb = 0;
   if (r < rows)
-    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(src[(size_t)r * lds + k]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const double s = mx > 0 ? mx / two : 1.0;
-  const double inv = 1.0 / s;
+    for (int k = lane; k < K; k += 32) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(row[k]) & 0x7fffffffffffffffULL;
+      mb = b > mb ? b : mb;
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long b = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = b > mb ? b : mb;
+  }
+  const double mx = __longlong_as_double((long long)mb);
+  const double s = (mx > 0 && mx <= 1.7976931348623157e308) ? ldexp(mx, -bits) : 1.0;
   if (lane == 0 && r < rows) scale[r] = s;
-  for (int k = lane; k < Kpad; k += 32) {
-    double x = (r < rows && k < K) ? src[(size_t)r * lds + k] * inv : 0.0;
-    for (int a = 0; a < S; ++a) {
-      const double q = rint(x);
-      planes[((size_t)a * rows_pad + r) * Kpad + k] = __double2bfloat16(q);
-      x = (x - q) * two;
+  const size_t plane = (size_t)rows_pad * Kpad;
+  __nv_bfloat16* out = planes + (size_t)r * Kpad;
+  const int top = bits * (S - 1);
+  const double inv = ldexp(1.0 / s, top);  // 2^top / scale
+  if (bits * S <= 62 && isfinite(inv)) {
+    for (int k = lane; k < Kpad; k += 32) {
+      const double x = (r < rows && k < K) ? row[k] : 0.0;
+      if (!isfinite(x)) {
+        for (int a = 0; a < S; ++a) out[a * plane + k] = __float2bfloat16_rn(__int_as_float(0x7fc00000));
+        continue;
+      }
+      long long X = __double2ll_rn(x * inv);
+      for (int a = 0; a < S; ++a) {
+        const int sh = top - bits * a;
+        const long long q = sh > 0 ? ((X + (1LL << (sh - 1))) >> sh) : X;
+        X -= q * (1LL << sh);
+        out[a * plane + k] = __float2bfloat16_rn((float)(int)q);
+      }
+    }
+  } else {
+    const double two = ldexp(1.0, bits), inv = 1.0 / s;
+    for (int k = lane; k < Kpad; k += 32) {
+      double x = (r < rows && k < K) ? row[k] * inv : 0.0;
+      for (int a = 0; a < S; ++a) {
+        const double q = rint(x);
+        out[a * plane + k] = __double2bfloat16(q);
+        x = (x - q) * two;
+      }
     }
   }
 }
@@ -236,9 +296,9 @@ bool make_bf16_map_strided(CUtensorMap* map, const void* base, uint64_t rows, ui
 }
 
 void launch_slice_rows(gwas_ctx* c, const double* src, int64_t lds, int rows, int K, int rows_pad, int Kpad, int S,
-                       int bits, __nv_bfloat16* planes, double* scale) {
+                       int bits, __nv_bfloat16* planes, double* scale, const char* name) {
   const int warps = 8;
-  ProfScope ps(c, "slice_rows");
+  std::unique_ptr<ProfScope> ps(name ? new ProfScope(c, name) : nullptr);
   slice_rows_kernel<<<(rows_pad + warps - 1) / warps, warps * 32, 0, c->stream>>>(src, lds, rows, K, rows_pad, Kpad, S,
                                                                                   bits, planes, scale);
   c->launches++;
@@ -260,7 +320,7 @@ static int run_xgemm(gwas_ctx* c, const XgemmArgs& g, const __nv_bfloat16* A, co
   // after the last one); those columns are >= g.cols and never stored
   dim3 grid((g.rowsB_pad + Cfg::BN - 1) / Cfg::BN, g.rowsA_pad / BM);
   if (grid.y > 65535) return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "xgemm: more than 65535 row tiles");
-  ProfScope ps(c, g.name ? g.name : "xgemm");
+  std::unique_ptr<ProfScope> ps(g.untimed ? nullptr : new ProfScope(c, g.name ? g.name : "xgemm"));
   xgemm_kernel<SA, SB, L><<<grid, 192, Cfg::SMEM, c->stream>>>(ma, mb, g);
   c->launches++;
   return GWAS_OK;
@@ -270,14 +330,18 @@ int launch_xgemm(gwas_ctx* c, int SA, int SB, int L, const XgemmArgs& args, cons
                  const __nv_bfloat16* B) {
   if (args.rowsA_pad % BM || args.rowsB_pad % 64 || args.Kpad % BK)
     return ctx_fail(c, GWAS_ERR_ARG, "xgemm: padded sizes are not tile multiples");
-  if (!((SA == 4 && SB == 4 && L == 3) || (SA == 1 && SB == 4 && L == 3)))
+  if (!((SA == 4 && SB == 4 && L == 3) || (SA == 1 && SB == 4 && L == 3) || (SA == 8 && SB == 8 && L == 7)))
     return ctx_fail(c, GWAS_ERR_UNSUPPORTED, "xgemm: slice configuration not instantiated");
-  for (int k0 = 0; k0 < args.Kpad; k0 += XGEMM_KCHUNK) {
+  const int chunk = args.kchunk > 0 ? args.kchunk : XGEMM_KCHUNK;
+  if (chunk % BK || chunk > XGEMM_KCHUNK) return ctx_fail(c, GWAS_ERR_ARG, "xgemm: bad K chunk");
+  for (int k0 = 0; k0 < args.Kpad; k0 += chunk) {
     XgemmArgs g = args;
     g.kb0 = k0 / BK;
-    g.kb1 = std::min(args.Kpad, k0 + XGEMM_KCHUNK) / BK;
-    g.accumulate = k0 > 0;
-    const int rc = SA == 4 ? run_xgemm<4, 4, 3>(c, g, A, B) : run_xgemm<1, 4, 3>(c, g, A, B);
+    g.kb1 = std::min(args.Kpad, k0 + chunk) / BK;
+    g.accumulate = k0 > 0 || args.add_to_out;
+    const int rc = SA == 8   ? run_xgemm<8, 8, 7>(c, g, A, B)
+                   : SA == 4 ? run_xgemm<4, 4, 3>(c, g, A, B)
+                             : run_xgemm<1, 4, 3>(c, g, A, B);
     if (rc != GWAS_OK) return rc;
   }
   return GWAS_OK;

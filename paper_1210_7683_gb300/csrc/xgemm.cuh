@@ -18,6 +18,9 @@ struct XgemmArgs {
   int64_t ldo;               // output row stride (elements)
   unsigned long long* status;  // status[0] <- 1 when a bounded wait expires
   const char* name;          // timer name in profiling mode
+  int untimed;               // nonzero: no timer of its own (the caller times an enclosing region)
+  int kchunk;                // K chunk of one launch (multiple of 64; 0 = XGEMM_KCHUNK)
+  int add_to_out;            // nonzero: the first chunk also adds to the output (out += A B^T)
   // set by launch_xgemm: the K blocks [kb0, kb1) of one launch, and whether it adds to the output
   int kb0, kb1, accumulate;
 };
@@ -36,7 +39,12 @@ inline int xgemm_bits(int Kpad) {
   return b > 8 ? 8 : b;
 }
 
+// `name`: timer name in profiling mode (NULL: untimed, inside a region the caller times).
 void launch_slice_rows(gwas_ctx* c, const double* src, int64_t lds, int rows, int K, int rows_pad, int Kpad, int S,
-                       int bits, __nv_bfloat16* planes, double* scale);
+                       int bits, __nv_bfloat16* planes, double* scale, const char* name = "slice_rows");
+// Instantiated slice configurations (SA, SB, L): (1, 4, 3) and (4, 4, 3), the 28-bit rotations,
+// and (8, 8, 7), 56-bit operands for products accurate to FP64 (with kchunk <= 256 every level
+// sum stays below 2^24 and is exact: 7-bit slices, |q_0| <= 2^7, |q_a| <= 2^6, so a level-l
+// term is at most 2^12 (l + 3)).
 int launch_xgemm(gwas_ctx* c, int SA, int SB, int L, const XgemmArgs& g, const __nv_bfloat16* A,
                  const __nv_bfloat16* B);
