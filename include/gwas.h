@@ -21,8 +21,10 @@
  *   trait j are contiguous.
  * - Every array argument may be a host pointer (pageable or pinned) or a device
  *   pointer on the context's device; the library tells them apart with
- *   cudaPointerGetAttributes and copies host data itself.  The caller keeps
- *   ownership of all its buffers and may release them when the call returns.
+ *   cudaPointerGetAttributes and copies host data itself (where the device reads
+ *   the CPU's page tables, kernels read page-locked genotypes and store
+ *   page-locked outputs directly instead).  The caller keeps ownership of all
+ *   its buffers and may release them when the call returns.
  * - The context owns every device allocation it makes (Z, Lambda, the rotated
  *   covariates, the resident rotated genotypes and the work buffers) and gives
  *   them back in gwas_destroy to the library's device memory pool, which keeps
@@ -288,6 +290,9 @@ GWAS_API int gwas_autotune(gwas_ctx* ctx, const double* Y, int t_sample, int64_t
  *   GWAS_SERVE_SLOTS=<k>, GWAS_SERVE_ROUND=<k>  serving arena trait-tile slots and units per round
  *   GWAS_HOST_OUTPUT=staged               gwas_solve copies page-locked host outputs through device
  *                                         staging instead of storing them from the kernels
+ *   GWAS_HOST_INPUT=staged                gwas_load_snps (mixed precision) copies page-locked host
+ *                                         genotypes to the device instead of reading them from the
+ *                                         conversion kernel
  *   GWAS_S_BR=exact                       the mixed path contracts S_BR for every pair (read when a
  *                                         context plans it: its first solve, or after gwas_set_h2)
  *   GWAS_POOL=0                           device buffers from cudaMalloc/cudaFree instead of the

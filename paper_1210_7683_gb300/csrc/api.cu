@@ -205,10 +205,10 @@ int ptr_kind(gwas_ctx* c, const void* p, bool* is_device) {
 // and the device addresses of the ends are as far apart as the host ones.  Page-locked memory
 // is resident, so the stores never wait for a page fault.  GWAS_HOST_OUTPUT=staged in the
 // environment keeps the staged copies.
-static bool direct_host_output(gwas_ctx* c, void* p, size_t bytes, void** dptr) {
+static bool direct_host_output(gwas_ctx* c, void* p, size_t bytes, void** dptr, bool input = false) {
   if (bytes == 0) return false;
   if (const char* e = getenv("GWAS_HOST_OUTPUT"))
-    if (!strcmp(e, "staged")) return false;
+    if (!input && !strcmp(e, "staged")) return false;
   int ats = 0;
   if (cudaDeviceGetAttribute(&ats, cudaDevAttrPageableMemoryAccessUsesHostPageTables, c->device) != cudaSuccess) {
     cudaGetLastError();
@@ -225,6 +225,21 @@ static bool direct_host_output(gwas_ctx* c, void* p, size_t bytes, void** dptr) 
     return false;
   if ((const char*)a1.devicePointer - (const char*)a0.devicePointer != (ptrdiff_t)(bytes - 1)) return false;
   *dptr = a0.devicePointer;
+  return true;
+}
+
+// Whether a kernel can read the host input [p, p + bytes) directly, under the same conditions as
+// direct_host_output (a device that reads the CPU's page tables, page-locked memory mapped for the
+// device).  On this kind of system the copy engines' host -> device rate from page-locked buffers
+// that have existed for a while fell to 17-54 GB/s in processes that followed other large GPU
+// processes, while kernel accesses to the same memory kept the link's rate.
+// GWAS_HOST_INPUT=staged in the environment keeps the copies.
+static bool direct_host_input(gwas_ctx* c, const void* p, size_t bytes, const void** dptr) {
+  if (const char* e = getenv("GWAS_HOST_INPUT"))
+    if (!strcmp(e, "staged")) return false;
+  void* d = nullptr;
+  if (!direct_host_output(c, const_cast<void*>(p), bytes, &d, true)) return false;
+  *dptr = d;
   return true;
 }
 
@@ -600,11 +615,16 @@ extern "C" int gwas_load_snps(gwas_ctx* c, int64_t m, const int8_t* XR) {
   if ((rc = ptr_kind(c, XR, &dev))) return rc;
   const size_t bytes = (size_t)m * c->n;
   int8_t* dX = nullptr;
+  // mixed path, page-locked host genotypes the device can read: the conversion kernel reads them
+  // once and leaves the device copy the other kernels read
+  const void* mapped = nullptr;
+  const bool direct = !dev && c->precision == GWAS_MIXED && direct_host_input(c, XR, bytes, &mapped);
   if (dev) {
     dX = (int8_t*)XR;
   } else {
     if ((rc = ctx_alloc(c, bytes, (void**)&dX))) return rc;
-    if (!ctx_cuda_ok(c, cudaMemcpyAsync(dX, XR, bytes, cudaMemcpyHostToDevice, c->stream), "genotype upload", &rc)) {
+    if (!direct &&
+        !ctx_cuda_ok(c, cudaMemcpyAsync(dX, XR, bytes, cudaMemcpyHostToDevice, c->stream), "genotype upload", &rc)) {
       ctx_free(c, dX);
       return rc;
     }
@@ -613,6 +633,8 @@ extern "C" int gwas_load_snps(gwas_ctx* c, int64_t m, const int8_t* XR) {
     // X'_R := Z^T X_R (Algorithm 5, gemm), kept resident as [m][n] FP64
     if ((rc = ctx_alloc(c, sizeof(double) * m * c->n, (void**)&c->Xt)) == GWAS_OK)
       launch_rotate_fp64_i8(c, dX, m, c->n, c->Xt);
+  } else if (direct) {
+    rc = mixed_load(c, (const int8_t*)mapped, m, false, dX);
   } else {
     rc = mixed_load(c, dX, m);
   }

@@ -137,7 +137,10 @@ int consts_stride(int pm1);
 // Genotypes already on the device -> resident mixed-path arrays.  reuse: keep the arrays and
 // the rotation scratch when they are large enough (out-of-core slabs), with no final
 // synchronisation.
-int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m, bool reuse = false);
+// `dXR`: device-readable genotypes; with `copy` (device, m x n) the conversion kernel, which reads
+// them once, also writes them there and every later kernel reads the copy (dXR may then be mapped
+// host memory).
+int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m, bool reuse = false, int8_t* copy = nullptr);
 struct MixedWs;  // work buffers of one gwas_solve call (mixed.cu)
 int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** ws);
 void mixed_ws_free(gwas_ctx* c, MixedWs* ws);

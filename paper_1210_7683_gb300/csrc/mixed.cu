@@ -134,10 +134,11 @@ __global__ void transpose_kernel(const double* __restrict__ in, int n, double* _
     if (ox < n && oy0 + dy < n) out[(size_t)(oy0 + dy) * n + ox] = t[threadIdx.x][dy];
 }
 
-// int8 genotypes [m][n] -> bf16 [mpad][Kpad] (zero padded).  One thread per 8 consecutive
-// values of a row: an 8-byte load when the row's bytes allow it, one 16-byte store.
+// int8 genotypes [m][n] -> bf16 [mpad][Kpad] (zero padded), and with `copy` the int8 bytes again
+// into copy [m][n] (X may then be host memory the device reads, read once).  One thread per 8
+// consecutive values of a row: an 8-byte load when the row's bytes allow it, one 16-byte store.
 __global__ void geno_bf16_kernel(const int8_t* __restrict__ X, int64_t m, int n, int64_t mpad, int Kpad,
-                                 __nv_bfloat16* __restrict__ G) {
+                                 __nv_bfloat16* __restrict__ G, int8_t* __restrict__ copy) {
   const int per_row = Kpad / 8;
   const int64_t total = mpad * (int64_t)per_row;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -145,8 +146,11 @@ __global__ void geno_bf16_kernel(const int8_t* __restrict__ X, int64_t m, int n,
     const int k0 = (int)(e - i * per_row) * 8;
     float v[8];
     const int64_t src = i * (int64_t)n + k0;
-    if (i < m && k0 + 8 <= n && (src & 7) == 0) {
+    // 8-byte accesses only where both addresses allow them (a caller's device or host pointer
+    // may start anywhere)
+    if (i < m && k0 + 8 <= n && ((uintptr_t)(X + src) & 7) == 0 && (!copy || ((uintptr_t)(copy + src) & 7) == 0)) {
       const uint2 w = *reinterpret_cast<const uint2*>(X + src);
+      if (copy) *reinterpret_cast<uint2*>(copy + src) = w;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         v[j] = (float)(int8_t)((w.x >> (8 * j)) & 0xffu);
@@ -154,7 +158,12 @@ __global__ void geno_bf16_kernel(const int8_t* __restrict__ X, int64_t m, int n,
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = (i < m && k0 + j < n) ? (float)X[src + j] : 0.f;
+      for (int j = 0; j < 8; ++j) {
+        const bool in = i < m && k0 + j < n;
+        const int8_t x = in ? X[src + j] : (int8_t)0;
+        if (in && copy) copy[src + j] = x;
+        v[j] = (float)x;
+      }
     }
     uint32_t u[4];
 #pragma unroll
@@ -542,7 +551,7 @@ static int mixed_setup(gwas_ctx* c) {
   return GWAS_OK;
 }
 
-int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m, bool reuse) {
+int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m, bool reuse, int8_t* copy) {
   int rc = mixed_setup(c);
   if (rc) return rc;
   MixedState* s = c->mixed;
@@ -562,8 +571,10 @@ int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m, bool reuse) {
   }
   ++s->load_gen;
   { ProfScope ps(c, "genotypes_bf16");
-  geno_bf16_kernel<<<16 * 152, 256, 0, c->stream>>>(dXR, m, n, s->mpad, s->Kpad, s->G);
+  geno_bf16_kernel<<<16 * 152, 256, 0, c->stream>>>(dXR, m, n, s->mpad, s->Kpad, s->G, copy);
   c->launches++; }
+  // the genotypes read by the later kernels: the device copy the conversion made, if any
+  if (copy) dXR = copy;
   // rotate in chunks of SNPs to bound the FP32 scratch
   const int64_t chunk = std::min<int64_t>(s->mpad, 1 << 18);
   if (s->xc_rows < chunk) {

@@ -272,6 +272,37 @@ def test_page_locked_output_direct_and_staged(gw, monkeypatch, precision, output
     assert np.isfinite(ref).all()
 
 
+@pytest.mark.parametrize("offset", [0, 1])
+def test_page_locked_genotypes_read_directly(gw, monkeypatch, offset):
+    # page-locked host genotypes are read by the conversion kernel itself where the device reads
+    # the CPU's page tables, else (and with GWAS_HOST_INPUT=staged) copied first; both give the
+    # results of device genotypes bit for bit, also from a buffer that starts off an 8-byte boundary
+    import torch
+    P = make_problem(301, 1500, 40, seed=2031)
+    flat = torch.zeros(P.m * P.n + 8, dtype=torch.int8).pin_memory()
+    pinned = flat[offset:offset + P.m * P.n].view(P.m, P.n)
+    pinned.copy_(torch.from_numpy(P.XR))
+    outs = []
+    for XR, mode in ((torch.from_numpy(P.XR).cuda(), None), (pinned, None), (pinned, "staged")):
+        if mode:
+            monkeypatch.setenv("GWAS_HOST_INPUT", mode)
+        else:
+            monkeypatch.delenv("GWAS_HOST_INPUT", raising=False)
+        o = gw.gwas_default_opts(precision=gw.GWAS_MIXED, output=gw.GWAS_OUT_LAST_SE)
+        ctx = gw.gwas_setup(P.n, P.pm1, P.phi, P.XL, P.t, P.h2, o)
+        try:
+            gw.gwas_load_snps(ctx, P.m, XR, P.n)
+            out = np.full((2, P.t, P.m), np.nan, dtype=np.float32)
+            gw.gwas_solve(ctx, P.Y, 0, P.m, out)
+        finally:
+            gw.gwas_destroy(ctx)
+        outs.append(out)
+    np.testing.assert_array_equal(outs[1], outs[0])
+    np.testing.assert_array_equal(outs[2], outs[0])
+    b, se = EigOracle(P.phi, P.XL).solve(P.XR[:200], P.Y, P.h2)
+    check_last(outs[0][:, :, :200], b, se)
+
+
 def test_extreme_heritabilities(gw):
     # h^2 over the whole range of the model, both ends included: M_j = I (ordinary least
     # squares) at 0 and M_j = Phi at 1; near 1 the weights e_j = 1/(h^2 lambda + 1 - h^2)
