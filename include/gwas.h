@@ -252,8 +252,8 @@ GWAS_API int64_t gwas_singular_count(const gwas_ctx* ctx);
  * accuracy by the iteration of Ogita and Aishima (2018) with FP64-accurate products on the tensor
  * cores, took *steps refinement steps until max |(Z^T Z - I)_ij| and
  * max_{i != j} |(Z^T Phi Z)_ij| / max |lambda| were both <= 16 u sqrt(n), u = 2^-53;
- * *steps = -1: the FP64 eigensolver (cuSOLVER Dsyevd) computed it, because the refinement did not
- * converge within 8 steps, the FP32 solver failed, or GWAS_EIG=fp64 was set.  Either way Lambda
+ * *steps = -1: the FP64 eigensolver (cuSOLVER Dsyevd) computed it, because n > 2048, the
+ * refinement did not converge within 8 steps, the FP32 solver failed, or GWAS_EIG=fp64 was set.  Either way Lambda
  * is ascending and Z column-major.  Returns GWAS_OK or GWAS_ERR_ARG (NULL argument). */
 GWAS_API int gwas_eig_info(const gwas_ctx* ctx, int* steps);
 

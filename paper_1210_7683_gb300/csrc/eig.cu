@@ -32,8 +32,8 @@
 // 16 u max(sqrt(n), 8) (u = 2^-53); Z is accepted only after the same test on Z^T Z and Z^T Phi Z
 // recomputed from Z with FP64-accurate products, and the eigenvalues are S_ii / (Z^T Z)_ii of that
 // recomputation.  If the test fails, the iteration has not converged after 8 steps, the FP32
-// solver failed, or the scratch memory is not available, the caller computes the decomposition
-// with the FP64 solver instead.
+// solver failed, the scratch memory is not available, or n > 2048 (where the measured steps did
+// not converge), the caller computes the decomposition with the FP64 solver instead.
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -58,6 +58,12 @@ struct RowStat {
 constexpr int kSlices = 8, kBits = 7, kLevels = 7, kChunk = 256, kMaxSteps = 8, kCheapSlices = 4;
 // largest correction from which the steps continue incrementally
 constexpr double kIncremental = 1e-5;
+// Largest n refined.  Measured on kinships of 5000 markers against the FP64 solver: n = 1000
+// 16.7 / 34.4 ms (4 steps), 1500 39 / 64 ms (7), 2000 73 / 101 ms (8), 2500 116 / 165 ms (6);
+// at n = 3000 the steps stalled with the off-diagonal of S at twice the tolerance (the floor
+// u ||Phi|| / gap of the closest pairs grows faster than sqrt(n)), and at n = 4096 and above
+// they did not converge either, so those sizes go to the FP64 solver directly.
+constexpr int kRefineMaxN = 2048;
 
 __global__ void f64_to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, size_t N) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
@@ -242,6 +248,7 @@ int eig_refined(gwas_ctx* c, void* solver, const double* phi, int n, double* Z, 
   cusolverDnHandle_t h = (cusolverDnHandle_t)solver;
   constexpr int kFallBack = EIG_FALL_BACK;
   *steps = 0;
+  if (n > kRefineMaxN) return kFallBack;
   const size_t nn = (size_t)n * n;
   const int Np = (int)rup(n, 128), Kpad = (int)rup(n, 64);
   const size_t planes8 = (size_t)kSlices * Np * Kpad, planes4 = (size_t)kCheapSlices * Np * Kpad;

@@ -79,3 +79,16 @@ def test_refined_eigendecomposition_in_the_mixed_path(gw, monkeypatch):
     a, r = outs
     assert np.max(np.abs(a[0] - r[0]) / np.maximum(np.abs(r[0]), r[1])) <= 1e-6
     assert np.max(np.abs(a[1] - r[1]) / r[1]) <= 1e-6
+
+
+def test_larger_kinships_go_to_the_fp64_solver(gw):
+    # above n = 2048 the refinement's steps were measured not to converge: the FP64 solver runs
+    # directly
+    n = 2049
+    phi, XL = kinship(n, seed=777), make_problem(n, 1, 1, seed=777, with_snps=False).XL
+    o = gw.gwas_default_opts(precision=gw.GWAS_FP64)
+    ctx = gw.gwas_setup(n, 3, phi, XL, 1, np.array([0.5]), o)
+    try:
+        assert gw.gwas_eig_info(ctx) == -1
+    finally:
+        gw.gwas_destroy(ctx)
