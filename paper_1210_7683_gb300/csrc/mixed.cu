@@ -439,24 +439,30 @@ __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__
     __syncthreads();
     const double inv = 1.0 / smax;
     const int nsl = c == 0 ? 4 : 2;
+    // Digits below the first: w: three of 8 bits; v': one of 9 bits (|q| <= 256 is exact in bf16
+    // and 2 * 256 * n stays below 2^24), which halves z's truncation error.  They come from one
+    // 64-bit fixed-point integer per element, X = round(t * 2^fb) with fb = 24 (w) or 9 (v'), each
+    // digit the rounded quotient of the remainder by the next power of two: the digits of rounding
+    // digit by digit, with two FP64 operations for all of them instead of three per digit.
+    const int fb = c == 0 ? 24 : 9, db = c == 0 ? 8 : 9;
+    const double sc = ldexp(inv, fb);
     for (int l = threadIdx.x; l < Kpad; l += blockDim.x) {
       double t = 0;
       if (l < n) {
         t = col[l];
         for (int a = 0; a < PM1; ++a) t -= XL[(size_t)a * n + l] * coef[a];
-        t *= inv;
       }
+      long long X = __double2ll_rn(t * sc);  // |t * inv| <= 256: |X| <= 2^32
       for (int s = 0; s < nsl; ++s) {
-        const double q = rint(t);
+        const int sh = fb - (s == 0 ? 0 : s * db);
+        const long long q = sh > 0 ? ((X + (1LL << (sh - 1))) >> sh) : X;
+        X -= q * (1LL << sh);
         // one CTA: groups [slice 1 of w, v_1..q | slice 2 of w, v_1..q | w3 | w4];
         // CTA pair (q = 3): [Q1 | Q3] for the first CTA, [Q2 | Q4] for the second
         int row;
         if (!pair) row = (s < 2 ? s * (1 + Q) + c : 2 * Q + s) * TT + jj;
         else row = (s == 0 ? 0 : s == 1 ? 5 * TT : s == 2 ? 4 * TT : 9 * TT) + (s < 2 ? c * TT : 0) + jj;
-        b1[(size_t)row * Kpad + l] = __float2bfloat16((float)q);
-        // w: 8-bit slices below the first; v': a 9-bit second slice (|q| <= 256 is exact in bf16
-        // and 2 * 256 * n stays below 2^24), which halves z's truncation error
-        t = (t - q) * (c == 0 ? 256.0 : 512.0);
+        b1[(size_t)row * Kpad + l] = __float2bfloat16_rn((float)(int)q);
       }
     }
     __syncthreads();
