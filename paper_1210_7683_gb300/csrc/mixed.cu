@@ -704,11 +704,13 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h
   g.status = c->d_status;
   g.name = "xgemm_rotate_traits";
   if ((rc = launch_xgemm(c, 4, 4, 3, g, Ysl, s->Bzt)) == GWAS_OK) {
-    // per-trait algebra and the C2 operand
-    ProfScope ps(c, "prep_traits");
-    Q_DISPATCH_ALL(q, prep_mixed_kernel<Q><<<tb, 256, 0, c->stream>>>(Yt, Kpad, h2, c->lam, c->XLt, n, Kpad, Wt, B2, cst,
-                                                                  slot, pair, s->rk));
-    c->launches++;
+    {
+      // per-trait algebra and the C2 operand
+      ProfScope ps(c, "prep_traits");
+      Q_DISPATCH_ALL(q, prep_mixed_kernel<Q><<<tb, 256, 0, c->stream>>>(Yt, Kpad, h2, c->lam, c->XLt, n, Kpad, Wt, B2,
+                                                                    cst, slot, pair, s->rk));
+      c->launches++;
+    }
     // back-rotation [w | v] = Z [e.r' | (e.X'_L) L^-T]
     launch_slice_rows(c, Wt, Kpad, tb * p, n, rowsW, Kpad, 4, s->bits, Wsl, sW);
     XgemmArgs b = g;
