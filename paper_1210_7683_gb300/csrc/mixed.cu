@@ -902,26 +902,32 @@ void cheb_nodes(int R, double lo, double hi, double* h) {
 static double cheb_bound(int n, const double* lam, const unsigned char* reach, double lo, double hi, int R) {
   std::vector<double> h(R);
   cheb_nodes(R, lo, hi, h.data());
-  // log max |omega| over a fine grid of [lo, hi], with a margin for the grid
-  double lmax = -1e300;
+  // max |omega| over a fine grid of [lo, hi], with a margin for the grid.  Every factor is at most
+  // hi - lo <= 1, so the products neither overflow nor, at their maximum (about
+  // 2^(2-R) ((hi - lo) / 2)^R >= 1e-90), underflow; the loop over the grid vectorises.
   const int G = 4096;
-  for (int g = 0; g <= G; ++g) {
-    const double x = lo + (hi - lo) * g / G;
-    double l = 0;
-    for (int r = 0; r < R; ++r) l += std::log(std::fabs(x - h[r]) + 1e-300);
-    lmax = std::max(lmax, l);
+  std::vector<double> w(G + 1, 1.0);
+  for (int r = 0; r < R; ++r) {
+    const double hr = h[r];
+    for (int g = 0; g <= G; ++g) w[g] *= std::fabs(lo + (hi - lo) * g / G - hr) + 1e-300;
   }
-  lmax += std::log(2.0);
-  double worst = 0;
+  const double lmax = std::log(*std::max_element(w.begin(), w.end())) + std::log(2.0);
+  // min over the reached k of log |omega(pole_k)|: factors in groups of 8 stay inside FP64's range
+  // (each is between the distance of the pole to [lo, hi] and |pole| + 1 <= 2^53 + 1)
+  double lmin = INFINITY;
   for (int k = 0; k < n; ++k) {
     if (!reach[k] || lam[k] == 1.0) continue;
     const double hs = 1.0 / (1.0 - lam[k]);   // the pole of 1 / (1 - h + h lambda_k)
     if (hs >= lo && hs <= hi) return INFINITY;
     double l = 0;
-    for (int r = 0; r < R; ++r) l += std::log(std::fabs(hs - h[r]));
-    worst = std::max(worst, std::exp(lmax - l));
+    for (int r0 = 0; r0 < R; r0 += 8) {
+      double p = 1.0;
+      for (int r = r0; r < std::min(R, r0 + 8); ++r) p *= std::fabs(hs - h[r]);
+      l += std::log(p);
+    }
+    lmin = std::min(lmin, l);
   }
-  return worst;
+  return lmin == INFINITY ? 0.0 : std::exp(lmax - lmin);
 }
 
 extern "C" int gwas_cheb_plan(int n, const double* lam, const unsigned char* reach, double lo, double hi, double tol,
