@@ -257,6 +257,20 @@ GWAS_API int64_t gwas_singular_count(const gwas_ctx* ctx);
  * is ascending and Z column-major.  Returns GWAS_OK or GWAS_ERR_ARG (NULL argument). */
 GWAS_API int gwas_eig_info(const gwas_ctx* ctx, int* steps);
 
+/* The mixed path's e2m1 operands.  At p = 4, for blocks whose S_BR is interpolated (gwas_sbr_info)
+ * and with the CTA-pair launch shape (gwas_tune_shape), the fused kernel contracts the genotypes
+ * and the fixed-point slices of the per-trait columns as e2m1 values on the block-scaled FP4 tensor
+ * cores (tcgen05 kind::mxf4): the genotypes are exact, each 9-bit slice digit q is split into three
+ * e2m1 digits, q = 64 d0 + 8 d1 + d2 with |d| <= 4, and the three digits are contracted into the
+ * slice's accumulator with scale factors 2^6, 2^3 and 2^0.  Every partial sum is the same integer as
+ * with bf16 slices, so the results are identical; the kernel streams half the operand bytes.
+ *   *ready     1 when the loaded genotypes have their e2m1 copy: a one-time gwas_load_snps at p = 4
+ *              of genotypes that are all in {0, +-1, +-2, +-3, +-4, +-6} (not set by the slabs of
+ *              gwas_solve_ooc, nor under GWAS_FP4=0)
+ *   *launches  launches of the e2m1 kernel since the context was created
+ * Either pointer may be NULL.  Returns GWAS_OK or GWAS_ERR_ARG (NULL context). */
+GWAS_API int gwas_fp4_info(gwas_ctx* ctx, int* ready, int64_t* launches);
+
 /* Number of kernels this context launched since it was created. */
 GWAS_API int64_t gwas_kernel_launches(const gwas_ctx* ctx);
 
@@ -298,7 +312,9 @@ GWAS_API int gwas_autotune(gwas_ctx* ctx, const double* Y, int t_sample, int64_t
  *   GWAS_POOL=0                           device buffers from cudaMalloc/cudaFree instead of the
  *                                         library's pool (read once per process)
  *   GWAS_EIG=fp64                         gwas_setup computes the eigendecomposition with the FP64
- *                                         solver (see gwas_eig_info) */
+ *                                         solver (see gwas_eig_info)
+ *   GWAS_FP4=0                            gwas_load_snps makes no e2m1 copy of the genotypes: the
+ *                                         fused kernel runs on bf16 operands (see gwas_fp4_info) */
 GWAS_API int gwas_tune_shape(const gwas_ctx* ctx, int* shape);
 
 /* Accumulated device time (ms, from CUDA events recorded on the context's stream

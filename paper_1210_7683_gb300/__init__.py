@@ -112,6 +112,8 @@ def _load():
     lib.gwas_destroy.restype = None
     lib.gwas_eig_info.argtypes = [vp, C.POINTER(ci)]
     lib.gwas_eig_info.restype = ci
+    lib.gwas_fp4_info.argtypes = [vp, C.POINTER(ci), C.POINTER(C.c_int64)]
+    lib.gwas_fp4_info.restype = ci
     lib.gwas_pool_info.argtypes = [ci, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
     lib.gwas_pool_info.restype = ci
     lib.gwas_pool_trim.argtypes = [ci, C.c_uint64]
@@ -412,6 +414,14 @@ def gwas_eig_info(ctx) -> int:
     st = C.c_int()
     _check(lib.gwas_eig_info(ctx, C.byref(st)), ctx)
     return st.value
+
+
+def gwas_fp4_info(ctx) -> dict:
+    """Whether the loaded genotypes have their e2m1 copy, and the launches of the fused kernel on
+    e2m1 operands so far."""
+    ready, launches = C.c_int(), C.c_int64()
+    _check(lib.gwas_fp4_info(ctx, C.byref(ready), C.byref(launches)), ctx)
+    return {"ready": bool(ready.value), "launches": launches.value}
 
 
 def gwas_pool_info(device=0) -> dict:

@@ -103,6 +103,13 @@ cudaError_t dev_malloc(int dev, void** p, size_t bytes) {
   DevicePool dp = device_pool(dev);
   if (!dp.pool) return cudaMalloc(p, bytes);
   cudaError_t e = cudaMallocFromPoolAsync(p, bytes, dp.pool, dp.stream);
+  if (e == cudaErrorMemoryAllocation) {
+    // the pool's free blocks may hold the room in pieces too small for this buffer: give them
+    // back to the device and try once more
+    cudaGetLastError();
+    cudaMemPoolTrimTo(dp.pool, 0);
+    e = cudaMallocFromPoolAsync(p, bytes, dp.pool, dp.stream);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(dp.stream);
   if (e == cudaSuccess && (reinterpret_cast<uintptr_t>(*p) & 255)) {
     cudaFreeAsync(*p, dp.stream);
@@ -390,6 +397,13 @@ extern "C" int64_t gwas_singular_count(const gwas_ctx* c) { return c ? c->singul
 extern "C" int gwas_eig_info(const gwas_ctx* c, int* steps) {
   if (!c || !steps) return GWAS_ERR_ARG;
   *steps = c->eig_steps;
+  return GWAS_OK;
+}
+
+extern "C" int gwas_fp4_info(gwas_ctx* c, int* ready, int64_t* launches) {
+  if (!c) return GWAS_ERR_ARG;
+  if (ready) *ready = c->precision == GWAS_MIXED ? mixed_fp4_ready(c) : 0;
+  if (launches) *launches = c->fp4_launches;
   return GWAS_OK;
 }
 

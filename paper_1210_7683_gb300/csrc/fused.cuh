@@ -119,6 +119,7 @@ struct FusedArgs {
   int group;          // cluster-wide SNP super-tiles per traversal group (L2 reuse of genotype tiles)
   int ntrait;         // traits in this block
   int Kpad;           // padded n (multiple of 64)
+  int Kp4;            // padded n of the e2m1 operands (multiple of 256; FP4 kernel only)
   int64_t mpad;       // rows per plane of G and of the x'_c^2 planes
   float dof;          // n - p
   const float* sA;    // [m] scale of the x'_c^2 slices of each SNP (0 marks a singular SNP)
@@ -169,6 +170,13 @@ int launch_fused_cheb_wide(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bf
 // The CTA-pair shape of the same (q = 3, trait operands in the pair layout).
 int launch_fused_cheb_pair(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* B1,
                            int b_tiles);
+// The CTA-pair shape with S_BR interpolated on e2m1 operands (fused_fp4.cu, q = 3): G4 the
+// genotypes [mpad][Kp4 / 2] (two e2m1 values per byte), B1_4 the C1 trait columns as three
+// e2m1 digits per fixed-point slice, [trait tile][CTA half][digit][120 rows][Kp4 / 2].  The
+// accumulators hold the same integers as the bf16 kernel's, so the outputs are the same.
+int launch_fused_cheb_pair_fp4(gwas_ctx* c, const FusedArgs& a, const uint8_t* G4, const uint8_t* B1_4, int b_tiles);
+// Rows of B1_4 per trait tile: 3 digits x the 240 C1 rows of a 24-trait tile.
+constexpr int FP4_TILE_ROWS = 3 * 240;
 // Single-trait kernel (gemv.cu): the same solve for a.ntrait == 1, streaming the SNPs'
 // operands once through a TMA ring (HBM-bound); for the one-CTA operand layout, 0 <= q <= 19.
 bool gemv1_supported(int q, int Kpad);

@@ -79,13 +79,32 @@ __host__ __device__ constexpr int slot_bytes(bool interp, int q, bool pair = fal
 __host__ __device__ constexpr int ring_bytes(bool pair, bool interp, int q) {
   return (interp ? interp_slots(q, pair) : pair ? PSLOTS : SLOTS) * slot_bytes(interp, q, pair);
 }
-// INTERP: the tile's Chebyshev coefficients [CHEB_MAX_R + 1][128 SNPs] and T_k(x_j) [CHEB_MAX_R][TT]
-__host__ __device__ constexpr int cheb_stage_bytes(bool interp, int q) {
-  return interp ? ((CHEB_MAX_R + 1) * 128 + CHEB_MAX_R * mixed_tt(q)) * 4 : 0;
+// INTERP: the tile's Chebyshev coefficients [CHEB_MAX_R + 1][128 SNPs] and T_k(x_j) [CHEB_MAX_R][TT].
+// The CTA pair stages them one tile ahead by bulk copies: two buffers of the coefficients and of T
+// as stored ([TT][CHEB_MAX_R]), and one array of T transposed for the series.
+__host__ __device__ constexpr int cheb_pair_buf(int q) { return (CHEB_MAX_R + 1) * 128 + tile_traits(q, true) * CHEB_MAX_R; }
+__host__ __device__ constexpr int cheb_stage_bytes(bool interp, int q, bool pair = false) {
+  return !interp ? 0
+         : pair  ? (2 * cheb_pair_buf(q) + CHEB_MAX_R * tile_traits(q, true)) * 4
+                 : ((CHEB_MAX_R + 1) * 128 + CHEB_MAX_R * mixed_tt(q)) * 4;
 }
 __host__ __device__ constexpr int smem_bytes(bool pair, int q, bool interp = false) {
-  return ring_bytes(pair, interp, q) + 2 * cst_bytes(q) + cheb_stage_bytes(interp, q) + 1024 + 512;
+  return ring_bytes(pair, interp, q) + 2 * cst_bytes(q) + cheb_stage_bytes(interp, q, pair) + 1024 + 512;
 }
+// e2m1 operands (the interpolated CTA pair, q = 3): a ring item is one K block of 256, i.e. one
+// 128-byte row of packed e2m1 values per operand row: the CTA's 128 genotype rows and its 120 C1
+// rows in each of the three digits (16 KB + 45 KB), in three slots.
+constexpr int BK4 = 256;
+constexpr int F4_HALF = 120;
+constexpr int F4_ITEM = G_BYTES + 3 * F4_HALF * ROWB;
+constexpr int F4_SLOTS = 3;
+// TMEM columns of the constant scale factors, beside the accumulator buffers [0, 240) and [256, 496)
+constexpr int SF_A = 240, SF_B0 = 248, SF_B1 = 496, SF_B2 = 504;
+__host__ __device__ constexpr int smem_bytes_fp4() {
+  return F4_SLOTS * F4_ITEM + 2 * cst_bytes(3) + cheb_stage_bytes(true, 3, true) + 1024 + 512;
+}
+static_assert(F4_ITEM % 1024 == 0 && (F4_HALF * ROWB) % 1024 == 0 && smem_bytes_fp4() <= 227 * 1024, "e2m1 ring");
+static_assert(2 * F4_HALF == c1_rows_of(3, true), "e2m1 C1 rows");
 constexpr int TMEM_COLS = 512;
 constexpr bool fits_all_q() {
   for (int q = 0; q <= MIXED_MAX_Q; ++q)
@@ -125,13 +144,18 @@ __device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us,
 // INTERP: S_BR is not contracted here but evaluated per pair from its Chebyshev series in
 // h^2 (FusedArgs::cheb_*): the K loop streams only the C1 operands (genotypes and the trait
 // columns [w | v']), one item per K block.
-template <int EPW, bool SERVE, bool PAIR, int Q, bool INTERP = false>
+// FP4 (PAIR, INTERP, q = 3): the C1 operands as e2m1 values (kind::mxf4).  A fixed-point slice
+// digit q (|q| <= 292) is written as 64 d0 + 8 d1 + d2 with d in [-4, 4], and the three digits are
+// contracted into the slice's own accumulator by MMAs whose B scale factors are 2^6, 2^3 and 2^0:
+// every partial sum is the same integer as the bf16 kernel's, so the outputs do not change.
+template <int EPW, bool SERVE, bool PAIR, int Q, bool INTERP = false, bool FP4 = false>
 __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     fused_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapA2,
                  const __grid_constant__ CUtensorMap mapB1, const __grid_constant__ CUtensorMap mapB2, FusedArgs a) {
   constexpr int CS = PAIR ? 2 : 1;                  // SNP tiles per cluster (the CTA pair: 2)
   static_assert(!PAIR || (!SERVE && Q == 3), "the pair shape is built for q = 3 outside serving");
   static_assert(!INTERP || !SERVE, "the interpolated S_BR is built for the solve kernels");
+  static_assert(!FP4 || (PAIR && INTERP && Q == 3), "the e2m1 operands are built for the interpolated pair");
   constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1, TT = tile_traits(Q, INTERP), CSTR = cst_stride(Q);
   constexpr int B1_ROWS = c1_groups(Q) * TT, B2_ROWS = c2_rows(Q), B2_ROWS_PAIR = c2_alloc(Q);
   // the pair with S_BR interpolated: one MMA of N = B1_ROWS per K step, each CTA holding half of its rows
@@ -152,24 +176,31 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   // tile and the C1 trait rows in one or two boxes; the three x'^2 planes, stored next to
   // one another, in two halves and the C2 trait rows).  The TMA unit pays a fixed cost per
   // box of the order of 50 cycles, so large boxes keep the load rate up.
-  constexpr int NSL = INTERP ? interp_slots(Q, PAIR) : PAIR ? PSLOTS : SLOTS;  // ring slots
-  constexpr int SLB = slot_bytes(INTERP, Q, PAIR);                             // and their size
+  constexpr int NSL = FP4 ? F4_SLOTS : INTERP ? interp_slots(Q, PAIR) : PAIR ? PSLOTS : SLOTS;  // ring slots
+  constexpr int SLB = FP4 ? F4_ITEM : slot_bytes(INTERP, Q, PAIR);                             // and their size
   constexpr int NI = INTERP ? 1 : PAIR ? 3 : 2;                           // ring items per K block
-  constexpr int RING = ring_bytes(PAIR, INTERP, Q);
+  constexpr int RING = FP4 ? F4_SLOTS * F4_ITEM : ring_bytes(PAIR, INTERP, Q);
   // Double-buffered accumulators where a tile's C1 columns fit 256 (with S_BR interpolated: at
   // p = 4 the 24-trait tiles): tile u accumulates into columns [256 (u & 1), +B1_ROWS), so the
   // MMAs of the next tile do not wait for the epilogue to read this one.
   constexpr bool DB = INTERP && B1_ROWS <= 256;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // PSTAGE (the interpolated CTA pair): a tile's constants, Chebyshev coefficients and T_k(x_j) are
+  // copied by one thread with bulk copies while the tile before is in the epilogue
+  constexpr bool PSTAGE = PAIR && INTERP;
+  constexpr int CBUF = cheb_pair_buf(Q);
   float* cst_smem = (float*)(smem + RING);  // [2][TT][CSTR], double-buffered by tile
-  float* cheb_c = cst_smem + 2 * TT * CSTR;                // INTERP: [CHEB_MAX_R + 1][128]
-  float* cheb_t = cheb_c + (CHEB_MAX_R + 1) * 128;          // INTERP: [CHEB_MAX_R][TT]
-  uint64_t* full = (uint64_t*)(smem + RING + 2 * cst_bytes(Q) + cheb_stage_bytes(INTERP, Q));
+  float* cheb_c = (float*)(smem + RING + 2 * cst_bytes(Q));  // INTERP: [CHEB_MAX_R + 1][128]
+  float* cheb_t = cheb_c + (CHEB_MAX_R + 1) * 128;          // INTERP, one CTA: [CHEB_MAX_R][TT]
+  // PSTAGE: buffers b = 0, 1 at cheb_c + b * CBUF (coefficients [CHEB_MAX_R + 1][128], then T as
+  // [TT][CHEB_MAX_R]) and T transposed, [CHEB_MAX_R][TT], at cheb_c + 2 * CBUF
+  uint64_t* full = (uint64_t*)(smem + RING + 2 * cst_bytes(Q) + cheb_stage_bytes(INTERP, Q, PAIR));
   uint64_t* empty = full + NSL;
   uint64_t* acc_full = empty + NSL;          // [2]
   uint64_t* acc_empty = acc_full + 2;        // [2]
-  uint32_t* tslot = (uint32_t*)(acc_empty + 2);
+  uint64_t* stage_full = acc_empty + 2;      // [2] PSTAGE
+  uint32_t* tslot = (uint32_t*)(stage_full + 2);
   volatile int* abort = (volatile int*)(tslot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   uint32_t crank = 0, cid = blockIdx.x, ncl = gridDim.x;
@@ -182,7 +213,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   // serving: the round's work units (from device memory when the launch is a captured graph's)
   const int nsuper = SERVE ? (a.nunits_dev ? min(*a.nunits_dev, a.nunits) : a.nunits)
                            : ((a.n_stiles + CS - 1) / CS) * a.n_ttiles;
-  const int nkb = a.Kpad / BK;
+  const int nkb = FP4 ? a.Kp4 / BK4 : a.Kpad / BK;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSL; ++s) {
       tc::mbar_init(&full[s], 1);
@@ -191,6 +222,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&acc_full[b], 1);
       tc::mbar_init(&acc_empty[b], PAIR ? 2 * EPW : EPW);
+      tc::mbar_init(&stage_full[b], 1);
     }
     *abort = 0;
     tc::fence_mbar_init();
@@ -205,6 +237,22 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   tc::fence_after();
   const uint32_t tbase = *tslot;
   const bool leader = !PAIR || crank == 0;
+  if (FP4) {
+    // the scale factors: 1 for the genotypes, 2^6, 2^3, 2^0 for the three digits of the trait
+    // columns (UE8M0 bytes), in every lane of both CTAs before the first MMA
+    if (warp >= 2 && warp < 6) {
+      const uint32_t lanes = tbase + ((uint32_t)((warp % 4) * 32) << 16);
+      tc::tmem_st8_fill(lanes + SF_A, 0x7F7F7F7Fu);
+      tc::tmem_st8_fill(lanes + SF_B0, 0x85858585u);
+      tc::tmem_st8_fill(lanes + SF_B1, 0x82828282u);
+      tc::tmem_st8_fill(lanes + SF_B2, 0x7F7F7F7Fu);
+      tc::tmem_st_wait();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::cluster_sync();
+    tc::fence_after();
+  }
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -253,6 +301,18 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             if (PAIR) {
               // own SNP rows and own half of the trait rows, completing on the leader's barrier
               const uint32_t fb = tc::mapa(&full[s], 0);
+              if (FP4) {
+                // the K block's 128 bytes of each of the CTA's genotype rows and of its C1 rows
+                // of each digit
+                if (leader) tc::mbar_expect_tx(&full[s], 2 * F4_ITEM);
+                const int xb = kb * ROWB;
+                tc::tma_load_2d_pair(buf, &mapG, fb, xb, row);
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                  tc::tma_load_2d_pair(buf + G_BYTES + d * F4_HALF * ROWB, &mapB1, fb, xb,
+                                       ((tt * 2 + (int)crank) * 3 + d) * F4_HALF);
+                continue;
+              }
               if (leader)
                 tc::mbar_expect_tx(&full[s], 2 * (INTERP ? PI0I : it == 0 ? PI0_BYTES : it == 1 ? PI1_BYTES : PI2_BYTES));
               if (it == 0) {
@@ -296,6 +356,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       constexpr uint32_t id256 = tc::idesc_bf16(2 * BM, 8 * TT), id64 = tc::idesc_bf16(2 * BM, 2 * TT);
       constexpr uint32_t id96 = tc::idesc_bf16(2 * BM, 3 * TT), id32 = tc::idesc_bf16(2 * BM, TT);
       constexpr uint32_t idI = tc::idesc_bf16(2 * BM, B1_ROWS <= 256 ? B1_ROWS : 256);
+      constexpr uint32_t idF4 = tc::idesc_mxf4(2 * BM, B1_ROWS <= 256 ? B1_ROWS : 256);
       uint32_t h = 0, tcount = 0;
       bool ok = true;
       for (int u = cid; u < nsuper && ok; u += ncl, ++tcount) {
@@ -314,17 +375,28 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             tc::fence_after();
             uint8_t* buf = smem + s * SLB;
             const uint64_t dg = tc::sdesc_sw128(buf), db = tc::sdesc_sw128(buf + G_BYTES);
+            if (FP4) {
+              // four K steps of 64 (32 bytes of each row), each digit into the same accumulator
+              constexpr uint32_t sfb[3] = {SF_B0, SF_B1, SF_B2};
 #pragma unroll
-            for (int k = 0; k < BK / 16; ++k) {
-              const uint32_t acc = (kb | k) ? 1u : 0u;
-              if (INTERP) {
-                // one MMA over all C1 columns: each CTA supplies half of them, in the one-CTA order
-                tc::mma_bf16_pair(tacc, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), idI, acc);
-              } else {
-                // [Q1 | Q2] -> levels 0 and 1 of [w v1 v2 v3]; [Q3 | Q4] -> slices 3, 4 of w
-                tc::mma_bf16_pair(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), id256, acc);
-                tc::mma_bf16_pair(tbase + 8 * TT, tc::sdesc_add(dg, k * 32),
-                                  tc::sdesc_add(db, 4 * TT * ROWB + k * 32), id64, acc);
+              for (int k = 0; k < BK4 / 64; ++k)
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                  tc::mma_mxf4_pair(tacc, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, d * F4_HALF * ROWB + k * 32), idF4,
+                                    tbase + SF_A, tbase + sfb[d], (kb | k | d) ? 1u : 0u);
+            } else {
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k) {
+                const uint32_t acc = (kb | k) ? 1u : 0u;
+                if (INTERP) {
+                  // one MMA over all C1 columns: each CTA supplies half of them, in the one-CTA order
+                  tc::mma_bf16_pair(tacc, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), idI, acc);
+                } else {
+                  // [Q1 | Q2] -> levels 0 and 1 of [w v1 v2 v3]; [Q3 | Q4] -> slices 3, 4 of w
+                  tc::mma_bf16_pair(tbase + 0, tc::sdesc_add(dg, k * 32), tc::sdesc_add(db, k * 32), id256, acc);
+                  tc::mma_bf16_pair(tbase + 8 * TT, tc::sdesc_add(dg, k * 32),
+                                    tc::sdesc_add(db, 4 * TT * ROWB + k * 32), id64, acc);
+                }
               }
             }
             tc::mma_commit_pair(&empty[s], (uint16_t)3);
@@ -420,6 +492,26 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     const int jbeg = (ew / 4) * JPW;
     const uint32_t lane_base = tbase + ((uint32_t)(q * 32) << 16);
     const float inv_dof = 1.f / a.dof;
+    // PSTAGE: the bulk copies of tile uu's constants (TT traits; all allocated), its SNPs' Chebyshev
+    // coefficients (none for the pair's tile past the last SNP tile, which stores nothing) and its
+    // traits' T_k(x_j) (only those of the block) into buffer b
+    auto issue_stage = [&](int uu, int b) {
+      int us, ut;
+      super_coords<CS>(uu, a, us, ut);
+      const int64_t s0 = a.row0 + (int64_t)(us * CS + sr) * BM;
+      const int jb = ut * TT, nvt = min(TT, a.ntrait - jb), R = a.cheb_R;
+      const bool snps = s0 < a.cheb_ld;
+      float* cc = cheb_c + b * CBUF;
+      tc::mbar_expect_tx(&stage_full[b], TT * CSTR * 4 + (snps ? (R + 1) * 512 : 0) + nvt * CHEB_MAX_R * 4);
+      tc::bulk_copy_g2s(cst_smem + b * TT * CSTR, a.cst + (size_t)jb * CSTR, TT * CSTR * 4, &stage_full[b]);
+      if (snps)
+        for (int k = 0; k <= R; ++k)
+          tc::bulk_copy_g2s(cc + 128 * k, a.cheb_coef + (int64_t)(k < R ? k : CHEB_MAX_R) * a.cheb_ld + s0, 512,
+                            &stage_full[b]);
+      tc::bulk_copy_g2s(cc + (CHEB_MAX_R + 1) * 128, a.cheb_T + (size_t)jb * CHEB_MAX_R, nvt * CHEB_MAX_R * 4,
+                        &stage_full[b]);
+    };
+    if (PSTAGE && ew == 0 && lane == 0 && cid < nsuper) issue_stage(cid, 0);
     uint32_t tcount = 0;
     unsigned long long nsing = 0;
     for (int u = cid; u < nsuper; u += ncl, ++tcount) {
@@ -448,9 +540,22 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       // stage this tile's per-trait constants (double buffer: the barrier of the previous
       // tile guarantees every epilogue warp has finished reading this buffer)
       float* cs = cst_smem + (tcount & 1) * TT * CSTR;
+      const float* ccur = PSTAGE ? cheb_c + (tcount & 1) * CBUF : cheb_c;
+      const float* tcur = PSTAGE ? cheb_c + 2 * CBUF : cheb_t;
+      bool staged = true;
+      if (PSTAGE) {
+        // this tile's bulk copies (issued during the tile before); T transposed for the series
+        // (every warp passed barrier 2 of the previous tile, after its last read of the array)
+        staged = tc::mbar_wait(&stage_full[tcount & 1], (tcount >> 1) & 1, a.status, abort);
+        const float* tsrc = ccur + (CHEB_MAX_R + 1) * 128;
+        float* tdst = cheb_c + 2 * CBUF;
+        for (int e = ew * 32 + lane; e < a.cheb_R * TT; e += EPW * 32) tdst[e] = tsrc[(e % TT) * CHEB_MAX_R + e / TT];
+        (void)cst_tile;
+      } else {
       for (int e = ew * 32 + lane; e < TT * CSTR; e += EPW * 32)
         cs[e] = jbase + e / CSTR < ntrait ? cst_tile[e] : 0.f;
-      if (INTERP) {
+      }
+      if (INTERP && !PSTAGE) {
         // the tile's Chebyshev coefficients (rows 0..R-1: c_k; row R: low part of c_0) and its
         // traits' T_k(x_j); one buffer: every warp passed barrier 2 of the previous tile, which
         // follows its last read of these
@@ -466,8 +571,10 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         }
       }
       tc::named_sync(1, EPW * 32);
+      // every warp is done with the previous tile: its buffer takes the next tile's copies
+      if (PSTAGE && ew == 0 && lane == 0 && u + (int)ncl < nsuper) issue_stage(u + ncl, (tcount & 1) ^ 1);
       const uint32_t ab = DB ? (tcount & 1) : 0;
-      const bool ok = tc::mbar_wait(&acc_full[ab], (DB ? tcount >> 1 : tcount) & 1, a.status, abort);
+      const bool ok = staged && tc::mbar_wait(&acc_full[ab], (DB ? tcount >> 1 : tcount) & 1, a.status, abort);
       const uint32_t lb = lane_base + ab * 256;  // this tile's accumulator buffer
       tc::fence_after();
       const int64_t snp = snp0 + q * 32 + lane;
@@ -575,20 +682,50 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
         for (int r = 0; r < JPW; ++r) s_r[r] = 0.f;
         for (int k = R - 1; k >= 2; --k) {
-          const float ck = cheb_c[k * 128 + i];
+          const float ck = ccur[k * 128 + i];
 #pragma unroll
-          for (int r = 0; r < JPW; ++r) s_r[r] = fmaf(ck, cheb_t[k * TT + jbeg + r], s_r[r]);
+          for (int r = 0; r < JPW; ++r) s_r[r] = fmaf(ck, tcur[k * TT + jbeg + r], s_r[r]);
         }
-        const float c0 = cheb_c[i], c1 = cheb_c[128 + i], c0lo = cheb_c[R * 128 + i];
+        const float c0 = ccur[i], c1 = ccur[128 + i], c0lo = ccur[R * 128 + i];
 #pragma unroll
         for (int r = 0; r < JPW; ++r) {
-          const float t1 = cheb_t[TT + jbeg + r];
+          const float t1 = tcur[TT + jbeg + r];
           const float pp = c1 * t1, pe = fmaf(c1, t1, -pp);
           s_r[r] = c0 + (pp + ((s_r[r] + pe) + c0lo));
         }
         tc::named_sync(2, EPW * 32);
       }
-      if (valid_i && full_b != 2) {
+      if (valid_i && full_b == 0) {
+        // beta and SE of all the warp's traits first (independent chains that overlap), then the
+        // stores of those in the block; the same operations per pair as below
+        float beta_r[JPW], se_r[JPW];
+        uint32_t singm = 0;
+#pragma unroll
+        for (int r = 0; r < JPW; ++r) {
+          const float num = num_r[r], s = s_r[r];
+          const float delta = s - zz_r[r];
+          const bool sing = !(delta > 1e-6f * s) || !(sA > 0.f);
+          const float inv = __frcp_rn(delta);
+          const float beta = num * inv;
+          const float rss = fmaxf(fmaf(-num, beta, cs[(jbeg + r) * CSTR + cst_rr(Q)]), 0.f);
+          const float se = __fsqrt_rn(rss * inv * inv_dof);
+          beta_r[r] = sing ? __int_as_float(0x7fc00000) : beta;
+          se_r[r] = sing ? __int_as_float(0x7fc00000) : se;
+          singm |= (sing ? 1u : 0u) << r;
+        }
+        const int nvalid = ntrait - (jbase + jbeg);
+#pragma unroll
+        for (int r = 0; r < JPW; ++r)
+          if (r < nvalid) {
+            const int64_t o = (int64_t)(jbase + jbeg + r) * ldo + (snp - oi0);
+            // streaming stores: the grid is never re-read here, so it should not push the
+            // genotype and trait tiles out of L2
+            __stcs(obeta + o, beta_r[r]);
+            __stcs(ose + o, se_r[r]);
+            tsing += (singm >> r) & 1u;
+          }
+      }
+      if (valid_i && full_b == 1) {
 #pragma unroll
         for (int r = 0; r < JPW; ++r) {
           const int jl = jbeg + r;
@@ -621,11 +758,6 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               ob[c] = sing ? (double)beta : (double)t;
             }
             ob[PM1] = (double)beta;
-          } else {
-            // streaming stores: the grid is never re-read here, so it should not push the
-            // genotype and trait tiles out of L2
-            __stcs(obeta + o, beta);
-            __stcs(ose + o, se);
           }
         }
       }
@@ -649,12 +781,12 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   }
 }
 
-template <int EPW, bool SERVE, bool PAIR, int Q, bool INTERP = false>
+template <int EPW, bool SERVE, bool PAIR, int Q, bool INTERP = false, bool FP4 = false>
 int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const CUtensorMap& ma,
                  const CUtensorMap& m1, const CUtensorMap& m2) {
   constexpr int NC = PAIR ? 2 : 1;
-  constexpr int SMEM = smem_bytes(PAIR, Q, INTERP);
-  auto kern = fused_kernel<EPW, SERVE, PAIR, Q, INTERP>;
+  constexpr int SMEM = FP4 ? smem_bytes_fp4() : smem_bytes(PAIR, Q, INTERP);
+  auto kern = fused_kernel<EPW, SERVE, PAIR, Q, INTERP, FP4>;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);

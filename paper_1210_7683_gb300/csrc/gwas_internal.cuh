@@ -57,6 +57,7 @@ struct gwas_ctx {
   unsigned long long* d_status = nullptr;
   int64_t singular = 0;
   int64_t launches = 0;
+  int64_t fp4_launches = 0;  // launches of the fused kernel on e2m1 operands
   int eig_steps = -1;  // refinement steps of the eigendecomposition; -1: the FP64 solver computed it
   int64_t h2_gen = 0;  // incremented whenever the heritabilities change (gwas_set_h2)
 
@@ -148,8 +149,9 @@ void mixed_ws_free(gwas_ctx* c, MixedWs* ws);
 // trait tiles slot[j/32] (identity when slot is NULL) of the operand arrays B1, B2, cst, in the
 // one-CTA layout or (pair != 0) the CTA-pair layout of the fused kernel.
 // tt: trait-tile width of the C1 layout (0: mixed_tt; the interpolated kernel's tile_traits(q, true)).
+// B1_4: the C1 operand as e2m1 digits instead of B1 (p = 4, interpolated 24-trait tiles, mixed_prep_block).
 int mixed_prep_traits(gwas_ctx* c, MixedWs* ws, const double* dY, const double* h2, int tb, __nv_bfloat16* B1,
-                      __nv_bfloat16* B2, float* cst, const int* slot, int pair, int tt = 0);
+                      __nv_bfloat16* B2, float* cst, const int* slot, int pair, int tt = 0, uint8_t* B1_4 = nullptr);
 // Enqueues (no synchronisation) the per-trait operands of traits [j0, j0+tb) into the workspace.
 int mixed_prep_block(gwas_ctx* c, MixedWs* ws, const double* dY, int j0, int tb);
 // Enqueues the fused kernel for the workspace's tb traits x SNPs [i0, i1) into dout.
@@ -157,8 +159,9 @@ int mixed_fused_block(gwas_ctx* c, MixedWs* ws, int tb, int64_t i0, int64_t i1, 
 // The same for trait operands prepared elsewhere (mixed_prep_traits into B1, B2, cst).
 // j0: the first trait of the block among the context's traits (its S_BR may then be interpolated
 // in h^2), or -1 for traits with heritabilities of their own.
+// B1_4: the C1 operand as e2m1 digits (then B1 is not read).
 int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B2, const float* cst, int tb, int64_t i0,
-                    int64_t i1, int64_t ldo, void* dout, int j0);
+                    int64_t i1, int64_t ldo, void* dout, int j0, const uint8_t* B1_4 = nullptr);
 // Enqueues (no synchronisation) the solve of traits [j0, j0+tb) x SNPs [i0, i1) into dout.
 int mixed_solve_block(gwas_ctx* c, MixedWs* ws, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,
                       void* dout);
@@ -182,6 +185,9 @@ const float* mixed_sA(gwas_ctx* c);
 const float* mixed_acoef(gwas_ctx* c);
 const __nv_bfloat16* mixed_G(gwas_ctx* c);
 const __nv_bfloat16* mixed_A2(gwas_ctx* c);
+// 1 when the loaded genotypes also have their e2m1 copy (every value in {0, +-1, +-2, +-3, +-4, +-6})
+// for the kernel on e2m1 operands
+int mixed_fp4_ready(gwas_ctx* c);
 
 // ---------------------------------------------------------------- serving (serve.cu)
 void serve_shutdown(gwas_ctx* c);  // stops the scheduler thread and frees its memory

@@ -4,6 +4,8 @@
 //
 // Resident data (per loaded genotype set):
 //   G   [mpad][Kpad] bf16  exact genotypes x_i
+//   G4  [mpad][Kp4 / 2]     the same as packed e2m1 pairs (when every value is one of e2m1's
+//                             integers), the A operand of the CTA-pair kernel on e2m1 operands
 //   A2  [mpad/128][3][128][Kpad] bf16  slices of x'_c^2 (a2_row), x'_c = Z^T P_c x_i (P_c: projector onto
 //                             the complement of span(X_L), applied through the B operand)
 //   sA  [m] float            per-SNP scale of the slices (0 for SNPs in span(X_L))
@@ -27,6 +29,10 @@ struct MixedState {
   double* XtXinv = nullptr;                                       // (X_L^T X_L)^-1 on the device
   int64_t m = 0, mpad = 0;
   __nv_bfloat16 *G = nullptr, *A2 = nullptr;
+  int Kp4 = 0;             // padded n of the e2m1 operands (multiple of 256)
+  uint8_t* G4 = nullptr;   // e2m1 genotypes, or NULL
+  int* g4_bad = nullptr;   // device flag: a genotype outside e2m1's integers
+  bool g4_ok = false;      // G4 holds the loaded genotypes exactly
   float *sA = nullptr, *acoef = nullptr;
   float* Xc = nullptr;     // FP32 scratch of the rotation, kept while slabs are reloaded
   int64_t xc_rows = 0;
@@ -134,12 +140,27 @@ __global__ void transpose_kernel(const double* __restrict__ in, int n, double* _
     if (ox < n && oy0 + dy < n) out[(size_t)(oy0 + dy) * n + ox] = t[threadIdx.x][dy];
 }
 
+// e2m1 code of an integer genotype: magnitudes 0, 1, 2, 3, 4, 6 are codes 0, 2, 4, 5, 6, 7 (bit 3
+// the sign); any other value clears *ok and codes as 0.
+__device__ __forceinline__ uint32_t e2m1_of_int(int x, bool& ok) {
+  const int a = x < 0 ? -x : x;
+  uint32_t c = a == 0 ? 0u : a == 1 ? 2u : a == 2 ? 4u : a == 3 ? 5u : a == 4 ? 6u : a == 6 ? 7u : 16u;
+  if (c == 16u) {
+    ok = false;
+    c = 0u;
+  }
+  return c | (x < 0 ? 8u : 0u);
+}
+
 // int8 genotypes [m][n] -> bf16 [mpad][Kpad] (zero padded), and with `copy` the int8 bytes again
-// into copy [m][n] (X may then be host memory the device reads, read once).  One thread per 8
-// consecutive values of a row: an 8-byte load when the row's bytes allow it, one 16-byte store.
+// into copy [m][n] (X may then be host memory the device reads, read once).  With G4 also the
+// packed e2m1 pairs [mpad][Kp4 / 2] (element 2k in the low nibble of byte k), setting *bad when a
+// value has no e2m1 code.  One thread per 8 consecutive values of a row: an 8-byte load when the
+// row's bytes allow it, one 16-byte store (and one 4-byte store of e2m1 codes).
 __global__ void geno_bf16_kernel(const int8_t* __restrict__ X, int64_t m, int n, int64_t mpad, int Kpad,
-                                 __nv_bfloat16* __restrict__ G, int8_t* __restrict__ copy) {
-  const int per_row = Kpad / 8;
+                                 __nv_bfloat16* __restrict__ G, int8_t* __restrict__ copy, uint8_t* __restrict__ G4,
+                                 int Kp4, int* __restrict__ bad) {
+  const int per_row = (G4 ? Kp4 : Kpad) / 8;
   const int64_t total = mpad * (int64_t)per_row;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / per_row;
@@ -165,13 +186,23 @@ __global__ void geno_bf16_kernel(const int8_t* __restrict__ X, int64_t m, int n,
         v[j] = (float)x;
       }
     }
-    uint32_t u[4];
+    if (k0 < Kpad) {
+      uint32_t u[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-      u[j] = *reinterpret_cast<const uint32_t*>(&b);
+      for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        u[j] = *reinterpret_cast<const uint32_t*>(&b);
+      }
+      *reinterpret_cast<uint4*>(G + i * Kpad + k0) = make_uint4(u[0], u[1], u[2], u[3]);
     }
-    *reinterpret_cast<uint4*>(G + i * Kpad + k0) = make_uint4(u[0], u[1], u[2], u[3]);
+    if (G4) {
+      bool ok = true;
+      uint32_t w = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w |= e2m1_of_int((int)v[j], ok) << (4 * j);
+      if (!ok) atomicOr(bad, 1);
+      *reinterpret_cast<uint32_t*>(G4 + i * (Kp4 / 2) + k0 / 2) = w;
+    }
   }
 }
 
@@ -383,12 +414,16 @@ __global__ void __launch_bounds__(256) prep_mixed_kernel(const double* __restric
 }
 
 // Per trait: project the back-rotated columns [w | v_1..q] with P_c and write their
-// fixed-point slices in the C1 operand layout (w: 4 slices, v: 2 slices).
+// fixed-point slices in the C1 operand layout (w: 4 slices, v: 2 slices).  With B1_4 (q = 3, the
+// interpolated kernel's 24-trait tiles in the one-CTA order) the slices go there instead, as e2m1
+// digits: slice digit q = 64 d0 + 8 d1 + d2 (|q| <= 256, so every d is in [-4, 4]), digit plane d
+// of row r of a tile at [tile][r / 120][d][r % 120][Kp4 / 2], element 2k in the low nibble of byte k.
 template <int Q>
 __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__ W, const double* __restrict__ XL,
                                                       const double* __restrict__ XtXinv, int n, int Kpad,
                                                       __nv_bfloat16* __restrict__ B1, float* __restrict__ cst,
-                                                      const int* __restrict__ slot, int pair, int TT) {
+                                                      const int* __restrict__ slot, int pair, int TT,
+                                                      uint8_t* __restrict__ B1_4, int Kp4) {
   constexpr int PM1 = Q, Q1 = Q > 0 ? Q : 1;
   const int j = blockIdx.x;
   const int p = PM1 + 1;
@@ -446,6 +481,44 @@ __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__
     // digit by digit, with two FP64 operations for all of them instead of three per digit.
     const int fb = c == 0 ? 24 : 9, db = c == 0 ? 8 : 9;
     const double sc = ldexp(inv, fb);
+    if (B1_4) {
+      const int half_rows = c1_rows_of(3, true) / 2;
+      const size_t rb = (size_t)Kp4 / 2;
+      for (int l2 = threadIdx.x; l2 < Kp4 / 2; l2 += blockDim.x) {
+        long long X2[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int l = 2 * l2 + e;
+          double t = 0;
+          if (l < n) {
+            t = col[l];
+            for (int a = 0; a < PM1; ++a) t -= XL[(size_t)a * n + l] * coef[a];
+          }
+          X2[e] = __double2ll_rn(t * sc);
+        }
+        for (int s = 0; s < nsl; ++s) {
+          const int sh = fb - (s == 0 ? 0 : s * db);
+          uint32_t code[3] = {0u, 0u, 0u};
+          bool ok = true;  // |q| <= 256: every digit has a code
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const long long q = sh > 0 ? ((X2[e] + (1LL << (sh - 1))) >> sh) : X2[e];
+            X2[e] -= q * (1LL << sh);
+            const int qi = (int)q, d0 = (qi + 32) >> 6, r = qi - 64 * d0, d1 = (r + 4) >> 3, d2 = r - 8 * d1;
+            code[0] |= e2m1_of_int(d0, ok) << (4 * e);
+            code[1] |= e2m1_of_int(d1, ok) << (4 * e);
+            code[2] |= e2m1_of_int(d2, ok) << (4 * e);
+          }
+          const int row = (s < 2 ? s * (1 + Q) + c : 2 * Q + s) * TT + jj;  // one-CTA order
+          const int hf = row / half_rows, rr = row % half_rows;
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            B1_4[((((size_t)tile * 2 + hf) * 3 + d) * half_rows + rr) * rb + l2] = (uint8_t)code[d];
+        }
+      }
+      __syncthreads();
+      continue;
+    }
     for (int l = threadIdx.x; l < Kpad; l += blockDim.x) {
       double t = 0;
       if (l < n) {
@@ -477,6 +550,7 @@ const float* mixed_sA(gwas_ctx* c) { return c->mixed ? c->mixed->sA : nullptr; }
 const float* mixed_acoef(gwas_ctx* c) { return c->mixed ? c->mixed->acoef : nullptr; }
 const __nv_bfloat16* mixed_G(gwas_ctx* c) { return c->mixed ? c->mixed->G : nullptr; }
 const __nv_bfloat16* mixed_A2(gwas_ctx* c) { return c->mixed ? c->mixed->A2 : nullptr; }
+int mixed_fp4_ready(gwas_ctx* c) { return c->mixed && c->mixed->G4 && c->mixed->g4_ok ? 1 : 0; }
 
 void mixed_destroy(gwas_ctx* c) {
   if (!c->mixed) return;
@@ -493,6 +567,11 @@ void mixed_free(gwas_ctx* c) {
   ctx_free(c, s->sA);
   ctx_free(c, s->acoef);
   ctx_free(c, s->Xc);
+  ctx_free(c, s->G4);
+  ctx_free(c, s->g4_bad);
+  s->G4 = nullptr;
+  s->g4_bad = nullptr;
+  s->g4_ok = false;
   s->G = s->A2 = nullptr;
   s->sA = s->acoef = s->Xc = nullptr;
   s->m = s->mpad = s->xc_rows = 0;
@@ -516,6 +595,7 @@ static int mixed_setup(gwas_ctx* c) {
   MixedState* s = c->mixed;
   const int n = c->n, PM1 = c->pm1;
   s->Kpad = (int)rup(n, 64);
+  s->Kp4 = (int)rup(n, 256);
   s->bits = xgemm_bits(s->Kpad);
   s->ldx = (int)rup(n + PM1, 64);
   int rc;
@@ -564,20 +644,29 @@ int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m, bool reuse, int8_t* co
   const int n = c->n, PM1 = c->pm1;
   // a slab reuses the arrays when they hold enough rows (rows past m keep stale values,
   // which the fused kernel never writes out)
+  // The e2m1 copy of the genotypes, for the CTA-pair kernel on e2m1 operands (p = 4), on a
+  // one-time load; GWAS_FP4=0 leaves it out.
+  const char* fp4_env = getenv("GWAS_FP4");
+  const bool want_g4 = !reuse && PM1 == 3 && !(fp4_env && !strcmp(fp4_env, "0"));
   if (!reuse || !s->G || s->mpad < rup(m, 128)) {
     mixed_free(c);
     s->mpad = rup(m, 128);
     if ((rc = ctx_alloc(c, 2ull * s->mpad * s->Kpad, (void**)&s->G)) ||
         (rc = ctx_alloc(c, 2ull * 3 * s->mpad * s->Kpad, (void**)&s->A2)) ||
         (rc = ctx_alloc(c, sizeof(float) * s->mpad, (void**)&s->sA)) ||
-        (rc = ctx_alloc(c, sizeof(float) * s->mpad * std::max(1, PM1), (void**)&s->acoef))) {
+        (rc = ctx_alloc(c, sizeof(float) * s->mpad * std::max(1, PM1), (void**)&s->acoef)) ||
+        (want_g4 && (rc = ctx_alloc(c, (size_t)s->mpad * (s->Kp4 / 2), (void**)&s->G4))) ||
+        (want_g4 && (rc = ctx_alloc(c, sizeof(int), (void**)&s->g4_bad)))) {
       mixed_free(c);
       return rc;
     }
   }
+  s->g4_ok = false;
   ++s->load_gen;
+  uint8_t* G4 = want_g4 ? s->G4 : nullptr;
+  if (G4) cudaMemsetAsync(s->g4_bad, 0, sizeof(int), c->stream);
   { ProfScope ps(c, "genotypes_bf16");
-  geno_bf16_kernel<<<16 * 152, 256, 0, c->stream>>>(dXR, m, n, s->mpad, s->Kpad, s->G, copy);
+  geno_bf16_kernel<<<16 * 152, 256, 0, c->stream>>>(dXR, m, n, s->mpad, s->Kpad, s->G, copy, G4, s->Kp4, s->g4_bad);
   c->launches++; }
   // the genotypes read by the later kernels: the device copy the conversion made, if any
   if (copy) dXR = copy;
@@ -630,6 +719,11 @@ int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m, bool reuse, int8_t* co
     ctx_free(c, s->Xc);
     s->Xc = nullptr;
     s->xc_rows = 0;
+    if (G4) {
+      int bad = 1;
+      s->g4_ok = cudaMemcpy(&bad, s->g4_bad, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && bad == 0;
+      cudaGetLastError();
+    }
   }
   s->m = m;
   return GWAS_OK;
@@ -640,11 +734,13 @@ struct MixedWs {
   __nv_bfloat16 *Ysl = nullptr, *Wsl = nullptr, *B1 = nullptr, *B2 = nullptr;
   double *sY = nullptr, *Yt = nullptr, *Wt = nullptr, *sW = nullptr;
   float* cst = nullptr;
+  uint8_t* B1_4 = nullptr;  // the C1 operand as e2m1 digits (allocated by the first block that uses it)
+  bool fp4 = false;         // the last prepared block's C1 operand is in B1_4
 };
 
 void mixed_ws_free(gwas_ctx* c, MixedWs* w) {
   if (!w) return;
-  void* ps[] = {w->Ysl, w->Wsl, w->B1, w->B2, w->sY, w->Yt, w->Wt, w->sW, w->cst};
+  void* ps[] = {w->Ysl, w->Wsl, w->B1, w->B2, w->sY, w->Yt, w->Wt, w->sW, w->cst, w->B1_4};
   for (void* q : ps) ctx_free(c, q);
   delete w;
 }
@@ -679,7 +775,7 @@ int mixed_ws_alloc(gwas_ctx* c, int tb_max, MixedWs** out) {
 }
 
 int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h2, int tb, __nv_bfloat16* B1,
-                      __nv_bfloat16* B2, float* cst, const int* slot, int pair, int tt) {
+                      __nv_bfloat16* B2, float* cst, const int* slot, int pair, int tt, uint8_t* B1_4) {
   MixedState* s = c->mixed;
   if (!s || !s->Brot) return ctx_fail(c, GWAS_ERR_STATE, "mixed path not set up");
   if (tb > w->tb_max) return ctx_fail(c, GWAS_ERR_ARG, "trait block larger than its workspace");
@@ -727,7 +823,7 @@ int mixed_prep_traits(gwas_ctx* c, MixedWs* w, const double* dY, const double* h
     ProfScope ps(c, "pack_trait_columns");
     const int TTc = tt > 0 ? tt : mixed_tt(q);
     Q_DISPATCH_ALL(q, pack_c1_kernel<Q><<<tb, 256, 0, c->stream>>>(Wt, c->XL, s->XtXinv, n, Kpad, B1, cst, slot, pair,
-                                                                    TTc));
+                                                                    TTc, B1_4, s->Kp4));
     c->launches++;
   }
   return rc;
@@ -741,17 +837,29 @@ int mixed_prep_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb) 
   const int nt_tiles = (tb + TT - 1) / TT;
   const int nt_alloc = (nt_tiles + fused_trait_tile_multiple() - 1) / fused_trait_tile_multiple() *
                        fused_trait_tile_multiple();
-  cudaMemsetAsync(w->B1, 0, 2ull * c1_alloc_rows(q, tb) * Kpad, c->stream);
-  cudaMemsetAsync(w->B2, 0, 2ull * nt_alloc * c2_alloc(q) * Kpad, c->stream);
   // the trait operands in the layout of the kernel that will run: the interpolated kernel's
-  // (its tile width, one-CTA order), or the contracting kernel's (pair order for the CTA pair)
+  // (its tile width, one-CTA order), or the contracting kernel's (pair order for the CTA pair);
+  // the interpolated pair at p = 4 on genotypes with an e2m1 copy: e2m1 digits of the C1 slices
   const bool ip = mixed_block_interp(c, tb);
+  w->fp4 = ip && q == 3 && mixed_pair_layout(c) && mixed_fp4_ready(c);
+  if (w->fp4) {
+    const size_t bytes = (size_t)((w->tb_max + 23) / 24 + 3) / 4 * 4 * FP4_TILE_ROWS * (s->Kp4 / 2);
+    if (!w->B1_4) {
+      int rc = ctx_alloc(c, bytes, (void**)&w->B1_4);
+      if (rc) return rc;
+    }
+    const size_t used = (size_t)((tb + 23) / 24 + 3) / 4 * 4 * FP4_TILE_ROWS * (s->Kp4 / 2);
+    cudaMemsetAsync(w->B1_4, 0, used, c->stream);
+  } else {
+    cudaMemsetAsync(w->B1, 0, 2ull * c1_alloc_rows(q, tb) * Kpad, c->stream);
+  }
+  cudaMemsetAsync(w->B2, 0, 2ull * nt_alloc * c2_alloc(q) * Kpad, c->stream);
   return mixed_prep_traits(c, w, dY, c->h2 + j0, tb, w->B1, w->B2, w->cst, nullptr, ip ? 0 : mixed_pair_layout(c),
-                           ip ? tile_traits(q, true) : 0);
+                           ip ? tile_traits(q, true) : 0, w->fp4 ? w->B1_4 : nullptr);
 }
 
 int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B2, const float* cst, int tb, int64_t i0,
-                    int64_t i1, int64_t ldo, void* out, int j0) {
+                    int64_t i1, int64_t ldo, void* out, int j0, const uint8_t* B1_4) {
   MixedState* s = c->mixed;
   if (!s || !s->G) return ctx_fail(c, GWAS_ERR_STATE, "mixed genotypes not loaded");
   const int n = c->n, q = c->pm1, p = q + 1, Kpad = s->Kpad;
@@ -773,6 +881,7 @@ int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B
     if (const char* e = getenv("GWAS_FUSED_GROUP")) a.group = std::max(1, atoi(e));
     a.ntrait = tb;
     a.Kpad = Kpad;
+    a.Kp4 = s->Kp4;
     a.mpad = s->mpad;
     a.dof = (float)(n - p);
     (void)n;
@@ -799,14 +908,20 @@ int mixed_fused_ops(gwas_ctx* c, const __nv_bfloat16* B1, const __nv_bfloat16* B
       a.cheb_ld = s->cheb.ld;
     }
     // one trait: the contractions are matrix-vector products, bound by HBM (gemv.cu)
-    if (gemv) rc = launch_gemv1(c, q, a, s->G, s->A2, B1, B2);
+    if (B1_4) {
+      // the C1 operand was prepared as e2m1 digits for the interpolated pair (mixed_prep_block)
+      if (!interp || q != 3 || !mixed_pair_layout(c) || !mixed_fp4_ready(c))
+        return ctx_fail(c, GWAS_ERR_STATE, "e2m1 trait operands without the kernel that reads them");
+      if (a.n_stiles == 0 || a.n_ttiles == 0) return GWAS_OK;
+      rc = launch_fused_cheb_pair_fp4(c, a, s->G4, B1_4, (a.n_ttiles + 3) / 4 * 4);
+    } else if (gemv) rc = launch_gemv1(c, q, a, s->G, s->A2, B1, B2);
     else rc = launch_fused(c, q, a, s->G, s->A2, B1, B2);
   }
   return rc;
 }
 
 int mixed_fused_block(gwas_ctx* c, MixedWs* w, int tb, int64_t i0, int64_t i1, int64_t ldo, void* out, int j0) {
-  return mixed_fused_ops(c, w->B1, w->B2, w->cst, tb, i0, i1, ldo, out, j0);
+  return mixed_fused_ops(c, w->B1, w->B2, w->cst, tb, i0, i1, ldo, out, j0, w->fp4 ? w->B1_4 : nullptr);
 }
 
 int mixed_solve_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb, int64_t i0, int64_t i1, int64_t ldo,

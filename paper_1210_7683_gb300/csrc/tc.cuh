@@ -75,6 +75,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
 }
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global memory
+// into this CTA's shared memory, completing the bytes on the mbarrier.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
 // Prefetch of a 2-D tile into L2 (no shared-memory destination, no completion).
 __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
   asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(map), "r"(x), "r"(y) : "memory");
@@ -110,6 +118,16 @@ __device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t a, uint6
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
           d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Block-scaled MMA of a CTA pair on packed e2m1 operands (kind::mxf4, K = 64 per instruction,
+// one UE8M0 scale per 32 K-elements of every row of A and of B, read from TMEM at sa and sb).
+__device__ __forceinline__ void mma_mxf4_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t sa,
+                                              uint32_t sb, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(sa), "r"(sb), "r"(accumulate)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit_pair(uint64_t* bar, uint16_t mask) {
@@ -158,6 +176,12 @@ __device__ __forceinline__ uint64_t sdesc_add(uint64_t d, uint32_t bytes) { retu
 // Instruction descriptor: kind::f16 with bf16 A and B, FP32 accumulator, K-major operands.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor of the block-scaled kinds: e2m1 A and B (format 1 of kind::mxf4),
+// K-major operands, UE8M0 scale factors (bit 23), scale-factor byte 0 of A and B, dense K = 64.
+__host__ __device__ constexpr uint32_t idesc_mxf4(int M, int N) {
+  return (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | (1u << 23) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
@@ -225,6 +249,12 @@ __device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Warp-wide store of the same 32-bit value into 8 consecutive TMEM columns of the warp's 32 lanes;
+// complete after tmem_st_wait().
+__device__ __forceinline__ void tmem_st8_fill(uint32_t taddr, uint32_t v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 // Orders later uses of the registers after the preceding tmem_ld_wait().
 __device__ __forceinline__ void reg_fence(uint32_t (&r)[8]) {
   asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]));
@@ -236,6 +266,9 @@ __device__ __forceinline__ void reg_fence(uint32_t (&r)[8]) {
 // with a box of box_rows x box_cols elements (64: 128-byte swizzle, 32: 64-byte swizzle).
 bool make_bf16_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows,
                    uint32_t box_cols = 64);
+// Host: 2-D tensor map of a row-major byte matrix [rows][cols] (packed e2m1 pairs) with boxes of
+// box_rows rows x 128 bytes and the 128-byte swizzle; cols (bytes) a multiple of 16.
+bool make_u8_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows);
 // Host: 2-D tensor map of `rows` bf16 rows of `cols` elements, row r at base + r * row_stride
 // elements, box of box_rows x box_cols, no swizzle.
 bool make_bf16_map_strided(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t row_stride,
