@@ -50,45 +50,54 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # multi-pass metrics).  The trait operands of all trait tiles are streamed once per traversal group
 # of SNP tiles (they do not fit L2 at t = 1e4), the SNP operands once, the results written once.
 # The check is valid only while the kernel's sources hash to the value it was taken on.
-FUSED_TRAFFIC_CHECK = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "tc.cuh", "fused_cheb.cu"],
-                       "sha256": "49793b74e8877d39b09a8de28bc1d20adacf2cdb6f8b61ba305a600a9633c233",
-                       # n = 1000, m = 16384, t = 1e4 (profiles/fused_kernel_traffic_n1000_m16384_t1e4.md)
+FUSED_TRAFFIC_CHECK = {"sources": ["fused_impl.cuh", "fused.cu", "fused.cuh", "tc.cuh", "fused_cheb.cu", "fused_fp4.cu"],
+                       "sha256": "fa03f5a3a24f7e67660e27abfccc9599b798f4d64d86c6b13e2e1c27681c73dc",
+                       # n = 1000, m = 16384, t = 1e4 (profiles/fused_kernel_traffic_n1000_m16384_t1e4.md):
+                       # the CTA pair on e2m1 operands, traversal groups of 8; one CTA on bf16 operands
                        "case": (1000, 3, 16384, 10_000),
-                       "measured": {"pair_g8": (1688.7e6, 1275.8e6), "one_g16": (1689.0e6, 1279.8e6)},
-                       "model": {"pair_g8": (1674.9e6, 1310.7e6), "one_g16": (1674.9e6, 1310.7e6)}}
+                       "measured": {"pair_fp4_g8": (1254.0e6, 1267.3e6), "one_g16": (1688.7e6, 1279.7e6)},
+                       "model": {"pair_fp4_g8": (1239.8e6, 1310.7e6), "one_g16": (1674.9e6, 1310.7e6)}}
 
 
 # sm__pipe_tensor_cycles_active (% of peak, active cycles) of the interpolated fused kernel from the
 # full-set ncu captures of the small case n = 1000, m = 131072, t = 1024 (one launch each;
-# profiles/fused_kernel_interp_n1000_m131072_t1024.md), valid for the same sources as the check above.
-TENSOR_PIPE_NCU = {"pair": 69.7, "one_cta": 62.3}
+# profiles/fused_kernel_interp_n1000_m131072_t1024.md), valid for the same sources as the check above:
+# the CTA pair on e2m1 operands and one CTA on bf16 operands (the pair on bf16 operands, which runs
+# only without the genotypes' e2m1 copy, was not captured on these sources).
+TENSOR_PIPE_NCU = {"pair_fp4": 81.2, "one_cta": 61.6, "pair": None}
 
 
-def tensor_pipe_counter(shape):
+def tensor_pipe_counter(shape, fp4=False):
     """The ncu tensor-pipe counter of the launch shape, or None when the sources changed since."""
     if fused_traffic((1000, 3, 128, 32)) is None:
         return None
-    return TENSOR_PIPE_NCU["pair" if (shape or {}).get("pair") else "one_cta"]
+    return TENSOR_PIPE_NCU[("pair_fp4" if fp4 else "pair") if (shape or {}).get("pair") else "one_cta"]
 
 
-def fused_traffic_model(n, m, t, q=3, group=16, cs=1, interp=True):
+def fused_traffic_model(n, m, t, q=3, group=16, cs=1, interp=True, fp4=False):
     """DRAM bytes of one fused_kernel launch (p = 4 geometry): reads of the SNP operands (the
     genotypes, and the three x'^2 planes when S_BR is contracted), of the trait operands once per
     traversal group (group super-tiles of cs SNP tiles), of the Chebyshev coefficients, and the
-    8-byte result of every pair."""
+    8-byte result of every pair.  fp4: the genotypes and the C1 rows as e2m1 (half a byte per
+    value, K padded to 256), three digit rows per C1 row."""
     kpad = (n + 63) // 64 * 64
+    kp4 = (n + 255) // 256 * 256
     tt = 24 if interp and q == 3 else 32      # the interpolated kernel's tiles of 24 traits at p = 4
     ttiles = (t + tt - 1) // tt
     stiles = (m + 127) // 128
     mpad = stiles * 128
     c1_rows, c2_rows = (4 + 2 * q) * tt, (0 if interp else (6 if cs == 2 else 4) * tt)
-    trait_bytes = ttiles * (c1_rows + c2_rows) * kpad * 2
-    snp_bytes = mpad * kpad * 2 * (1 if interp else 4) + (25 * 4 * mpad if interp else 0)
+    if fp4:
+        trait_bytes = ttiles * 3 * c1_rows * kp4 // 2
+        snp_bytes = mpad * kp4 // 2 + 25 * 4 * mpad
+    else:
+        trait_bytes = ttiles * (c1_rows + c2_rows) * kpad * 2
+        snp_bytes = mpad * kpad * 2 * (1 if interp else 4) + (25 * 4 * mpad if interp else 0)
     groups = -(-stiles // (group * cs))
     return {"read": snp_bytes + groups * trait_bytes, "write": 8.0 * m * t}
 
 
-def fused_traffic(workload, shape=None, interp=True):
+def fused_traffic(workload, shape=None, interp=True, fp4=False):
     """Model traffic of one launch of the timed workload, or None when the model's check was not
     taken on the current kernel sources."""
     import hashlib
@@ -103,7 +112,7 @@ def fused_traffic(workload, shape=None, interp=True):
         return None
     n, q, m, t = workload
     sh = shape or {"group": 16, "pair": 0}
-    mod = fused_traffic_model(n, m, t, q, sh.get("group", 16), 2 if sh.get("pair") else 1, interp)
+    mod = fused_traffic_model(n, m, t, q, sh.get("group", 16), 2 if sh.get("pair") else 1, interp, fp4)
     return mod["read"] + mod["write"]
 
 
@@ -335,6 +344,8 @@ def step(g, opts, n, m, t, inp, out, phases=None):
                  "pack_trait_columns", "cheb_nodes", "cheb_coefficients", "fused", "rotate_fp64", "prep_fp64",
                  "fused_fp64"]
         times = {k: g.gwas_kernel_time(ctx, k) for k in names}
+        # launches of the fused kernel on e2m1 operands (a count only)
+        times["fused_fp4"] = (0.0, g.gwas_fp4_info(ctx)["launches"])
         return rc, {k: v for k, v in times.items() if v[1]}, g.gwas_kernel_launches(ctx)
     finally:
         g.gwas_destroy(ctx)
@@ -690,26 +701,37 @@ def main():
     # ---------------------------------------------------------------- roofline of the fused kernel
     pk, pk_src = peaks()
     fused_ms = ktimes["fused"][0] / ktimes["fused"][1]
+    # the timed steps' fused kernel ran on e2m1 operands (every step's launch)
+    fp4 = ktimes.get("fused_fp4", [0.0, 0])[1] == args.steps
     useful = algorithmic_flops(n, PM1 + 1, pairs)            # 2 (p+1) n flops per pair
     kpad = (n + 63) // 64 * 64
+    kp4 = (n + 255) // 256 * 256
     # MMA columns per tile per K: the C1 block (num and z: 4 + 2(p-1) = 10 slice groups of the
     # tile's traits: 24 with S_BR interpolated, 32 otherwise), plus 192 for the S_BR contraction
-    # when it is not interpolated
+    # when it is not interpolated; on e2m1 operands every column is three digit MMAs over Kp4
     tt = 24 if sbr["terms"] > 0 else 32
     tiles = ((m + 127) // 128) * ((t + tt - 1) // tt)
     mma_cols = 10 * tt if sbr["terms"] > 0 else 512
-    issued = 2.0 * 128 * mma_cols * kpad * tiles
-    peak = pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+    issued = 2.0 * 128 * mma_cols * (3 * kp4 if fp4 else kpad) * tiles
+    bf16_peak = pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+    # a contraction's peak is its own dtype's: e2m1 is the measured bf16 peak x the nominal ratio
+    # of the dense FP4 and bf16 tensor rates (13.5 / 2.25 PFLOP/s)
+    peak = bf16_peak * (13.5 / 2.25 if fp4 else 1.0)
     achieved = useful / (fused_ms / 1e3) / 1e12
-    traffic = fused_traffic((n, PM1, m, t), tune["shape"], sbr["terms"] > 0)
+    traffic = fused_traffic((n, PM1, m, t), tune["shape"], sbr["terms"] > 0, fp4)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "fused_kernel",
-                "peak_source": f"{pk_src} bf16 sustained (kernel runs ~{fused_ms:.0f} ms inside a long step)",
+                "traffic": traffic, "kernel": "fused_kernel", "operands": "e2m1 (kind::mxf4)" if fp4 else "bf16",
+                "peak_source": (f"{pk_src} bf16 sustained x 6 (nominal dense FP4 / bf16)" if fp4 else
+                                f"{pk_src} bf16 sustained") + f" (kernel runs ~{fused_ms:.0f} ms inside a long step)",
                 "issued_tflops": issued / (fused_ms / 1e3) / 1e12,
                 "issued_frac": issued / (fused_ms / 1e3) / 1e12 / peak,
-                "issued_note": "issued = MMA columns x 128 rows x 2 Kpad per tile (an analytic count of the "
-                               "tcgen05.mma work, not the ncu tensor-pipe counter)",
-                "tensor_pipe_ncu_pct": tensor_pipe_counter(tune["shape"]) if sbr["terms"] > 0 else None,
+                "issued_note": ("issued = MMA columns x 3 e2m1 digits x 128 rows x 2 Kp4 per tile" if fp4 else
+                                "issued = MMA columns x 128 rows x 2 Kpad per tile") +
+                               " (an analytic count of the tcgen05.mma work, not the ncu tensor-pipe counter)" +
+                               ("; a kind::mxf4 MMA of K = 64 measured the cycles of a bf16 one of K = 16 (4x "
+                                "the bf16 rate, not 6x): against 4x the bf16 peak the issued fraction is "
+                                f"{issued / (fused_ms / 1e3) / 1e12 / (4 * bf16_peak):.2f}" if fp4 else ""),
+                "tensor_pipe_ncu_pct": tensor_pipe_counter(tune["shape"], fp4) if sbr["terms"] > 0 else None,
                 "tensor_pipe_note": "sm__pipe_tensor_cycles_active of this launch shape in a full-set ncu capture "
                                     "of the small case n=1000 m=131072 t=1024 (profiles/); null if the kernel "
                                     "sources changed since",
@@ -720,7 +742,7 @@ def main():
     solve_ms = sum(v[0] for k, v in ktimes.items() if k in (
         "xgemm_rotate_traits", "prep_traits", "xgemm_back_rotate", "pack_trait_columns", "cheb_nodes",
         "cheb_coefficients", "fused")) / args.steps
-    breakdown = {k: round(v[0] / args.steps, 3) for k, v in ktimes.items()}
+    breakdown = {k: round(v[0] / args.steps, 3) for k, v in ktimes.items() if k != "fused_fp4"}
     # the genotype rotation X'_R = (P_c Z)^T X_R (Algorithm 5's preloop gemm) as an exact sliced
     # GEMM: one bf16 plane of genotypes against 4 slices of the rotation, 4 slice products
     rot = None
@@ -734,7 +756,7 @@ def main():
         rot = {"kernel": "xgemm_kernel (genotype rotation)", "ms_per_step": rot_ms,
                "launches_per_step": ktimes["xgemm_rotate_snps"][1] // args.steps,
                "issued_tflops": issued_r / (rot_ms / 1e3) / 1e12,
-               "issued_frac": issued_r / (rot_ms / 1e3) / 1e12 / peak,
+               "issued_frac": issued_r / (rot_ms / 1e3) / 1e12 / bf16_peak,
                "useful_tflops": useful_r / (rot_ms / 1e3) / 1e12,
                "dram_gbs": bytes_r / (rot_ms / 1e3) / 1e9,
                "dram_frac": bytes_r / (rot_ms / 1e3) / 1e9 / pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]),
@@ -743,7 +765,12 @@ def main():
 
     result = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-              "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+              "vs_baseline": None, "dtype": "e2m1" if fp4 else "bf16", "data": "synthetic",
+              "dtype_note": ("the fused kernel's products: exact integer digits (genotypes, and three e2m1 "
+                             "digits of each 9-bit fixed-point slice) on the block-scaled FP4 tensor cores, "
+                             "FP32 accumulation of exact integer sums; " if fp4 else
+                             "the fused kernel's products: exact bf16 fixed-point slices, FP32 accumulation "
+                             "of exact integer sums; ") + "FP32 epilogue; FP64 eigendecomposition and per-trait algebra",
               "config": {"workload": f"GLS grid n={n} p=4 m={m} t={t}, mixed precision, beta+SE fp32 out",
                          "n": n, "p": 4, "m": m, "t": t, "parallelism": f"snp-shard x{world}",
                          "problem": f"one grid of {m_total} SNPs x {t} traits; this rank's shard [{s_i0},{s_i1})"

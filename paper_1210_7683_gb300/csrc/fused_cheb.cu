@@ -21,10 +21,12 @@ int launch_fused_cheb(gwas_ctx* c, int q, const FusedArgs& a, const __nv_bfloat1
 int launch_fused_cheb_pair(gwas_ctx* c, const FusedArgs& a, const __nv_bfloat16* G, const __nv_bfloat16* B1,
                            int b_tiles) {
   if (a.cheb_R < 2 || a.cheb_R > CHEB_MAX_R) return ctx_fail(c, GWAS_ERR_ARG, "Chebyshev terms outside [2, 24]");
-  // each CTA of the pair: its own 128 SNP rows and its half (120 rows) of the tile's 240 C1 rows
-  CUtensorMap mg, m1;
+  // each CTA of the pair: its own 128 SNP rows and its half (120 rows) of the tile's 240 C1 rows;
+  // the second map: a tile's Chebyshev coefficient rows 0..CHEB_MAX_R, for the epilogue's staging
+  CUtensorMap mg, m1, mc;
   if (!make_bf16_map(&mg, G, a.mpad, a.Kpad, BM, BK) ||
-      !make_bf16_map(&m1, B1, (uint64_t)b_tiles * c1_rows_of(3, true), a.Kpad, c1_rows_of(3, true) / 2, BK))
+      !make_bf16_map(&m1, B1, (uint64_t)b_tiles * c1_rows_of(3, true), a.Kpad, c1_rows_of(3, true) / 2, BK) ||
+      !make_f32_map(&mc, a.cheb_coef, CHEB_MAX_R + 1, a.cheb_ld, CHEB_MAX_R + 1, BM))
     return ctx_fail(c, GWAS_ERR_CUDA, "tensor map encoding failed");
-  return launch_shape<epw_interp(3), false, true, 3, true>(c, a, mg, mg, m1, m1);
+  return launch_shape<epw_interp(3), false, true, 3, true>(c, a, mg, mc, m1, m1);
 }

@@ -148,8 +148,12 @@ __device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us,
 // digit q (|q| <= 292) is written as 64 d0 + 8 d1 + d2 with d in [-4, 4], and the three digits are
 // contracted into the slice's own accumulator by MMAs whose B scale factors are 2^6, 2^3 and 2^0:
 // every partial sum is the same integer as the bf16 kernel's, so the outputs do not change.
+// Threads of a CTA: the TMA producer and MMA warps, EPW epilogue warps and, in the interpolated
+// CTA pair, a warp that stages the epilogue's per-tile data.
+__host__ __device__ constexpr int fused_threads(int epw, bool pair, bool interp) { return 64 + 32 * epw + (pair && interp ? 32 : 0); }
+
 template <int EPW, bool SERVE, bool PAIR, int Q, bool INTERP = false, bool FP4 = false>
-__global__ void __launch_bounds__(64 + 32 * EPW, 1)
+__global__ void __launch_bounds__(fused_threads(EPW, PAIR, INTERP), 1)
     fused_kernel(const __grid_constant__ CUtensorMap mapG, const __grid_constant__ CUtensorMap mapA2,
                  const __grid_constant__ CUtensorMap mapB1, const __grid_constant__ CUtensorMap mapB2, FusedArgs a) {
   constexpr int CS = PAIR ? 2 : 1;                  // SNP tiles per cluster (the CTA pair: 2)
@@ -200,7 +204,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   uint64_t* acc_full = empty + NSL;          // [2]
   uint64_t* acc_empty = acc_full + 2;        // [2]
   uint64_t* stage_full = acc_empty + 2;      // [2] PSTAGE
-  uint32_t* tslot = (uint32_t*)(stage_full + 2);
+  uint64_t* stage_empty = stage_full + 2;    // [2] PSTAGE
+  uint32_t* tslot = (uint32_t*)(stage_empty + 2);
   volatile int* abort = (volatile int*)(tslot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   uint32_t crank = 0, cid = blockIdx.x, ncl = gridDim.x;
@@ -223,6 +228,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       tc::mbar_init(&acc_full[b], 1);
       tc::mbar_init(&acc_empty[b], PAIR ? 2 * EPW : EPW);
       tc::mbar_init(&stage_full[b], 1);
+      tc::mbar_init(&stage_empty[b], EPW);
     }
     *abort = 0;
     tc::fence_mbar_init();
@@ -254,6 +260,22 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     tc::fence_after();
   }
 
+  // PSTAGE: the copies of tile uu's constants (TT traits; all allocated), its SNPs' Chebyshev
+  // coefficient rows 0..CHEB_MAX_R (one TMA box from mapA2, which the interpolated kernels do not
+  // otherwise use; the pair's tile past the last SNP tile reads the fill value and stores nothing)
+  // and its traits' T_k(x_j) (only those of the block) into buffer b
+  auto issue_stage = [&](int uu, int b) {
+    int us, ut;
+    super_coords<CS>(uu, a, us, ut);
+    const int64_t s0 = a.row0 + (int64_t)(us * CS + sr) * BM;
+    const int jb = ut * TT, nvt = min(TT, a.ntrait - jb);
+    float* cc = cheb_c + b * CBUF;
+    tc::mbar_expect_tx(&stage_full[b], TT * CSTR * 4 + (CHEB_MAX_R + 1) * 128 * 4 + nvt * CHEB_MAX_R * 4);
+    tc::bulk_copy_g2s(cst_smem + b * TT * CSTR, a.cst + (size_t)jb * CSTR, TT * CSTR * 4, &stage_full[b]);
+    tc::tma_load_2d(cc, &mapA2, &stage_full[b], (int)s0, 0);
+    tc::bulk_copy_g2s(cc + (CHEB_MAX_R + 1) * 128, a.cheb_T + (size_t)jb * CHEB_MAX_R, nvt * CHEB_MAX_R * 4,
+                      &stage_full[b]);
+  };
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
@@ -484,6 +506,16 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         if (ok) tc::mma_commit(&acc_full[ab]);
       }
     }
+  } else if (PSTAGE && warp == 2 + EPW) {
+    // ------------------------------------------------------------ epilogue staging
+    // tile k's data into buffer k & 1 once every epilogue warp is done with tile k - 2
+    if (lane == 0) {
+      uint32_t k = 0;
+      for (int u = cid; u < nsuper; u += ncl, ++k) {
+        if (k >= 2 && !tc::mbar_wait(&stage_empty[k & 1], ((k >> 1) - 1) & 1, a.status, abort)) break;
+        issue_stage(u, (int)(k & 1));
+      }
+    }
   } else {
     // ------------------------------------------------------------ epilogue (EPW warps)
     const int ew = warp - 2;
@@ -492,26 +524,6 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     const int jbeg = (ew / 4) * JPW;
     const uint32_t lane_base = tbase + ((uint32_t)(q * 32) << 16);
     const float inv_dof = 1.f / a.dof;
-    // PSTAGE: the bulk copies of tile uu's constants (TT traits; all allocated), its SNPs' Chebyshev
-    // coefficients (none for the pair's tile past the last SNP tile, which stores nothing) and its
-    // traits' T_k(x_j) (only those of the block) into buffer b
-    auto issue_stage = [&](int uu, int b) {
-      int us, ut;
-      super_coords<CS>(uu, a, us, ut);
-      const int64_t s0 = a.row0 + (int64_t)(us * CS + sr) * BM;
-      const int jb = ut * TT, nvt = min(TT, a.ntrait - jb), R = a.cheb_R;
-      const bool snps = s0 < a.cheb_ld;
-      float* cc = cheb_c + b * CBUF;
-      tc::mbar_expect_tx(&stage_full[b], TT * CSTR * 4 + (snps ? (R + 1) * 512 : 0) + nvt * CHEB_MAX_R * 4);
-      tc::bulk_copy_g2s(cst_smem + b * TT * CSTR, a.cst + (size_t)jb * CSTR, TT * CSTR * 4, &stage_full[b]);
-      if (snps)
-        for (int k = 0; k <= R; ++k)
-          tc::bulk_copy_g2s(cc + 128 * k, a.cheb_coef + (int64_t)(k < R ? k : CHEB_MAX_R) * a.cheb_ld + s0, 512,
-                            &stage_full[b]);
-      tc::bulk_copy_g2s(cc + (CHEB_MAX_R + 1) * 128, a.cheb_T + (size_t)jb * CHEB_MAX_R, nvt * CHEB_MAX_R * 4,
-                        &stage_full[b]);
-    };
-    if (PSTAGE && ew == 0 && lane == 0 && cid < nsuper) issue_stage(cid, 0);
     uint32_t tcount = 0;
     unsigned long long nsing = 0;
     for (int u = cid; u < nsuper; u += ncl, ++tcount) {
@@ -571,8 +583,6 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         }
       }
       tc::named_sync(1, EPW * 32);
-      // every warp is done with the previous tile: its buffer takes the next tile's copies
-      if (PSTAGE && ew == 0 && lane == 0 && u + (int)ncl < nsuper) issue_stage(u + ncl, (tcount & 1) ^ 1);
       const uint32_t ab = DB ? (tcount & 1) : 0;
       const bool ok = staged && tc::mbar_wait(&acc_full[ab], (DB ? tcount >> 1 : tcount) & 1, a.status, abort);
       const uint32_t lb = lane_base + ab * 256;  // this tile's accumulator buffer
@@ -686,7 +696,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
           for (int r = 0; r < JPW; ++r) s_r[r] = fmaf(ck, tcur[k * TT + jbeg + r], s_r[r]);
         }
-        const float c0 = ccur[i], c1 = ccur[128 + i], c0lo = ccur[R * 128 + i];
+        const float c0 = ccur[i], c1 = ccur[128 + i], c0lo = ccur[(PSTAGE ? CHEB_MAX_R : R) * 128 + i];
 #pragma unroll
         for (int r = 0; r < JPW; ++r) {
           const float t1 = tcur[TT + jbeg + r];
@@ -761,6 +771,11 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
           }
         }
       }
+      if (PSTAGE) {
+        // this warp's last read of the tile's staged data is done
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&stage_empty[tcount & 1]);
+      }
       if (SERVE && sing_ctr) {
         unsigned long long v = tsing;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -798,7 +813,7 @@ int launch_shape(gwas_ctx* c, const FusedArgs& a, const CUtensorMap& mg, const C
   at[0].val.clusterDim.x = NC;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(64 + 32 * EPW);
+  cfg.blockDim = dim3(fused_threads(EPW, PAIR, INTERP));
   cfg.dynamicSmemBytes = SMEM;
   cfg.stream = c->stream;
   cfg.attrs = at;

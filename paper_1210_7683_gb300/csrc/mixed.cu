@@ -140,16 +140,24 @@ __global__ void transpose_kernel(const double* __restrict__ in, int n, double* _
     if (ox < n && oy0 + dy < n) out[(size_t)(oy0 + dy) * n + ox] = t[threadIdx.x][dy];
 }
 
-// e2m1 code of an integer genotype: magnitudes 0, 1, 2, 3, 4, 6 are codes 0, 2, 4, 5, 6, 7 (bit 3
-// the sign); any other value clears *ok and codes as 0.
+// e2m1 codes (bit 3 the sign; magnitudes 0, 0.5, 1, 1.5, 2, 3, 4, 6 are codes 0..7) of the integers
+// -8..7, nibble x + 8 of the table; the bit x + 8 of the mask marks the integers without a code.
+constexpr uint64_t kE2m1Codes = 0x07065420ACDE0F00ull;  // x = -8 .. 7 from the low nibble up
+constexpr uint32_t kE2m1Bad = 0xA00Bu;                  // -8, -7, -5, 5, 7
+// e2m1 code of an integer genotype; a value without one (not in {0, +-1, +-2, +-3, +-4, +-6})
+// clears ok and codes as 0.
 __device__ __forceinline__ uint32_t e2m1_of_int(int x, bool& ok) {
-  const int a = x < 0 ? -x : x;
-  uint32_t c = a == 0 ? 0u : a == 1 ? 2u : a == 2 ? 4u : a == 3 ? 5u : a == 4 ? 6u : a == 6 ? 7u : 16u;
-  if (c == 16u) {
+  const uint32_t u = (uint32_t)(x + 8);
+  if (u > 15u || ((kE2m1Bad >> u) & 1u)) {
     ok = false;
-    c = 0u;
+    return 0u;
   }
-  return c | (x < 0 ? 8u : 0u);
+  return (uint32_t)(kE2m1Codes >> (4 * u)) & 15u;
+}
+// e2m1 code of a slice digit d in [-4, 4]: magnitude a has code a + min(a, 2)
+__device__ __forceinline__ uint32_t e2m1_of_digit(int d) {
+  const uint32_t a = (uint32_t)(d < 0 ? -d : d);
+  return (a + min(a, 2u)) | (d < 0 ? 8u : 0u);
 }
 
 // int8 genotypes [m][n] -> bf16 [mpad][Kpad] (zero padded), and with `copy` the int8 bytes again
@@ -499,15 +507,15 @@ __global__ void __launch_bounds__(256) pack_c1_kernel(const double* __restrict__
         for (int s = 0; s < nsl; ++s) {
           const int sh = fb - (s == 0 ? 0 : s * db);
           uint32_t code[3] = {0u, 0u, 0u};
-          bool ok = true;  // |q| <= 256: every digit has a code
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
             const long long q = sh > 0 ? ((X2[e] + (1LL << (sh - 1))) >> sh) : X2[e];
             X2[e] -= q * (1LL << sh);
+            // |q| <= 256: every digit is in [-4, 4]
             const int qi = (int)q, d0 = (qi + 32) >> 6, r = qi - 64 * d0, d1 = (r + 4) >> 3, d2 = r - 8 * d1;
-            code[0] |= e2m1_of_int(d0, ok) << (4 * e);
-            code[1] |= e2m1_of_int(d1, ok) << (4 * e);
-            code[2] |= e2m1_of_int(d2, ok) << (4 * e);
+            code[0] |= e2m1_of_digit(d0) << (4 * e);
+            code[1] |= e2m1_of_digit(d1) << (4 * e);
+            code[2] |= e2m1_of_digit(d2) << (4 * e);
           }
           const int row = (s < 2 ? s * (1 + Q) + c : 2 * Q + s) * TT + jj;  // one-CTA order
           const int hf = row / half_rows, rr = row % half_rows;

@@ -269,6 +269,10 @@ bool make_bf16_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t c
 // Host: 2-D tensor map of a row-major byte matrix [rows][cols] (packed e2m1 pairs) with boxes of
 // box_rows rows x 128 bytes and the 128-byte swizzle; cols (bytes) a multiple of 16.
 bool make_u8_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows);
+// Host: 2-D tensor map of a row-major FP32 matrix [rows][cols] (cols a multiple of 4), boxes of
+// box_rows x box_cols elements, no swizzle.
+bool make_f32_map(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint32_t box_rows,
+                  uint32_t box_cols);
 // Host: 2-D tensor map of `rows` bf16 rows of `cols` elements, row r at base + r * row_stride
 // elements, box of box_rows x box_cols, no swizzle.
 bool make_bf16_map_strided(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t row_stride,

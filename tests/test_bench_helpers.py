@@ -75,3 +75,16 @@ def test_serving_loads_default_headline_first():
         sys.argv = argv
     loads = [float(x) for x in args.serving_load.split(",")]
     assert loads[0] == 0.8 and sorted(loads) == [0.5, 0.8, 0.95]
+
+
+def test_traffic_model_fp4_terms():
+    # e2m1 operands: half a byte per genotype and per digit, K padded to 256, three digit rows per
+    # C1 row; the coefficients and the results as on bf16 operands
+    mod = bench.fused_traffic_model(1000, 128 * 16, 64, group=16, cs=2, fp4=True)
+    assert mod["write"] == 8.0 * 128 * 16 * 64
+    assert mod["read"] == 2048 * 1024 // 2 + 25 * 4 * 2048 + 3 * 3 * 240 * 1024 // 2
+    bf = bench.fused_traffic_model(1000, 128 * 16, 64, group=16, cs=2)
+    assert mod["read"] < bf["read"]
+    # n = 1100: Kpad = 1152, Kp4 = 1280
+    m4 = bench.fused_traffic_model(1100, 128, 24, group=1, fp4=True)
+    assert m4["read"] == 128 * 640 + 25 * 4 * 128 + 3 * 240 * 640

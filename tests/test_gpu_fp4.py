@@ -69,11 +69,12 @@ def test_fp4_kernel_full_b(gw, monkeypatch):
     assert full_b_err(got.transpose(1, 0, 2), b, se) <= TOL
 
 
-def test_genotypes_without_e2m1_codes_keep_the_bf16_kernel(gw, monkeypatch):
-    # a dosage of 5 has no e2m1 code (the integers of e2m1 are 0, 1, 2, 3, 4 and 6)
+@pytest.mark.parametrize("value", [5, 7, -5, -8, 9, 127, -128])
+def test_genotypes_without_e2m1_codes_keep_the_bf16_kernel(gw, monkeypatch, value):
+    # one genotype without an e2m1 code (the integers of e2m1 are 0, +-1, +-2, +-3, +-4 and +-6)
     P = make_problem(256, 600, 40, pm1=3, seed=941)
     XR = P.XR.copy()
-    XR[3, 17] = 5
+    XR[3, 17] = value
     got, info = solve(gw, P, gw.GWAS_OUT_LAST_SE, monkeypatch, True, XR=XR)
     assert not info["ready"] and info["launches"] == 0
     b, se = EigOracle(P.phi, P.XL).solve(XR, P.Y, P.h2)
@@ -81,7 +82,7 @@ def test_genotypes_without_e2m1_codes_keep_the_bf16_kernel(gw, monkeypatch):
     assert last_coef_err(beta, s, b, se) <= TOL
     # the other e2m1 integers (3, 4, 6 and negatives) have codes: the e2m1 kernel runs, unchanged
     XR2 = P.XR.copy()
-    XR2[0, :6] = [3, 4, 6, -1, -2, -6]
+    XR2[0, :8] = [3, 4, 6, -1, -2, -6, -3, -4]
     got2, info2 = solve(gw, P, gw.GWAS_OUT_LAST_SE, monkeypatch, True, XR=XR2)
     ref2, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE, monkeypatch, False, XR=XR2)
     assert info2["ready"] and info2["launches"] >= 1
