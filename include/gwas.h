@@ -408,6 +408,16 @@ GWAS_API int gwas_solve_fp64_noalloc(int n, int pm1, const double* lam, const do
  */
 GWAS_API int gwas_check_bounded_wait(int device, double limit_s, double* waited_s);
 
+/*
+ * Self-test of the fused kernel's epilogue arithmetic: evaluates on the device, for each of the
+ * count values x[i] (host array, 1 <= count <= 2^20), the reciprocal and the square root that
+ * the mixed path's per-pair solve uses (the hardware approximation of 1/x refined by one
+ * Newton-Raphson step, and the hardware approximation of sqrt(x)) beside CUDA's correctly
+ * rounded __frcp_rn and __fsqrt_rn.  out (host, 4 * count floats) receives, per value, those
+ * four results in that order.  Returns GWAS_OK, GWAS_ERR_ARG or GWAS_ERR_CUDA.
+ */
+GWAS_API int gwas_check_epilogue_math(int device, const float* x, int count, float* out);
+
 /* One-line description of the last failure on ctx (or of the last failed
  * gwas_setup when ctx is NULL).  Owned by the library. */
 GWAS_API const char* gwas_last_error(const gwas_ctx* ctx);

@@ -107,6 +107,8 @@ def _load():
                                    C.POINTER(C.c_double)]
     lib.gwas_cheb_plan.restype = ci
     lib.gwas_check_bounded_wait.argtypes = [ci, C.c_double, C.POINTER(C.c_double)]
+    lib.gwas_check_epilogue_math.argtypes = [ci, vp, ci, vp]
+    lib.gwas_check_epilogue_math.restype = ci
     lib.gwas_check_bounded_wait.restype = ci
     lib.gwas_destroy.argtypes = [vp]
     lib.gwas_destroy.restype = None
@@ -391,6 +393,17 @@ def gwas_cheb_plan(lam, reach, lo, hi, tol=1e-10):
     if rc != GWAS_OK:
         raise GwasError(rc, "gwas_cheb_plan: invalid arguments")
     return r.value, b.value
+
+
+def gwas_check_epilogue_math(x, device=0):
+    """The epilogue's reciprocal and square root of x (float32 values) and CUDA's correctly rounded
+    ones, as an array [count][4]: rcp, rcp_rn, sqrt, sqrt_rn."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty((x.size, 4), np.float32)
+    rc = lib.gwas_check_epilogue_math(int(device), x.ctypes.data, int(x.size), out.ctypes.data)
+    if rc != GWAS_OK:
+        raise GwasError(rc, "gwas_check_epilogue_math failed")
+    return out
 
 
 def gwas_check_bounded_wait(device=0, limit_s=0.05):

@@ -689,12 +689,21 @@ __global__ void __launch_bounds__(fused_threads(EPW, PAIR, INTERP), 1)
         // in FP32 from the smallest term up, then c_0 (two floats) + c_1 T_1 (with the product's
         // rounding error) added last, so that s carries about one rounding of its own size
         const int R = a.cheb_R, i = q * 32 + lane;
+        // two traits per packed FMA (each lane rounds as fmaf): the same sums, half the instructions
+        float2 s2[JPW / 2];
 #pragma unroll
-        for (int r = 0; r < JPW; ++r) s_r[r] = 0.f;
+        for (int r = 0; r < JPW / 2; ++r) s2[r] = make_float2(0.f, 0.f);
         for (int k = R - 1; k >= 2; --k) {
           const float ck = ccur[k * 128 + i];
+          const float2 ck2 = make_float2(ck, ck);
 #pragma unroll
-          for (int r = 0; r < JPW; ++r) s_r[r] = fmaf(ck, tcur[k * TT + jbeg + r], s_r[r]);
+          for (int r = 0; r < JPW / 2; ++r)
+            s2[r] = tc::ffma2(ck2, *reinterpret_cast<const float2*>(tcur + k * TT + jbeg + 2 * r), s2[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < JPW / 2; ++r) {
+          s_r[2 * r] = s2[r].x;
+          s_r[2 * r + 1] = s2[r].y;
         }
         const float c0 = ccur[i], c1 = ccur[128 + i], c0lo = ccur[(PSTAGE ? CHEB_MAX_R : R) * 128 + i];
 #pragma unroll
@@ -715,10 +724,10 @@ __global__ void __launch_bounds__(fused_threads(EPW, PAIR, INTERP), 1)
           const float num = num_r[r], s = s_r[r];
           const float delta = s - zz_r[r];
           const bool sing = !(delta > 1e-6f * s) || !(sA > 0.f);
-          const float inv = __frcp_rn(delta);
+          const float inv = tc::rcp_nr(delta);
           const float beta = num * inv;
           const float rss = fmaxf(fmaf(-num, beta, cs[(jbeg + r) * CSTR + cst_rr(Q)]), 0.f);
-          const float se = __fsqrt_rn(rss * inv * inv_dof);
+          const float se = tc::sqrt_approx(rss * inv * inv_dof);
           beta_r[r] = sing ? __int_as_float(0x7fc00000) : beta;
           se_r[r] = sing ? __int_as_float(0x7fc00000) : se;
           singm |= (sing ? 1u : 0u) << r;
@@ -750,10 +759,10 @@ __global__ void __launch_bounds__(fused_threads(EPW, PAIR, INTERP), 1)
             beta = se = __int_as_float(0x7fc00000);
             ++tsing;
           } else {
-            const float inv = __frcp_rn(delta);
+            const float inv = tc::rcp_nr(delta);
             beta = num * inv;
             const float rss = fmaxf(fmaf(-num, beta, cj[cst_rr(Q)]), 0.f);
-            se = __fsqrt_rn(rss * inv * inv_dof);
+            se = tc::sqrt_approx(rss * inv * inv_dof);
           }
           const int64_t o = (int64_t)jj * ldo + (snp - oi0);
           if (full_b == 1) {
