@@ -152,20 +152,27 @@ def pinned_host_array(shape, dtype, torch, fallback=True):
 
 def hugepage_fraction(addr, nbytes):
     """Share of [addr, addr + nbytes) backed by transparent huge pages, from /proc/self/smaps
-    (None where that file is not readable)."""
+    (None where that file is not readable).  smaps counts huge pages per mapping, so a mapping
+    that overlaps the range only in part contributes in proportion to the overlap."""
     try:
         lines = open("/proc/self/smaps").read().splitlines()
     except OSError:
         return None
-    huge = 0
-    inside = False
+    return hugepage_share(lines, addr, nbytes)
+
+
+def hugepage_share(lines, addr, nbytes):
+    """hugepage_fraction's arithmetic on the lines of an smaps file."""
+    huge = 0.0
+    share = 0.0
     for ln in lines:
         head = ln.split()[0] if ln else ""
         if "-" in head and not head.endswith(":"):
             lo, hi = (int(x, 16) for x in head.split("-"))
-            inside = lo < addr + nbytes and hi > addr
-        elif inside and head == "AnonHugePages:":
-            huge += int(ln.split()[1]) * 1024
+            overlap = min(hi, addr + nbytes) - max(lo, addr)
+            share = overlap / (hi - lo) if overlap > 0 and hi > lo else 0.0
+        elif share > 0 and head == "AnonHugePages:":
+            huge += int(ln.split()[1]) * 1024 * share
     return huge / nbytes if nbytes else None
 
 
@@ -515,23 +522,33 @@ def c2_run(g, torch, dev, local, stream):
                                                 "over all pairs"}}
 
 
-def c5_run(g, torch, dev, local, stream, tune_path, XR_dev, phi, XL):
+def c5_run(g, torch, dev, local, stream, tune_path, XR_dev, phi, XL, host=None):
     """The paper-scale shape (the out-of-core example of Section 4): n = 1000, p = 4, m = 1e6
     SNPs resident, t = 1e5 traits in blocks of 5000, the SNP coefficient and its SE of every
     block streamed to one of two page-locked host buffers (40 GB each) by gwas_solve_stream
     while the next block computes.  Reports pairs/s of the whole gwas_solve_stream, the floor
-    the device -> host link sets (800 GB / measured link rate) and the share of it achieved."""
+    the device -> host link sets (800 GB / measured link rate) and the share of it achieved.
+    host: a registered page-locked array of at least 80 GB (the e2e result grid) whose two halves
+    serve as the buffers; otherwise two are allocated (base pages, where the host has no free
+    huge pages left, halve the device -> host rate)."""
     n, m, t5, blk = 1000, 1_000_000, 100_000, 5000
     Y5, h5 = phenotypes(n, t5), heritabilities(t5)
     Yd = torch.from_numpy(Y5).to(dev)
-    bufs = []
-    for _ in range(2):
-        b, reg = pinned_host_array((2, blk, m), np.float32, torch, fallback=False)
-        if b is None:
-            for x in bufs:
-                torch.cuda.cudart().cudaHostUnregister(x.ctypes.data)
-            return {"skipped": "could not allocate two 40 GB page-locked host buffers"}
-        bufs.append(b)
+    per = 2 * blk * m
+    bufs, owned = [], False
+    if isinstance(host, np.ndarray) and host.dtype == np.float32 and host.size >= 2 * per:
+        flat = host.reshape(-1)
+        bufs = [flat[:per].reshape(2, blk, m), flat[per:2 * per].reshape(2, blk, m)]
+        source = "the two halves of the e2e result buffer"
+    else:
+        owned, source = True, "two page-locked buffers allocated for this run"
+        for _ in range(2):
+            b, reg = pinned_host_array((2, blk, m), np.float32, torch, fallback=False)
+            if b is None:
+                for x in bufs:
+                    torch.cuda.cudart().cudaHostUnregister(x.ctypes.data)
+                return {"skipped": "could not allocate two 40 GB page-locked host buffers"}
+            bufs.append(b)
     samples = {}
 
     def on_block(j0, nb, ptr):
@@ -554,9 +571,12 @@ def c5_run(g, torch, dev, local, stream, tune_path, XR_dev, phi, XL):
         t3 = time.perf_counter()
     finally:
         g.gwas_destroy(ctx)
-    link = host_link_probe(torch, dev, bufs[0])
-    for b in bufs:
-        torch.cuda.cudart().cudaHostUnregister(b.ctypes.data)
+    buf_diag = [{"d2h_gbs": host_link_probe(torch, dev, b), "hugepage_frac": hugepage_fraction(b.ctypes.data, b.nbytes)}
+                for b in bufs]
+    link = [x for d in buf_diag for x in d["d2h_gbs"]]
+    if owned:
+        for b in bufs:
+            torch.cuda.cudart().cudaHostUnregister(b.ctypes.data)
     del bufs
     # sampled pairs of every block against the oracle: SNPs [0, 64) x the block's first 4 traits
     from oracle import EigOracle
@@ -573,7 +593,8 @@ def c5_run(g, torch, dev, local, stream, tune_path, XR_dev, phi, XL):
                         f"two page-locked host buffers of {2 * 4 * blk * m / 1e9:.0f} GB",
             "value": m * t5 / (solve_ms / 1e3), "unit": "pairs/s", "solve_stream_ms": solve_ms,
             "setup_ms": (t1 - t0) * 1e3, "load_snps_ms": (t2 - t1) * 1e3,
-            "blocks": len(samples), "d2h_bytes": d2h, "link_d2h_gbs": link,
+            "blocks": len(samples), "d2h_bytes": d2h, "link_d2h_gbs": link, "host_buffers": buf_diag,
+            "buffers": source,
             "link_floor_ms": floor_ms, "link_floor_frac": floor_ms / solve_ms,
             "err": {"max": err, "se_max": float(np.max(np.abs(got_s - so) / so)), "pairs": int(bl.size),
                     "sample": "SNPs [0,64) x the first 4 traits of every block, against the oracle"},
@@ -842,6 +863,7 @@ def main():
         del out1
 
     # ---------------------------------------------------------------- end to end from pinned host buffers
+    e2e_host = (None, False)
     if not args.no_e2e:
         pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in inp_h.items()}
         hout, registered = pinned_host_array((2, t, m), np.float32, torch)
@@ -879,8 +901,8 @@ def main():
                              "phase_ms": phases,
                              "note": out_note + "; inputs from pinned host memory; wall clock around the C calls; "
                                                 "value from the median step"}
-            if registered:
-                torch.cuda.cudart().cudaHostUnregister(hout.ctypes.data)
+            # the paper-scale run below reuses this registered buffer's two halves
+            e2e_host = (hout, registered)
             del hout
 
     # ---------------------------------------------------------------- out of core: genotype slabs from host memory
@@ -925,8 +947,12 @@ def main():
         torch.cuda.empty_cache()
     # ---------------------------------------------------------------- paper scale: t=1e5 streamed to host
     if not args.no_c5 and not args.no_e2e and rank == 0 and m == M_SNP and n == N_IND:
-        result["paper_scale"] = c5_run(g, torch, dev, local, stream, tune_path, inp_d["XR"], inp_d["phi"], inp_d["XL"])
+        result["paper_scale"] = c5_run(g, torch, dev, local, stream, tune_path, inp_d["XR"], inp_d["phi"], inp_d["XL"],
+                                       host=e2e_host[0] if e2e_host[1] else None)
         torch.cuda.empty_cache()
+    if e2e_host[1]:
+        torch.cuda.cudart().cudaHostUnregister(e2e_host[0].ctypes.data)
+    e2e_host = None
 
     # ---------------------------------------------------------------- serving (continuous batching)
     if args.serving_requests > 0 and rank == 0:

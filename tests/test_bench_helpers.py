@@ -88,3 +88,14 @@ def test_traffic_model_fp4_terms():
     # n = 1100: Kpad = 1152, Kp4 = 1280
     m4 = bench.fused_traffic_model(1100, 128, 24, group=1, fp4=True)
     assert m4["read"] == 128 * 640 + 25 * 4 * 128 + 3 * 240 * 640
+
+
+def test_hugepage_share_of_a_range_inside_a_mapping():
+    # two mappings of 4 MiB: the first on huge pages, the second on base pages
+    smaps = ["10000000-10400000 rw-p 00000000 00:00 0", "Size:               4096 kB", "AnonHugePages:      4096 kB",
+             "10400000-10800000 rw-p 00000000 00:00 0", "Size:               4096 kB", "AnonHugePages:         0 kB"]
+    mib = 1 << 20
+    assert bench.hugepage_share(smaps, 0x10000000, 4 * mib) == 1.0
+    assert bench.hugepage_share(smaps, 0x10000000, 2 * mib) == 1.0          # half of the first mapping
+    assert bench.hugepage_share(smaps, 0x10200000, 4 * mib) == 0.5          # its second half and half the next
+    assert bench.hugepage_share(smaps, 0x10400000, 4 * mib) == 0.0
