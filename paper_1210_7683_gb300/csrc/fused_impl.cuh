@@ -614,12 +614,20 @@ __global__ void __launch_bounds__(fused_threads(EPW, PAIR, INTERP), 1)
           tc::tmem_ld4(lb + (3 + 2 * PM1) * TT + j0, w4);
           tc::tmem_ld_wait();
           tc::reg_fence(hw); tc::reg_fence(lw); tc::reg_fence(w3); tc::reg_fence(w4);
+          // two traits per packed instruction (each lane rounds as the scalar form would):
+          // num = scale * (((w4 F + w3) F + lw) F + hw)
+          const float2 F2 = make_float2(F, F);
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            num_r[4 * g + v] = cs[(j0 + v) * CSTR] *
-                               fmaf(F, fmaf(F, fmaf(F, __uint_as_float(w4[v]), __uint_as_float(w3[v])),
-                                            __uint_as_float(lw[v])), __uint_as_float(hw[v]));
+          for (int v = 0; v < 4; v += 2) {
+            float2 t = tc::ffma2(F2, make_float2(__uint_as_float(w4[v]), __uint_as_float(w4[v + 1])),
+                                 make_float2(__uint_as_float(w3[v]), __uint_as_float(w3[v + 1])));
+            t = tc::ffma2(F2, t, make_float2(__uint_as_float(lw[v]), __uint_as_float(lw[v + 1])));
+            t = tc::ffma2(F2, t, make_float2(__uint_as_float(hw[v]), __uint_as_float(hw[v + 1])));
+            const float2 nm = tc::fmul2(make_float2(cs[(j0 + v) * CSTR], cs[(j0 + v + 1) * CSTR]), t);
+            num_r[4 * g + v] = nm.x;
+            num_r[4 * g + v + 1] = nm.y;
             zz_r[4 * g + v] = 0.f;
+            zz_r[4 * g + v + 1] = 0.f;
           }
         }
         // C1, v_c: slices 1 and 2 (groups 1 + c and 2 + q + c) -> z_c, three covariates per wait
@@ -637,15 +645,25 @@ __global__ void __launch_bounds__(fused_threads(EPW, PAIR, INTERP), 1)
 #pragma unroll
           for (int c = 0; c < CB; ++c)
             if (c0 + c < PM1) { tc::reg_fence(hz[c]); tc::reg_fence(lz[c]); }
+          // z = scale * (lz FV + hz), zz += z^2, two traits per packed instruction
+          const float2 FV2 = make_float2(FV, FV);
 #pragma unroll
-          for (int v = 0; v < 4; ++v)
+          for (int v = 0; v < 4; v += 2) {
+            float2 zz2 = make_float2(zz_r[4 * g + v], zz_r[4 * g + v + 1]);
 #pragma unroll
             for (int c = 0; c < CB; ++c)
               if (c0 + c < PM1) {
-                const float z = cs[(j0 + v) * CSTR + 1 + c0 + c] * fmaf(FV, __uint_as_float(lz[c][v]), __uint_as_float(hz[c][v]));
-                z_r[4 * g + v][c0 + c] = z;
-                zz_r[4 * g + v] = fmaf(z, z, zz_r[4 * g + v]);
+                const float2 z2 = tc::fmul2(
+                    make_float2(cs[(j0 + v) * CSTR + 1 + c0 + c], cs[(j0 + v + 1) * CSTR + 1 + c0 + c]),
+                    tc::ffma2(FV2, make_float2(__uint_as_float(lz[c][v]), __uint_as_float(lz[c][v + 1])),
+                              make_float2(__uint_as_float(hz[c][v]), __uint_as_float(hz[c][v + 1]))));
+                z_r[4 * g + v][c0 + c] = z2.x;
+                z_r[4 * g + v + 1][c0 + c] = z2.y;
+                zz2 = tc::ffma2(z2, z2, zz2);
               }
+            zz_r[4 * g + v] = zz2.x;
+            zz_r[4 * g + v + 1] = zz2.y;
+          }
         }
         if (!INTERP) {
           // C2: level 0 and the five level-1 groups -> s
@@ -719,18 +737,25 @@ __global__ void __launch_bounds__(fused_threads(EPW, PAIR, INTERP), 1)
         // stores of those in the block; the same operations per pair as below
         float beta_r[JPW], se_r[JPW];
         uint32_t singm = 0;
+        // two traits per packed instruction where the operations allow it; each lane rounds as
+        // the scalar tc::rcp_nr, products and FMAs would
 #pragma unroll
-        for (int r = 0; r < JPW; ++r) {
-          const float num = num_r[r], s = s_r[r];
-          const float delta = s - zz_r[r];
-          const bool sing = !(delta > 1e-6f * s) || !(sA > 0.f);
-          const float inv = tc::rcp_nr(delta);
-          const float beta = num * inv;
-          const float rss = fmaxf(fmaf(-num, beta, cs[(jbeg + r) * CSTR + cst_rr(Q)]), 0.f);
-          const float se = tc::sqrt_approx(rss * inv * inv_dof);
-          beta_r[r] = sing ? __int_as_float(0x7fc00000) : beta;
-          se_r[r] = sing ? __int_as_float(0x7fc00000) : se;
-          singm |= (sing ? 1u : 0u) << r;
+        for (int r = 0; r < JPW; r += 2) {
+          const float2 num = make_float2(num_r[r], num_r[r + 1]), s = make_float2(s_r[r], s_r[r + 1]);
+          const float2 delta = make_float2(s.x - zz_r[r], s.y - zz_r[r + 1]);
+          const bool sing0 = !(delta.x > 1e-6f * s.x) || !(sA > 0.f), sing1 = !(delta.y > 1e-6f * s.y) || !(sA > 0.f);
+          const float2 y = make_float2(tc::rcp_approx(delta.x), tc::rcp_approx(delta.y));
+          const float2 inv = tc::ffma2(y, tc::ffma2(make_float2(-delta.x, -delta.y), y, make_float2(1.f, 1.f)), y);
+          const float2 beta = tc::fmul2(num, inv);
+          const float2 rr = make_float2(cs[(jbeg + r) * CSTR + cst_rr(Q)], cs[(jbeg + r + 1) * CSTR + cst_rr(Q)]);
+          const float2 rss0 = tc::ffma2(make_float2(-num.x, -num.y), beta, rr);
+          const float2 rss = make_float2(fmaxf(rss0.x, 0.f), fmaxf(rss0.y, 0.f));
+          const float2 x = tc::fmul2(tc::fmul2(rss, inv), make_float2(inv_dof, inv_dof));
+          beta_r[r] = sing0 ? __int_as_float(0x7fc00000) : beta.x;
+          beta_r[r + 1] = sing1 ? __int_as_float(0x7fc00000) : beta.y;
+          se_r[r] = sing0 ? __int_as_float(0x7fc00000) : tc::sqrt_approx(x.x);
+          se_r[r + 1] = sing1 ? __int_as_float(0x7fc00000) : tc::sqrt_approx(x.y);
+          singm |= ((sing0 ? 1u : 0u) | (sing1 ? 2u : 0u)) << r;
         }
         const int nvalid = ntrait - (jbase + jbeg);
 #pragma unroll

@@ -265,9 +265,13 @@ __device__ __forceinline__ void reg_fence(uint32_t (&r)[8]) {
 // multiply-add form (e = 1 - d y0, y1 = y0 + y0 e; Markstein, IBM J. Res. Dev. 34(1), 1990).
 // Branch-free; within one ulp of the correctly rounded reciprocal for normal d (checked on the
 // GPU against __frcp_rn by gwas_check_epilogue_math).  d = 0 gives NaN.
-__device__ __forceinline__ float rcp_nr(float d) {
+__device__ __forceinline__ float rcp_approx(float d) {
   float y;
   asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(d));
+  return y;
+}
+__device__ __forceinline__ float rcp_nr(float d) {
+  const float y = rcp_approx(d);
   return fmaf(y, fmaf(-d, y, 1.f), y);
 }
 // Square root: the hardware approximation (relative error within 2^-22 of __fsqrt_rn, checked
@@ -276,6 +280,15 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
   asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
+}
+// Two products in one instruction (mul.rn.f32x2): each lane rounds as a * b does.
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 pa, pb, pd;\n mov.b64 pa, {%2, %3};\n mov.b64 pb, {%4, %5};\n mul.rn.f32x2 pd, pa, pb;\n"
+      " mov.b64 {%0, %1}, pd;\n}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
 }
 // Two FMAs in one instruction (fma.rn.f32x2): each lane rounds as fmaf does.
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
