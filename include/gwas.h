@@ -266,7 +266,9 @@ GWAS_API int gwas_eig_info(const gwas_ctx* ctx, int* steps);
  * with bf16 slices, so the results are identical; the kernel streams half the operand bytes.
  *   *ready     1 when the loaded genotypes have their e2m1 copy: a one-time gwas_load_snps at p = 4
  *              of genotypes that are all in {0, +-1, +-2, +-3, +-4, +-6} (not set by the slabs of
- *              gwas_solve_ooc, nor under GWAS_FP4=0)
+ *              gwas_solve_ooc, under GWAS_FP4=0, in a context with an HBM budget, or where the
+ *              device had no room for the copy: mpad x roundup(n, 256) / 2 bytes; a block whose
+ *              e2m1 trait digits find no room runs on bf16 operands)
  *   *launches  launches of the e2m1 kernel since the context was created
  * Either pointer may be NULL.  Returns GWAS_OK or GWAS_ERR_ARG (NULL context). */
 GWAS_API int gwas_fp4_info(gwas_ctx* ctx, int* ready, int64_t* launches);

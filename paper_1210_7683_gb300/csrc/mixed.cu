@@ -64,6 +64,14 @@ constexpr double RK_NULL = 1e-16;
 
 static int cheb_coefficients(gwas_ctx* c);
 
+// An allocation the caller can do without: on failure the context's last error is left as it was.
+static bool try_alloc(gwas_ctx* c, size_t bytes, void** out) {
+  const std::string saved = c->err;
+  if (ctx_alloc(c, bytes, out) == GWAS_OK) return true;
+  c->err = saved;
+  return false;
+}
+
 namespace {
 
 inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -653,25 +661,31 @@ int mixed_load(gwas_ctx* c, const int8_t* dXR, int64_t m, bool reuse, int8_t* co
   // a slab reuses the arrays when they hold enough rows (rows past m keep stale values,
   // which the fused kernel never writes out)
   // The e2m1 copy of the genotypes, for the CTA-pair kernel on e2m1 operands (p = 4), on a
-  // one-time load; GWAS_FP4=0 leaves it out.
+  // one-time load.  Left out under GWAS_FP4=0, and in a context with an HBM budget: the copy and
+  // the trait digits are memory such a budget did not account for, and an optional buffer held
+  // from here could take the room a later call needs.
   const char* fp4_env = getenv("GWAS_FP4");
-  const bool want_g4 = !reuse && PM1 == 3 && !(fp4_env && !strcmp(fp4_env, "0"));
+  const bool want_g4 = !reuse && PM1 == 3 && !(fp4_env && !strcmp(fp4_env, "0")) && c->budget == 0;
   if (!reuse || !s->G || s->mpad < rup(m, 128)) {
     mixed_free(c);
     s->mpad = rup(m, 128);
     if ((rc = ctx_alloc(c, 2ull * s->mpad * s->Kpad, (void**)&s->G)) ||
         (rc = ctx_alloc(c, 2ull * 3 * s->mpad * s->Kpad, (void**)&s->A2)) ||
         (rc = ctx_alloc(c, sizeof(float) * s->mpad, (void**)&s->sA)) ||
-        (rc = ctx_alloc(c, sizeof(float) * s->mpad * std::max(1, PM1), (void**)&s->acoef)) ||
-        (want_g4 && (rc = ctx_alloc(c, (size_t)s->mpad * (s->Kp4 / 2), (void**)&s->G4))) ||
-        (want_g4 && (rc = ctx_alloc(c, sizeof(int), (void**)&s->g4_bad)))) {
+        (rc = ctx_alloc(c, sizeof(float) * s->mpad * std::max(1, PM1), (void**)&s->acoef))) {
       mixed_free(c);
       return rc;
+    }
+    // the e2m1 copy is optional: without room for it the bf16 operands serve
+    if (want_g4 && !try_alloc(c, (size_t)s->mpad * (s->Kp4 / 2), (void**)&s->G4)) s->G4 = nullptr;
+    if (s->G4 && !try_alloc(c, sizeof(int), (void**)&s->g4_bad)) {
+      ctx_free(c, s->G4);
+      s->G4 = nullptr;
     }
   }
   s->g4_ok = false;
   ++s->load_gen;
-  uint8_t* G4 = want_g4 ? s->G4 : nullptr;
+  uint8_t* G4 = want_g4 ? s->G4 : nullptr;  // NULL when there was no room for it
   if (G4) cudaMemsetAsync(s->g4_bad, 0, sizeof(int), c->stream);
   { ProfScope ps(c, "genotypes_bf16");
   geno_bf16_kernel<<<16 * 152, 256, 0, c->stream>>>(dXR, m, n, s->mpad, s->Kpad, s->G, copy, G4, s->Kp4, s->g4_bad);
@@ -850,12 +864,15 @@ int mixed_prep_block(gwas_ctx* c, MixedWs* w, const double* dY, int j0, int tb) 
   // the interpolated pair at p = 4 on genotypes with an e2m1 copy: e2m1 digits of the C1 slices
   const bool ip = mixed_block_interp(c, tb);
   w->fp4 = ip && q == 3 && mixed_pair_layout(c) && mixed_fp4_ready(c);
-  if (w->fp4) {
+  if (w->fp4 && !w->B1_4) {
+    // optional too: without room for the e2m1 digits the block runs on bf16 operands
     const size_t bytes = (size_t)((w->tb_max + 23) / 24 + 3) / 4 * 4 * FP4_TILE_ROWS * (s->Kp4 / 2);
-    if (!w->B1_4) {
-      int rc = ctx_alloc(c, bytes, (void**)&w->B1_4);
-      if (rc) return rc;
+    if (!try_alloc(c, bytes, (void**)&w->B1_4)) {
+      w->B1_4 = nullptr;
+      w->fp4 = false;
     }
+  }
+  if (w->fp4) {
     const size_t used = (size_t)((tb + 23) / 24 + 3) / 4 * 4 * FP4_TILE_ROWS * (s->Kp4 / 2);
     cudaMemsetAsync(w->B1_4, 0, used, c->stream);
   } else {

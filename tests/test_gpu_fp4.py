@@ -87,3 +87,42 @@ def test_genotypes_without_e2m1_codes_keep_the_bf16_kernel(gw, monkeypatch, valu
     ref2, _ = solve(gw, P, gw.GWAS_OUT_LAST_SE, monkeypatch, False, XR=XR2)
     assert info2["ready"] and info2["launches"] >= 1
     assert same(got2, ref2)
+
+
+def solve_budget(g, P, monkeypatch, fp4, budget):
+    """solve() with an HBM budget; None when the budget is too small for the call."""
+    monkeypatch.setenv("GWAS_FUSED_SHAPE", "2x1x16x1")
+    monkeypatch.delenv("GWAS_S_BR", raising=False)
+    if fp4:
+        monkeypatch.delenv("GWAS_FP4", raising=False)
+    else:
+        monkeypatch.setenv("GWAS_FP4", "0")
+    o = g.gwas_default_opts(precision=g.GWAS_MIXED, output=g.GWAS_OUT_LAST_SE, hbm_budget=int(budget))
+    try:
+        ctx = g.gwas_setup(P.n, P.pm1, P.phi, P.XL, P.t, P.h2, o)
+    except g.GwasError as e:
+        assert e.code == g.GWAS_ERR_OOM
+        return None
+    try:
+        g.gwas_load_snps(ctx, P.m, P.XR, P.n)
+        out = np.empty((2, P.t, P.m), np.float32)
+        g.gwas_solve(ctx, P.Y, 0, P.m, out)
+        return out, g.gwas_fp4_info(ctx)
+    except g.GwasError as e:
+        assert e.code == g.GWAS_ERR_OOM
+        return None
+    finally:
+        g.gwas_destroy(ctx)
+
+
+def test_no_e2m1_copies_under_an_hbm_budget(gw, monkeypatch):
+    # the e2m1 genotypes and trait digits are extra device memory that a context's HBM budget did
+    # not account for: with a budget the calls run on bf16 operands, with the same results
+    P = make_problem(256, 600, 40, pm1=3, seed=951)
+    ref, _ = solve_budget(gw, P, monkeypatch, False, 1 << 30)
+    got, info = solve_budget(gw, P, monkeypatch, True, 1 << 30)
+    assert not info["ready"] and info["launches"] == 0
+    assert same(got, ref)
+    free, info = solve(gw, P, gw.GWAS_OUT_LAST_SE, monkeypatch, True)
+    assert info["ready"] and info["launches"] >= 1
+    assert same(free, ref)
