@@ -145,7 +145,7 @@ __device__ __forceinline__ void super_coords(int u, const FusedArgs& a, int& us,
 // h^2 (FusedArgs::cheb_*): the K loop streams only the C1 operands (genotypes and the trait
 // columns [w | v']), one item per K block.
 // FP4 (PAIR, INTERP, q = 3): the C1 operands as e2m1 values (kind::mxf4).  A fixed-point slice
-// digit q (|q| <= 292) is written as 64 d0 + 8 d1 + d2 with d in [-4, 4], and the three digits are
+// digit q (|q| <= 256; the split covers -288..287) is 64 d0 + 8 d1 + d2, d in [-4, 4], and the three digits are
 // contracted into the slice's own accumulator by MMAs whose B scale factors are 2^6, 2^3 and 2^0:
 // every partial sum is the same integer as the bf16 kernel's, so the outputs do not change.
 // Threads of a CTA: the TMA producer and MMA warps, EPW epilogue warps and, in the interpolated

@@ -11,11 +11,19 @@ import bench
 
 
 def _current_sha():
-    h = hashlib.sha256()
-    for f in bench.FUSED_TRAFFIC_CHECK["sources"]:
-        with open(os.path.join(bench.ROOT, "paper_1210_7683_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()
+    return bench.sources_sha(bench.FUSED_TRAFFIC_CHECK["sources"])
+
+
+def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_1210_7683_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (csrc / "k.cu").write_text("int a = 1;  // one\n/* block\n comment */\nint b = a;\n")
+    h0 = bench.sources_sha(["k.cu"])
+    (csrc / "k.cu").write_text("int a = 1;  // another comment\n\nint b = a;   \n")
+    assert bench.sources_sha(["k.cu"]) == h0
+    (csrc / "k.cu").write_text("int a = 2;\nint b = a;\n")
+    assert bench.sources_sha(["k.cu"]) != h0
 
 
 def test_traffic_model_terms():
