@@ -35,7 +35,11 @@
 // on one another's accumulator (a chain of dependent N <= 128 MMAs runs at the MMA
 // latency, not at the tensor-core rate); the epilogue adds the level-1 groups.
 // With S_BR interpolated (INTERP, the default where its bound holds) the C2 columns are
-// not used: only [0, 320) at p = 4, and the K loop streams only the C1 operands.
+// not used and the K loop streams only the C1 operands; at p = 4 its tiles hold 24 traits
+// (C1 = 240 columns, one MMA per K step), accumulated alternately in [0, 240) and [256, 496)
+// so that a tile's MMAs overlap the epilogue of the one before.  The CTA pair of that kernel
+// can contract e2m1 operands instead of bf16 (FP4, see fused_kernel): its constant scale
+// factors sit in [240, 256) and [496, 512), and a 15th warp stages the epilogue's per-tile data.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
