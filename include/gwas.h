@@ -62,7 +62,7 @@ extern "C" {
 #define GWAS_ERR_SINGULAR_PAIRS 6  /* warning: some pairs have a (numerically) singular p x p system;
                                       their outputs are NaN, every other output is valid */
 #define GWAS_ERR_STATE          7  /* call out of order (e.g. gwas_solve before gwas_load_snps) */
-#define GWAS_ERR_UNSUPPORTED    8  /* a size or mode this build does not implement */
+#define GWAS_ERR_UNSUPPORTED    8  /* a size or mode the library does not implement */
 
 /* precision modes */
 #define GWAS_FP64  0  /* every step in FP64 (the paper's arithmetic, Section 6) */
